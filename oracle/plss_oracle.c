@@ -1,0 +1,443 @@
+/*
+ * plss_oracle.c -- plain, slow, single-threaded FP64 CPU PLSS.
+ *
+ * TEST INFRASTRUCTURE ONLY. This file is the parity oracle for the CUDA
+ * path: only the test suite, the package smoke check and the benchmark's CPU
+ * baseline load it. It shares no code with the CUDA library and is compiled
+ * with -ffp-contract=off so that every a*b+c is two roundings, as written.
+ *
+ * What it follows (Brust & Saunders, "PLSS: a projected linear systems
+ * solver", arXiv 2207.07615):
+ *   - plss_oracle_residual: Algorithm 1 (Sec. 5), the residual-sketch
+ *     recursion of Theorem 4.1 (eq:pkShort), with the optional diagonal
+ *     weight of Sec. 4.1 (eq:pkShortW), written step by step in the
+ *     algorithm's order. Sums run in ascending index order.
+ *   - plss_oracle_kaczmarz: the identity sketch of Sec. 7 (eq:pkKacz),
+ *     with a dense history P (n x K) and Theta = diag(||p_j||^2).
+ *   - plss_oracle_colweights: W = diag(1/||A_{:,j}||) of Sec. 4.1.
+ *
+ * Readings where the paper is silent or inconsistent (all listed in the
+ * design notes of the repository):
+ *   - gamma: Algorithm 1's gamma = (theta/rho) * beta. The closed form in the
+ *     statement of Theorem 4.1 differs by a factor rho; gamma_form = 1 plants
+ *     that statement form, for tests that show the pins reject it.
+ *   - stopping: stop when sqrt(rho)/||b|| <= tol, tested right after rho is
+ *     formed (Sec. 5 suggests sqrt(rho)/||b|| < tau); maxit caps the number
+ *     of updates p applied to x; the residual of the returned x is always
+ *     formed (the row sweep after the last update runs).
+ *   - breakdown: the initial phi must be > 0 and finite; later the factor
+ *     (s/rho - 1)(s/rho + 1) must be > 0 and finite (it is <= 0 only when
+ *     y is parallel to p); otherwise return the current x with status
+ *     BREAKDOWN.
+ *   - FP32 storage (prec = 1): A's values, r, p and W y are held as float,
+ *     sums of products are accumulated in float, inner products and the
+ *     scalar recursion in double, x in double; every `refine` updates the
+ *     residual is recomputed as b - A x in double and the recursion restarts
+ *     from it (this extension is not in the paper).
+ *   - Kaczmarz order: rows are visited without replacement in a fresh
+ *     permutation per pass (SplitMix64 stream + Fisher-Yates shuffle), the
+ *     history is cleared when it holds K updates, a row whose projected
+ *     norm delta is <= 1e-14 ||a_i||^2 is skipped, and an update with
+ *     ||p|| = 0 (r_i = 0) is not stored in the history (its theta would
+ *     divide by zero in the next projection).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+enum {
+    ORC_CONVERGED = 0,
+    ORC_NOT_CONVERGED = 1,
+    ORC_BREAKDOWN = -4,
+    ORC_INVALID = -1,
+    ORC_NOMEM = -2
+};
+
+/* ------------------------------------------------------------------ */
+/* plain sparse products                                               */
+/* ------------------------------------------------------------------ */
+
+/* out = A v, CSR, ascending nonzero order per row. */
+void plss_oracle_spmv(int64_t m, const int64_t *row_ptr, const int32_t *col_idx,
+                      const double *val, const double *v, double *out)
+{
+    for (int64_t i = 0; i < m; ++i) {
+        double s = 0.0;
+        for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k)
+            s += val[k] * v[col_idx[k]];
+        out[i] = s;
+    }
+}
+
+/* Builds the CSC of A (col_ptr[n+1], row_idx[nnz], cval[nnz]) with row
+ * indices ascending inside each column (a stable counting sort). */
+static void csr_to_csc(int64_t m, int64_t n, const int64_t *row_ptr, const int32_t *col_idx,
+                       const double *val, int64_t *col_ptr, int64_t *row_idx, double *cval)
+{
+    int64_t nnz = row_ptr[m];
+    for (int64_t j = 0; j <= n; ++j) col_ptr[j] = 0;
+    for (int64_t k = 0; k < nnz; ++k) col_ptr[col_idx[k] + 1] += 1;
+    for (int64_t j = 0; j < n; ++j) col_ptr[j + 1] += col_ptr[j];
+    int64_t *next = (int64_t *)malloc((size_t)(n + 1) * sizeof(int64_t));
+    for (int64_t j = 0; j <= n; ++j) next[j] = col_ptr[j];
+    for (int64_t i = 0; i < m; ++i)
+        for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+            int64_t dst = next[col_idx[k]]++;
+            row_idx[dst] = i;
+            cval[dst] = val[k];
+        }
+    free(next);
+}
+
+/* out = A^T r, computed column by column from the CSC (ascending rows). */
+static void csc_spmv(int64_t n, const int64_t *col_ptr, const int64_t *row_idx,
+                     const double *cval, const double *r, double *out)
+{
+    for (int64_t j = 0; j < n; ++j) {
+        double s = 0.0;
+        for (int64_t k = col_ptr[j]; k < col_ptr[j + 1]; ++k)
+            s += cval[k] * r[row_idx[k]];
+        out[j] = s;
+    }
+}
+
+/* out = A^T r through a freshly built CSC. */
+int plss_oracle_spmvt(int64_t m, int64_t n, const int64_t *row_ptr, const int32_t *col_idx,
+                      const double *val, const double *r, double *out)
+{
+    int64_t nnz = row_ptr[m];
+    int64_t *cp = (int64_t *)malloc((size_t)(n + 1) * sizeof(int64_t));
+    int64_t *ri = (int64_t *)malloc((size_t)(nnz ? nnz : 1) * sizeof(int64_t));
+    double *cv = (double *)malloc((size_t)(nnz ? nnz : 1) * sizeof(double));
+    if (!cp || !ri || !cv) { free(cp); free(ri); free(cv); return ORC_NOMEM; }
+    csr_to_csc(m, n, row_ptr, col_idx, val, cp, ri, cv);
+    csc_spmv(n, cp, ri, cv, r, out);
+    free(cp); free(ri); free(cv);
+    return 0;
+}
+
+static double dot(int64_t len, const double *a, const double *b)
+{
+    double s = 0.0;
+    for (int64_t i = 0; i < len; ++i) s += a[i] * b[i];
+    return s;
+}
+
+/* W = diag(w) from the column norms of A (Sec. 4.1): mode 1 gives
+ * w_j = 1/||A_{:,j}||, mode 2 gives w_j = 1/||A_{:,j}||^2; an empty
+ * column gets w_j = 1. */
+void plss_oracle_colweights(int64_t m, int64_t n, const int64_t *row_ptr, const int32_t *col_idx,
+                            const double *val, int mode, double *w)
+{
+    double *ss = (double *)calloc((size_t)(n ? n : 1), sizeof(double));
+    for (int64_t i = 0; i < m; ++i)
+        for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k)
+            ss[col_idx[k]] += val[k] * val[k];
+    for (int64_t j = 0; j < n; ++j) {
+        if (ss[j] == 0.0) w[j] = 1.0;
+        else if (mode == 2) w[j] = 1.0 / ss[j];
+        else w[j] = 1.0 / sqrt(ss[j]);
+    }
+    free(ss);
+}
+
+/* ------------------------------------------------------------------ */
+/* Residual sketch: Algorithm 1                                        */
+/* ------------------------------------------------------------------ */
+
+static inline double rf(double v, int f32) { return f32 ? (double)(float)v : v; }
+
+/* r = b - A x, double accumulation; returns nothing. */
+static void true_residual(int64_t m, const int64_t *row_ptr, const int32_t *col_idx,
+                          const double *val, const double *b, const double *x, double *r)
+{
+    for (int64_t i = 0; i < m; ++i) {
+        double s = 0.0;
+        for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k)
+            s += val[k] * x[col_idx[k]];
+        r[i] = b[i] - s;
+    }
+}
+
+/*
+ * PLSS with the residual sketch S_k = [r_0 ... r_{k-1}] (Sec. 4, eq:S),
+ * following Algorithm 1:
+ *   r = b - A x0;  y = A^T r;  rho = r^T r;  u = W y;  phi = y^T u;
+ *   p = (rho/phi) u;  theta = p^T W^{-1} p;  x = x + p;
+ *   repeat: r = r - A p; y = A^T r; rho = r^T r; u = W y; phi = y^T u;
+ *           beta = 1/((sqrt(theta phi)/rho - 1)(sqrt(theta phi)/rho + 1));
+ *           gamma = (theta/rho) beta;  p = beta p + gamma u;
+ *           theta = p^T W^{-1} p;  x = x + p.
+ * W = diag(w) (w = NULL means W = I).
+ *
+ * Arguments: CSR A (m x n), b[m], x0[n] (NULL = 0), w[n] (NULL = I),
+ * tol >= 0, maxit >= 0 (cap on updates), prec 0 = FP64, 1 = FP32 storage,
+ * refine = restart period in updates for prec 1 (0 = never), stop_on_true:
+ * the stop decision uses the residual b - A x recomputed in double,
+ * gamma_form 0 = Algorithm 1, 1 = the statement form (planted defect).
+ * Outputs: x_out[n], *iters (updates applied), *relres_rec (sqrt(rho)/||b||
+ * of the last rho), *relres_true (||b - A x||/||b||), return value = status.
+ * Optional history (any pointer may be NULL; hist_cap rows):
+ *   hist_s[k*5 + 0..4] = rho_{k}, phi_{k+1}, beta_{k}, gamma_{k}, theta_{k+1}
+ *   for update k+1 (k = 0..), i.e. the scalars that formed p_{k+1};
+ *   hist_x[k*n] = x_{k+1}, hist_p[k*n] = p_{k+1}, hist_y[k*n] = y_{k+1} = A^T r_k,
+ *   hist_r[k*m] = r_k (residual before update k+1; hist_cap+1 rows).
+ */
+int plss_oracle_residual(int64_t m, int64_t n, const int64_t *row_ptr, const int32_t *col_idx,
+                         const double *val_in, const double *b, const double *x0, const double *w,
+                         double tol, int64_t maxit, int prec, int64_t refine, int stop_on_true,
+                         int gamma_form, double *x_out, int64_t *iters_out, double *relres_rec,
+                         double *relres_true, int64_t hist_cap, double *hist_s, double *hist_x,
+                         double *hist_p, double *hist_y, double *hist_r)
+{
+    const int f32 = (prec == 1);
+    int64_t nnz = row_ptr[m];
+    double *val = (double *)malloc((size_t)(nnz ? nnz : 1) * sizeof(double));
+    double *r = (double *)malloc((size_t)(m ? m : 1) * sizeof(double));
+    double *rt = (double *)malloc((size_t)(m ? m : 1) * sizeof(double));
+    double *y = (double *)malloc((size_t)(n ? n : 1) * sizeof(double));
+    double *u = (double *)malloc((size_t)(n ? n : 1) * sizeof(double));
+    double *p = (double *)calloc((size_t)(n ? n : 1), sizeof(double));
+    double *x = x_out;
+    int64_t *cp = (int64_t *)malloc((size_t)(n + 1) * sizeof(int64_t));
+    int64_t *ri = (int64_t *)malloc((size_t)(nnz ? nnz : 1) * sizeof(int64_t));
+    double *cv = (double *)malloc((size_t)(nnz ? nnz : 1) * sizeof(double));
+    int status = ORC_NOT_CONVERGED;
+    if (!val || !r || !rt || !y || !u || !p || !cp || !ri || !cv) { status = ORC_NOMEM; goto done; }
+
+    for (int64_t k = 0; k < nnz; ++k) val[k] = rf(val_in[k], f32);
+    csr_to_csc(m, n, row_ptr, col_idx, val, cp, ri, cv);
+    for (int64_t j = 0; j < n; ++j) x[j] = x0 ? x0[j] : 0.0;
+
+    double nb = sqrt(dot(m, b, b));
+    double rho = 0.0, phi = 0.0, theta = 0.0, beta = 0.0, gamma = 0.0;
+    int64_t k = 0;          /* updates applied */
+    int64_t since = 0;      /* updates since the last (re)start */
+    int restart = 1;        /* next update is the initial one (p = (rho/phi) u) */
+
+    /* r_0 = b - A x_0 (Algorithm 1, initialization) */
+    true_residual(m, row_ptr, col_idx, val, b, x, rt);
+    for (int64_t i = 0; i < m; ++i) r[i] = rf(rt[i], f32);
+    rho = dot(m, r, r);
+    if (nb == 0.0) { status = ORC_CONVERGED; goto done; }
+
+    for (;;) {
+        if (hist_r && k <= hist_cap) memcpy(hist_r + k * m, r, (size_t)m * sizeof(double));
+        /* stopping rule (Sec. 5): sqrt(rho)/||b|| <= tol */
+        if (sqrt(rho) / nb <= tol) {
+            if (!stop_on_true || restart) { status = ORC_CONVERGED; break; }
+            /* confirm on b - A x before stopping */
+            true_residual(m, row_ptr, col_idx, val, b, x, rt);
+            for (int64_t i = 0; i < m; ++i) r[i] = rf(rt[i], f32);
+            rho = dot(m, r, r);
+            restart = 1; since = 0;
+            continue;
+        }
+        if (k >= maxit) { status = ORC_NOT_CONVERGED; break; }
+
+        /* y = A^T r (column sweep), u = W y, phi = y^T u */
+        if (!f32) {
+            csc_spmv(n, cp, ri, cv, r, y);
+        } else {
+            for (int64_t j = 0; j < n; ++j) {
+                float s = 0.0f;
+                for (int64_t q = cp[j]; q < cp[j + 1]; ++q)
+                    s = s + (float)cv[q] * (float)r[ri[q]];
+                y[j] = (double)s;
+            }
+        }
+        for (int64_t j = 0; j < n; ++j) u[j] = rf(w ? w[j] * y[j] : y[j], f32);
+        phi = 0.0;
+        for (int64_t j = 0; j < n; ++j) phi += y[j] * u[j];
+
+        if (restart) {
+            /* initial update p = (rho/phi) W y */
+            if (!(phi > 0.0) || !isfinite(phi)) { status = ORC_BREAKDOWN; break; }
+            beta = 0.0;
+            gamma = rho / phi;
+            for (int64_t j = 0; j < n; ++j) p[j] = rf(gamma * u[j], f32);
+        } else {
+            /* Theorem 4.1 / Algorithm 1 scalars */
+            double s = sqrt(theta * phi);
+            double q = s / rho;
+            double d = (q - 1.0) * (q + 1.0);
+            if (!(d > 0.0) || !isfinite(d)) { status = ORC_BREAKDOWN; break; }
+            beta = 1.0 / d;
+            if (gamma_form == 1)
+                gamma = theta / (theta * phi - rho * rho);   /* statement form */
+            else
+                gamma = (theta / rho) * beta;                /* Algorithm 1 */
+            for (int64_t j = 0; j < n; ++j) p[j] = rf(beta * p[j] + gamma * u[j], f32);
+        }
+        /* theta = p^T W^{-1} p; x = x + p */
+        theta = 0.0;
+        for (int64_t j = 0; j < n; ++j) theta += w ? (p[j] * p[j]) / w[j] : p[j] * p[j];
+        for (int64_t j = 0; j < n; ++j) x[j] += p[j];
+        if (hist_s && k < hist_cap) {
+            double *h = hist_s + k * 5;
+            h[0] = rho; h[1] = phi; h[2] = beta; h[3] = gamma; h[4] = theta;
+        }
+        if (hist_x && k < hist_cap) memcpy(hist_x + k * n, x, (size_t)n * sizeof(double));
+        if (hist_p && k < hist_cap) memcpy(hist_p + k * n, p, (size_t)n * sizeof(double));
+        if (hist_y && k < hist_cap) memcpy(hist_y + k * n, y, (size_t)n * sizeof(double));
+        k += 1;
+        since += 1;
+        restart = 0;
+
+        if (f32 && refine > 0 && since >= refine) {
+            /* FP64 refinement: recompute the residual and restart */
+            true_residual(m, row_ptr, col_idx, val, b, x, rt);
+            for (int64_t i = 0; i < m; ++i) r[i] = rf(rt[i], f32);
+            restart = 1; since = 0;
+        } else if (!f32) {
+            /* r = r - A p */
+            for (int64_t i = 0; i < m; ++i) {
+                double s = 0.0;
+                for (int64_t q = row_ptr[i]; q < row_ptr[i + 1]; ++q)
+                    s += val[q] * p[col_idx[q]];
+                r[i] = r[i] - s;
+            }
+        } else {
+            for (int64_t i = 0; i < m; ++i) {
+                float s = 0.0f;
+                for (int64_t q = row_ptr[i]; q < row_ptr[i + 1]; ++q)
+                    s = s + (float)val[q] * (float)p[col_idx[q]];
+                r[i] = (double)((float)r[i] - s);
+            }
+        }
+        rho = dot(m, r, r);
+    }
+
+done:
+    if (status != ORC_NOMEM) {
+        *iters_out = k;
+        *relres_rec = nb > 0.0 ? sqrt(rho) / nb : 0.0;
+        true_residual(m, row_ptr, col_idx, val, b, x, rt);
+        *relres_true = nb > 0.0 ? sqrt(dot(m, rt, rt)) / nb : 0.0;
+    }
+    free(val); free(r); free(rt); free(y); free(u); free(p); free(cp); free(ri); free(cv);
+    return status;
+}
+
+/* ------------------------------------------------------------------ */
+/* Identity sketch: PLSS Kaczmarz (Sec. 7)                             */
+/* ------------------------------------------------------------------ */
+
+/* SplitMix64 (Steele, Lea & Flood, 2014): state advances by the golden
+ * gamma 0x9e3779b97f4a7c15 and the output is the state passed through the
+ * variant-13 mixing function. */
+static uint64_t splitmix_next(uint64_t *s)
+{
+    uint64_t z = (*s += 0x9e3779b97f4a7c15ULL);
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+    return z ^ (z >> 31);
+}
+
+/* Fills perm with 0..m-1 then shuffles it (Durstenfeld's Fisher-Yates:
+ * for i = m-1 down to 1, swap perm[i] with perm[next() mod (i+1)]). */
+void plss_oracle_permutation(uint64_t *state, int64_t m, int32_t *perm)
+{
+    for (int64_t i = 0; i < m; ++i) perm[i] = (int32_t)i;
+    for (int64_t i = m - 1; i > 0; --i) {
+        uint64_t j = splitmix_next(state) % (uint64_t)(i + 1);
+        int32_t t = perm[i]; perm[i] = perm[j]; perm[j] = t;
+    }
+}
+
+/*
+ * PLSS Kaczmarz (eq:pkKacz): for row i = i_k,
+ *   r_i = b_i - a_i^T x;  c_j = p_j^T a_i (j in the history);
+ *   ||d||^2 = sum_j c_j^2 / theta_j;
+ *   gamma = r_i / ((||a_i|| - ||d||)(||a_i|| + ||d||));
+ *   p = gamma (a_i - sum_j (c_j/theta_j) p_j);  x = x + p;
+ *   append p and theta = ||p||^2 to the history.
+ * With K = 0 (no history) this is the classical Kaczmarz step.
+ * maxit caps the rows visited; after every full pass over the rows the
+ * residual ||b - A x||/||b|| is tested against tol.
+ * Outputs: x_out, *iters (rows visited), *n_skipped, *relres_true; returns status.
+ */
+int plss_oracle_kaczmarz(int64_t m, int64_t n, const int64_t *row_ptr, const int32_t *col_idx,
+                         const double *val, const double *b, const double *x0, double tol,
+                         int64_t maxit, int64_t K, uint64_t seed, double *x_out,
+                         int64_t *iters_out, int64_t *n_skipped, double *relres_true)
+{
+    double *x = x_out;
+    double *P = (double *)malloc((size_t)((K > 0 ? K : 1) * (n ? n : 1)) * sizeof(double));
+    double *th = (double *)malloc((size_t)(K > 0 ? K : 1) * sizeof(double));
+    double *c = (double *)malloc((size_t)(K > 0 ? K : 1) * sizeof(double));
+    double *p = (double *)malloc((size_t)(n ? n : 1) * sizeof(double));
+    double *rt = (double *)malloc((size_t)(m ? m : 1) * sizeof(double));
+    int32_t *perm = (int32_t *)malloc((size_t)(m ? m : 1) * sizeof(int32_t));
+    int status = ORC_NOT_CONVERGED;
+    int64_t k = 0, nh = 0, skipped = 0;
+    uint64_t state = seed;
+    double nb;
+    if (!P || !th || !c || !p || !rt || !perm) { status = ORC_NOMEM; goto kdone; }
+
+    for (int64_t j = 0; j < n; ++j) x[j] = x0 ? x0[j] : 0.0;
+    nb = sqrt(dot(m, b, b));
+    if (nb == 0.0 || m == 0) { status = ORC_CONVERGED; goto kdone; }
+    true_residual(m, row_ptr, col_idx, val, b, x, rt);
+    if (sqrt(dot(m, rt, rt)) / nb <= tol) { status = ORC_CONVERGED; goto kdone; }
+
+    while (k < maxit) {
+        plss_oracle_permutation(&state, m, perm);
+        for (int64_t t = 0; t < m && k < maxit; ++t, ++k) {
+            int64_t i = perm[t];
+            int64_t s0 = row_ptr[i], s1 = row_ptr[i + 1];
+            /* r_i = b_i - a_i^T x */
+            double ax = 0.0, a2 = 0.0;
+            for (int64_t q = s0; q < s1; ++q) ax += val[q] * x[col_idx[q]];
+            for (int64_t q = s0; q < s1; ++q) a2 += val[q] * val[q];
+            double r_i = b[i] - ax;
+            /* c = P^T a_i, ||d||^2 = sum c_j^2 / theta_j */
+            double d2 = 0.0;
+            for (int64_t j = 0; j < nh; ++j) {
+                double s = 0.0;
+                for (int64_t q = s0; q < s1; ++q) s += val[q] * P[j * n + col_idx[q]];
+                c[j] = s;
+                d2 += (s * s) / th[j];
+            }
+            double na = sqrt(a2), nd = sqrt(d2);
+            double delta = (na - nd) * (na + nd);
+            if (!(delta > 1e-14 * a2)) { skipped += 1; continue; }
+            double gamma = r_i / delta;
+            /* p = gamma (a_i - sum_j (c_j/theta_j) p_j) */
+            for (int64_t jj = 0; jj < n; ++jj) p[jj] = 0.0;
+            for (int64_t q = s0; q < s1; ++q) p[col_idx[q]] = val[q];
+            for (int64_t j = 0; j < nh; ++j) {
+                double cj = c[j] / th[j];
+                for (int64_t jj = 0; jj < n; ++jj) p[jj] -= cj * P[j * n + jj];
+            }
+            double thn = 0.0;
+            for (int64_t jj = 0; jj < n; ++jj) {
+                p[jj] = gamma * p[jj];
+                thn += p[jj] * p[jj];
+                x[jj] += p[jj];
+            }
+            if (K > 0 && thn > 0.0) {
+                /* a zero update (r_i = 0: the row already holds) is not stored */
+                if (nh == K) nh = 0;   /* history full: restart the window */
+                memcpy(P + nh * n, p, (size_t)n * sizeof(double));
+                th[nh] = thn;
+                nh += 1;
+            }
+        }
+        /* test after each full pass */
+        true_residual(m, row_ptr, col_idx, val, b, x, rt);
+        if (sqrt(dot(m, rt, rt)) / nb <= tol) { status = ORC_CONVERGED; break; }
+    }
+
+kdone:
+    if (status != ORC_NOMEM) {
+        *iters_out = k;
+        *n_skipped = skipped;
+        nb = sqrt(dot(m, b, b));
+        true_residual(m, row_ptr, col_idx, val, b, x, rt);
+        *relres_true = nb > 0.0 ? sqrt(dot(m, rt, rt)) / nb : 0.0;
+    }
+    free(P); free(th); free(c); free(p); free(rt); free(perm);
+    return status;
+}
