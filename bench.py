@@ -1,0 +1,405 @@
+#!/usr/bin/env python
+"""Benchmark: PLSS time to ||b - A x||/||b|| <= 1e-8 on one GB300.
+
+Workload (synthetic, seeded; stands in for the paper's large sparse
+SuiteSparse systems): the consistent overdetermined 1,000,000 x 200,000 CSR
+with 8 nonzeros per row at uniform columns, values N(0,1) times column scales
+10**U(-2, 2) rounded to FP32 once, b = A x*, x0 = 0.
+
+A step is one whole solve (every update of Algorithm 1 until the true
+relative residual is <= tol), inputs resident in HBM. The line also carries
+the roofline of the dominant sweep (CUDA events recorded on the solve's
+stream between the captured kernels of the timed solves), the oracle's time
+on the host cores for a bounded sample, and an end-to-end figure through the
+C ABI with host buffers.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2207_07615_gb300 import synth  # noqa: E402
+
+WORKLOAD = "plss_overdetermined_1e6x2e5_nnz8_colscale1e-2..1e2"
+METRIC = "time to ||r||/||b||<=1e-8"
+# Updates the FP64 W = I solve of this workload needs on GB300 (measured by
+# this benchmark; the reference arm scales its sampled per-update time by it).
+REF_UPDATES_TO_TOL = 183000
+L2_FLUSH_BYTES = 512 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="plss", choices=["plss", "reference"])
+    ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--w-mode", type=int, default=0)
+    ap.add_argument("--m", type=int, default=1_000_000)
+    ap.add_argument("--n", type=int, default=200_000)
+    ap.add_argument("--tol", type=float, default=1e-8)
+    ap.add_argument("--maxit", type=int, default=3_000_000)
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--oracle-updates", type=int, default=100)
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- helpers
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def host_info():
+    cpu = "unknown"
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part", "hardware")):
+                    cpu = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return cpu, os.cpu_count()
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def ncu_traffic(kernel):
+    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, or
+    None when absent or taken on a different version of the kernel source."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    src = os.path.join(ROOT, "paper_2207_07615_gb300", "csrc", "plss_kernels.cu")
+    try:
+        kv = {}
+        with open(path) as f:
+            for line in f:
+                if ":" in line and not line.startswith("#"):
+                    k, v = line.split(":", 1)
+                    kv[k.strip()] = v.strip()
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        if kv.get("kernels_sha256_16") != sha:
+            return None
+        return float(kv[f"{kernel}_dram_bytes_per_launch"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.tmp.flush()
+        rows = []
+        with open(self.tmp.name) as f:
+            for line in f:
+                p = [s.strip() for s in line.split(",")]
+                if len(p) >= 8:
+                    rows.append(p)
+        os.unlink(self.tmp.name)
+        if not rows:
+            return None
+
+        def num(s):
+            try:
+                return float(s)
+            except ValueError:
+                return float("nan")
+        sm = np.array([num(r[0]) for r in rows])
+        mx = np.array([num(r[1]) for r in rows])
+        pw = np.array([num(r[2]) for r in rows])
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[4 + i].lower() == "active"})
+        load = sm[pw >= np.nanmedian(pw)] if np.isfinite(pw).any() else sm
+        return {"sm_mhz": float(np.nanmedian(load if load.size else sm)),
+                "sm_max_mhz": float(np.nanmax(mx)), "reasons": reasons,
+                "samples": int(len(rows)), "power_w_max": float(np.nanmax(pw))}
+
+
+def sweep_bytes(kind, m, n, nnz, sv):
+    """Algorithmic HBM bytes of one launch (each array touched once)."""
+    if kind == "row_sweep":      # CSR (col_idx, val, row_ptr), p gathered once, r read + written
+        return nnz * (4 + sv) + (m + 1) * 4 + 2 * m * sv + n * sv
+    if kind == "col_sweep":      # CSC (row_idx, val, col_ptr), r gathered once, W y written
+        return nnz * (4 + sv) + (n + 1) * 4 + m * sv + n * sv
+    if kind == "update":         # p, W y read; p written; x (double) read + written
+        return n * (3 * sv + 16)
+    raise KeyError(kind)
+
+
+def make_workload(args):
+    A, b, xs = synth.overdetermined_scaled(m=args.m, n=args.n, per_row=8, seed=1)
+    if args.prec == "fp64":
+        A = A.astype(np.float64)
+    return A, b, xs
+
+
+def cpu_baseline(A, b, args, updates_to_tol):
+    """The oracle (plain C, 1 thread) on a bounded sample: the time of a
+    1-update solve (set-up included) plus the per-update time of the next
+    `oracle_updates` updates, scaled to the updates the solve needs."""
+    import oracle
+    oracle.build()
+    prec = 1 if args.prec == "fp32" else 0
+    w = oracle.colweights(A, args.w_mode) if args.w_mode else None
+    t0 = time.perf_counter()
+    oracle.residual(A, b, w=w, tol=0.0, maxit=1, prec=prec)
+    t1 = time.perf_counter()
+    oracle.residual(A, b, w=w, tol=0.0, maxit=1 + args.oracle_updates, prec=prec)
+    t2 = time.perf_counter()
+    per_update = ((t2 - t1) - (t1 - t0)) / args.oracle_updates
+    value = (t1 - t0) + per_update * max(0, updates_to_tol - 1)
+    cpu, cores = host_info()
+    return {"value": value, "unit": "s", "cores": 1, "kind": "oracle",
+            "sample": (f"1 update ({t1 - t0:.2f} s incl. set-up) + {args.oracle_updates} updates "
+                       f"({per_update * 1e3:.1f} ms/update) of the same system, scaled to "
+                       f"{updates_to_tol} updates; host {cpu}, {cores} cores, 1 used")}
+
+
+# ------------------------------------------------------------ reference arm
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    A, b, _ = make_workload(args)
+    cpu, cores = host_info()
+    t_all = time.perf_counter()
+    vals = []
+    for i in range(args.warmup + args.steps):
+        cb = cpu_baseline(A, b, args, REF_UPDATES_TO_TOL)
+        if i >= args.warmup:
+            vals.append(cb["value"])
+    wall = time.perf_counter() - t_all
+    v = float(np.mean(vals))
+    line = {"metric": METRIC, "value": v, "unit": "s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": wall / (args.warmup + args.steps) * 1e3,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if args.prec == "fp64" else "f32+f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": WORKLOAD, "m": args.m, "n": args.n, "nnz": int(A.nnz),
+                       "tol": args.tol, "w_mode": args.w_mode, "precision": args.prec,
+                       "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": v, "unit": "s", "cores": 1, "kind": "oracle",
+                             "sample": cb["sample"]},
+            "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ our arm
+
+def run_plss(args):
+    import torch
+    from paper_2207_07615_gb300 import plss
+    import __graft_entry__ as g
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        dist = None
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if rank == 0:
+        g.build()
+    if dist is not None:
+        dist.barrier()
+    plss.lib()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    A, b, xs = make_workload(args)
+    m, n, nnz = A.m, A.n, A.nnz
+    sv = 8 if args.prec == "fp64" else 4
+    ctx = plss.Context(A, precision=args.prec)
+    b_dev = torch.from_numpy(b).to(dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    kw = dict(tol=args.tol, maxit=args.maxit, stop_on_true=1, w_mode=args.w_mode)
+
+    for _ in range(args.warmup):
+        ctx.solve(b_dev, **kw)
+        flush.zero_()
+    ctx.kernel_times(reset=True)
+    clocks = Clocks(local)
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    results = []
+    for _ in range(args.steps):
+        x, r = ctx.solve(b_dev, profile=1, **kw)
+        results.append(r)
+        flush.zero_()
+    e1.record()
+    barrier()
+    clk = clocks.stop()
+    ms_total = e0.elapsed_time(e1)
+    kt = ctx.kernel_times(reset=True)
+    ms_step = ms_total / args.steps
+    if dist is not None:
+        t = torch.tensor([ms_step], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    last = results[-1]
+    x_np = x.cpu().numpy()
+    err_xstar = float(np.linalg.norm(x_np - xs) / np.linalg.norm(xs))
+
+    # roofline of the dominant sweep
+    peaks, peak_src = measured_peaks()
+    kinds = ("row_sweep", "col_sweep", "update")
+    per = {}
+    for k in kinds:
+        ms, cnt = kt[k]
+        if cnt > 0:
+            avg = ms / cnt
+            byt = sweep_bytes(k, m, n, nnz, sv)
+            per[k] = {"ms_total": ms, "launches": cnt, "us_per_launch": avg * 1e3,
+                      "bytes_per_launch": byt, "gbs": byt / (avg * 1e-3) / 1e9}
+    dom = max(per, key=lambda k: per[k]["ms_total"]) if per else None
+    roof = None
+    if dom:
+        ach = per[dom]["gbs"]
+        roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": ach / peaks["hbm_gbs"],
+                "traffic": ncu_traffic(dom), "peak_source": f"{peak_src} hbm_gbs (copy)",
+                "algorithmic_bytes_per_launch": per[dom]["bytes_per_launch"],
+                "us_per_launch": per[dom]["us_per_launch"], "sweeps": per}
+
+    # end to end through the C ABI with host buffers
+    torch.cuda.synchronize()
+    te = []
+    for _ in range(args.e2e_steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        xh, rh = ctx.solve(b, **kw)
+        te.append(time.perf_counter() - t0)
+    e2e = {"value": float(np.mean(te)), "unit": "s", "h2d_bytes_per_step": 8 * m,
+           "d2h_bytes_per_step": 8 * n}
+
+    variants = {}
+    if not args.no_variants and rank == 0:
+        variants = run_variants(args, A, b, xs, x_np, ctx, b_dev, flush)
+
+    cb = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cb = cpu_baseline(A, b, args, last["iters"])
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": ms_step / 1e3, "unit": "s", "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+                "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64" if args.prec == "fp64" else "f32+f64", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "m": m, "n": n, "nnz": int(nnz), "tol": args.tol,
+                           "w_mode": args.w_mode, "precision": args.prec,
+                           "parallelism": "replicas" if ws > 1 else "single",
+                           "l2": "inputs larger than L2 (per-update working set "
+                                 f"{(sweep_bytes('row_sweep', m, n, nnz, sv) + sweep_bytes('col_sweep', m, n, nnz, sv)) / 1e6:.0f} MB)"
+                                 " and a 512 MB write between steps"},
+                "solve": {"updates": last["iters"], "status": last["status"],
+                          "relres_true": last["relres_true"], "relres_rec": last["relres_rec"],
+                          "ms_per_update": ms_step / max(1, last["iters"]),
+                          "rel_err_vs_xstar": err_xstar},
+                "roofline": roof, "cpu_baseline": cb, "e2e": e2e,
+                "gpu_launches": int(kt["all_launches"]), "clocks": clk, "variants": variants}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def run_variants(args, A, b, xs, x_ref, ctx, b_dev, flush):
+    """One solve each of the other forms on the same system: PLSS W
+    (W = diag(1/||A_j||^2) and diag(1/||A_j||), Sec. 4.1) and FP32 storage
+    with FP64 refinement; error against the FP64 W = I answer."""
+    import torch
+    from paper_2207_07615_gb300 import plss
+    out = {}
+
+    def timed(c, bb, **kw):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        x, r = c.solve(bb, **kw)
+        e1.record()
+        torch.cuda.synchronize()
+        xn = x.cpu().numpy()
+        return {"seconds": e0.elapsed_time(e1) / 1e3, "updates": r["iters"], "status": r["status"],
+                "relres_true": r["relres_true"],
+                "rel_err_vs_fp64": float(np.linalg.norm(xn - x_ref) / np.linalg.norm(x_ref)),
+                "rel_err_vs_xstar": float(np.linalg.norm(xn - xs) / np.linalg.norm(xs))}
+    base = dict(tol=args.tol, maxit=args.maxit, stop_on_true=1)
+    if args.prec == "fp64":
+        out["fp64_w2"] = timed(ctx, b_dev, w_mode=2, **base)
+        out["fp64_w1"] = timed(ctx, b_dev, w_mode=1, **base)
+        c32 = plss.Context(A, precision="fp32")
+        out["fp32_w2"] = timed(c32, b_dev, w_mode=2, **base)
+        out["fp32_w1"] = timed(c32, b_dev, w_mode=1, **base)
+        out["fp32_w0"] = timed(c32, b_dev, w_mode=0, **dict(base, maxit=min(args.maxit, 400000)))
+        c32.close()
+    return out
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_plss(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,228 @@
+/*
+ * plss.h -- C ABI of the GB300 (sm_103a) PLSS library, libplss.so.
+ *
+ * PLSS (Brust & Saunders, "PLSS: a projected linear systems solver",
+ * arXiv 2207.07615) solves consistent systems A x = b, b in range(A), with A
+ * sparse and m x n of any shape (Sec. 1, eq:axb). Two sketches are offered:
+ *   - residual sketch S_k = [r_0 ... r_{k-1}] (Sec. 4, eq:S): the 1-step
+ *     recursion of Theorem 4.1 as laid out in Algorithm 1 (Sec. 5), with an
+ *     optional diagonal weight W (Sec. 4.1, eq:pkShortW);
+ *   - identity sketch S_k = [e_{i_1} ... e_{i_k}] (Sec. 7, eq:pkKacz), the
+ *     generalised Kaczmarz method, with a history window of K updates.
+ *
+ * Conventions for every entry point:
+ *   - Nothing is thrown across the ABI; each call returns a plss_status and
+ *     plss_last_error() gives a message for the calling thread.
+ *   - The caller owns every pointer it passes and may free it once the call
+ *     returns; the library copies what it keeps. The library owns the device
+ *     memory it allocates for a context and frees it in plss_destroy.
+ *   - Host/device: arrays are host memory unless the flag next to them
+ *     (plss_csr.on_device, plss_opts.io_device) says device memory of the
+ *     current CUDA device.
+ *   - Indexing is 0-based. row_ptr is int64 with row_ptr[0] = 0,
+ *     row_ptr[m] = nnz, non-decreasing; col_idx are int32 in [0, n), strictly
+ *     increasing within each row. A context holds at most 2^31 - 1 nonzeros
+ *     and rows/columns in total (larger inputs return PLSS_ERR_INVALID).
+ *   - Distinct contexts may be used from different host threads; one
+ *     context must not be used by two threads at once.
+ */
+#ifndef PLSS_H
+#define PLSS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PLSS_OK = 0,              /* converged: ||r||/||b|| <= tol              */
+    PLSS_NOT_CONVERGED = 1,   /* maxit reached; x is the last iterate      */
+    PLSS_PENDING = 2,         /* plss_poll: request not finished yet        */
+    PLSS_ERR_INVALID = -1,    /* bad argument or malformed CSR              */
+    PLSS_ERR_NOMEM = -2,      /* device or host allocation failed           */
+    PLSS_ERR_CUDA = -3,       /* a CUDA runtime call failed                 */
+    PLSS_ERR_BREAKDOWN = -4,  /* recursion broke down (see plss_solve)      */
+    PLSS_ERR_TIMEOUT = -5,    /* a bounded device wait expired              */
+    PLSS_ERR_BUSY = -6,       /* server queue full / admission refused      */
+    PLSS_ERR_NOT_FOUND = -7   /* unknown ticket                             */
+} plss_status;
+
+enum { PLSS_SKETCH_RESIDUAL = 0, PLSS_SKETCH_IDENTITY = 1 };
+/* PLSS_FP64: A, vectors and sums in double.
+ * PLSS_FP32: A and the vectors r, p, W y stored as float, sums of products
+ * accumulated in float; inner products, the scalar recursion, x and a
+ * periodic true residual b - A x (refinement) in double. */
+enum { PLSS_FP64 = 0, PLSS_FP32 = 1 };
+/* Diagonal weight W of Sec. 4.1: identity, 1/||A_{:,j}||, 1/||A_{:,j}||^2
+ * (an empty column gets weight 1). */
+enum { PLSS_W_IDENTITY = 0, PLSS_W_COLNORM = 1, PLSS_W_COLNORM2 = 2 };
+
+/* A sparse matrix in CSR form (see the conventions above). val holds nnz
+ * doubles, or floats when val_f32 = 1. */
+typedef struct {
+    int64_t m, n, nnz;
+    const int64_t *row_ptr;
+    const int32_t *col_idx;
+    const void *val;
+    int32_t val_f32;
+    int32_t on_device;
+} plss_csr;
+
+/* Options. Call plss_opts_default() first, then override fields. */
+typedef struct {
+    int32_t sketch;         /* PLSS_SKETCH_*                                        */
+    int32_t precision;      /* PLSS_FP64 / PLSS_FP32 (fixed at create: storage)     */
+    int32_t w_mode;         /* PLSS_W_*                                             */
+    int32_t stop_on_true;   /* 1: stop only when b - A x (recomputed in double)     */
+                            /*    passes the test; forced to 1 for PLSS_FP32       */
+    double tol;             /* stop when ||r||/||b|| <= tol (Sec. 5)                */
+    int64_t maxit;          /* cap on updates (residual) or rows visited (identity);*/
+                            /* < 0 means n                                          */
+    int64_t refine_period;  /* PLSS_FP32: restart from b - A x every this many      */
+                            /* updates (<= 0: only when the test passes)           */
+    int64_t kacz_hist;      /* identity sketch: history window K (0 = Kaczmarz)     */
+    uint64_t seed;          /* identity sketch: row-order stream seed               */
+    int32_t io_device;      /* 1: b, x0, x_out are device pointers                  */
+    int32_t symmetric;      /* create: caller asserts A^T = A (square); A^T r then  */
+                            /* reuses the CSR and no transpose is stored           */
+    void *stream;           /* cudaStream_t to run on (NULL: the legacy stream)     */
+    double *hist;           /* optional host array [hist_cap][5]: for update k+1 of */
+                            /* system 0, (rho_k, phi_{k+1}, beta_k, gamma_k,        */
+                            /* theta_{k+1}) -- the scalars of Algorithm 1          */
+    int64_t hist_cap;
+    int32_t profile;        /* 1: time every sweep launch with CUDA events recorded */
+                            /* on the solve's stream (see plss_kernel_times)       */
+    int32_t reserved;
+} plss_opts;
+
+/* Outcome of one solve. relres_rec is sqrt(rho)/||b|| of the last recursive
+ * (or refined) residual; relres_true is ||b - A x||/||b|| recomputed in
+ * double after the solve; seconds is device time between the solve's first
+ * and last kernel. */
+typedef struct {
+    int32_t status;
+    int32_t reserved;
+    int64_t iters;
+    double relres_rec;
+    double relres_true;
+    double seconds;
+} plss_result;
+
+typedef struct plss_ctx plss_ctx;
+
+void plss_opts_default(plss_opts *o);
+
+/* Copies A to the device, validates it, builds its transpose (unless
+ * o->symmetric) and the tile schedule of the sparse sweeps. The storage
+ * precision is o->precision. On error *out is NULL. */
+plss_status plss_create(const plss_csr *A, const plss_opts *o, plss_ctx **out);
+
+/* As plss_create for nsys independent systems As[0..nsys-1], packed into one
+ * block-diagonal context so that every sweep covers all systems in one
+ * launch while scalars, stopping and status stay per system. */
+plss_status plss_create_batched(const plss_csr *As, int32_t nsys, const plss_opts *o,
+                                plss_ctx **out);
+
+void plss_destroy(plss_ctx *ctx);
+
+/* Sizes of a context: systems, total rows, total columns, total nonzeros. */
+plss_status plss_ctx_info(const plss_ctx *ctx, int32_t *nsys, int64_t *m, int64_t *n,
+                          int64_t *nnz);
+
+/*
+ * Solves A x = b for a single-system context.
+ *   b[m], x0[n] (NULL = zero start), x_out[n]: host, or device when
+ *   o->io_device. The residual sketch runs Algorithm 1; the identity sketch
+ *   runs eq:pkKacz with rows in a fresh SplitMix64/Fisher-Yates permutation
+ *   per pass (seed o->seed) and tests ||b - A x|| after every pass.
+ * Returns PLSS_OK, PLSS_NOT_CONVERGED (x_out holds the last iterate), or
+ * PLSS_ERR_BREAKDOWN when phi_1 <= 0 (A^T r_0 = 0 with r_0 != 0: b is not in
+ * range(A)) or when (sqrt(theta phi)/rho - 1)(sqrt(theta phi)/rho + 1) <= 0,
+ * which happens only when A^T r_k is parallel to p_k; x_out then holds the
+ * last iterate. ||b|| = 0 returns x0 at once with PLSS_OK.
+ */
+plss_status plss_solve(plss_ctx *ctx, const double *b, const double *x0, double *x_out,
+                       const plss_opts *o, plss_result *res);
+
+/* Solves every system of a batched context at once: b[s], x0[s] (array of
+ * NULL or NULL entries = zero start), x_out[s] for s < nsys; res[nsys].
+ * Systems stop independently; the return value is PLSS_OK when all
+ * converged, else the first non-OK system status. Residual sketch only. */
+plss_status plss_solve_batched(plss_ctx *ctx, const double *const *b, const double *const *x0,
+                               double *const *x_out, const plss_opts *o, plss_result *res);
+
+/* Many right-hand sides on one matrix (SpMM form): B is m x nrhs, X0 and X
+ * are n x nrhs, all row-major double (X0 may be NULL). Each column is an
+ * independent PLSS solve with its own scalars; converged columns freeze.
+ * res[nrhs]. Residual sketch only; nrhs <= 64. */
+plss_status plss_solve_rhs(plss_ctx *ctx, int32_t nrhs, const double *B, const double *X0,
+                           double *X, const plss_opts *o, plss_result *res);
+
+/* One sparse product with the context's stored matrix in double:
+ * transpose = 0: out[m] = A v[n]; transpose = 1: out[n] = A^T v[m].
+ * v and out follow o->io_device. Single-system contexts. */
+plss_status plss_spmv(plss_ctx *ctx, int32_t transpose, const double *v, double *out,
+                      const plss_opts *o);
+
+/* Device time of the residual-sketch sweeps accumulated over the solves of
+ * this context that ran with o->profile = 1: ms[0..2] = total milliseconds
+ * of the row sweep (r = r - A p, rho), the column sweep (y = A^T r, phi,
+ * scalar step) and the update (p, theta, x), over the graph launches in
+ * which a system stayed active throughout; launches[0..2] = the launches
+ * those totals cover; launches[3] = every kernel the profiled solves
+ * launched. reset = 1 clears the totals after reading. Either array may be
+ * NULL (ms has 3 entries, launches 4). */
+plss_status plss_kernel_times(plss_ctx *ctx, double *ms, int64_t *launches, int32_t reset);
+
+/* Message of the last error on the calling thread ("" when none). */
+const char *plss_last_error(void);
+
+/* ------------------------------------------------------------------ */
+/* Serving: continuous batching of independent solves                  */
+/* ------------------------------------------------------------------ */
+
+typedef struct plss_server plss_server;
+
+typedef struct {
+    int32_t max_slots;        /* systems resident on the device at once          */
+    int32_t max_queue;        /* pending requests before plss_submit says BUSY   */
+    int64_t hbm_budget_bytes; /* admission budget (<= 0: 80% of free memory)     */
+    int32_t precision;        /* PLSS_FP64 / PLSS_FP32 for every request         */
+    int32_t reserved;
+} plss_server_opts;
+
+void plss_server_opts_default(plss_server_opts *o);
+
+/* Starts a server: a host thread that admits queued requests into device
+ * slots while memory and slots allow, and runs all admitted systems
+ * together, one block-diagonal sweep per step. */
+plss_status plss_server_create(const plss_server_opts *so, plss_server **out);
+
+/* Queues one solve. A, b (length A->m) and x0 (length A->n, or NULL) are host
+ * arrays, copied before the call returns. o gives tol and maxit (residual
+ * sketch). *ticket identifies the request. PLSS_ERR_BUSY when the queue is
+ * full; PLSS_ERR_INVALID for a malformed request. */
+plss_status plss_submit(plss_server *srv, const plss_csr *A, const double *b, const double *x0,
+                        const plss_opts *o, uint64_t *ticket);
+
+/* Never blocks. PLSS_PENDING while the request runs; once finished, copies
+ * x (length n) to the host array x_out (may be NULL), fills *res (may be
+ * NULL; res->seconds = submit-to-completion wall time) and forgets the
+ * ticket, returning the solve's status. PLSS_ERR_NOT_FOUND for an unknown
+ * or already collected ticket. */
+plss_status plss_poll(plss_server *srv, uint64_t ticket, double *x_out, plss_result *res);
+
+/* Counters: completed requests, queued, running, device bytes in use. */
+plss_status plss_server_stats(plss_server *srv, int64_t *completed, int64_t *queued,
+                              int64_t *running, int64_t *bytes_in_use);
+
+/* Stops the server thread (pending requests are dropped) and frees it. */
+void plss_server_destroy(plss_server *srv);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PLSS_H */

@@ -1,0 +1,93 @@
+// plss_ctx.h -- the context object behind the opaque plss_ctx handle.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <map>
+#include <vector>
+
+#include "plss.h"
+#include "plss_dev.cuh"
+
+namespace plss {
+
+constexpr int64_t kTileNnz = 2048;      // target nonzeros per sweep tile
+constexpr int64_t kTileMaxSegs = 1024;  // max rows/columns per sweep tile
+constexpr int64_t kVecTile = 2048;      // entries per update tile
+constexpr int kCtasPerSm = 8;           // resident CTAs per SM assumed for grids
+constexpr int kMaxChunk = 64;           // bodies per graph launch (max)
+
+struct KaczState;   // identity-sketch buffers (plss_kaczmarz.cu)
+struct RhsState;    // multi-right-hand-side buffers (plss_spmm.cu)
+
+}  // namespace plss
+
+struct plss_ctx {
+    int32_t nsys = 0;
+    int64_t m = 0, n = 0, nnz = 0;   // totals over the packed systems
+    bool f32 = false;
+    bool symmetric = false;
+    int device = 0;
+    int nsm = 1;
+    std::vector<plss::SysDesc> h_desc;
+    std::vector<plss::Tile> h_rt, h_ct, h_vt;
+
+    // matrix (CSR and its transpose) and schedules
+    int32_t *d_row_ptr = nullptr, *d_col_idx = nullptr;
+    void *d_val = nullptr;
+    int32_t *d_col_ptr = nullptr, *d_row_idx = nullptr;
+    void *d_cval = nullptr;
+    plss::Tile *d_rt = nullptr, *d_ct = nullptr, *d_vt = nullptr;
+    plss::SysDesc *d_desc = nullptr;
+    plss::SysState *d_st = nullptr;
+    double *d_part_row = nullptr, *d_part_col = nullptr, *d_part_upd = nullptr, *d_part_res = nullptr;
+    int32_t *d_active = nullptr;
+
+    // iteration vectors
+    double *d_b = nullptr, *d_x = nullptr, *d_w = nullptr;
+    void *d_r = nullptr, *d_p = nullptr, *d_u = nullptr;
+    double *d_vin = nullptr, *d_vout = nullptr;
+    double *d_hist = nullptr;
+    int64_t hist_cap_alloc = 0;
+    int32_t w_mode_cur = -1;
+
+    plss::SysState *h_st = nullptr;   // pinned
+    int32_t *h_active = nullptr;      // pinned
+
+    int grid_r = 1, grid_c = 1, grid_v = 1;
+    plss::SweepArgs args{};
+    cudaStream_t cap_stream = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    std::map<int, cudaGraphExec_t> graphs;
+    std::vector<cudaEvent_t> prof_ev;   // 4 per body of the largest profiled chunk
+    double prof_ms[3] = {0.0, 0.0, 0.0};
+    int64_t prof_n[3] = {0, 0, 0};
+    int64_t prof_all = 0;               // every kernel launched by profiled solves
+
+    plss::KaczState *kacz = nullptr;
+    plss::RhsState *rhs = nullptr;
+};
+
+namespace plss {
+
+plss_status fail(plss_status s, const char *fmt, ...);
+void clear_error();
+const char *last_error();
+plss_status dalloc(void **p, size_t bytes, const char *what);
+void dfree(void *p);
+plss_status put_vec(double *dst, const double *src, int64_t len, bool dev, cudaStream_t s);
+plss_status get_vec(double *dst, const double *src, int64_t len, bool dev, cudaStream_t s);
+plss_status check_opts(const plss_opts *o);
+plss_status ensure_weights(plss_ctx *c, int32_t w_mode, cudaStream_t s);
+plss_status true_relres(plss_ctx *c, cudaStream_t s, std::vector<double> &rel);
+void build_tiles(const int32_t *ptr, int64_t begin, int64_t end, int32_t sys, int64_t target,
+                 int64_t max_segs, std::vector<Tile> &out);
+
+// identity sketch (plss_kaczmarz.cu)
+plss_status run_identity(plss_ctx *c, const double *b, const double *x0, double *x_out,
+                         const plss_opts *o, plss_result *res);
+// extra per-context state of the other solvers
+void free_extra(plss_ctx *c);
+
+}  // namespace plss

@@ -1,0 +1,781 @@
+// plss_host.cu -- C ABI of libplss: validation, packing, tile schedules,
+// device memory, the CUDA-graph iteration driver and results.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "plss.h"
+#include "plss_ctx.h"
+#include "plss_dev.cuh"
+#include "plss_launch.h"
+
+namespace plss {
+
+static thread_local std::string g_err;
+
+plss_status fail(plss_status s, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+void clear_error() { g_err.clear(); }
+const char *last_error() { return g_err.c_str(); }
+
+// ---------------------------------------------------------------------------
+// Tile schedules
+// ---------------------------------------------------------------------------
+
+// Lanes per segment: the smallest power of two >= the mean segment length,
+// clamped to [1, 32].
+static int32_t pick_group(double mean) {
+    int32_t g = 1;
+    while (g < 32 && g < mean) g <<= 1;
+    return g;
+}
+
+// Cuts segments [begin, end) (offsets in ptr) of system `sys` into tiles of
+// about `target` nonzeros; a segment longer than `target` gets a tile of its
+// own worked by the whole CTA (group 0). An empty range still gets one
+// (empty) tile so that every system reaches its scalar step.
+void build_tiles(const int32_t *ptr, int64_t begin, int64_t end, int32_t sys, int64_t target,
+                 int64_t max_segs, std::vector<Tile> &out) {
+    if (begin == end) {
+        out.push_back({sys, int32_t(begin), int32_t(begin), 1});
+        return;
+    }
+    int64_t i = begin;
+    while (i < end) {
+        const int64_t li = int64_t(ptr[i + 1]) - ptr[i];
+        if (li > target) {
+            out.push_back({sys, int32_t(i), int32_t(i + 1), 0});
+            ++i;
+            continue;
+        }
+        int64_t j = i, nz = 0;
+        while (j < end && j - i < max_segs) {
+            const int64_t l = int64_t(ptr[j + 1]) - ptr[j];
+            if (l > target) break;
+            if (nz + l > target && j > i) break;
+            nz += l;
+            ++j;
+        }
+        out.push_back({sys, int32_t(i), int32_t(j), pick_group(double(nz) / double(j - i))});
+        i = j;
+    }
+}
+
+void build_vec_tiles(int64_t begin, int64_t end, int32_t sys, int64_t chunk, std::vector<Tile> &out) {
+    if (begin == end) {
+        out.push_back({sys, int32_t(begin), int32_t(begin), 1});
+        return;
+    }
+    for (int64_t i = begin; i < end; i += chunk)
+        out.push_back({sys, int32_t(i), int32_t(std::min(end, i + chunk)), 1});
+}
+
+// ---------------------------------------------------------------------------
+// Validation and packing
+// ---------------------------------------------------------------------------
+
+// Host copy of one CSR with values in double.
+struct HostCsr {
+    int64_t m = 0, n = 0, nnz = 0;
+    std::vector<int64_t> row_ptr;
+    std::vector<int32_t> col_idx;
+    std::vector<double> val;
+};
+
+plss_status fetch_csr(const plss_csr *A, HostCsr &h) {
+    if (!A) return fail(PLSS_ERR_INVALID, "A is NULL");
+    if (A->m < 0 || A->n < 0 || A->nnz < 0)
+        return fail(PLSS_ERR_INVALID, "negative size (m=%lld n=%lld nnz=%lld)", (long long)A->m,
+                    (long long)A->n, (long long)A->nnz);
+    if (A->m >= INT32_MAX || A->n >= INT32_MAX || A->nnz >= INT32_MAX)
+        return fail(PLSS_ERR_INVALID, "sizes above 2^31-1 are not supported");
+    if (!A->row_ptr || (A->nnz > 0 && (!A->col_idx || !A->val)))
+        return fail(PLSS_ERR_INVALID, "NULL CSR array");
+    h.m = A->m;
+    h.n = A->n;
+    h.nnz = A->nnz;
+    h.row_ptr.resize(size_t(A->m + 1));
+    h.col_idx.resize(size_t(A->nnz));
+    h.val.resize(size_t(A->nnz));
+    // host input: plain copies (no CUDA call, so validation works anywhere)
+    auto fetch = [&](void *dst, const void *src, size_t bytes) -> bool {
+        if (bytes == 0) return true;
+        if (!A->on_device) {
+            std::memcpy(dst, src, bytes);
+            return true;
+        }
+        return cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToHost) == cudaSuccess;
+    };
+    if (!fetch(h.row_ptr.data(), A->row_ptr, size_t(A->m + 1) * 8))
+        return fail(PLSS_ERR_CUDA, "copying row_ptr failed: %s", cudaGetErrorString(cudaGetLastError()));
+    if (!fetch(h.col_idx.data(), A->col_idx, size_t(A->nnz) * 4))
+        return fail(PLSS_ERR_CUDA, "copying col_idx failed: %s", cudaGetErrorString(cudaGetLastError()));
+    if (A->val_f32) {
+        std::vector<float> tmp(static_cast<size_t>(A->nnz));
+        if (!fetch(tmp.data(), A->val, size_t(A->nnz) * 4))
+            return fail(PLSS_ERR_CUDA, "copying val failed: %s", cudaGetErrorString(cudaGetLastError()));
+        for (size_t k = 0; k < tmp.size(); ++k) h.val[k] = double(tmp[k]);
+    } else if (!fetch(h.val.data(), A->val, size_t(A->nnz) * 8)) {
+        return fail(PLSS_ERR_CUDA, "copying val failed: %s", cudaGetErrorString(cudaGetLastError()));
+    }
+    // structure checks
+    if (h.row_ptr[0] != 0) return fail(PLSS_ERR_INVALID, "row_ptr[0] = %lld, expected 0", (long long)h.row_ptr[0]);
+    if (h.row_ptr[size_t(h.m)] != h.nnz)
+        return fail(PLSS_ERR_INVALID, "row_ptr[m] = %lld, expected nnz = %lld",
+                    (long long)h.row_ptr[size_t(h.m)], (long long)h.nnz);
+    for (int64_t i = 0; i < h.m; ++i)
+        if (h.row_ptr[size_t(i + 1)] < h.row_ptr[size_t(i)])
+            return fail(PLSS_ERR_INVALID, "row_ptr decreases at row %lld", (long long)i);
+    for (int64_t i = 0; i < h.m; ++i) {
+        const int64_t s = h.row_ptr[size_t(i)], e = h.row_ptr[size_t(i + 1)];
+        for (int64_t k = s; k < e; ++k) {
+            const int32_t c = h.col_idx[size_t(k)];
+            if (c < 0 || c >= h.n)
+                return fail(PLSS_ERR_INVALID, "col_idx[%lld] = %d outside [0, %lld)", (long long)k, c,
+                            (long long)h.n);
+            if (k > s && c <= h.col_idx[size_t(k - 1)])
+                return fail(PLSS_ERR_INVALID, "columns not strictly increasing in row %lld", (long long)i);
+        }
+    }
+    for (int64_t k = 0; k < h.nnz; ++k)
+        if (!std::isfinite(h.val[size_t(k)]))
+            return fail(PLSS_ERR_INVALID, "non-finite value at nonzero %lld", (long long)k);
+    return PLSS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Device memory helpers
+// ---------------------------------------------------------------------------
+
+plss_status dalloc(void **p, size_t bytes, const char *what) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    const cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return fail(e == cudaErrorMemoryAllocation ? PLSS_ERR_NOMEM : PLSS_ERR_CUDA,
+                    "cudaMalloc(%s, %zu bytes): %s", what, bytes, cudaGetErrorString(e));
+    }
+    return PLSS_OK;
+}
+
+template <typename T>
+plss_status upload(T **dst, const std::vector<T> &src, const char *what) {
+    plss_status s = dalloc(reinterpret_cast<void **>(dst), src.size() * sizeof(T), what);
+    if (s != PLSS_OK) return s;
+    if (!src.empty() && cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess)
+        return fail(PLSS_ERR_CUDA, "upload of %s failed", what);
+    return PLSS_OK;
+}
+
+void dfree(void *p) {
+    if (p) cudaFree(p);
+}
+
+#define CUDA_TRY(expr)                                                                           \
+    do {                                                                                         \
+        cudaError_t e_ = (expr);                                                                 \
+        if (e_ != cudaSuccess) {                                                                 \
+            cudaGetLastError();                                                                  \
+            return fail(PLSS_ERR_CUDA, "%s: %s (%s:%d)", #expr, cudaGetErrorString(e_), __FILE__, \
+                        __LINE__);                                                               \
+        }                                                                                        \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// Context creation
+// ---------------------------------------------------------------------------
+
+static void ctx_free(plss_ctx *c) {
+    if (!c) return;
+    for (auto &kv : c->graphs) cudaGraphExecDestroy(kv.second);
+    c->graphs.clear();
+    for (cudaEvent_t ev : c->prof_ev) cudaEventDestroy(ev);
+    c->prof_ev.clear();
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    if (c->ev0) cudaEventDestroy(c->ev0);
+    if (c->ev1) cudaEventDestroy(c->ev1);
+    void *ptrs[] = {c->d_row_ptr, c->d_col_idx, c->d_val, c->d_rt, c->d_ct, c->d_vt, c->d_desc,
+                    c->d_st, c->d_part_row, c->d_part_col, c->d_part_upd, c->d_part_res, c->d_active,
+                    c->d_b, c->d_x, c->d_w, c->d_r, c->d_p, c->d_u, c->d_hist, c->d_vin, c->d_vout};
+    for (void *p : ptrs) dfree(p);
+    if (!c->symmetric) {
+        dfree(c->d_col_ptr);
+        dfree(c->d_row_idx);
+        dfree(c->d_cval);
+    }
+    if (c->h_st) cudaFreeHost(c->h_st);
+    if (c->h_active) cudaFreeHost(c->h_active);
+    free_extra(c);
+    delete c;
+}
+
+static plss_status ctx_build(const plss_csr *As, int32_t nsys, const plss_opts *o, plss_ctx **out) {
+    *out = nullptr;
+    if (nsys <= 0) return fail(PLSS_ERR_INVALID, "nsys must be positive");
+    if (!As) return fail(PLSS_ERR_INVALID, "A is NULL");
+    plss_opts od;
+    plss_opts_default(&od);
+    if (!o) o = &od;
+    if (o->precision != PLSS_FP64 && o->precision != PLSS_FP32)
+        return fail(PLSS_ERR_INVALID, "unknown precision %d", o->precision);
+
+    std::vector<HostCsr> hs(static_cast<size_t>(nsys));
+    int64_t M = 0, N = 0, NNZ = 0;
+    for (int32_t s = 0; s < nsys; ++s) {
+        plss_status st = fetch_csr(&As[s], hs[size_t(s)]);
+        if (st != PLSS_OK) {
+            if (nsys > 1) return fail(st, "system %d: %s", s, last_error());
+            return st;
+        }
+        M += hs[size_t(s)].m;
+        N += hs[size_t(s)].n;
+        NNZ += hs[size_t(s)].nnz;
+    }
+    if (M >= INT32_MAX || N >= INT32_MAX || NNZ >= INT32_MAX)
+        return fail(PLSS_ERR_INVALID, "packed sizes above 2^31-1 are not supported");
+    const bool sym = o->symmetric != 0;
+    if (sym) {
+        for (int32_t s = 0; s < nsys; ++s)
+            if (hs[size_t(s)].m != hs[size_t(s)].n)
+                return fail(PLSS_ERR_INVALID, "symmetric requires square systems");
+    }
+
+    plss_ctx *c = new plss_ctx();
+    c->nsys = nsys;
+    c->m = M;
+    c->n = N;
+    c->nnz = NNZ;
+    c->f32 = o->precision == PLSS_FP32;
+    c->symmetric = sym;
+    if (cudaGetDevice(&c->device) != cudaSuccess) {
+        delete c;
+        return fail(PLSS_ERR_CUDA, "no CUDA device");
+    }
+    cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, c->device);
+    if (c->nsm <= 0) c->nsm = 1;
+
+    // pack (block diagonal, global column indices)
+    std::vector<int32_t> rp(static_cast<size_t>(M + 1));
+    std::vector<int32_t> ci(static_cast<size_t>(NNZ));
+    std::vector<double> v64;
+    std::vector<float> v32;
+    if (c->f32) v32.resize(size_t(NNZ)); else v64.resize(size_t(NNZ));
+    c->h_desc.resize(size_t(nsys));
+    int64_t ro = 0, co = 0, zo = 0;
+    rp[0] = 0;
+    for (int32_t s = 0; s < nsys; ++s) {
+        const HostCsr &h = hs[size_t(s)];
+        SysDesc &d = c->h_desc[size_t(s)];
+        d.row_off = ro;
+        d.col_off = co;
+        d.m = int32_t(h.m);
+        d.n = int32_t(h.n);
+        for (int64_t i = 0; i < h.m; ++i) rp[size_t(ro + i + 1)] = int32_t(zo + h.row_ptr[size_t(i + 1)]);
+        for (int64_t k = 0; k < h.nnz; ++k) {
+            ci[size_t(zo + k)] = int32_t(co + h.col_idx[size_t(k)]);
+            if (c->f32) v32[size_t(zo + k)] = float(h.val[size_t(k)]);
+            else v64[size_t(zo + k)] = h.val[size_t(k)];
+        }
+        ro += h.m;
+        co += h.n;
+        zo += h.nnz;
+    }
+    hs.clear();
+
+    // transpose (stable counting sort: rows ascending inside each column)
+    std::vector<int32_t> cp, ri;
+    std::vector<double> cv64;
+    std::vector<float> cv32;
+    if (!sym) {
+        cp.assign(size_t(N + 1), 0);
+        ri.resize(size_t(NNZ));
+        if (c->f32) cv32.resize(size_t(NNZ)); else cv64.resize(size_t(NNZ));
+        for (int64_t k = 0; k < NNZ; ++k) cp[size_t(ci[size_t(k)] + 1)] += 1;
+        for (int64_t j = 0; j < N; ++j) cp[size_t(j + 1)] += cp[size_t(j)];
+        std::vector<int32_t> next(cp.begin(), cp.end() - 1);
+        for (int64_t i = 0; i < M; ++i)
+            for (int32_t k = rp[size_t(i)]; k < rp[size_t(i + 1)]; ++k) {
+                const int32_t dst = next[size_t(ci[size_t(k)])]++;
+                ri[size_t(dst)] = int32_t(i);
+                if (c->f32) cv32[size_t(dst)] = v32[size_t(k)]; else cv64[size_t(dst)] = v64[size_t(k)];
+            }
+    }
+    const int32_t *colp = sym ? rp.data() : cp.data();
+
+    // tile schedules
+    for (int32_t s = 0; s < nsys; ++s) {
+        SysDesc &d = c->h_desc[size_t(s)];
+        d.rt_begin = int32_t(c->h_rt.size());
+        build_tiles(rp.data(), d.row_off, d.row_off + d.m, s, kTileNnz, kTileMaxSegs, c->h_rt);
+        d.rt_count = int32_t(c->h_rt.size()) - d.rt_begin;
+        d.ct_begin = int32_t(c->h_ct.size());
+        build_tiles(colp, d.col_off, d.col_off + d.n, s, kTileNnz, kTileMaxSegs, c->h_ct);
+        d.ct_count = int32_t(c->h_ct.size()) - d.ct_begin;
+        d.vt_begin = int32_t(c->h_vt.size());
+        build_vec_tiles(d.col_off, d.col_off + d.n, s, kVecTile, c->h_vt);
+        d.vt_count = int32_t(c->h_vt.size()) - d.vt_begin;
+    }
+
+    plss_status st = PLSS_OK;
+#define TRY_ST(x)                  \
+    do {                           \
+        st = (x);                  \
+        if (st != PLSS_OK) {       \
+            ctx_free(c);           \
+            return st;             \
+        }                          \
+    } while (0)
+    TRY_ST(upload(&c->d_row_ptr, rp, "row_ptr"));
+    TRY_ST(upload(&c->d_col_idx, ci, "col_idx"));
+    if (c->f32) TRY_ST(upload(reinterpret_cast<float **>(&c->d_val), v32, "val"));
+    else TRY_ST(upload(reinterpret_cast<double **>(&c->d_val), v64, "val"));
+    if (sym) {
+        c->d_col_ptr = c->d_row_ptr;
+        c->d_row_idx = c->d_col_idx;
+        c->d_cval = c->d_val;
+    } else {
+        TRY_ST(upload(&c->d_col_ptr, cp, "col_ptr"));
+        TRY_ST(upload(&c->d_row_idx, ri, "row_idx"));
+        if (c->f32) TRY_ST(upload(reinterpret_cast<float **>(&c->d_cval), cv32, "cval"));
+        else TRY_ST(upload(reinterpret_cast<double **>(&c->d_cval), cv64, "cval"));
+    }
+    TRY_ST(upload(&c->d_rt, c->h_rt, "row tiles"));
+    TRY_ST(upload(&c->d_ct, c->h_ct, "col tiles"));
+    TRY_ST(upload(&c->d_vt, c->h_vt, "vec tiles"));
+    TRY_ST(upload(&c->d_desc, c->h_desc, "desc"));
+    const size_t sb = c->f32 ? 4 : 8;
+    TRY_ST(dalloc(reinterpret_cast<void **>(&c->d_st), sizeof(SysState) * size_t(nsys), "state"));
+    TRY_ST(dalloc(reinterpret_cast<void **>(&c->d_part_row), 16 * c->h_rt.size(), "partials"));
+    TRY_ST(dalloc(reinterpret_cast<void **>(&c->d_part_col), 8 * c->h_ct.size(), "partials"));
+    TRY_ST(dalloc(reinterpret_cast<void **>(&c->d_part_upd), 8 * c->h_vt.size(), "partials"));
+    TRY_ST(dalloc(reinterpret_cast<void **>(&c->d_part_res), 8 * c->h_rt.size(), "partials"));
+    TRY_ST(dalloc(reinterpret_cast<void **>(&c->d_active), 16, "counter"));
+    TRY_ST(dalloc(reinterpret_cast<void **>(&c->d_b), 8 * size_t(M), "b"));
+    TRY_ST(dalloc(reinterpret_cast<void **>(&c->d_x), 8 * size_t(N), "x"));
+    TRY_ST(dalloc(reinterpret_cast<void **>(&c->d_w), 8 * size_t(N), "w"));
+    TRY_ST(dalloc(&c->d_r, sb * size_t(M), "r"));
+    TRY_ST(dalloc(&c->d_p, sb * size_t(N), "p"));
+    TRY_ST(dalloc(&c->d_u, sb * size_t(N), "u"));
+    TRY_ST(dalloc(reinterpret_cast<void **>(&c->d_vin), 8 * size_t(std::max(M, N)), "tmp"));
+    TRY_ST(dalloc(reinterpret_cast<void **>(&c->d_vout), 8 * size_t(std::max(M, N)), "tmp"));
+    if (cudaMemset(c->d_st, 0, sizeof(SysState) * size_t(nsys)) != cudaSuccess ||
+        cudaMemset(c->d_p, 0, sb * size_t(N)) != cudaSuccess) {
+        ctx_free(c);
+        return fail(PLSS_ERR_CUDA, "cudaMemset failed");
+    }
+    if (cudaMallocHost(reinterpret_cast<void **>(&c->h_st), sizeof(SysState) * size_t(nsys)) != cudaSuccess ||
+        cudaMallocHost(reinterpret_cast<void **>(&c->h_active), 16) != cudaSuccess) {
+        ctx_free(c);
+        return fail(PLSS_ERR_NOMEM, "pinned host allocation failed");
+    }
+    if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess) {
+        ctx_free(c);
+        return fail(PLSS_ERR_CUDA, "stream/event creation failed");
+    }
+#undef TRY_ST
+    c->grid_r = std::max(1, std::min(int(c->h_rt.size()), c->nsm * kCtasPerSm));
+    c->grid_c = std::max(1, std::min(int(c->h_ct.size()), c->nsm * kCtasPerSm));
+    c->grid_v = std::max(1, std::min(int(c->h_vt.size()), c->nsm * kCtasPerSm));
+
+    SweepArgs &a = c->args;
+    a.row_ptr = c->d_row_ptr;
+    a.col_idx = c->d_col_idx;
+    a.val = c->d_val;
+    a.col_ptr = c->d_col_ptr;
+    a.row_idx = c->d_row_idx;
+    a.cval = c->d_cval;
+    a.rtiles = c->d_rt;
+    a.ctiles = c->d_ct;
+    a.vtiles = c->d_vt;
+    a.n_rtiles = int32_t(c->h_rt.size());
+    a.n_ctiles = int32_t(c->h_ct.size());
+    a.n_vtiles = int32_t(c->h_vt.size());
+    a.desc = c->d_desc;
+    a.st = c->d_st;
+    a.part_row = c->d_part_row;
+    a.part_col = c->d_part_col;
+    a.part_upd = c->d_part_upd;
+    a.n_active = c->d_active;
+    a.b = c->d_b;
+    a.x = c->d_x;
+    a.r = c->d_r;
+    a.p = c->d_p;
+    a.u = c->d_u;
+    a.w = nullptr;
+    *out = c;
+    return PLSS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// The iteration driver: chunks of bodies captured once as CUDA graphs
+// ---------------------------------------------------------------------------
+
+static plss_status get_graph(plss_ctx *c, int chunk, bool w_on, bool prof, cudaGraphExec_t *out) {
+    const int key = chunk * 4 + (w_on ? 1 : 0) + (prof ? 2 : 0);
+    auto it = c->graphs.find(key);
+    if (it != c->graphs.end()) {
+        *out = it->second;
+        return PLSS_OK;
+    }
+    SweepArgs a = c->args;
+    a.w = w_on ? c->d_w : nullptr;
+    cudaGraph_t g = nullptr;
+    CUDA_TRY(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    while (prof && c->prof_ev.size() < size_t(4 * chunk)) {
+        cudaEvent_t ev;
+        if (cudaEventCreate(&ev) != cudaSuccess) {
+            e = cudaErrorMemoryAllocation;
+            break;
+        }
+        c->prof_ev.push_back(ev);
+    }
+    for (int i = 0; i < chunk && e == cudaSuccess; ++i) {
+        cudaEvent_t *ev = prof ? &c->prof_ev[size_t(4 * i)] : nullptr;
+        if (prof) e = cudaEventRecord(ev[0], c->cap_stream);
+        if (e == cudaSuccess) e = launch_col_sweep(a, c->f32, c->grid_c, c->cap_stream);
+        if (prof && e == cudaSuccess) e = cudaEventRecord(ev[1], c->cap_stream);
+        if (e == cudaSuccess) e = launch_update(a, c->f32, c->grid_v, c->cap_stream);
+        if (prof && e == cudaSuccess) e = cudaEventRecord(ev[2], c->cap_stream);
+        if (e == cudaSuccess) e = launch_row_sweep(a, c->f32, c->grid_r, c->cap_stream);
+        if (prof && e == cudaSuccess) e = cudaEventRecord(ev[3], c->cap_stream);
+    }
+    const cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return fail(PLSS_ERR_CUDA, "graph capture failed: %s",
+                    cudaGetErrorString(e != cudaSuccess ? e : e2));
+    }
+    cudaGraphExec_t ge = nullptr;
+    const cudaError_t e3 = cudaGraphInstantiate(&ge, g, 0);
+    cudaGraphDestroy(g);
+    if (e3 != cudaSuccess) {
+        cudaGetLastError();
+        return fail(PLSS_ERR_CUDA, "graph instantiate failed: %s", cudaGetErrorString(e3));
+    }
+    c->graphs[key] = ge;
+    *out = ge;
+    return PLSS_OK;
+}
+
+plss_status ensure_weights(plss_ctx *c, int32_t w_mode, cudaStream_t s) {
+    if (w_mode == PLSS_W_IDENTITY) return PLSS_OK;
+    if (w_mode != PLSS_W_COLNORM && w_mode != PLSS_W_COLNORM2)
+        return fail(PLSS_ERR_INVALID, "unknown w_mode %d", w_mode);
+    if (c->w_mode_cur == w_mode) return PLSS_OK;
+    CUDA_TRY(launch_colweights(c->d_col_ptr, c->d_cval, c->f32, c->n, w_mode, c->d_w, s));
+    c->w_mode_cur = w_mode;
+    return PLSS_OK;
+}
+
+plss_status check_opts(const plss_opts *o) {
+    if (!o) return fail(PLSS_ERR_INVALID, "opts is NULL");
+    if (!(o->tol >= 0.0) || !std::isfinite(o->tol)) return fail(PLSS_ERR_INVALID, "tol must be finite and >= 0");
+    if (o->hist_cap < 0) return fail(PLSS_ERR_INVALID, "hist_cap < 0");
+    if (o->hist_cap > 0 && !o->hist) return fail(PLSS_ERR_INVALID, "hist_cap > 0 with hist NULL");
+    return PLSS_OK;
+}
+
+// Copies one input vector into the context's device buffer.
+plss_status put_vec(double *dst, const double *src, int64_t len, bool dev, cudaStream_t s) {
+    if (len == 0) return PLSS_OK;
+    if (!src) {
+        CUDA_TRY(cudaMemsetAsync(dst, 0, size_t(len) * 8, s));
+        return PLSS_OK;
+    }
+    CUDA_TRY(cudaMemcpyAsync(dst, src, size_t(len) * 8, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    return PLSS_OK;
+}
+
+plss_status get_vec(double *dst, const double *src, int64_t len, bool dev, cudaStream_t s) {
+    if (len == 0 || !dst) return PLSS_OK;
+    CUDA_TRY(cudaMemcpyAsync(dst, src, size_t(len) * 8, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    return PLSS_OK;
+}
+
+// ||b - A x||/||b|| per system, from the context's b and x buffers.
+plss_status true_relres(plss_ctx *c, cudaStream_t s, std::vector<double> &rel) {
+    CUDA_TRY(launch_spmv(c->d_row_ptr, c->d_col_idx, c->d_val, c->f32, c->d_rt, int32_t(c->h_rt.size()),
+                         c->d_x, c->d_vout, c->d_b, c->d_part_res, c->grid_r, s));
+    std::vector<double> part(c->h_rt.size());
+    CUDA_TRY(cudaMemcpyAsync(part.data(), c->d_part_res, 8 * part.size(), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    rel.assign(size_t(c->nsys), 0.0);
+    for (int32_t sy = 0; sy < c->nsys; ++sy) {
+        const SysDesc &d = c->h_desc[size_t(sy)];
+        double ss = 0.0;
+        for (int32_t t = 0; t < d.rt_count; ++t) ss += part[size_t(d.rt_begin + t)];
+        const double nb = c->h_st[sy].nb;
+        rel[size_t(sy)] = nb > 0.0 ? std::sqrt(ss) / nb : 0.0;
+    }
+    return PLSS_OK;
+}
+
+plss_status run_residual(plss_ctx *c, const double *const *b, const double *const *x0,
+                         double *const *xo, const plss_opts *o, plss_result *res) {
+    plss_status st = check_opts(o);
+    if (st != PLSS_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(o->stream);
+    const bool dev = o->io_device != 0;
+    for (int32_t sy = 0; sy < c->nsys; ++sy) {
+        const SysDesc &d = c->h_desc[size_t(sy)];
+        if (d.m > 0 && !b[sy]) return fail(PLSS_ERR_INVALID, "b is NULL (system %d)", sy);
+        st = put_vec(c->d_b + d.row_off, b[sy], d.m, dev, s);
+        if (st != PLSS_OK) return st;
+        st = put_vec(c->d_x + d.col_off, x0 ? x0[sy] : nullptr, d.n, dev, s);
+        if (st != PLSS_OK) return st;
+    }
+    st = ensure_weights(c, o->w_mode, s);
+    if (st != PLSS_OK) return st;
+    const bool w_on = o->w_mode != PLSS_W_IDENTITY;
+    if (o->hist_cap > 0 && o->hist_cap > c->hist_cap_alloc) {
+        dfree(c->d_hist);
+        c->d_hist = nullptr;
+        c->hist_cap_alloc = 0;
+        st = dalloc(reinterpret_cast<void **>(&c->d_hist), size_t(o->hist_cap) * 5 * 8, "hist");
+        if (st != PLSS_OK) return st;
+        c->hist_cap_alloc = o->hist_cap;
+    }
+    int64_t maxit_all = 0;
+    CUDA_TRY(cudaStreamSynchronize(s));   // h_st may still be read by an earlier copy
+    for (int32_t sy = 0; sy < c->nsys; ++sy) {
+        const SysDesc &d = c->h_desc[size_t(sy)];
+        SysState z;
+        std::memset(&z, 0, sizeof z);
+        z.tol = o->tol;
+        z.maxit = o->maxit < 0 ? int64_t(d.n) : o->maxit;
+        z.refine = c->f32 ? std::max<int64_t>(0, o->refine_period) : 0;
+        z.stop_on_true = (c->f32 || o->stop_on_true) ? 1 : 0;
+        z.phase = PH_SETUP;
+        z.nb = 0.0;
+        if (sy == 0 && o->hist_cap > 0) {
+            z.hist = c->d_hist;
+            z.hist_cap = o->hist_cap;
+        }
+        c->h_st[sy] = z;
+        maxit_all = std::max(maxit_all, z.maxit);
+    }
+    *c->h_active = c->nsys;
+    CUDA_TRY(cudaMemcpyAsync(c->d_st, c->h_st, sizeof(SysState) * size_t(c->nsys), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(c->d_active, c->h_active, 4, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaEventRecord(c->ev0, s));
+    // Every body either applies an update or finishes a system, except
+    // restarts (at most one per update), so 2 (maxit + 2) bodies suffice.
+    const int64_t body_cap = 2 * (maxit_all + 2) + 8;
+    const bool prof = o->profile != 0;
+    int64_t bodies = 0;
+    int chunk = 1;
+    for (;;) {
+        cudaGraphExec_t g;
+        st = get_graph(c, chunk, w_on, prof, &g);
+        if (st != PLSS_OK) return st;
+        CUDA_TRY(cudaGraphLaunch(g, s));
+        bodies += chunk;
+        CUDA_TRY(cudaMemcpyAsync(c->h_active, c->d_active, 4, cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(cudaStreamSynchronize(s));
+        if (prof) c->prof_all += 3 * int64_t(chunk);
+        // time only chunks in which some system stayed active throughout
+        // (after the set-up body), so that launches returning at once after
+        // convergence do not enter the per-launch averages
+        if (prof && *c->h_active > 0 && bodies > 1) {
+            for (int i = 0; i < chunk; ++i) {
+                const cudaEvent_t *ev = &c->prof_ev[size_t(4 * i)];
+                float t[3] = {0.0f, 0.0f, 0.0f};
+                CUDA_TRY(cudaEventElapsedTime(&t[1], ev[0], ev[1]));
+                CUDA_TRY(cudaEventElapsedTime(&t[2], ev[1], ev[2]));
+                CUDA_TRY(cudaEventElapsedTime(&t[0], ev[2], ev[3]));
+                for (int q = 0; q < 3; ++q) {
+                    c->prof_ms[q] += double(t[q]);
+                    c->prof_n[q] += 1;
+                }
+            }
+        }
+        if (*c->h_active <= 0) break;
+        if (bodies > body_cap) return fail(PLSS_ERR_TIMEOUT, "iteration driver exceeded %lld bodies", (long long)body_cap);
+        chunk = std::min(chunk * 4, kMaxChunk);
+    }
+    CUDA_TRY(cudaEventRecord(c->ev1, s));
+    CUDA_TRY(cudaMemcpyAsync(c->h_st, c->d_st, sizeof(SysState) * size_t(c->nsys), cudaMemcpyDeviceToHost, s));
+    for (int32_t sy = 0; sy < c->nsys; ++sy) {
+        const SysDesc &d = c->h_desc[size_t(sy)];
+        st = get_vec(xo ? xo[sy] : nullptr, c->d_x + d.col_off, d.n, dev, s);
+        if (st != PLSS_OK) return st;
+    }
+    CUDA_TRY(cudaStreamSynchronize(s));
+    if (o->hist_cap > 0) {
+        const int64_t k = std::min<int64_t>(o->hist_cap, c->h_st[0].iters);
+        if (k > 0) CUDA_TRY(cudaMemcpy(o->hist, c->d_hist, size_t(k) * 5 * 8, cudaMemcpyDeviceToHost));
+    }
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+    std::vector<double> rel;
+    if (prof) c->prof_all += 1;
+    st = true_relres(c, s, rel);
+    if (st != PLSS_OK) return st;
+    plss_status overall = PLSS_OK;
+    for (int32_t sy = 0; sy < c->nsys; ++sy) {
+        const SysState &z = c->h_st[sy];
+        if (res) {
+            res[sy].status = z.status;
+            res[sy].reserved = 0;
+            res[sy].iters = z.iters;
+            res[sy].relres_rec = z.relres_rec;
+            res[sy].relres_true = rel[size_t(sy)];
+            res[sy].seconds = double(ms) * 1e-3;
+        }
+        if (overall == PLSS_OK && z.status != PLSS_OK) overall = plss_status(z.status);
+    }
+    return overall;
+}
+
+}  // namespace plss
+
+using namespace plss;
+
+// ---------------------------------------------------------------------------
+// Exported C ABI
+// ---------------------------------------------------------------------------
+
+extern "C" {
+
+void plss_opts_default(plss_opts *o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof *o);
+    o->sketch = PLSS_SKETCH_RESIDUAL;
+    o->precision = PLSS_FP64;
+    o->w_mode = PLSS_W_IDENTITY;
+    o->stop_on_true = 0;
+    o->tol = 1e-8;
+    o->maxit = -1;
+    o->refine_period = 0;
+    o->kacz_hist = 0;
+    o->seed = 0;
+    o->io_device = 0;
+    o->symmetric = 0;
+    o->stream = nullptr;
+    o->hist = nullptr;
+    o->hist_cap = 0;
+    o->profile = 0;
+    o->reserved = 0;
+}
+
+plss_status plss_create(const plss_csr *A, const plss_opts *o, plss_ctx **out) {
+    clear_error();
+    if (!out) return fail(PLSS_ERR_INVALID, "out is NULL");
+    return ctx_build(A, 1, o, out);
+}
+
+plss_status plss_create_batched(const plss_csr *As, int32_t nsys, const plss_opts *o, plss_ctx **out) {
+    clear_error();
+    if (!out) return fail(PLSS_ERR_INVALID, "out is NULL");
+    return ctx_build(As, nsys, o, out);
+}
+
+void plss_destroy(plss_ctx *ctx) { ctx_free(ctx); }
+
+plss_status plss_ctx_info(const plss_ctx *ctx, int32_t *nsys, int64_t *m, int64_t *n, int64_t *nnz) {
+    clear_error();
+    if (!ctx) return fail(PLSS_ERR_INVALID, "ctx is NULL");
+    if (nsys) *nsys = ctx->nsys;
+    if (m) *m = ctx->m;
+    if (n) *n = ctx->n;
+    if (nnz) *nnz = ctx->nnz;
+    return PLSS_OK;
+}
+
+plss_status plss_solve(plss_ctx *ctx, const double *b, const double *x0, double *x_out,
+                       const plss_opts *o, plss_result *res) {
+    clear_error();
+    if (!ctx) return fail(PLSS_ERR_INVALID, "ctx is NULL");
+    if (ctx->nsys != 1) return fail(PLSS_ERR_INVALID, "plss_solve needs a single-system context");
+    plss_opts od;
+    plss_opts_default(&od);
+    if (!o) o = &od;
+    if (o->sketch == PLSS_SKETCH_IDENTITY) return run_identity(ctx, b, x0, x_out, o, res);
+    if (o->sketch != PLSS_SKETCH_RESIDUAL) return fail(PLSS_ERR_INVALID, "unknown sketch %d", o->sketch);
+    const double *bb[1] = {b};
+    const double *xx[1] = {x0};
+    double *oo[1] = {x_out};
+    return run_residual(ctx, bb, xx, oo, o, res);
+}
+
+plss_status plss_solve_batched(plss_ctx *ctx, const double *const *b, const double *const *x0,
+                               double *const *x_out, const plss_opts *o, plss_result *res) {
+    clear_error();
+    if (!ctx) return fail(PLSS_ERR_INVALID, "ctx is NULL");
+    if (!b) return fail(PLSS_ERR_INVALID, "b is NULL");
+    plss_opts od;
+    plss_opts_default(&od);
+    if (!o) o = &od;
+    if (o->sketch != PLSS_SKETCH_RESIDUAL)
+        return fail(PLSS_ERR_INVALID, "plss_solve_batched supports the residual sketch only");
+    return run_residual(ctx, b, x0, x_out, o, res);
+}
+
+plss_status plss_spmv(plss_ctx *ctx, int32_t transpose, const double *v, double *out, const plss_opts *o) {
+    clear_error();
+    if (!ctx) return fail(PLSS_ERR_INVALID, "ctx is NULL");
+    if (ctx->nsys != 1) return fail(PLSS_ERR_INVALID, "plss_spmv needs a single-system context");
+    plss_opts od;
+    plss_opts_default(&od);
+    if (!o) o = &od;
+    cudaStream_t s = static_cast<cudaStream_t>(o->stream);
+    const bool dev = o->io_device != 0;
+    const int64_t lin = transpose ? ctx->m : ctx->n;
+    const int64_t lout = transpose ? ctx->n : ctx->m;
+    if ((lin > 0 && !v) || (lout > 0 && !out)) return fail(PLSS_ERR_INVALID, "NULL vector");
+    plss_status st = put_vec(ctx->d_vin, v, lin, dev, s);
+    if (st != PLSS_OK) return st;
+    if (transpose) {
+        CUDA_TRY(launch_spmv(ctx->d_col_ptr, ctx->d_row_idx, ctx->d_cval, ctx->f32, ctx->d_ct,
+                             int32_t(ctx->h_ct.size()), ctx->d_vin, ctx->d_vout, nullptr, nullptr, ctx->grid_c, s));
+    } else {
+        CUDA_TRY(launch_spmv(ctx->d_row_ptr, ctx->d_col_idx, ctx->d_val, ctx->f32, ctx->d_rt,
+                             int32_t(ctx->h_rt.size()), ctx->d_vin, ctx->d_vout, nullptr, nullptr, ctx->grid_r, s));
+    }
+    st = get_vec(out, ctx->d_vout, lout, dev, s);
+    if (st != PLSS_OK) return st;
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return PLSS_OK;
+}
+
+plss_status plss_kernel_times(plss_ctx *ctx, double *ms, int64_t *launches, int32_t reset) {
+    clear_error();
+    if (!ctx) return fail(PLSS_ERR_INVALID, "ctx is NULL");
+    for (int q = 0; q < 3; ++q) {
+        if (ms) ms[q] = ctx->prof_ms[q];
+        if (launches) launches[q] = ctx->prof_n[q];
+    }
+    if (launches) launches[3] = ctx->prof_all;
+    if (reset) {
+        for (int q = 0; q < 3; ++q) {
+            ctx->prof_ms[q] = 0.0;
+            ctx->prof_n[q] = 0;
+        }
+        ctx->prof_all = 0;
+    }
+    return PLSS_OK;
+}
+
+const char *plss_last_error(void) { return last_error(); }
+
+}  // extern "C"

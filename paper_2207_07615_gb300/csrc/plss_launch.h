@@ -1,0 +1,28 @@
+// plss_launch.h -- host-side launchers of the device kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "plss_dev.cuh"
+
+namespace plss {
+
+// Residual-sketch sweeps (plss_kernels.cu). f32 selects float storage of A
+// and of the vectors r, p, u.
+cudaError_t launch_row_sweep(const SweepArgs &a, bool f32, int grid, cudaStream_t s);
+cudaError_t launch_col_sweep(const SweepArgs &a, bool f32, int grid, cudaStream_t s);
+cudaError_t launch_update(const SweepArgs &a, bool f32, int grid, cudaStream_t s);
+
+// out[seg] = (A v)[seg] over the segments of `tiles` in double; with b,
+// part[tile] = sum over the tile of (b - out)^2.
+cudaError_t launch_spmv(const int32_t *ptr, const int32_t *idx, const void *val, bool f32,
+                        const Tile *tiles, int32_t ntiles, const double *v, double *out,
+                        const double *b, double *part, int grid, cudaStream_t s);
+
+// Diagonal weights of Sec. 4.1 from column segments (ptr over n columns).
+cudaError_t launch_colweights(const int32_t *ptr, const void *val, bool f32, int64_t n,
+                              int32_t mode, double *w, cudaStream_t s);
+
+}  // namespace plss

@@ -1,0 +1,112 @@
+"""C ABI checks that need no GPU: the library builds, loads, exports every
+symbol include/plss.h declares, and rejects malformed input on the host."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2207_07615_gb300 import build as pbuild
+from paper_2207_07615_gb300 import plss, synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    pbuild.build()
+    return plss.lib()
+
+
+def header_functions():
+    src = open(os.path.join(ROOT, "include", "plss.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(plss_[a-z_]+)\s*\(", src)))
+
+
+def test_exports_match_header(L):
+    names = header_functions()
+    assert set(names) == set(plss.EXPORTS), (names, plss.EXPORTS)
+    for name in names:
+        assert hasattr(L, name), name
+
+
+def test_struct_layouts(L):
+    assert C.sizeof(plss.Opts) == 96
+    assert C.sizeof(plss.Csr) == 56
+    assert C.sizeof(plss.Result) == 40
+    o = plss.Opts()
+    L.plss_opts_default(C.byref(o))
+    assert o.tol == 1e-8 and o.maxit == -1 and o.sketch == 0 and o.precision == 0
+
+
+def _create(L, csr):
+    h = C.c_void_p()
+    o = plss.Opts()
+    L.plss_opts_default(C.byref(o))
+    code = L.plss_create(C.byref(csr), C.byref(o), C.byref(h))
+    return code, L.plss_last_error().decode(), h
+
+
+def _csr(rp, ci, val, m, n):
+    rp = np.asarray(rp, dtype=np.int64)
+    ci = np.asarray(ci, dtype=np.int32)
+    val = np.asarray(val, dtype=np.float64)
+    keep = (rp, ci, val)
+    c = plss.Csr(m, n, int(rp[-1]), rp.ctypes.data, ci.ctypes.data, val.ctypes.data, 0, 0)
+    return c, keep
+
+
+@pytest.mark.parametrize("case,msg", [
+    (([1, 2], [0, 1], [1.0, 1.0], 1, 2), "row_ptr[0]"),
+    (([0, 2, 1], [0], [1.0], 2, 2), "decreases"),
+    (([0, 2], [1, 0], [1.0, 1.0], 1, 2), "strictly increasing"),
+    (([0, 2], [0, 0], [1.0, 1.0], 1, 2), "strictly increasing"),
+    (([0, 1], [5], [1.0], 1, 2), "outside"),
+    (([0, 1], [-1], [1.0], 1, 2), "outside"),
+    (([0, 1], [0], [np.nan], 1, 2), "non-finite"),
+])
+def test_malformed_csr_rejected(L, case, msg):
+    rp, ci, val, m, n = case
+    if rp[-1] != len(ci):
+        pytest.skip("inconsistent fixture")
+    c, keep = _csr(rp, ci, val, m, n)
+    code, err, h = _create(L, c)
+    assert code == plss.ERR_INVALID
+    assert msg in err
+    assert not h.value
+
+
+def test_rowptr_end_mismatch(L):
+    rp = np.array([0, 1], dtype=np.int64)
+    ci = np.array([0], dtype=np.int32)
+    val = np.array([1.0])
+    c = plss.Csr(1, 2, 2, rp.ctypes.data, ci.ctypes.data, val.ctypes.data, 0, 0)
+    code, err, h = _create(L, c)
+    assert code == plss.ERR_INVALID and "row_ptr[m]" in err
+
+
+def test_null_and_negative(L):
+    h = C.c_void_p()
+    assert L.plss_create(None, None, C.byref(h)) == plss.ERR_INVALID
+    c = plss.Csr(-1, 2, 0, None, None, None, 0, 0)
+    code, err, _ = _create(L, c)
+    assert code == plss.ERR_INVALID and "negative" in err
+    assert L.plss_solve(None, None, None, None, None, None) == plss.ERR_INVALID
+    assert L.plss_create_batched(None, 0, None, C.byref(h)) == plss.ERR_INVALID
+
+
+def test_last_error_is_per_thread(L):
+    import threading
+    c = plss.Csr(-1, 2, 0, None, None, None, 0, 0)
+    _create(L, c)
+    seen = {}
+
+    def other():
+        seen["err"] = L.plss_last_error().decode()
+    t = threading.Thread(target=other)
+    t.start()
+    t.join()
+    assert seen["err"] == ""
+    assert "negative" in L.plss_last_error().decode()

@@ -1,0 +1,222 @@
+"""GPU parity of the residual-sketch path (Algorithm 1) against the CPU oracle.
+
+All solves go through the C ABI (libplss.so) via the thin Python binding.
+Tolerance: FP64 mode, the per-update scalars (rho, phi, beta, gamma, theta)
+and the iterates x_k agree with the oracle to 1e-10 relative (the parity bar
+for double precision; the two sides differ only in summation order).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2207_07615_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def plss():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+    from paper_2207_07615_gb300 import plss as P
+    return P
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def scal_rel(h_gpu, h_ref):
+    """Max relative difference of the per-update scalars, column by column."""
+    k = min(len(h_gpu), len(h_ref))
+    g, r = np.asarray(h_gpu[:k]), np.asarray(h_ref[:k])
+    d = np.abs(g - r) / np.maximum(np.abs(r), 1e-300)
+    d[:, 2][r[:, 2] == 0] = np.abs(g[:, 2])[r[:, 2] == 0]   # beta = 0 on the first update
+    return float(d.max()) if d.size else 0.0
+
+
+def test_smoke():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.smoke()
+
+
+def test_square_2000_every_iterate(plss):
+    """The 2,000 x 2,000 diagonally dominant system, tol 1e-10: same number
+    of updates, every update's scalars within 1e-10, same final x."""
+    A, b, xs = synth.square_diag_dominant()
+    ref = oracle.residual(A, b, tol=1e-10, maxit=2000, hist=2000)
+    with plss.Context(A) as ctx:
+        x, res, hist = ctx.solve(b, tol=1e-10, maxit=2000, hist=2000)
+        assert res["status"] == "converged"
+        assert res["iters"] == ref["iters"]
+        assert scal_rel(hist, ref["hist_s"]) < RTOL
+        assert rel(x, ref["x"]) < RTOL
+        assert res["relres_true"] <= 2e-10
+        np.testing.assert_allclose(res["relres_rec"], ref["relres_rec"], rtol=1e-6)
+        # iterates x_k at sampled k
+        for k in (1, 2, 3, 7, 15):
+            xk, rk = ctx.solve(b, tol=0.0, maxit=k)
+            assert rk["iters"] == k and rk["status"] == "not_converged"
+            assert rel(xk, ref["hist_x"][k - 1]) < RTOL, k
+
+
+def test_device_io_matches_host_io(plss):
+    import torch
+    A, b, xs = synth.square_diag_dominant(n=1500, per_row=8, seed=3)
+    x0 = synth.rng_for(4).standard_normal(A.n)
+    with plss.Context(A) as ctx:
+        xh, rh = ctx.solve(b, x0, tol=1e-9)
+        xd, rd = ctx.solve(torch.from_numpy(b).cuda(), torch.from_numpy(x0).cuda(), tol=1e-9)
+        torch.cuda.synchronize()
+    assert rh["iters"] == rd["iters"]
+    np.testing.assert_array_equal(xh, xd.cpu().numpy())   # same kernels, same order
+
+
+def test_determinism(plss):
+    A, b, xs = synth.overdetermined_scaled(m=20000, n=4000, per_row=8, seed=5, scale_decades=1.0)
+    with plss.Context(A.astype(np.float64)) as ctx:
+        x1, r1 = ctx.solve(b, tol=1e-9, maxit=500)
+        x2, r2 = ctx.solve(b, tol=1e-9, maxit=500)
+    assert r1["iters"] == r2["iters"]
+    np.testing.assert_array_equal(x1, x2)
+
+
+@pytest.mark.parametrize("shape", ["tall", "wide", "powerlaw"])
+def test_parity_shapes(plss, shape):
+    """Overdetermined with column scales, underdetermined, and power-law rows
+    (rows longer than a tile run one CTA per row): first 60 updates within
+    1e-10, final x against the oracle's x at the same iteration count."""
+    if shape == "tall":
+        A, b, xs = synth.overdetermined_scaled(m=30000, n=6000, per_row=8, seed=7, scale_decades=1.0)
+    elif shape == "wide":
+        A, b, xs = synth.overdetermined_scaled(m=3000, n=9000, per_row=12, seed=8, scale_decades=0.5)
+    else:
+        A, b, xs = synth.powerlaw_underdetermined(m=4000, n=40000, mean_len=20, max_len=5000, seed=9)
+    A = A.astype(np.float64)
+    K = 60
+    ref = oracle.residual(A, b, tol=0.0, maxit=K, hist=K)
+    with plss.Context(A) as ctx:
+        x, res, hist = ctx.solve(b, tol=0.0, maxit=K, hist=K)
+    assert res["iters"] == K
+    assert scal_rel(hist, ref["hist_s"]) < RTOL
+    assert rel(x, ref["x"]) < RTOL
+
+
+@pytest.mark.parametrize("w_mode", [1, 2])
+def test_weighted_parity(plss, w_mode):
+    """PLSS W (Sec. 4.1) with W = diag(1/||A_j||) or diag(1/||A_j||^2)."""
+    A, b, xs = synth.overdetermined_scaled(m=20000, n=3000, per_row=8, seed=11, scale_decades=1.5)
+    A = A.astype(np.float64)
+    w = oracle.colweights(A, w_mode)
+    K = 80
+    ref = oracle.residual(A, b, w=w, tol=0.0, maxit=K, hist=K)
+    with plss.Context(A) as ctx:
+        x, res, hist = ctx.solve(b, tol=0.0, maxit=K, hist=K, w_mode=w_mode)
+    assert scal_rel(hist, ref["hist_s"]) < RTOL
+    assert rel(x, ref["x"]) < RTOL
+
+
+def test_fp32_storage_parity_and_accuracy(plss):
+    """FP32 storage, FP64 scalars and refinement: early scalars follow the
+    oracle's FP32 emulation to float rounding; with W = diag(1/||A_j||^2) the
+    answer reaches the FP64 tolerance on b - A x and the FP64 oracle's x."""
+    A, b, xs = synth.overdetermined_scaled(m=40000, n=8000, per_row=8, seed=12, scale_decades=1.0)
+    emu = oracle.residual(A, b, tol=0.0, maxit=20, prec=1, stop_on_true=True, hist=20)
+    w = oracle.colweights(A, 2)
+    ref = oracle.residual(A, b, w=w, tol=1e-11, maxit=5000)
+    with plss.Context(A, precision="fp32") as ctx:
+        _, _, hist = ctx.solve(b, tol=0.0, maxit=20, hist=20)
+        assert scal_rel(hist[:10], emu["hist_s"][:10]) < 1e-4
+        x, res = ctx.solve(b, tol=1e-8, maxit=5000, w_mode=2)
+    assert res["status"] == "converged"
+    assert res["relres_true"] <= 1e-8
+    assert rel(x, ref["x"]) < 1e-6
+
+
+def test_spmv_primitives(plss):
+    A, b, xs = synth.powerlaw_underdetermined(m=3000, n=20000, mean_len=20, max_len=5000, seed=13)
+    A = A.astype(np.float64)
+    v = synth.rng_for(1).standard_normal(A.n)
+    r = synth.rng_for(2).standard_normal(A.m)
+    with plss.Context(A) as ctx:
+        np.testing.assert_allclose(ctx.spmv(v), oracle.spmv(A, v), rtol=1e-12, atol=1e-12)
+        np.testing.assert_allclose(ctx.spmv(r, transpose=True), oracle.spmvt(A, r), rtol=1e-12, atol=1e-12)
+
+
+def test_edge_cases(plss):
+    A, b, xs = synth.square_diag_dominant(n=300, per_row=4, seed=2)
+    x0 = np.linspace(-1, 1, 300)
+    with plss.Context(A) as ctx:
+        x, r = ctx.solve(np.zeros(300), x0, tol=1e-10)          # ||b|| = 0: x0 back at once
+        assert r["status"] == "converged" and r["iters"] == 0
+        np.testing.assert_array_equal(x, x0)
+        x, r = ctx.solve(b, xs, tol=1e-10)                       # exact start
+        assert r["iters"] == 0 and r["status"] == "converged"
+        x, r = ctx.solve(b, tol=1e-12, maxit=0)                  # no update allowed
+        assert r["iters"] == 0 and r["status"] == "not_converged"
+        np.testing.assert_array_equal(x, np.zeros(300))
+    # b outside range(A): A^T r0 = 0 gives phi_1 = 0 (breakdown)
+    D = synth.from_dense(np.array([[1.0, 0.0], [0.0, 0.0]]))
+    with plss.Context(D) as ctx:
+        x, r = ctx.solve(np.array([0.0, 1.0]), tol=1e-12)
+        assert r["status"] == "breakdown"
+    # a 1 x 1 system and an empty-row / empty-column system
+    with plss.Context(synth.from_dense(np.array([[4.0]]))) as ctx:
+        x, r = ctx.solve(np.array([2.0]), tol=1e-14)
+        assert r["status"] == "converged" and abs(x[0] - 0.5) < 1e-15
+    Dz = np.zeros((5, 6))
+    Dz[0, 1] = 2.0
+    Dz[3, 4] = -1.0
+    Dz[3, 1] = 0.5
+    bz = Dz @ np.arange(1.0, 7.0)
+    ref = oracle.residual(synth.from_dense(Dz), bz, tol=1e-13)
+    with plss.Context(synth.from_dense(Dz)) as ctx:
+        x, r = ctx.solve(bz, tol=1e-13)
+    assert r["status"] == "converged" and r["iters"] == ref["iters"]
+    assert rel(x, ref["x"]) < RTOL
+
+
+def test_ragged_tails(plss):
+    """Row counts just off the tile and group boundaries."""
+    for m in (1, 31, 33, 255, 257, 2049):
+        A, b, xs = synth.powerlaw_underdetermined(m=m, n=3 * m + 7, mean_len=6, max_len=50, seed=m)
+        A = A.astype(np.float64)
+        ref = oracle.residual(A, b, tol=0.0, maxit=12, hist=12)
+        with plss.Context(A) as ctx:
+            x, res, hist = ctx.solve(b, tol=0.0, maxit=12, hist=12)
+        k = min(res["iters"], ref["iters"])
+        assert res["iters"] == ref["iters"], m
+        assert scal_rel(hist[:k], ref["hist_s"][:k]) < RTOL, m
+        assert rel(x, ref["x"]) < RTOL, m
+
+
+def test_batched_matches_single(plss):
+    """Independent systems packed into one context: each result equals the
+    oracle's solve of that system alone (first 40 updates, then to tol)."""
+    systems = synth.batched_systems(nsys=6, m_lo=200, m_hi=4000, len_lo=5, len_hi=20, seed0=50)
+    As = [A.astype(np.float64) for A, _, _ in systems]
+    bs = [b for _, b, _ in systems]
+    with plss.Context(As) as ctx:
+        xs, rs = ctx.solve_batched(bs, tol=0.0, maxit=40)
+        for A, b, x, r in zip(As, bs, xs, rs):
+            ref = oracle.residual(A, b, tol=0.0, maxit=40)
+            assert r["iters"] == 40 and r["status"] == "not_converged"
+            assert rel(x, ref["x"]) < 1e-9
+        # different maxit per system is not exposed; a common tol stops each on its own
+        xs, rs = ctx.solve_batched(bs, tol=1e-6, maxit=5000)
+    for A, b, x, r in zip(As, bs, xs, rs):
+        if r["status"] == "converged":
+            assert r["relres_true"] <= 2e-6
+        ref = oracle.residual(A, b, tol=1e-6, maxit=5000)
+        assert r["status"] == ref["status"]
+        assert abs(r["iters"] - ref["iters"]) <= max(2, ref["iters"] // 50)
