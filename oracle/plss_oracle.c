@@ -28,15 +28,19 @@
  *   - breakdown: the initial phi must be > 0 and finite; later the factor
  *     (s/rho - 1)(s/rho + 1) must be > 0 and finite (it is <= 0 only when
  *     y is parallel to p); otherwise return the current x with status
- *     BREAKDOWN.
+ *     BREAKDOWN -- except when stopping on the true residual, where a
+ *     breakdown after the first update (rounding has destroyed the
+ *     orthogonality the recursion relies on) restarts from b - A x.
  *   - FP32 storage (prec = 1): A's values, r, p and W y are held as float,
  *     sums of products are accumulated in float, inner products and the
  *     scalar recursion in double, x in double; every `refine` updates the
  *     residual is recomputed as b - A x in double and the recursion restarts
  *     from it (this extension is not in the paper).
  *   - Kaczmarz order: rows are visited without replacement in a fresh
- *     permutation per pass (SplitMix64 stream + Fisher-Yates shuffle), the
- *     history is cleared when it holds K updates, a row whose projected
+ *     permutation per pass (SplitMix64 stream + Fisher-Yates shuffle); the
+ *     history holds at most K updates and, once full, is emptied before the
+ *     next row (which then takes a plain Kaczmarz step, so every stored
+ *     update lives on the union of the window's rows); a row whose projected
  *     norm delta is <= 1e-14 ||a_i||^2 is skipped, and an update with
  *     ||p|| = 0 (r_i = 0) is not stored in the history (its theta would
  *     divide by zero in the next projection).
@@ -262,7 +266,15 @@ int plss_oracle_residual(int64_t m, int64_t n, const int64_t *row_ptr, const int
             double s = sqrt(theta * phi);
             double q = s / rho;
             double d = (q - 1.0) * (q + 1.0);
-            if (!(d > 0.0) || !isfinite(d)) { status = ORC_BREAKDOWN; break; }
+            if (!(d > 0.0) || !isfinite(d)) {
+                if (!stop_on_true) { status = ORC_BREAKDOWN; break; }
+                /* verifying on b - A x: restart from it instead */
+                true_residual(m, row_ptr, col_idx, val, b, x, rt);
+                for (int64_t i = 0; i < m; ++i) r[i] = rf(rt[i], f32);
+                rho = dot(m, r, r);
+                restart = 1; since = 0;
+                continue;
+            }
             beta = 1.0 / d;
             if (gamma_form == 1)
                 gamma = theta / (theta * phi - rho * rho);   /* statement form */
@@ -387,6 +399,7 @@ int plss_oracle_kaczmarz(int64_t m, int64_t n, const int64_t *row_ptr, const int
         for (int64_t t = 0; t < m && k < maxit; ++t, ++k) {
             int64_t i = perm[t];
             int64_t s0 = row_ptr[i], s1 = row_ptr[i + 1];
+            if (K > 0 && nh == K) nh = 0;   /* window full: restart it empty */
             /* r_i = b_i - a_i^T x */
             double ax = 0.0, a2 = 0.0;
             for (int64_t q = s0; q < s1; ++q) ax += val[q] * x[col_idx[q]];
@@ -419,7 +432,6 @@ int plss_oracle_kaczmarz(int64_t m, int64_t n, const int64_t *row_ptr, const int
             }
             if (K > 0 && thn > 0.0) {
                 /* a zero update (r_i = 0: the row already holds) is not stored */
-                if (nh == K) nh = 0;   /* history full: restart the window */
                 memcpy(P + nh * n, p, (size_t)n * sizeof(double));
                 th[nh] = thn;
                 nh += 1;

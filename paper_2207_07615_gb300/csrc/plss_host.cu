@@ -450,13 +450,13 @@ static plss_status get_graph(plss_ctx *c, int chunk, bool w_on, bool prof, cudaG
     }
     for (int i = 0; i < chunk && e == cudaSuccess; ++i) {
         cudaEvent_t *ev = prof ? &c->prof_ev[size_t(4 * i)] : nullptr;
-        if (prof) e = cudaEventRecord(ev[0], c->cap_stream);
+        if (prof) e = cudaEventRecordWithFlags(ev[0], c->cap_stream, cudaEventRecordExternal);
         if (e == cudaSuccess) e = launch_col_sweep(a, c->f32, c->grid_c, c->cap_stream);
-        if (prof && e == cudaSuccess) e = cudaEventRecord(ev[1], c->cap_stream);
+        if (prof && e == cudaSuccess) e = cudaEventRecordWithFlags(ev[1], c->cap_stream, cudaEventRecordExternal);
         if (e == cudaSuccess) e = launch_update(a, c->f32, c->grid_v, c->cap_stream);
-        if (prof && e == cudaSuccess) e = cudaEventRecord(ev[2], c->cap_stream);
+        if (prof && e == cudaSuccess) e = cudaEventRecordWithFlags(ev[2], c->cap_stream, cudaEventRecordExternal);
         if (e == cudaSuccess) e = launch_row_sweep(a, c->f32, c->grid_r, c->cap_stream);
-        if (prof && e == cudaSuccess) e = cudaEventRecord(ev[3], c->cap_stream);
+        if (prof && e == cudaSuccess) e = cudaEventRecordWithFlags(ev[3], c->cap_stream, cudaEventRecordExternal);
     }
     const cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &g);
     if (e != cudaSuccess || e2 != cudaSuccess) {

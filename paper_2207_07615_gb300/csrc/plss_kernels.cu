@@ -303,7 +303,17 @@ __device__ void finish_col(const SweepArgs &a, int32_t sys) {
         const double s = __dsqrt_rn(__dmul_rn(theta, phi));
         const double q = __ddiv_rn(s, rho);
         const double dd = __dmul_rn(__dsub_rn(q, 1.0), __dadd_rn(q, 1.0));
-        if (!(dd > 0.0) || !isfinite(dd)) { finish_system(a, st, -4); return; }
+        if (!(dd > 0.0) || !isfinite(dd)) {
+            if (st->stop_on_true) {
+                // the recursion lost orthogonality to rounding: restart from
+                // b - A x (the next row sweep) instead of stopping
+                st->since = 0;
+                st->phase = PH_SETUP;
+            } else {
+                finish_system(a, st, -4);
+            }
+            return;
+        }
         const double beta = __ddiv_rn(1.0, dd);
         st->beta = beta;
         st->gamma = __dmul_rn(__ddiv_rn(theta, rho), beta);
