@@ -80,8 +80,8 @@ typedef struct {
     double tol;             /* stop when ||r||/||b|| <= tol (Sec. 5)                */
     int64_t maxit;          /* cap on updates (residual) or rows visited (identity);*/
                             /* < 0 means n                                          */
-    int64_t refine_period;  /* PLSS_FP32: restart from b - A x every this many      */
-                            /* updates (<= 0: only when the test passes)           */
+    int64_t refine_period;  /* PLSS_FP32: also restart from b - A x every this many */
+                            /* updates (<= 0: off)                                 */
     int64_t kacz_hist;      /* identity sketch: history window K (0 = Kaczmarz)     */
     uint64_t seed;          /* identity sketch: row-order stream seed               */
     int32_t io_device;      /* 1: b, x0, x_out are device pointers                  */
@@ -95,6 +95,9 @@ typedef struct {
     int32_t profile;        /* 1: time every sweep launch with CUDA events recorded */
                             /* on the solve's stream (see plss_kernel_times)       */
     int32_t reserved;
+    double inner_tol;       /* PLSS_FP32: restart from b - A x (refinement) once   */
+                            /* the recursive residual has fallen by this factor    */
+                            /* since the last start (default 1e-4; 0 = off)        */
 } plss_opts;
 
 /* Outcome of one solve. relres_rec is sqrt(rho)/||b|| of the last recursive

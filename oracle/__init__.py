@@ -47,7 +47,8 @@ def _load():
             i64, i32, d, vp, u64 = C.c_int64, C.c_int, C.c_double, C.c_void_p, C.c_uint64
             lib.plss_oracle_residual.restype = i32
             lib.plss_oracle_residual.argtypes = [i64, i64, vp, vp, vp, vp, vp, vp, d, i64, i32, i64,
-                                                 i32, i32, vp, vp, vp, vp, i64, vp, vp, vp, vp, vp]
+                                                 d, i32, i32, vp, vp, vp, vp, i64, vp, vp, vp, vp,
+                                                 vp]
             lib.plss_oracle_kaczmarz.restype = i32
             lib.plss_oracle_kaczmarz.argtypes = [i64, i64, vp, vp, vp, vp, vp, d, i64, i64, u64,
                                                  vp, vp, vp, vp]
@@ -120,7 +121,7 @@ def permutation(state: int, m: int):
     return perm, int(st[0])
 
 
-def residual(A, b, x0=None, w=None, tol=1e-10, maxit=None, prec=0, refine=0,
+def residual(A, b, x0=None, w=None, tol=1e-10, maxit=None, prec=0, refine=0, inner_tol=0.0,
              stop_on_true=False, gamma_form=0, hist=0):
     """PLSS residual sketch (Algorithm 1). Returns a dict with x, iters,
     status, relres_rec, relres_true and, when hist > 0, the per-update
@@ -144,7 +145,7 @@ def residual(A, b, x0=None, w=None, tol=1e-10, maxit=None, prec=0, refine=0,
     hy = np.zeros((H, A.n)) if H else None
     hr = np.zeros((H + 1, A.m)) if H else None
     st = lib.plss_oracle_residual(A.m, A.n, _p(rp), _p(ci), _p(val), _p(b), _p(x0), _p(w),
-                                  float(tol), int(maxit), int(prec), int(refine),
+                                  float(tol), int(maxit), int(prec), int(refine), float(inner_tol),
                                   int(bool(stop_on_true)), int(gamma_form), _p(x), _p(it),
                                   _p(rr), _p(rt), H, _p(hs), _p(hx), _p(hp), _p(hy), _p(hr))
     if st == -2:

@@ -33,9 +33,12 @@
  *     orthogonality the recursion relies on) restarts from b - A x.
  *   - FP32 storage (prec = 1): A's values, r, p and W y are held as float,
  *     sums of products are accumulated in float, inner products and the
- *     scalar recursion in double, x in double; every `refine` updates the
- *     residual is recomputed as b - A x in double and the recursion restarts
- *     from it (this extension is not in the paper).
+ *     scalar recursion in double, x in double; the residual is recomputed as
+ *     b - A x in double and the recursion restarts from it every `refine`
+ *     updates and whenever rho has fallen by inner_tol^2 since the last
+ *     start -- iterative refinement, which keeps the float recursion away
+ *     from its rounding floor where it turns unstable (this extension is not
+ *     in the paper).
  *   - Kaczmarz order: rows are visited without replacement in a fresh
  *     permutation per pass (SplitMix64 stream + Fisher-Yates shuffle); the
  *     history holds at most K updates and, once full, is emptied before the
@@ -177,7 +180,9 @@ static void true_residual(int64_t m, const int64_t *row_ptr, const int32_t *col_
  *
  * Arguments: CSR A (m x n), b[m], x0[n] (NULL = 0), w[n] (NULL = I),
  * tol >= 0, maxit >= 0 (cap on updates), prec 0 = FP64, 1 = FP32 storage,
- * refine = restart period in updates for prec 1 (0 = never), stop_on_true:
+ * refine = restart period in updates for prec 1 (0 = never), inner_tol > 0:
+ * restart from b - A x once rho has fallen by inner_tol^2 since the last
+ * start (the inner solve of iterative refinement; 0 = never), stop_on_true:
  * the stop decision uses the residual b - A x recomputed in double,
  * gamma_form 0 = Algorithm 1, 1 = the statement form (planted defect).
  * Outputs: x_out[n], *iters (updates applied), *relres_rec (sqrt(rho)/||b||
@@ -190,8 +195,9 @@ static void true_residual(int64_t m, const int64_t *row_ptr, const int32_t *col_
  */
 int plss_oracle_residual(int64_t m, int64_t n, const int64_t *row_ptr, const int32_t *col_idx,
                          const double *val_in, const double *b, const double *x0, const double *w,
-                         double tol, int64_t maxit, int prec, int64_t refine, int stop_on_true,
-                         int gamma_form, double *x_out, int64_t *iters_out, double *relres_rec,
+                         double tol, int64_t maxit, int prec, int64_t refine, double inner_tol,
+                         int stop_on_true, int gamma_form, double *x_out, int64_t *iters_out,
+                         double *relres_rec,
                          double *relres_true, int64_t hist_cap, double *hist_s, double *hist_x,
                          double *hist_p, double *hist_y, double *hist_r)
 {
@@ -216,6 +222,7 @@ int plss_oracle_residual(int64_t m, int64_t n, const int64_t *row_ptr, const int
 
     double nb = sqrt(dot(m, b, b));
     double rho = 0.0, phi = 0.0, theta = 0.0, beta = 0.0, gamma = 0.0;
+    double rho_start = 0.0;   /* rho at the last (re)start */
     int64_t k = 0;          /* updates applied */
     int64_t since = 0;      /* updates since the last (re)start */
     int restart = 1;        /* next update is the initial one (p = (rho/phi) u) */
@@ -227,6 +234,7 @@ int plss_oracle_residual(int64_t m, int64_t n, const int64_t *row_ptr, const int
     if (nb == 0.0) { status = ORC_CONVERGED; goto done; }
 
     for (;;) {
+        if (restart) rho_start = rho;
         if (hist_r && k <= hist_cap) memcpy(hist_r + k * m, r, (size_t)m * sizeof(double));
         /* stopping rule (Sec. 5): sqrt(rho)/||b|| <= tol */
         if (sqrt(rho) / nb <= tol) {
@@ -239,6 +247,15 @@ int plss_oracle_residual(int64_t m, int64_t n, const int64_t *row_ptr, const int
             continue;
         }
         if (k >= maxit) { status = ORC_NOT_CONVERGED; break; }
+        if (!restart && inner_tol > 0.0 && rho <= inner_tol * inner_tol * rho_start) {
+            /* inner solve done (residual reduced by inner_tol since the last
+             * start): refine from b - A x */
+            true_residual(m, row_ptr, col_idx, val, b, x, rt);
+            for (int64_t i = 0; i < m; ++i) r[i] = rf(rt[i], f32);
+            rho = dot(m, r, r);
+            restart = 1; since = 0;
+            continue;
+        }
 
         /* y = A^T r (column sweep), u = W y, phi = y^T u */
         if (!f32) {

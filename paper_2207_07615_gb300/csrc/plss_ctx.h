@@ -14,7 +14,7 @@ namespace plss {
 
 constexpr int64_t kTileNnz = 2048;      // target nonzeros per sweep tile
 constexpr int64_t kTileMaxSegs = 1024;  // max rows/columns per sweep tile
-constexpr int64_t kVecTile = 2048;      // entries per update tile
+constexpr int64_t kVecTile = 1024;      // entries per update tile
 constexpr int kCtasPerSm = 8;           // resident CTAs per SM assumed for grids
 constexpr int kMaxChunk = 64;           // bodies per graph launch (max)
 
@@ -87,7 +87,10 @@ void build_tiles(const int32_t *ptr, int64_t begin, int64_t end, int32_t sys, in
 // identity sketch (plss_kaczmarz.cu)
 plss_status run_identity(plss_ctx *c, const double *b, const double *x0, double *x_out,
                          const plss_opts *o, plss_result *res);
-// extra per-context state of the other solvers
+plss_status run_identity_multi(plss_ctx *c, const double *const *b, const double *const *x0,
+                               double *const *xo, const plss_opts *o, plss_result *res);
+// per-context state of the other solvers
 void free_extra(plss_ctx *c);
+void free_rhs(plss_ctx *c);
 
 }  // namespace plss

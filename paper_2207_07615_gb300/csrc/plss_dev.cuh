@@ -56,6 +56,8 @@ struct SysState {
     int64_t maxit;
     int64_t since;      // updates since the last (re)start
     int64_t refine;     // FP32 storage: restart period (0 = never)
+    double rho0;        // rho at the last (re)start
+    double inner_tol2;  // FP32 storage: restart once rho <= inner_tol2 * rho0 (0 = off)
     double *hist;       // optional device array [hist_cap][5]
     int64_t hist_cap;
     int32_t phase;

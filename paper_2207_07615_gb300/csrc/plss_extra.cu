@@ -2,21 +2,8 @@
 #include "plss.h"
 #include "plss_ctx.h"
 
-namespace plss {
-plss_status run_identity(plss_ctx *, const double *, const double *, double *, const plss_opts *,
-                         plss_result *) {
-    return fail(PLSS_ERR_INVALID, "identity sketch not available in this build");
-}
-void free_extra(plss_ctx *) {}
-}  // namespace plss
-
 using namespace plss;
 extern "C" {
-plss_status plss_solve_rhs(plss_ctx *, int32_t, const double *, const double *, double *,
-                           const plss_opts *, plss_result *) {
-    clear_error();
-    return fail(PLSS_ERR_INVALID, "plss_solve_rhs not available in this build");
-}
 void plss_server_opts_default(plss_server_opts *o) {
     if (o) { o->max_slots = 64; o->max_queue = 4096; o->hbm_budget_bytes = 0; o->precision = 0; o->reserved = 0; }
 }

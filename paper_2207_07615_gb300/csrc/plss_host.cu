@@ -491,6 +491,7 @@ plss_status check_opts(const plss_opts *o) {
     if (!o) return fail(PLSS_ERR_INVALID, "opts is NULL");
     if (!(o->tol >= 0.0) || !std::isfinite(o->tol)) return fail(PLSS_ERR_INVALID, "tol must be finite and >= 0");
     if (o->hist_cap < 0) return fail(PLSS_ERR_INVALID, "hist_cap < 0");
+    if (!(o->inner_tol >= 0.0) || !(o->inner_tol < 1.0)) return fail(PLSS_ERR_INVALID, "inner_tol must be in [0, 1)");
     if (o->hist_cap > 0 && !o->hist) return fail(PLSS_ERR_INVALID, "hist_cap > 0 with hist NULL");
     return PLSS_OK;
 }
@@ -564,6 +565,7 @@ plss_status run_residual(plss_ctx *c, const double *const *b, const double *cons
         z.tol = o->tol;
         z.maxit = o->maxit < 0 ? int64_t(d.n) : o->maxit;
         z.refine = c->f32 ? std::max<int64_t>(0, o->refine_period) : 0;
+        z.inner_tol2 = c->f32 ? o->inner_tol * o->inner_tol : 0.0;
         z.stop_on_true = (c->f32 || o->stop_on_true) ? 1 : 0;
         z.phase = PH_SETUP;
         z.nb = 0.0;
@@ -676,6 +678,7 @@ void plss_opts_default(plss_opts *o) {
     o->hist_cap = 0;
     o->profile = 0;
     o->reserved = 0;
+    o->inner_tol = 1e-4;
 }
 
 plss_status plss_create(const plss_csr *A, const plss_opts *o, plss_ctx **out) {
@@ -726,8 +729,8 @@ plss_status plss_solve_batched(plss_ctx *ctx, const double *const *b, const doub
     plss_opts od;
     plss_opts_default(&od);
     if (!o) o = &od;
-    if (o->sketch != PLSS_SKETCH_RESIDUAL)
-        return fail(PLSS_ERR_INVALID, "plss_solve_batched supports the residual sketch only");
+    if (o->sketch == PLSS_SKETCH_IDENTITY) return run_identity_multi(ctx, b, x0, x_out, o, res);
+    if (o->sketch != PLSS_SKETCH_RESIDUAL) return fail(PLSS_ERR_INVALID, "unknown sketch %d", o->sketch);
     return run_residual(ctx, b, x0, x_out, o, res);
 }
 

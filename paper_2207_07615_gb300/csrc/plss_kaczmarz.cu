@@ -1,0 +1,483 @@
+// plss_kaczmarz.cu -- identity-sketch PLSS (generalised Kaczmarz), Sec. 7.
+//
+// For the sketch S_k = [e_{i_1} ... e_{i_k}] the update of eq:pkKacz is
+//   p = gamma (a_i - P Theta^{-1} P^T a_i),
+//   gamma = r_i / ((||a_i|| - ||d||)(||a_i|| + ||d||)),  d = Theta^{-1/2} P^T a_i,
+// with r_i = b_i - a_i^T x, P the stored updates and Theta = diag(||p_j||^2).
+// The window holds at most K updates; once full it is emptied before the
+// next row, so every stored update lives on U, the union of the supports of
+// the window's rows. P is therefore kept compactly as |U| x K (column j =
+// p_j restricted to U) with a column -> slot map, and one row costs
+// O(nnz(a_i) K + |U| K) instead of O(n K).
+//
+// The loop over rows is sequential by nature; one CTA runs one system, and
+// a batch of systems runs as one launch with one CTA per system. Rows are
+// visited without replacement in a fresh permutation per pass (SplitMix64
+// stream + Fisher-Yates shuffle, drawn on the host); ||b - A x|| is tested
+// after every pass.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "plss.h"
+#include "plss_ctx.h"
+#include "plss_dev.cuh"
+#include "plss_launch.h"
+
+namespace plss {
+
+constexpr int kKzThreads = 256;
+constexpr int kKzWarps = kKzThreads / 32;
+constexpr int kKzMaxK = 64;
+
+struct KzSys {
+    int64_t uoff;       // first U slot of the system (ucols, and rows of P)
+    int64_t ucap;       // capacity of U (column stride of P)
+    int64_t toff;       // first Theta entry
+    int64_t skipped;    // rows skipped (projected norm at rounding level)
+    int64_t rows_todo;  // rows to visit in this launch
+    int32_t nh, nU;     // updates in the window, columns in U
+    int32_t overflow;   // set if U outgrew its capacity (a bounds check)
+    int32_t pad;
+};
+
+struct KaczState {
+    int64_t K = -1;
+    int64_t p_entries = 0;
+    int32_t *d_slot = nullptr;    // [n_tot] slot of a column in its system's U, or -1
+    int32_t *d_ucols = nullptr;   // [sum ucap] global column of each slot
+    double *d_P = nullptr;        // per system: column j at P + uoff*K + j*ucap
+    double *d_theta = nullptr;    // [nsys*K]
+    KzSys *d_sys = nullptr;
+    int32_t *d_perm = nullptr;    // [m_tot] local row order of the current pass
+    int32_t *h_perm = nullptr;    // pinned
+    KzSys *h_sys = nullptr;       // pinned
+    std::vector<int64_t> ucap;
+};
+
+struct KzArgs {
+    const int32_t *row_ptr;
+    const int32_t *col_idx;
+    const void *val;
+    const SysDesc *desc;
+    KzSys *ks;
+    const int32_t *perm;
+    const double *b;
+    double *x;
+    int32_t *slot;
+    int32_t *ucols;
+    double *P;
+    double *theta;
+    int32_t K;
+};
+
+// Fixed-order CTA sum of two doubles (result in thread 0).
+__device__ __forceinline__ void kz_sum2(double &a, double &b, double (*sh)[kKzWarps]) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    __syncthreads();
+    if (lane == 0) {
+        sh[0][warp] = a;
+        sh[1][warp] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s0 = 0.0, s1 = 0.0;
+        for (int w = 0; w < kKzWarps; ++w) {
+            s0 += sh[0][w];
+            s1 += sh[1][w];
+        }
+        a = s0;
+        b = s1;
+    }
+}
+
+template <typename S>
+__global__ void __launch_bounds__(kKzThreads) k_kacz(KzArgs a) {
+    __shared__ double sh_c[kKzMaxK];
+    __shared__ double sh_red[2][kKzWarps];
+    __shared__ double sh_gamma;
+    __shared__ int sh_skip;
+    __shared__ int sh_store;
+    __shared__ int sh_wcnt[kKzWarps];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int sys = blockIdx.x;
+    const SysDesc d = a.desc[sys];
+    const KzSys ks = a.ks[sys];
+    const int K = a.K;
+    const int64_t ucap = ks.ucap;
+    const S *__restrict__ val = static_cast<const S *>(a.val);
+    int32_t *U = a.ucols + ks.uoff;
+    double *P = a.P + ks.uoff * int64_t(K);
+    double *th = a.theta + ks.toff;
+    int nh = ks.nh, nU = ks.nU;
+    int64_t skipped = ks.skipped;
+
+    for (int64_t t = 0; t < ks.rows_todo; ++t) {
+        const int32_t i = int32_t(d.row_off) + a.perm[d.row_off + t];
+        const int32_t s0 = a.row_ptr[i], s1 = a.row_ptr[i + 1];
+        if (K > 0 && nh == K) {
+            // window full: empty it (and U) before this row
+            for (int q = tid; q < nU; q += kKzThreads) a.slot[U[q]] = -1;
+            nh = 0;
+            nU = 0;
+            __syncthreads();
+        }
+        // c_j = p_j^T a_i for the window, one warp per j
+        for (int j = warp; j < nh; j += kKzWarps) {
+            double acc = 0.0;
+            for (int32_t k = s0 + lane; k < s1; k += 32) {
+                const int32_t sl = a.slot[a.col_idx[k]];
+                if (sl >= 0) acc = fma(double(val[k]), P[int64_t(j) * ucap + sl], acc);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (lane == 0) sh_c[j] = acc;
+        }
+        // a_i^T x and ||a_i||^2
+        double ax = 0.0, a2 = 0.0;
+        for (int32_t k = s0 + tid; k < s1; k += kKzThreads) {
+            const double v = double(val[k]);
+            ax = fma(v, a.x[a.col_idx[k]], ax);
+            a2 = fma(v, v, a2);
+        }
+        kz_sum2(ax, a2, sh_red);
+        if (tid == 0) {
+            const double ri = a.b[i] - ax;
+            double d2 = 0.0;
+            for (int j = 0; j < nh; ++j) d2 += (sh_c[j] * sh_c[j]) / th[j];
+            const double na = sqrt(a2), nd = sqrt(d2);
+            const double delta = (na - nd) * (na + nd);
+            int skip = !(delta > 1e-14 * a2) ? 1 : 0;
+            if (!skip) {
+                sh_gamma = ri / delta;
+                // r_i = 0: the row already holds; the zero update changes
+                // nothing and is not stored
+                if (sh_gamma == 0.0) skip = 2;
+                for (int j = 0; j < nh; ++j) sh_c[j] = sh_c[j] / th[j];
+            }
+            sh_skip = skip;
+        }
+        __syncthreads();
+        if (sh_skip) {
+            skipped += sh_skip == 1;
+            continue;
+        }
+        const double gamma = sh_gamma;
+        if (K == 0) {
+            // classical Kaczmarz: x += gamma a_i on the row's support
+            for (int32_t k = s0 + tid; k < s1; k += kKzThreads) {
+                const int32_t c = a.col_idx[k];
+                a.x[c] = __dadd_rn(a.x[c], __dmul_rn(gamma, double(val[k])));
+            }
+            __syncthreads();
+            continue;
+        }
+        // new columns of a_i get slots in row order (deterministic)
+        const int nU0 = nU;
+        for (int32_t base = s0; base < s1; base += kKzThreads) {
+            const int32_t k = base + tid;
+            const bool in = k < s1;
+            const int32_t c = in ? a.col_idx[k] : 0;
+            const bool isnew = in && a.slot[c] < 0;
+            const unsigned bal = __ballot_sync(0xffffffffu, isnew);
+            if (lane == 0) sh_wcnt[warp] = __popc(bal);
+            __syncthreads();
+            int off = nU, tot = 0;
+            for (int w = 0; w < kKzWarps; ++w) {
+                if (w < warp) off += sh_wcnt[w];
+                tot += sh_wcnt[w];
+            }
+            if (isnew) {
+                const int s = off + __popc(bal & ((1u << lane) - 1u));
+                if (s < ucap) {
+                    a.slot[c] = s;
+                    U[s] = c;
+                } else {
+                    a.ks[sys].overflow = 1;   // cannot happen: |U| <= K * max row length
+                }
+            }
+            nU += tot;
+            __syncthreads();
+        }
+        // clear the rows of P for new slots and the scratch column nh
+        for (int s = nU0 + tid; s < nU; s += kKzThreads)
+            for (int j = 0; j < K; ++j) P[int64_t(j) * ucap + s] = 0.0;
+        for (int s = tid; s < nU0; s += kKzThreads) P[int64_t(nh) * ucap + s] = 0.0;
+        __syncthreads();
+        // scatter a_i into column nh
+        for (int32_t k = s0 + tid; k < s1; k += kKzThreads)
+            P[int64_t(nh) * ucap + a.slot[a.col_idx[k]]] = double(val[k]);
+        __syncthreads();
+        // p = gamma (a_i - sum_j (c_j/theta_j) p_j) on U; x += p; theta = ||p||^2
+        double tp = 0.0, unused = 0.0;
+        for (int s = tid; s < nU; s += kKzThreads) {
+            double v = P[int64_t(nh) * ucap + s];
+            for (int j = 0; j < nh; ++j) v = __dsub_rn(v, __dmul_rn(sh_c[j], P[int64_t(j) * ucap + s]));
+            const double p = __dmul_rn(gamma, v);
+            P[int64_t(nh) * ucap + s] = p;
+            const int32_t c = U[s];
+            a.x[c] = __dadd_rn(a.x[c], p);
+            tp = __dadd_rn(tp, __dmul_rn(p, p));
+        }
+        kz_sum2(tp, unused, sh_red);
+        if (tid == 0) {
+            // a zero update (r_i = 0) is not stored
+            sh_store = tp > 0.0;
+            if (tp > 0.0) th[nh] = tp;
+        }
+        __syncthreads();
+        nh += sh_store;
+    }
+    if (tid == 0) {
+        a.ks[sys].nh = nh;
+        a.ks[sys].nU = nU;
+        a.ks[sys].skipped = skipped;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+
+// SplitMix64 (Steele, Lea & Flood 2014): add the golden-ratio increment,
+// then mix with two xor-shift-multiply rounds and a final xor-shift.
+static inline uint64_t splitmix64(uint64_t &state) {
+    state += 0x9e3779b97f4a7c15ULL;
+    uint64_t z = state;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+    return z ^ (z >> 31);
+}
+
+// Durstenfeld's Fisher-Yates shuffle of 0..m-1, one draw per position from
+// the top down, index = draw mod (i + 1).
+static void shuffle_rows(uint64_t &state, int32_t *perm, int64_t m) {
+    for (int64_t i = 0; i < m; ++i) perm[i] = int32_t(i);
+    for (int64_t i = m - 1; i > 0; --i) {
+        const int64_t j = int64_t(splitmix64(state) % uint64_t(i + 1));
+        std::swap(perm[i], perm[j]);
+    }
+}
+
+static void kacz_free(KaczState *k) {
+    if (!k) return;
+    dfree(k->d_slot);
+    dfree(k->d_ucols);
+    dfree(k->d_P);
+    dfree(k->d_theta);
+    dfree(k->d_sys);
+    dfree(k->d_perm);
+    if (k->h_perm) cudaFreeHost(k->h_perm);
+    if (k->h_sys) cudaFreeHost(k->h_sys);
+    delete k;
+}
+
+void free_extra(plss_ctx *c) {
+    kacz_free(c->kacz);
+    c->kacz = nullptr;
+    free_rhs(c);
+}
+
+static plss_status kacz_prepare(plss_ctx *c, int64_t K) {
+    if (c->kacz && c->kacz->K == K) return PLSS_OK;
+    kacz_free(c->kacz);
+    c->kacz = nullptr;
+    KaczState *k = new KaczState();
+    k->K = K;
+    std::vector<int32_t> rp(static_cast<size_t>(c->m + 1));
+    if (cudaMemcpy(rp.data(), c->d_row_ptr, rp.size() * 4, cudaMemcpyDeviceToHost) != cudaSuccess) {
+        delete k;
+        return fail(PLSS_ERR_CUDA, "reading row_ptr failed");
+    }
+    int64_t total = 0;
+    k->ucap.resize(size_t(c->nsys));
+    for (int32_t s = 0; s < c->nsys; ++s) {
+        const SysDesc &d = c->h_desc[size_t(s)];
+        int64_t maxlen = 0;
+        for (int64_t i = d.row_off; i < d.row_off + d.m; ++i)
+            maxlen = std::max<int64_t>(maxlen, rp[size_t(i + 1)] - rp[size_t(i)]);
+        k->ucap[size_t(s)] = K > 0 ? std::max<int64_t>(1, std::min<int64_t>(d.n, K * maxlen)) : 1;
+        total += k->ucap[size_t(s)];
+    }
+    k->p_entries = total * std::max<int64_t>(K, 1);
+    plss_status st = PLSS_OK;
+    if ((st = dalloc(reinterpret_cast<void **>(&k->d_slot), 4 * size_t(c->n), "slot")) != PLSS_OK ||
+        (st = dalloc(reinterpret_cast<void **>(&k->d_ucols), 4 * size_t(total), "U")) != PLSS_OK ||
+        (st = dalloc(reinterpret_cast<void **>(&k->d_P), 8 * size_t(k->p_entries), "P")) != PLSS_OK ||
+        (st = dalloc(reinterpret_cast<void **>(&k->d_theta), 8 * size_t(c->nsys) * size_t(std::max<int64_t>(K, 1)), "theta")) != PLSS_OK ||
+        (st = dalloc(reinterpret_cast<void **>(&k->d_sys), sizeof(KzSys) * size_t(c->nsys), "kz")) != PLSS_OK ||
+        (st = dalloc(reinterpret_cast<void **>(&k->d_perm), 4 * size_t(std::max<int64_t>(c->m, 1)), "perm")) != PLSS_OK) {
+        kacz_free(k);
+        return st;
+    }
+    if (cudaMallocHost(reinterpret_cast<void **>(&k->h_perm), 4 * size_t(std::max<int64_t>(c->m, 1))) != cudaSuccess ||
+        cudaMallocHost(reinterpret_cast<void **>(&k->h_sys), sizeof(KzSys) * size_t(c->nsys)) != cudaSuccess) {
+        kacz_free(k);
+        return fail(PLSS_ERR_NOMEM, "pinned allocation failed");
+    }
+    c->kacz = k;
+    return PLSS_OK;
+}
+
+// Sum over each system's rows of (b - A v)^2 with v in d_x (or zero when
+// use_zero), from the per-tile partials of the residual kernel.
+static plss_status resid2(plss_ctx *c, cudaStream_t s, bool use_zero, std::vector<double> &out) {
+    if (use_zero) {
+        cudaError_t e = cudaMemsetAsync(c->d_vin, 0, 8 * size_t(std::max<int64_t>(c->n, 1)), s);
+        if (e != cudaSuccess) return fail(PLSS_ERR_CUDA, "memset: %s", cudaGetErrorString(e));
+    }
+    cudaError_t e = launch_spmv(c->d_row_ptr, c->d_col_idx, c->d_val, c->f32, c->d_rt,
+                                int32_t(c->h_rt.size()), use_zero ? c->d_vin : c->d_x, c->d_vout,
+                                c->d_b, c->d_part_res, c->grid_r, s);
+    if (e != cudaSuccess) return fail(PLSS_ERR_CUDA, "residual kernel: %s", cudaGetErrorString(e));
+    std::vector<double> part(c->h_rt.size());
+    if (cudaMemcpyAsync(part.data(), c->d_part_res, 8 * part.size(), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return fail(PLSS_ERR_CUDA, "reading residual partials failed");
+    out.assign(size_t(c->nsys), 0.0);
+    for (int32_t sy = 0; sy < c->nsys; ++sy) {
+        const SysDesc &d = c->h_desc[size_t(sy)];
+        for (int32_t t = 0; t < d.rt_count; ++t) out[size_t(sy)] += part[size_t(d.rt_begin + t)];
+    }
+    return PLSS_OK;
+}
+
+plss_status run_identity_multi(plss_ctx *c, const double *const *b, const double *const *x0,
+                               double *const *xo, const plss_opts *o, plss_result *res) {
+    plss_status st = check_opts(o);
+    if (st != PLSS_OK) return st;
+    if (o->kacz_hist < 0 || o->kacz_hist > kKzMaxK)
+        return fail(PLSS_ERR_INVALID, "kacz_hist must be in [0, %d]", kKzMaxK);
+    if (o->w_mode != PLSS_W_IDENTITY) return fail(PLSS_ERR_INVALID, "the identity sketch takes W = I");
+    cudaStream_t s = static_cast<cudaStream_t>(o->stream);
+    const bool dev = o->io_device != 0;
+    const int64_t K = o->kacz_hist;
+    st = kacz_prepare(c, K);
+    if (st != PLSS_OK) return st;
+    KaczState *kz = c->kacz;
+    for (int32_t sy = 0; sy < c->nsys; ++sy) {
+        const SysDesc &d = c->h_desc[size_t(sy)];
+        if (d.m > 0 && !b[sy]) return fail(PLSS_ERR_INVALID, "b is NULL (system %d)", sy);
+        if ((st = put_vec(c->d_b + d.row_off, b[sy], d.m, dev, s)) != PLSS_OK) return st;
+        if ((st = put_vec(c->d_x + d.col_off, x0 ? x0[sy] : nullptr, d.n, dev, s)) != PLSS_OK) return st;
+    }
+    if (cudaMemsetAsync(kz->d_slot, 0xff, 4 * size_t(std::max<int64_t>(c->n, 1)), s) != cudaSuccess)
+        return fail(PLSS_ERR_CUDA, "memset failed");
+    std::vector<double> nb2, r2;
+    if ((st = resid2(c, s, true, nb2)) != PLSS_OK) return st;
+    if ((st = resid2(c, s, false, r2)) != PLSS_OK) return st;
+    const int n = c->nsys;
+    std::vector<int> active(static_cast<size_t>(n), 0), status(static_cast<size_t>(n), PLSS_NOT_CONVERGED);
+    std::vector<int64_t> visited(static_cast<size_t>(n), 0), maxit(static_cast<size_t>(n));
+    std::vector<uint64_t> rng(static_cast<size_t>(n));
+    std::vector<double> rel(static_cast<size_t>(n), 0.0);
+    int64_t uoff = 0;
+    for (int32_t sy = 0; sy < n; ++sy) {
+        const SysDesc &d = c->h_desc[size_t(sy)];
+        KzSys z;
+        std::memset(&z, 0, sizeof z);
+        z.uoff = uoff;
+        z.ucap = kz->ucap[size_t(sy)];
+        z.toff = int64_t(sy) * std::max<int64_t>(K, 1);
+        uoff += z.ucap;
+        kz->h_sys[sy] = z;
+        maxit[size_t(sy)] = o->maxit < 0 ? int64_t(d.n) : o->maxit;
+        rng[size_t(sy)] = o->seed + uint64_t(sy);
+        const double nb = std::sqrt(nb2[size_t(sy)]);
+        rel[size_t(sy)] = nb > 0.0 ? std::sqrt(r2[size_t(sy)]) / nb : 0.0;
+        if (nb == 0.0 || d.m == 0 || rel[size_t(sy)] <= o->tol) status[size_t(sy)] = PLSS_OK;
+        else if (maxit[size_t(sy)] > 0) active[size_t(sy)] = 1;
+    }
+    KzArgs ka;
+    ka.row_ptr = c->d_row_ptr;
+    ka.col_idx = c->d_col_idx;
+    ka.val = c->d_val;
+    ka.desc = c->d_desc;
+    ka.ks = kz->d_sys;
+    ka.perm = kz->d_perm;
+    ka.b = c->d_b;
+    ka.x = c->d_x;
+    ka.slot = kz->d_slot;
+    ka.ucols = kz->d_ucols;
+    ka.P = kz->d_P;
+    ka.theta = kz->d_theta;
+    ka.K = int32_t(K);
+    if (cudaEventRecord(c->ev0, s) != cudaSuccess) return fail(PLSS_ERR_CUDA, "event record failed");
+    for (;;) {
+        bool any = false;
+        for (int32_t sy = 0; sy < n; ++sy) {
+            const SysDesc &d = c->h_desc[size_t(sy)];
+            KzSys &z = kz->h_sys[sy];
+            z.rows_todo = 0;
+            if (!active[size_t(sy)]) continue;
+            z.rows_todo = std::min<int64_t>(d.m, maxit[size_t(sy)] - visited[size_t(sy)]);
+            shuffle_rows(rng[size_t(sy)], kz->h_perm + d.row_off, d.m);
+            any = true;
+        }
+        if (!any) break;
+        if (cudaMemcpyAsync(kz->d_perm, kz->h_perm, 4 * size_t(c->m), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            cudaMemcpyAsync(kz->d_sys, kz->h_sys, sizeof(KzSys) * size_t(n), cudaMemcpyHostToDevice, s) != cudaSuccess)
+            return fail(PLSS_ERR_CUDA, "upload of the row order failed");
+        if (c->f32) k_kacz<float><<<n, kKzThreads, 0, s>>>(ka);
+        else k_kacz<double><<<n, kKzThreads, 0, s>>>(ka);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return fail(PLSS_ERR_CUDA, "kaczmarz kernel: %s", cudaGetErrorString(e));
+        if (cudaMemcpyAsync(kz->h_sys, kz->d_sys, sizeof(KzSys) * size_t(n), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+            return fail(PLSS_ERR_CUDA, "reading the window state failed");
+        if ((st = resid2(c, s, false, r2)) != PLSS_OK) return st;
+        for (int32_t sy = 0; sy < n; ++sy)
+            if (kz->h_sys[sy].overflow) return fail(PLSS_ERR_CUDA, "identity sketch: support capacity exceeded (system %d)", sy);
+        for (int32_t sy = 0; sy < n; ++sy) {
+            if (!active[size_t(sy)]) continue;
+            visited[size_t(sy)] += kz->h_sys[sy].rows_todo;
+            const double nb = std::sqrt(nb2[size_t(sy)]);
+            rel[size_t(sy)] = std::sqrt(r2[size_t(sy)]) / nb;
+            if (rel[size_t(sy)] <= o->tol) {
+                status[size_t(sy)] = PLSS_OK;
+                active[size_t(sy)] = 0;
+            } else if (visited[size_t(sy)] >= maxit[size_t(sy)]) {
+                status[size_t(sy)] = PLSS_NOT_CONVERGED;
+                active[size_t(sy)] = 0;
+            }
+        }
+    }
+    if (cudaEventRecord(c->ev1, s) != cudaSuccess) return fail(PLSS_ERR_CUDA, "event record failed");
+    for (int32_t sy = 0; sy < n; ++sy) {
+        const SysDesc &d = c->h_desc[size_t(sy)];
+        if ((st = get_vec(xo ? xo[sy] : nullptr, c->d_x + d.col_off, d.n, dev, s)) != PLSS_OK) return st;
+    }
+    if (cudaStreamSynchronize(s) != cudaSuccess) return fail(PLSS_ERR_CUDA, "synchronize failed");
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+    plss_status overall = PLSS_OK;
+    for (int32_t sy = 0; sy < n; ++sy) {
+        if (res) {
+            res[sy].status = status[size_t(sy)];
+            res[sy].reserved = 0;
+            res[sy].iters = visited[size_t(sy)];
+            res[sy].relres_rec = rel[size_t(sy)];
+            res[sy].relres_true = rel[size_t(sy)];
+            res[sy].seconds = double(ms) * 1e-3;
+        }
+        if (overall == PLSS_OK && status[size_t(sy)] != PLSS_OK) overall = plss_status(status[size_t(sy)]);
+    }
+    return overall;
+}
+
+plss_status run_identity(plss_ctx *c, const double *b, const double *x0, double *x_out,
+                         const plss_opts *o, plss_result *res) {
+    const double *bb[1] = {b};
+    const double *xx[1] = {x0};
+    double *oo[1] = {x_out};
+    return run_identity_multi(c, bb, xx, oo, o, res);
+}
+
+}  // namespace plss

@@ -14,17 +14,30 @@
 //                 (re)start); the last tile then applies the stopping rule
 //                 sqrt(rho)/||b|| <= tol (Sec. 5) and the maxit cap.
 //
-// All three are HBM-bandwidth bound (about 2 flops per 12-16 bytes), so the
-// kernels are plain CUDA-core code: coalesced streaming of the CSR/CSC
-// arrays, a group of G lanes per row/column with G picked per tile from the
-// tile's mean segment length, register accumulation and warp-shuffle
-// reductions, FP64 partial sums per tile and a fixed-order final sum.
+// The sweeps are HBM-bandwidth bound (about 2 flops per 12-16 bytes), so the
+// kernels are plain CUDA-core code built for memory-level parallelism:
+//   * a tile is a run of whole rows (columns) holding at most 2,048
+//     nonzeros; its nonzeros are streamed with coalesced loads, 8 per thread
+//     issued back to back with their gathers, and the products are staged
+//     in shared memory;
+//   * the segments are then summed out of shared memory by groups of G
+//     lanes (G picked per tile from its mean segment length) with a
+//     warp-shuffle tree; a segment longer than a tile gets a tile of its own
+//     that the whole CTA streams;
+//   * each CTA owns a contiguous range of tiles; per-tile FP64 partial sums
+//     of rho / phi / theta are written to global memory and each CTA
+//     announces its tiles with one atomic per system it touched; the CTA
+//     that completes a system sums that system's partials in tile order
+//     (deterministic for a given schedule) and takes its scalar step.
 #include <cuda_runtime.h>
 
 #include "plss_dev.cuh"
 #include "plss_launch.h"
 
 namespace plss {
+
+constexpr int kUnroll = 8;                       // nonzeros per thread per tile
+constexpr int kStreamNnz = kThreads * kUnroll;   // nonzeros staged per tile
 
 __device__ __forceinline__ double fma_t(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ float fma_t(float a, float b, float c) { return fmaf(a, b, c); }
@@ -57,34 +70,67 @@ __device__ __forceinline__ void cta_sum(double (&v)[N]) {
     }
 }
 
-// Dot product of one sparse segment (nonzeros [s, e)) with a dense vector,
-// split over the G lanes of a group; the sum lands in every lane of the
-// group. All 32 lanes of the warp must call it (warp-uniform control flow).
-template <int G, typename VT, typename XT, typename ACC>
-__device__ __forceinline__ ACC group_dot(const int32_t *__restrict__ idx,
-                                         const VT *__restrict__ val, int32_t s, int32_t e,
-                                         int gl, const XT *__restrict__ x) {
-    ACC acc = ACC(0);
-#pragma unroll 2
-    for (int32_t k = s + gl; k < e; k += G)
-        acc = fma_t(ACC(__ldg(val + k)), ACC(__ldg(x + __ldg(idx + k))), acc);
+// Products val[z0+k] * x[idx[z0+k]] for k < nz (nz <= kStreamNnz) into
+// prod[k]: every thread issues its 8 index/value loads, then its 8 gathers,
+// before using any of them.
+template <typename VT, typename XT, typename PT>
+__device__ __forceinline__ void stage_products(const int32_t *__restrict__ idx,
+                                               const VT *__restrict__ val, int32_t z0, int32_t nz,
+                                               const XT *__restrict__ x, PT *prod) {
+    int32_t c[kUnroll];
+    VT v[kUnroll];
 #pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    return acc;
+    for (int u = 0; u < kUnroll; ++u) {
+        const int32_t k = threadIdx.x + u * kThreads;
+        const bool in = k < nz;
+        c[u] = in ? __ldg(idx + z0 + k) : 0;
+        v[u] = in ? __ldg(val + z0 + k) : VT(0);
+    }
+    XT g[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+        const int32_t k = threadIdx.x + u * kThreads;
+        g[u] = k < nz ? __ldg(x + c[u]) : XT(0);
+    }
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+        const int32_t k = threadIdx.x + u * kThreads;
+        if (k < nz) prod[k] = PT(v[u]) * PT(g[u]);
+    }
 }
 
-// Same with the whole CTA on one segment; lane partials in ACC, combined in
-// double (result in thread 0).
+// Dot product of one long segment [s, e) with a dense vector, streamed by
+// the whole CTA with 8 independent accumulators per thread; lane partials
+// combined in a fixed order in double (result in thread 0).
 template <typename VT, typename XT, typename ACC>
 __device__ __forceinline__ double cta_dot(const int32_t *__restrict__ idx,
                                           const VT *__restrict__ val, int32_t s, int32_t e,
                                           const XT *__restrict__ x) {
-    ACC acc = ACC(0);
-    for (int32_t k = s + threadIdx.x; k < e; k += kThreads)
-        acc = fma_t(ACC(__ldg(val + k)), ACC(__ldg(x + __ldg(idx + k))), acc);
-    double v[1] = {double(acc)};
-    cta_sum<1>(v);
-    return v[0];
+    ACC acc[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) acc[u] = ACC(0);
+    for (int32_t base = s; base < e; base += kStreamNnz) {
+        int32_t c[kUnroll];
+        VT v[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const int32_t k = base + threadIdx.x + u * kThreads;
+            const bool in = k < e;
+            c[u] = in ? __ldg(idx + k) : 0;
+            v[u] = in ? __ldg(val + k) : VT(0);
+        }
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const int32_t k = base + threadIdx.x + u * kThreads;
+            if (k < e) acc[u] = fma_t(ACC(v[u]), ACC(__ldg(x + c[u])), acc[u]);
+        }
+    }
+    double t = 0.0;
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) t += double(acc[u]);
+    double v1[1] = {t};
+    cta_sum<1>(v1);
+    return v1[0];
 }
 
 // Calls body(seg, s, e, gl, valid) for each segment of the tile with groups
@@ -103,18 +149,37 @@ __device__ __forceinline__ void for_segments(const int32_t *__restrict__ ptr, co
     }
 }
 
-// Arrival of one finished tile of system `sys`; returns (to all threads)
-// whether this CTA holds the system's last tile.
-__device__ __forceinline__ bool tile_arrive(uint32_t *cnt, int32_t count) {
+// Sum of the staged products of one segment over the G lanes of a group
+// (lane-strided, then a shuffle tree); valid in every lane of the group.
+template <int G, typename PT>
+__device__ __forceinline__ PT group_sum(const PT *prod, int32_t s, int32_t e, int gl) {
+    PT acc = PT(0);
+    for (int32_t k = s + gl; k < e; k += G) acc += prod[k];
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    return acc;
+}
+
+// Contiguous, balanced share of n tiles for this CTA.
+__device__ __forceinline__ void tile_range(int32_t n, int32_t &t0, int32_t &t1) {
+    const int32_t per = n / int32_t(gridDim.x), rem = n % int32_t(gridDim.x);
+    const int32_t b = int32_t(blockIdx.x);
+    t0 = b * per + (b < rem ? b : rem);
+    t1 = t0 + per + (b < rem ? 1 : 0);
+}
+
+// This CTA has finished `pending` tiles of a system with `total` tiles:
+// returns (to all threads) whether that completed the system.
+__device__ __forceinline__ bool arrive(uint32_t *cnt, uint32_t pending, int32_t total) {
     __shared__ int s_last;
+    __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
-        const uint32_t prev = atomicAdd(cnt, 1u);
-        s_last = prev == uint32_t(count - 1);
+        const uint32_t prev = atomicAdd(cnt, pending);
+        s_last = prev + pending == uint32_t(total);
     }
     __syncthreads();
     const bool last = s_last != 0;
-    __syncthreads();
     if (last) __threadfence();
     return last;
 }
@@ -135,12 +200,17 @@ __device__ __forceinline__ void finish_system(const SweepArgs &a, SysState *st, 
 
 template <int G, typename S>
 __device__ __forceinline__ void row_tile(const SweepArgs &a, const Tile &t, bool init,
-                                         double &acc_r, double &acc_b) {
+                                         double &acc_r, double &acc_b, double *smem) {
     const S *__restrict__ val = static_cast<const S *>(a.val);
     S *__restrict__ r = static_cast<S *>(a.r);
+    const int32_t z0 = __ldg(a.row_ptr + t.begin);
+    const int32_t nz = __ldg(a.row_ptr + t.end) - z0;
     if (init) {
+        stage_products<S, double, double>(a.col_idx, val, z0, nz, a.x, smem);
+        __syncthreads();
+        const double *prod = smem - z0;
         for_segments<G>(a.row_ptr, t, [&](int32_t row, int32_t s, int32_t e, int gl, bool valid) {
-            const double d = group_dot<G, S, double, double>(a.col_idx, val, s, e, gl, a.x);
+            const double d = group_sum<G>(prod, s, e, gl);
             if (valid && gl == 0) {
                 const double bi = a.b[row];
                 const S ri = S(bi - d);
@@ -150,9 +220,12 @@ __device__ __forceinline__ void row_tile(const SweepArgs &a, const Tile &t, bool
             }
         });
     } else {
-        const S *__restrict__ p = static_cast<const S *>(a.p);
+        S *sp = reinterpret_cast<S *>(smem);
+        stage_products<S, S, S>(a.col_idx, val, z0, nz, static_cast<const S *>(a.p), sp);
+        __syncthreads();
+        const S *prod = sp - z0;
         for_segments<G>(a.row_ptr, t, [&](int32_t row, int32_t s, int32_t e, int gl, bool valid) {
-            const S d = group_dot<G, S, S, S>(a.col_idx, val, s, e, gl, p);
+            const S d = group_sum<G>(prod, s, e, gl);
             if (valid && gl == 0) {
                 const S ri = r[row] - d;
                 r[row] = ri;
@@ -160,6 +233,7 @@ __device__ __forceinline__ void row_tile(const SweepArgs &a, const Tile &t, bool
             }
         });
     }
+    __syncthreads();
 }
 
 template <typename S>
@@ -199,7 +273,10 @@ __device__ void finish_row(const SweepArgs &a, int32_t sys, bool init) {
     SysState *st = a.st + sys;
     st->cnt_row = 0;
     const double rho = v[0];
-    if (init) st->nb = sqrt(v[1]);
+    if (init) {
+        st->nb = sqrt(v[1]);
+        st->rho0 = rho;
+    }
     const double nb = st->nb;
     st->rho = rho;
     if (nb == 0.0) {
@@ -218,6 +295,9 @@ __device__ void finish_row(const SweepArgs &a, int32_t sys, bool init) {
         }
     } else if (st->iters >= st->maxit) {
         finish_system(a, st, 1);
+    } else if (!init && st->inner_tol2 > 0.0 && rho <= st->inner_tol2 * st->rho0) {
+        st->since = 0;
+        st->phase = PH_SETUP;       // inner solve done: refine from b - A x
     } else {
         st->phase = init ? PH_FIRST : PH_RUN;
     }
@@ -225,29 +305,42 @@ __device__ void finish_row(const SweepArgs &a, int32_t sys, bool init) {
 
 template <typename S>
 __global__ void __launch_bounds__(kThreads) k_row_sweep(SweepArgs a) {
-    for (int32_t ti = blockIdx.x; ti < a.n_rtiles; ti += gridDim.x) {
+    __shared__ __align__(16) double smem[kStreamNnz];
+    int32_t t0, t1;
+    tile_range(a.n_rtiles, t0, t1);
+    int32_t cur = -1;
+    uint32_t pending = 0;
+    bool active = false, init = false;
+    for (int32_t ti = t0; ti < t1; ++ti) {
         const Tile t = a.rtiles[ti];
-        SysState *st = a.st + t.sys;
-        const int32_t phase = load_phase(st);
-        if (phase != PH_SETUP && phase != PH_RUN) continue;
-        const bool init = phase == PH_SETUP;
+        if (t.sys != cur) {
+            if (pending && arrive(&a.st[cur].cnt_row, pending, a.desc[cur].rt_count))
+                finish_row(a, cur, init);
+            cur = t.sys;
+            pending = 0;
+            const int32_t ph = load_phase(a.st + cur);
+            active = ph == PH_SETUP || ph == PH_RUN;
+            init = ph == PH_SETUP;
+        }
+        if (!active) continue;
         double acc[2] = {0.0, 0.0};
         switch (t.group) {
             case 0: row_tile_cta<S>(a, t, init, acc[0], acc[1]); break;
-            case 1: row_tile<1, S>(a, t, init, acc[0], acc[1]); break;
-            case 2: row_tile<2, S>(a, t, init, acc[0], acc[1]); break;
-            case 4: row_tile<4, S>(a, t, init, acc[0], acc[1]); break;
-            case 8: row_tile<8, S>(a, t, init, acc[0], acc[1]); break;
-            case 16: row_tile<16, S>(a, t, init, acc[0], acc[1]); break;
-            default: row_tile<32, S>(a, t, init, acc[0], acc[1]); break;
+            case 1: row_tile<1, S>(a, t, init, acc[0], acc[1], smem); break;
+            case 2: row_tile<2, S>(a, t, init, acc[0], acc[1], smem); break;
+            case 4: row_tile<4, S>(a, t, init, acc[0], acc[1], smem); break;
+            case 8: row_tile<8, S>(a, t, init, acc[0], acc[1], smem); break;
+            case 16: row_tile<16, S>(a, t, init, acc[0], acc[1], smem); break;
+            default: row_tile<32, S>(a, t, init, acc[0], acc[1], smem); break;
         }
         cta_sum<2>(acc);
         if (threadIdx.x == 0) {
             a.part_row[2 * ti] = acc[0];
             a.part_row[2 * ti + 1] = acc[1];
         }
-        if (tile_arrive(&st->cnt_row, a.desc[t.sys].rt_count)) finish_row(a, t.sys, init);
+        ++pending;
     }
+    if (pending && arrive(&a.st[cur].cnt_row, pending, a.desc[cur].rt_count)) finish_row(a, cur, init);
 }
 
 // ---------------------------------------------------------------------------
@@ -262,13 +355,19 @@ __device__ __forceinline__ void col_out(const SweepArgs &a, int32_t col, double 
 }
 
 template <int G, typename S>
-__device__ __forceinline__ void col_tile(const SweepArgs &a, const Tile &t, double &acc) {
+__device__ __forceinline__ void col_tile(const SweepArgs &a, const Tile &t, double &acc, double *smem) {
     const S *__restrict__ val = static_cast<const S *>(a.cval);
-    const S *__restrict__ r = static_cast<const S *>(a.r);
+    const int32_t z0 = __ldg(a.col_ptr + t.begin);
+    const int32_t nz = __ldg(a.col_ptr + t.end) - z0;
+    S *sp = reinterpret_cast<S *>(smem);
+    stage_products<S, S, S>(a.row_idx, val, z0, nz, static_cast<const S *>(a.r), sp);
+    __syncthreads();
+    const S *prod = sp - z0;
     for_segments<G>(a.col_ptr, t, [&](int32_t col, int32_t s, int32_t e, int gl, bool valid) {
-        const S d = group_dot<G, S, S, S>(a.row_idx, val, s, e, gl, r);
+        const S d = group_sum<G>(prod, s, e, gl);
         if (valid && gl == 0) col_out<S>(a, col, double(d), acc);
     });
+    __syncthreads();
 }
 
 template <typename S>
@@ -322,25 +421,37 @@ __device__ void finish_col(const SweepArgs &a, int32_t sys) {
 
 template <typename S>
 __global__ void __launch_bounds__(kThreads) k_col_sweep(SweepArgs a) {
-    for (int32_t ti = blockIdx.x; ti < a.n_ctiles; ti += gridDim.x) {
+    __shared__ __align__(16) double smem[kStreamNnz];
+    int32_t t0, t1;
+    tile_range(a.n_ctiles, t0, t1);
+    int32_t cur = -1;
+    uint32_t pending = 0;
+    bool active = false;
+    for (int32_t ti = t0; ti < t1; ++ti) {
         const Tile t = a.ctiles[ti];
-        SysState *st = a.st + t.sys;
-        const int32_t phase = load_phase(st);
-        if (phase != PH_FIRST && phase != PH_RUN) continue;
+        if (t.sys != cur) {
+            if (pending && arrive(&a.st[cur].cnt_col, pending, a.desc[cur].ct_count)) finish_col(a, cur);
+            cur = t.sys;
+            pending = 0;
+            const int32_t ph = load_phase(a.st + cur);
+            active = ph == PH_FIRST || ph == PH_RUN;
+        }
+        if (!active) continue;
         double acc[1] = {0.0};
         switch (t.group) {
             case 0: col_tile_cta<S>(a, t, acc[0]); break;
-            case 1: col_tile<1, S>(a, t, acc[0]); break;
-            case 2: col_tile<2, S>(a, t, acc[0]); break;
-            case 4: col_tile<4, S>(a, t, acc[0]); break;
-            case 8: col_tile<8, S>(a, t, acc[0]); break;
-            case 16: col_tile<16, S>(a, t, acc[0]); break;
-            default: col_tile<32, S>(a, t, acc[0]); break;
+            case 1: col_tile<1, S>(a, t, acc[0], smem); break;
+            case 2: col_tile<2, S>(a, t, acc[0], smem); break;
+            case 4: col_tile<4, S>(a, t, acc[0], smem); break;
+            case 8: col_tile<8, S>(a, t, acc[0], smem); break;
+            case 16: col_tile<16, S>(a, t, acc[0], smem); break;
+            default: col_tile<32, S>(a, t, acc[0], smem); break;
         }
         cta_sum<1>(acc);
         if (threadIdx.x == 0) a.part_col[ti] = acc[0];
-        if (tile_arrive(&st->cnt_col, a.desc[t.sys].ct_count)) finish_col(a, t.sys);
+        ++pending;
     }
+    if (pending && arrive(&a.st[cur].cnt_col, pending, a.desc[cur].ct_count)) finish_col(a, cur);
 }
 
 // ---------------------------------------------------------------------------
@@ -371,59 +482,98 @@ __device__ void finish_upd(const SweepArgs &a, int32_t sys) {
     st->since += 1;
     if (st->refine > 0 && st->since >= st->refine) {
         st->since = 0;
-        st->phase = PH_SETUP;   // FP64 refinement: restart from b - A x
+        st->phase = PH_SETUP;   // periodic refinement: restart from b - A x
     } else {
         st->phase = PH_RUN;
     }
 }
 
 template <typename S>
-__global__ void __launch_bounds__(kThreads) k_update(SweepArgs a) {
+__device__ __forceinline__ double update_tile(const SweepArgs &a, const Tile &t, bool first,
+                                              double beta, double gamma) {
     S *__restrict__ p = static_cast<S *>(a.p);
     const S *__restrict__ u = static_cast<const S *>(a.u);
-    for (int32_t ti = blockIdx.x; ti < a.n_vtiles; ti += gridDim.x) {
-        const Tile t = a.vtiles[ti];
-        SysState *st = a.st + t.sys;
-        const int32_t phase = load_phase(st);
-        if (phase != PH_FIRST && phase != PH_RUN) continue;
-        const bool first = phase == PH_FIRST;
-        const double beta = st->beta, gamma = st->gamma;
-        double acc[1] = {0.0};
-        for (int32_t j = t.begin + threadIdx.x; j < t.end; j += kThreads) {
-            const double uj = double(u[j]);
-            const double pn = first ? __dmul_rn(gamma, uj)
-                                    : __dadd_rn(__dmul_rn(beta, double(p[j])), __dmul_rn(gamma, uj));
-            const S ps = S(pn);
-            p[j] = ps;
-            const double pd = double(ps);
-            acc[0] += a.w ? __ddiv_rn(__dmul_rn(pd, pd), a.w[j]) : __dmul_rn(pd, pd);
-            a.x[j] = __dadd_rn(a.x[j], pd);
+    double *__restrict__ x = a.x;
+    const double *__restrict__ w = a.w;
+    double acc = 0.0;
+    constexpr int U = 4;
+    for (int32_t base = t.begin; base < t.end; base += kThreads * U) {
+        double uj[U], pj[U], xj[U], wj[U];
+#pragma unroll
+        for (int q = 0; q < U; ++q) {
+            const int32_t j = base + threadIdx.x + q * kThreads;
+            const bool in = j < t.end;
+            uj[q] = in ? double(u[j]) : 0.0;
+            pj[q] = in && !first ? double(p[j]) : 0.0;
+            xj[q] = in ? x[j] : 0.0;
+            wj[q] = in && w ? w[j] : 1.0;
         }
+#pragma unroll
+        for (int q = 0; q < U; ++q) {
+            const int32_t j = base + threadIdx.x + q * kThreads;
+            if (j < t.end) {
+                const double pn = first ? __dmul_rn(gamma, uj[q])
+                                        : __dadd_rn(__dmul_rn(beta, pj[q]), __dmul_rn(gamma, uj[q]));
+                const S ps = S(pn);
+                p[j] = ps;
+                const double pd = double(ps);
+                acc += w ? __ddiv_rn(__dmul_rn(pd, pd), wj[q]) : __dmul_rn(pd, pd);
+                x[j] = __dadd_rn(xj[q], pd);
+            }
+        }
+    }
+    return acc;
+}
+
+template <typename S>
+__global__ void __launch_bounds__(kThreads) k_update(SweepArgs a) {
+    int32_t t0, t1;
+    tile_range(a.n_vtiles, t0, t1);
+    int32_t cur = -1;
+    uint32_t pending = 0;
+    bool active = false, first = false;
+    double beta = 0.0, gamma = 0.0;
+    for (int32_t ti = t0; ti < t1; ++ti) {
+        const Tile t = a.vtiles[ti];
+        if (t.sys != cur) {
+            if (pending && arrive(&a.st[cur].cnt_upd, pending, a.desc[cur].vt_count)) finish_upd(a, cur);
+            cur = t.sys;
+            pending = 0;
+            const int32_t ph = load_phase(a.st + cur);
+            active = ph == PH_FIRST || ph == PH_RUN;
+            first = ph == PH_FIRST;
+            beta = a.st[cur].beta;
+            gamma = a.st[cur].gamma;
+        }
+        if (!active) continue;
+        double acc[1] = {update_tile<S>(a, t, first, beta, gamma)};
         cta_sum<1>(acc);
         if (threadIdx.x == 0) a.part_upd[ti] = acc[0];
-        if (tile_arrive(&st->cnt_upd, a.desc[t.sys].vt_count)) finish_upd(a, t.sys);
+        ++pending;
     }
+    if (pending && arrive(&a.st[cur].cnt_upd, pending, a.desc[cur].vt_count)) finish_upd(a, cur);
 }
 
 // ---------------------------------------------------------------------------
 // Auxiliary kernels: products in double, residual norms, column weights
 // ---------------------------------------------------------------------------
 
-template <int G, typename S>
-__device__ __forceinline__ void spmv_tile(const int32_t *ptr, const int32_t *idx, const S *val,
-                                          const Tile &t, const double *v, double *out) {
+template <int G>
+__device__ __forceinline__ void spmv_segments(const int32_t *ptr, const Tile &t, const double *prod,
+                                              double *out) {
     for_segments<G>(ptr, t, [&](int32_t seg, int32_t s, int32_t e, int gl, bool valid) {
-        const double d = group_dot<G, S, double, double>(idx, val, s, e, gl, v);
+        const double d = group_sum<G>(prod, s, e, gl);
         if (valid && gl == 0) out[seg] = d;
     });
 }
 
-// out[seg] = sum over the segment of val * v[idx]; with b given, the tile's
-// sum of (b - out)^2 goes to part[tile] (residual norms).
+// out[seg] = sum over the segment of val * v[idx] (double); with b given,
+// part[tile] = sum over the tile of (b - out)^2 (residual norms).
 template <typename S>
 __global__ void __launch_bounds__(kThreads)
 k_spmv(const int32_t *ptr, const int32_t *idx, const void *val_, const Tile *tiles, int32_t ntiles,
        const double *v, double *out, const double *b, double *part) {
+    __shared__ __align__(16) double smem[kStreamNnz];
     const S *val = static_cast<const S *>(val_);
     for (int32_t ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
         const Tile t = tiles[ti];
@@ -432,17 +582,21 @@ k_spmv(const int32_t *ptr, const int32_t *idx, const void *val_, const Tile *til
             const double d = cta_dot<S, double, double>(idx, val, s, e, v);
             if (threadIdx.x == 0) out[t.begin] = d;
         } else {
+            const int32_t z0 = ptr[t.begin];
+            stage_products<S, double, double>(idx, val, z0, ptr[t.end] - z0, v, smem);
+            __syncthreads();
+            const double *prod = smem - z0;
             switch (t.group) {
-                case 1: spmv_tile<1, S>(ptr, idx, val, t, v, out); break;
-                case 2: spmv_tile<2, S>(ptr, idx, val, t, v, out); break;
-                case 4: spmv_tile<4, S>(ptr, idx, val, t, v, out); break;
-                case 8: spmv_tile<8, S>(ptr, idx, val, t, v, out); break;
-                case 16: spmv_tile<16, S>(ptr, idx, val, t, v, out); break;
-                default: spmv_tile<32, S>(ptr, idx, val, t, v, out); break;
+                case 1: spmv_segments<1>(ptr, t, prod, out); break;
+                case 2: spmv_segments<2>(ptr, t, prod, out); break;
+                case 4: spmv_segments<4>(ptr, t, prod, out); break;
+                case 8: spmv_segments<8>(ptr, t, prod, out); break;
+                case 16: spmv_segments<16>(ptr, t, prod, out); break;
+                default: spmv_segments<32>(ptr, t, prod, out); break;
             }
         }
+        __syncthreads();
         if (b != nullptr) {
-            __syncthreads();
             double acc[1] = {0.0};
             for (int32_t i = t.begin + threadIdx.x; i < t.end; i += kThreads) {
                 const double ri = b[i] - out[i];
@@ -474,6 +628,8 @@ __global__ void k_colweights(const int32_t *ptr, const void *val_, int64_t n, in
 // ---------------------------------------------------------------------------
 // Host launchers
 // ---------------------------------------------------------------------------
+
+static_assert(kStreamNnz == 2048, "tile nonzero capacity must match the host tile builder");
 
 cudaError_t launch_row_sweep(const SweepArgs &a, bool f32, int grid, cudaStream_t s) {
     if (f32) k_row_sweep<float><<<grid, kThreads, 0, s>>>(a);

@@ -1,0 +1,576 @@
+// plss_spmm.cu -- many right-hand sides on one matrix (SpMM form of the
+// residual-sketch sweeps of Algorithm 1).
+//
+// With k right-hand sides the vectors become blocks R (m x k), P, U, X
+// (n x k), stored row-major with a row stride of 32, so that one warp owns
+// one matrix row and lane j owns right-hand side j: every nonzero a_ij is
+// read once for all k columns and the gathered row P[col, :] is one
+// coalesced 128/256-byte access. Each column keeps its own scalars (rho, phi,
+// theta, beta, gamma), its own stopping test and its own phase; a finished
+// column is frozen while the others go on.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <vector>
+
+#include "plss.h"
+#include "plss_ctx.h"
+#include "plss_dev.cuh"
+#include "plss_launch.h"
+
+namespace plss {
+
+constexpr int kRhsMax = 32;        // columns per solve (one warp lane each)
+constexpr int kRhsStride = 32;     // row stride of the blocks
+constexpr int kRhsRowsPerTile = 128;
+
+struct RhsArgs {
+    const int32_t *row_ptr, *col_idx;
+    const void *val;
+    const int32_t *col_ptr, *row_idx;
+    const void *cval;
+    const Tile *rtiles, *ctiles, *vtiles;
+    int32_t n_rtiles, n_ctiles, n_vtiles, k;
+    int64_t m, n;
+    SysState *st;        // [k]
+    double *part;        // [max tiles][2][32]
+    uint32_t *cnt;       // [3]
+    int32_t *n_active;
+    const double *B;     // m x 32
+    double *X;           // n x 32
+    void *R, *P, *U;     // storage type, (m|n) x 32
+    const double *w;
+};
+
+struct RhsState {
+    int32_t k = 0;
+    double *d_B = nullptr, *d_X = nullptr;
+    void *d_R = nullptr, *d_P = nullptr, *d_U = nullptr;
+    double *d_part = nullptr;
+    SysState *d_st = nullptr;
+    SysState *h_st = nullptr;
+    uint32_t *d_cnt = nullptr;
+    int32_t *d_active = nullptr;
+    int32_t *h_active = nullptr;
+    Tile *d_rt = nullptr, *d_ct = nullptr, *d_vt = nullptr;
+    int32_t n_rt = 0, n_ct = 0, n_vt = 0;
+    std::map<int, cudaGraphExec_t> graphs;
+    std::vector<double> hbuf;
+};
+
+__device__ __forceinline__ double rhs_fma(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float rhs_fma(float a, float b, float c) { return fmaf(a, b, c); }
+
+// Per-lane sum over the CTA's warps (lane j = column j) into part[0..31]
+// of the tile, fixed order.
+__device__ __forceinline__ void rhs_cta_sum(double v0, double v1, double *out0, double *out1) {
+    __shared__ double sh[2][kWarps][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncthreads();
+    sh[0][warp][lane] = v0;
+    sh[1][warp][lane] = v1;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double s0 = 0.0, s1 = 0.0;
+        for (int w = 0; w < kWarps; ++w) {
+            s0 += sh[0][w][threadIdx.x];
+            s1 += sh[1][w][threadIdx.x];
+        }
+        out0[threadIdx.x] = s0;
+        if (out1) out1[threadIdx.x] = s1;
+    }
+}
+
+// Last CTA of a sweep: sum the tiles' partials per column (fixed order);
+// returns true in the CTA that does it, with sums in sh_out (per lane).
+__device__ __forceinline__ bool rhs_arrive(uint32_t *cnt, int32_t ntiles) {
+    __shared__ int s_last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = atomicAdd(cnt, 1u) == uint32_t(ntiles - 1);
+    }
+    __syncthreads();
+    const bool last = s_last != 0;
+    __syncthreads();
+    if (last) __threadfence();
+    return last;
+}
+
+// In the last CTA: per-column sum of the CTAs' partials (stride 64 doubles
+// per CTA, column j at offset which*32 + j), in a fixed order; the result is
+// valid in threads 0..31.
+__device__ __forceinline__ void rhs_final_sums(const double *part, int32_t nparts, int which,
+                                               double &out) {
+    __shared__ double sh[kWarps][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double s = 0.0;
+    for (int32_t t = warp; t < nparts; t += kWarps) s += __ldcg(part + int64_t(t) * 64 + which * 32 + lane);
+    __syncthreads();
+    sh[warp][lane] = s;
+    __syncthreads();
+    out = 0.0;
+    if (threadIdx.x < 32)
+        for (int w = 0; w < kWarps; ++w) out += sh[w][threadIdx.x];
+}
+
+__device__ __forceinline__ void rhs_done(const RhsArgs &a, SysState *st, int32_t status) {
+    st->status = status;
+    st->phase = PH_DONE;
+    atomicSub(a.n_active, 1);
+}
+
+template <typename S>
+__global__ void __launch_bounds__(kThreads) k_rhs_row(RhsArgs a) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const bool mine = lane < a.k;
+    const int32_t ph = mine ? *reinterpret_cast<const volatile int32_t *>(&a.st[lane].phase) : PH_DONE;
+    const bool init = ph == PH_SETUP;
+    const bool act = init || ph == PH_RUN;
+    const S *val = static_cast<const S *>(a.val);
+    S *R = static_cast<S *>(a.R);
+    const S *P = static_cast<const S *>(a.P);
+    double acc_r = 0.0, acc_b = 0.0;
+    for (int32_t ti = blockIdx.x; ti < a.n_rtiles; ti += gridDim.x) {
+        const Tile t = a.rtiles[ti];
+        for (int32_t row = t.begin + warp; row < t.end; row += kWarps) {
+            const int32_t s = a.row_ptr[row], e = a.row_ptr[row + 1];
+            if (init) {
+                double d = 0.0;
+                for (int32_t q = s; q < e; ++q)
+                    d = fma(double(__ldg(val + q)), a.X[int64_t(__ldg(a.col_idx + q)) * kRhsStride + lane], d);
+                const double bi = a.B[int64_t(row) * kRhsStride + lane];
+                const S ri = S(bi - d);
+                R[int64_t(row) * kRhsStride + lane] = ri;
+                acc_r += double(ri) * double(ri);
+                acc_b += bi * bi;
+            } else if (act) {
+                S d = S(0);
+                for (int32_t q = s; q < e; ++q)
+                    d = rhs_fma(S(__ldg(val + q)), P[int64_t(__ldg(a.col_idx + q)) * kRhsStride + lane], d);
+                const S ri = R[int64_t(row) * kRhsStride + lane] - d;
+                R[int64_t(row) * kRhsStride + lane] = ri;
+                acc_r += double(ri) * double(ri);
+            }
+        }
+    }
+    rhs_cta_sum(acc_r, acc_b, a.part + int64_t(blockIdx.x) * 64, a.part + int64_t(blockIdx.x) * 64 + 32);
+    if (!rhs_arrive(&a.cnt[0], gridDim.x)) return;
+    double rho, nb2;
+    rhs_final_sums(a.part, gridDim.x, 0, rho);
+    rhs_final_sums(a.part, gridDim.x, 1, nb2);
+    if (threadIdx.x < 32 && mine && act) {
+        SysState *st = a.st + lane;
+        if (init) st->nb = sqrt(nb2);
+        const double nb = st->nb;
+        st->rho = rho;
+        if (nb == 0.0) {
+            st->relres_rec = 0.0;
+            rhs_done(a, st, 0);
+        } else {
+            const double rel = sqrt(rho) / nb;
+            st->relres_rec = rel;
+            if (rel <= st->tol) {
+                if (init || !st->stop_on_true) rhs_done(a, st, 0);
+                else {
+                    st->since = 0;
+                    st->phase = PH_SETUP;
+                }
+            } else if (st->iters >= st->maxit) {
+                rhs_done(a, st, 1);
+            } else {
+                st->phase = init ? PH_FIRST : PH_RUN;
+            }
+        }
+    }
+    if (threadIdx.x == 0) a.cnt[0] = 0;
+}
+
+template <typename S>
+__global__ void __launch_bounds__(kThreads) k_rhs_col(RhsArgs a) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const bool mine = lane < a.k;
+    const int32_t ph = mine ? *reinterpret_cast<const volatile int32_t *>(&a.st[lane].phase) : PH_DONE;
+    const bool act = ph == PH_FIRST || ph == PH_RUN;
+    const S *val = static_cast<const S *>(a.cval);
+    const S *R = static_cast<const S *>(a.R);
+    S *U = static_cast<S *>(a.U);
+    double acc = 0.0;
+    for (int32_t ti = blockIdx.x; ti < a.n_ctiles; ti += gridDim.x) {
+        const Tile t = a.ctiles[ti];
+        for (int32_t col = t.begin + warp; col < t.end; col += kWarps) {
+            if (!act) continue;
+            const int32_t s = a.col_ptr[col], e = a.col_ptr[col + 1];
+            S d = S(0);
+            for (int32_t q = s; q < e; ++q)
+                d = rhs_fma(S(__ldg(val + q)), R[int64_t(__ldg(a.row_idx + q)) * kRhsStride + lane], d);
+            const double y = double(d);
+            const S uj = a.w ? S(a.w[col] * y) : S(y);
+            U[int64_t(col) * kRhsStride + lane] = uj;
+            acc += y * double(uj);
+        }
+    }
+    rhs_cta_sum(acc, 0.0, a.part + int64_t(blockIdx.x) * 64, nullptr);
+    if (!rhs_arrive(&a.cnt[1], gridDim.x)) return;
+    double phi;
+    rhs_final_sums(a.part, gridDim.x, 0, phi);
+    if (threadIdx.x < 32 && mine && act) {
+        SysState *st = a.st + lane;
+        st->phi = phi;
+        const double rho = st->rho;
+        if (ph == PH_FIRST) {
+            if (!(phi > 0.0) || !isfinite(phi)) rhs_done(a, st, -4);
+            else {
+                st->beta = 0.0;
+                st->gamma = __ddiv_rn(rho, phi);
+            }
+        } else {
+            const double theta = st->theta;
+            const double sq = __dsqrt_rn(__dmul_rn(theta, phi));
+            const double q = __ddiv_rn(sq, rho);
+            const double dd = __dmul_rn(__dsub_rn(q, 1.0), __dadd_rn(q, 1.0));
+            if (!(dd > 0.0) || !isfinite(dd)) {
+                if (st->stop_on_true) {
+                    st->since = 0;
+                    st->phase = PH_SETUP;
+                } else {
+                    rhs_done(a, st, -4);
+                }
+            } else {
+                const double beta = __ddiv_rn(1.0, dd);
+                st->beta = beta;
+                st->gamma = __dmul_rn(__ddiv_rn(theta, rho), beta);
+            }
+        }
+    }
+    if (threadIdx.x == 0) a.cnt[1] = 0;
+}
+
+template <typename S>
+__global__ void __launch_bounds__(kThreads) k_rhs_update(RhsArgs a) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const bool mine = lane < a.k;
+    const int32_t ph = mine ? *reinterpret_cast<const volatile int32_t *>(&a.st[lane].phase) : PH_DONE;
+    const bool act = ph == PH_FIRST || ph == PH_RUN;
+    const bool first = ph == PH_FIRST;
+    const double beta = act ? a.st[lane].beta : 0.0, gamma = act ? a.st[lane].gamma : 0.0;
+    S *P = static_cast<S *>(a.P);
+    const S *U = static_cast<const S *>(a.U);
+    double acc = 0.0;
+    for (int32_t ti = blockIdx.x; ti < a.n_vtiles; ti += gridDim.x) {
+        const Tile t = a.vtiles[ti];
+        if (act) {
+            for (int32_t j = t.begin + warp; j < t.end; j += kWarps) {
+                const int64_t ix = int64_t(j) * kRhsStride + lane;
+                const double uj = double(U[ix]);
+                const double pn = first ? __dmul_rn(gamma, uj)
+                                        : __dadd_rn(__dmul_rn(beta, double(P[ix])), __dmul_rn(gamma, uj));
+                const S ps = S(pn);
+                P[ix] = ps;
+                const double pd = double(ps);
+                acc += a.w ? __ddiv_rn(__dmul_rn(pd, pd), a.w[j]) : __dmul_rn(pd, pd);
+                a.X[ix] = __dadd_rn(a.X[ix], pd);
+            }
+        }
+    }
+    rhs_cta_sum(acc, 0.0, a.part + int64_t(blockIdx.x) * 64, nullptr);
+    if (!rhs_arrive(&a.cnt[2], gridDim.x)) return;
+    double theta;
+    rhs_final_sums(a.part, gridDim.x, 0, theta);
+    if (threadIdx.x < 32 && mine && act) {
+        SysState *st = a.st + lane;
+        st->theta = theta;
+        const int64_t k = st->iters;
+        if (st->hist && k < st->hist_cap) {
+            double *h = st->hist + 5 * k;
+            h[0] = st->rho;
+            h[1] = st->phi;
+            h[2] = st->beta;
+            h[3] = st->gamma;
+            h[4] = theta;
+        }
+        st->iters = k + 1;
+        st->since += 1;
+        if (st->refine > 0 && st->since >= st->refine) {
+            st->since = 0;
+            st->phase = PH_SETUP;
+        } else {
+            st->phase = PH_RUN;
+        }
+    }
+    if (threadIdx.x == 0) a.cnt[2] = 0;
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+
+void free_rhs(plss_ctx *c) {
+    RhsState *r = c->rhs;
+    if (!r) return;
+    for (auto &kv : r->graphs) cudaGraphExecDestroy(kv.second);
+    void *ptrs[] = {r->d_B, r->d_X, r->d_R, r->d_P, r->d_U, r->d_part, r->d_st, r->d_cnt,
+                    r->d_active, r->d_rt, r->d_ct, r->d_vt};
+    for (void *p : ptrs) dfree(p);
+    if (r->h_st) cudaFreeHost(r->h_st);
+    if (r->h_active) cudaFreeHost(r->h_active);
+    delete r;
+    c->rhs = nullptr;
+}
+
+static void rhs_tiles(int64_t count, std::vector<Tile> &out) {
+    if (count == 0) out.push_back({0, 0, 0, 32});
+    for (int64_t i = 0; i < count; i += kRhsRowsPerTile)
+        out.push_back({0, int32_t(i), int32_t(std::min<int64_t>(count, i + kRhsRowsPerTile)), 32});
+}
+
+static plss_status rhs_prepare(plss_ctx *c) {
+    if (c->rhs) return PLSS_OK;
+    RhsState *r = new RhsState();
+    c->rhs = r;
+    std::vector<Tile> rt, ct, vt;
+    rhs_tiles(c->m, rt);
+    rhs_tiles(c->n, ct);
+    rhs_tiles(c->n, vt);
+    r->n_rt = int32_t(rt.size());
+    r->n_ct = int32_t(ct.size());
+    r->n_vt = int32_t(vt.size());
+    const size_t sb = c->f32 ? 4 : 8;
+    const size_t maxt = size_t(std::max(1, c->nsm * kCtasPerSm));   // one partial per CTA
+    plss_status st;
+    auto up = [&](Tile **d, const std::vector<Tile> &h) -> plss_status {
+        plss_status s2 = dalloc(reinterpret_cast<void **>(d), h.size() * sizeof(Tile), "rhs tiles");
+        if (s2 != PLSS_OK) return s2;
+        if (cudaMemcpy(*d, h.data(), h.size() * sizeof(Tile), cudaMemcpyHostToDevice) != cudaSuccess)
+            return fail(PLSS_ERR_CUDA, "tile upload failed");
+        return PLSS_OK;
+    };
+    if ((st = dalloc(reinterpret_cast<void **>(&r->d_B), 8 * kRhsStride * size_t(c->m), "B")) != PLSS_OK ||
+        (st = dalloc(reinterpret_cast<void **>(&r->d_X), 8 * kRhsStride * size_t(c->n), "X")) != PLSS_OK ||
+        (st = dalloc(&r->d_R, sb * kRhsStride * size_t(c->m), "R")) != PLSS_OK ||
+        (st = dalloc(&r->d_P, sb * kRhsStride * size_t(c->n), "P")) != PLSS_OK ||
+        (st = dalloc(&r->d_U, sb * kRhsStride * size_t(c->n), "U")) != PLSS_OK ||
+        (st = dalloc(reinterpret_cast<void **>(&r->d_part), 8 * 64 * maxt, "partials")) != PLSS_OK ||
+        (st = dalloc(reinterpret_cast<void **>(&r->d_st), sizeof(SysState) * kRhsMax, "state")) != PLSS_OK ||
+        (st = dalloc(reinterpret_cast<void **>(&r->d_cnt), 16, "counters")) != PLSS_OK ||
+        (st = dalloc(reinterpret_cast<void **>(&r->d_active), 16, "active")) != PLSS_OK ||
+        (st = up(&r->d_rt, rt)) != PLSS_OK || (st = up(&r->d_ct, ct)) != PLSS_OK ||
+        (st = up(&r->d_vt, vt)) != PLSS_OK) {
+        free_rhs(c);
+        return st;
+    }
+    if (cudaMemset(r->d_cnt, 0, 16) != cudaSuccess ||
+        cudaMemset(r->d_P, 0, sb * kRhsStride * size_t(c->n)) != cudaSuccess ||
+        cudaMallocHost(reinterpret_cast<void **>(&r->h_st), sizeof(SysState) * kRhsMax) != cudaSuccess ||
+        cudaMallocHost(reinterpret_cast<void **>(&r->h_active), 16) != cudaSuccess) {
+        free_rhs(c);
+        return fail(PLSS_ERR_CUDA, "set-up of the right-hand-side buffers failed");
+    }
+    return PLSS_OK;
+}
+
+static RhsArgs rhs_args(plss_ctx *c, int32_t k, bool w_on) {
+    RhsState *r = c->rhs;
+    RhsArgs a;
+    a.row_ptr = c->d_row_ptr;
+    a.col_idx = c->d_col_idx;
+    a.val = c->d_val;
+    a.col_ptr = c->d_col_ptr;
+    a.row_idx = c->d_row_idx;
+    a.cval = c->d_cval;
+    a.rtiles = r->d_rt;
+    a.ctiles = r->d_ct;
+    a.vtiles = r->d_vt;
+    a.n_rtiles = r->n_rt;
+    a.n_ctiles = r->n_ct;
+    a.n_vtiles = r->n_vt;
+    a.k = k;
+    a.m = c->m;
+    a.n = c->n;
+    a.st = r->d_st;
+    a.part = r->d_part;
+    a.cnt = r->d_cnt;
+    a.n_active = r->d_active;
+    a.B = r->d_B;
+    a.X = r->d_X;
+    a.R = r->d_R;
+    a.P = r->d_P;
+    a.U = r->d_U;
+    a.w = w_on ? c->d_w : nullptr;
+    return a;
+}
+
+static cudaError_t rhs_body(plss_ctx *c, const RhsArgs &a, cudaStream_t s) {
+    const int gr = std::max(1, std::min(a.n_rtiles, c->nsm * kCtasPerSm));
+    const int gc = std::max(1, std::min(a.n_ctiles, c->nsm * kCtasPerSm));
+    const int gv = std::max(1, std::min(a.n_vtiles, c->nsm * kCtasPerSm));
+    if (c->f32) {
+        k_rhs_col<float><<<gc, kThreads, 0, s>>>(a);
+        k_rhs_update<float><<<gv, kThreads, 0, s>>>(a);
+        k_rhs_row<float><<<gr, kThreads, 0, s>>>(a);
+    } else {
+        k_rhs_col<double><<<gc, kThreads, 0, s>>>(a);
+        k_rhs_update<double><<<gv, kThreads, 0, s>>>(a);
+        k_rhs_row<double><<<gr, kThreads, 0, s>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+static plss_status rhs_graph(plss_ctx *c, int chunk, int32_t k, bool w_on, cudaGraphExec_t *out) {
+    RhsState *r = c->rhs;
+    const int key = (chunk * 64 + k) * 2 + (w_on ? 1 : 0);
+    auto it = r->graphs.find(key);
+    if (it != r->graphs.end()) {
+        *out = it->second;
+        return PLSS_OK;
+    }
+    const RhsArgs a = rhs_args(c, k, w_on);
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+        return fail(PLSS_ERR_CUDA, "begin capture failed");
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < chunk && e == cudaSuccess; ++i) e = rhs_body(c, a, c->cap_stream);
+    const cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return fail(PLSS_ERR_CUDA, "capture failed: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+    }
+    cudaGraphExec_t ge = nullptr;
+    const cudaError_t e3 = cudaGraphInstantiate(&ge, g, 0);
+    cudaGraphDestroy(g);
+    if (e3 != cudaSuccess) return fail(PLSS_ERR_CUDA, "instantiate failed: %s", cudaGetErrorString(e3));
+    r->graphs[key] = ge;
+    *out = ge;
+    return PLSS_OK;
+}
+
+// Moves a row-major (rows x k) block between the caller and a stride-32 block.
+static plss_status rhs_put(double *dst, const double *src, int64_t rows, int32_t k, bool dev, cudaStream_t s) {
+    if (rows == 0) return PLSS_OK;
+    if (!src) {
+        if (cudaMemsetAsync(dst, 0, 8 * kRhsStride * size_t(rows), s) != cudaSuccess)
+            return fail(PLSS_ERR_CUDA, "memset failed");
+        return PLSS_OK;
+    }
+    if (cudaMemsetAsync(dst, 0, 8 * kRhsStride * size_t(rows), s) != cudaSuccess ||
+        cudaMemcpy2DAsync(dst, 8 * kRhsStride, src, 8 * size_t(k), 8 * size_t(k), size_t(rows),
+                          dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return fail(PLSS_ERR_CUDA, "copy of a right-hand-side block failed");
+    return PLSS_OK;
+}
+
+plss_status run_rhs(plss_ctx *c, int32_t k, const double *B, const double *X0, double *X,
+                    const plss_opts *o, plss_result *res) {
+    plss_status st = check_opts(o);
+    if (st != PLSS_OK) return st;
+    if (c->nsys != 1) return fail(PLSS_ERR_INVALID, "plss_solve_rhs needs a single-system context");
+    if (k < 1 || k > kRhsMax) return fail(PLSS_ERR_INVALID, "nrhs must be in [1, %d]", kRhsMax);
+    if (o->sketch != PLSS_SKETCH_RESIDUAL) return fail(PLSS_ERR_INVALID, "plss_solve_rhs runs the residual sketch");
+    if ((c->m > 0 && !B) || (c->n > 0 && !X)) return fail(PLSS_ERR_INVALID, "NULL block");
+    if ((st = rhs_prepare(c)) != PLSS_OK) return st;
+    RhsState *r = c->rhs;
+    cudaStream_t s = static_cast<cudaStream_t>(o->stream);
+    const bool dev = o->io_device != 0;
+    if ((st = rhs_put(r->d_B, B, c->m, k, dev, s)) != PLSS_OK) return st;
+    if ((st = rhs_put(r->d_X, X0, c->n, k, dev, s)) != PLSS_OK) return st;
+    if ((st = ensure_weights(c, o->w_mode, s)) != PLSS_OK) return st;
+    const bool w_on = o->w_mode != PLSS_W_IDENTITY;
+    if (o->hist_cap > 0 && o->hist_cap > c->hist_cap_alloc) {
+        dfree(c->d_hist);
+        c->d_hist = nullptr;
+        c->hist_cap_alloc = 0;
+        if ((st = dalloc(reinterpret_cast<void **>(&c->d_hist), size_t(o->hist_cap) * 40, "hist")) != PLSS_OK) return st;
+        c->hist_cap_alloc = o->hist_cap;
+    }
+    if (cudaStreamSynchronize(s) != cudaSuccess) return fail(PLSS_ERR_CUDA, "synchronize failed");
+    const int64_t maxit = o->maxit < 0 ? c->n : o->maxit;
+    for (int32_t j = 0; j < kRhsMax; ++j) {
+        SysState z;
+        std::memset(&z, 0, sizeof z);
+        z.tol = o->tol;
+        z.maxit = maxit;
+        z.refine = c->f32 ? std::max<int64_t>(0, o->refine_period) : 0;
+        z.inner_tol2 = c->f32 ? o->inner_tol * o->inner_tol : 0.0;
+        z.stop_on_true = (c->f32 || o->stop_on_true) ? 1 : 0;
+        z.phase = j < k ? PH_SETUP : PH_DONE;
+        if (j == 0 && o->hist_cap > 0) {
+            z.hist = c->d_hist;
+            z.hist_cap = o->hist_cap;
+        }
+        r->h_st[j] = z;
+    }
+    *r->h_active = k;
+    if (cudaMemcpyAsync(r->d_st, r->h_st, sizeof(SysState) * kRhsMax, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(r->d_active, r->h_active, 4, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaEventRecord(c->ev0, s) != cudaSuccess)
+        return fail(PLSS_ERR_CUDA, "state upload failed");
+    const int64_t body_cap = 2 * (maxit + 2) + 8;
+    int64_t bodies = 0;
+    int chunk = 1;
+    for (;;) {
+        cudaGraphExec_t g;
+        if ((st = rhs_graph(c, chunk, k, w_on, &g)) != PLSS_OK) return st;
+        if (cudaGraphLaunch(g, s) != cudaSuccess ||
+            cudaMemcpyAsync(r->h_active, r->d_active, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return fail(PLSS_ERR_CUDA, "iteration launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+        bodies += chunk;
+        if (*r->h_active <= 0) break;
+        if (bodies > body_cap) return fail(PLSS_ERR_TIMEOUT, "iteration driver exceeded %lld bodies", (long long)body_cap);
+        chunk = std::min(chunk * 4, kMaxChunk);
+    }
+    if (cudaEventRecord(c->ev1, s) != cudaSuccess ||
+        cudaMemcpyAsync(r->h_st, r->d_st, sizeof(SysState) * kRhsMax, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpy2DAsync(X, 8 * size_t(k), r->d_X, 8 * kRhsStride, 8 * size_t(k), size_t(c->n),
+                          dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return fail(PLSS_ERR_CUDA, "reading results failed");
+    if (o->hist_cap > 0) {
+        const int64_t kk = std::min<int64_t>(o->hist_cap, r->h_st[0].iters);
+        if (kk > 0 && cudaMemcpy(o->hist, c->d_hist, size_t(kk) * 40, cudaMemcpyDeviceToHost) != cudaSuccess)
+            return fail(PLSS_ERR_CUDA, "reading the history failed");
+    }
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+    // true residuals, one column at a time through the context's vectors
+    std::vector<double> col(static_cast<size_t>(std::max<int64_t>(c->m, c->n)));
+    plss_status overall = PLSS_OK;
+    for (int32_t j = 0; j < k; ++j) {
+        // x_j and b_j into the single-vector buffers (strided device copies)
+        if (cudaMemcpy2DAsync(c->d_x, 8, r->d_X + j, 8 * kRhsStride, 8, size_t(c->n), cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+            cudaMemcpy2DAsync(c->d_b, 8, r->d_B + j, 8 * kRhsStride, 8, size_t(c->m), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+            return fail(PLSS_ERR_CUDA, "column copy failed");
+        c->h_st[0].nb = r->h_st[j].nb;
+        std::vector<double> rel;
+        if ((st = true_relres(c, s, rel)) != PLSS_OK) return st;
+        const SysState &z = r->h_st[j];
+        if (res) {
+            res[j].status = z.status;
+            res[j].reserved = 0;
+            res[j].iters = z.iters;
+            res[j].relres_rec = z.relres_rec;
+            res[j].relres_true = rel[0];
+            res[j].seconds = double(ms) * 1e-3;
+        }
+        if (overall == PLSS_OK && z.status != PLSS_OK) overall = plss_status(z.status);
+    }
+    return overall;
+}
+
+}  // namespace plss
+
+using namespace plss;
+
+extern "C" plss_status plss_solve_rhs(plss_ctx *ctx, int32_t nrhs, const double *B, const double *X0,
+                                      double *X, const plss_opts *o, plss_result *res) {
+    clear_error();
+    if (!ctx) return fail(PLSS_ERR_INVALID, "ctx is NULL");
+    plss_opts od;
+    plss_opts_default(&od);
+    if (!o) o = &od;
+    return run_rhs(ctx, nrhs, B, X0, X, o, res);
+}

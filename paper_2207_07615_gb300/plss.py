@@ -43,7 +43,7 @@ class Opts(C.Structure):
                 ("refine_period", C.c_int64), ("kacz_hist", C.c_int64), ("seed", C.c_uint64),
                 ("io_device", C.c_int32), ("symmetric", C.c_int32), ("stream", C.c_void_p),
                 ("hist", C.c_void_p), ("hist_cap", C.c_int64), ("profile", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("reserved", C.c_int32), ("inner_tol", C.c_double)]
 
 
 class Result(C.Structure):

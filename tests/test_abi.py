@@ -33,12 +33,13 @@ def test_exports_match_header(L):
 
 
 def test_struct_layouts(L):
-    assert C.sizeof(plss.Opts) == 96
+    assert C.sizeof(plss.Opts) == 104
     assert C.sizeof(plss.Csr) == 56
     assert C.sizeof(plss.Result) == 40
     o = plss.Opts()
     L.plss_opts_default(C.byref(o))
     assert o.tol == 1e-8 and o.maxit == -1 and o.sketch == 0 and o.precision == 0
+    assert o.inner_tol == 1e-4
 
 
 def _create(L, csr):

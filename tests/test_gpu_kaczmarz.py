@@ -1,0 +1,112 @@
+"""GPU parity of the identity sketch (PLSS Kaczmarz, eq:pkKacz, Sec. 7)
+against the CPU oracle, through the C ABI.
+
+Both sides draw the same row order (SplitMix64 stream + Fisher-Yates
+shuffle per pass from the same seed). Tolerance: 1e-10 relative on x, or
+1e3 times the oracle's own rounding spread (the oracle run again on
+b (1 + 2^-50)) where that is larger.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2207_07615_gb300 import synth
+from tests import _pins
+
+pytestmark = pytest.mark.gpu
+
+F = 1.0 + 2.0 ** -50
+
+
+@pytest.fixture(scope="module")
+def plss():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+    from paper_2207_07615_gb300 import plss as P
+    return P
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300))
+
+
+def oracle_with_bar(A, b, maxit, K, seed):
+    r1 = oracle.kaczmarz(A, b, tol=0.0, maxit=maxit, K=K, seed=seed)
+    r2 = oracle.kaczmarz(A, b * F, tol=0.0, maxit=maxit, K=K, seed=seed)
+    spread = rel(r2["x"] / F, r1["x"])
+    return r1, max(1e-10, 1e3 * spread)
+
+
+def test_golden_2x2(plss):
+    """The 2x2 system worked by hand (eq:pkKacz) in both row orders."""
+    g = _pins.load_golden("plss_2x2_hand.txt")
+    A = synth.from_dense(g["A"])
+    seeds = {}
+    for seed in range(200):
+        perm, _ = oracle.permutation(seed, 2)
+        seeds.setdefault(tuple(perm), seed)
+    with plss.Context(A) as ctx:
+        for order, tag in (((0, 1), "kz01"), ((1, 0), "kz10")):
+            s = seeds[order]
+            x1, _ = ctx.solve(g["b"], sketch="identity", kacz_hist=4, seed=s, tol=0.0, maxit=1)
+            x2, _ = ctx.solve(g["b"], sketch="identity", kacz_hist=4, seed=s, tol=0.0, maxit=2)
+            np.testing.assert_allclose(x1, g[tag + "_x1"], rtol=1e-15)
+            np.testing.assert_allclose(x2, g[tag + "_x2"], rtol=1e-14)
+        x2k0, _ = ctx.solve(g["b"], sketch="identity", kacz_hist=0, seed=seeds[(0, 1)], tol=0.0, maxit=2)
+        np.testing.assert_allclose(x2k0, g["kz01_k0_x2"], rtol=1e-14)
+
+
+@pytest.mark.parametrize("K", [0, 1, 4, 16])
+def test_parity_powerlaw_rows(plss, K):
+    """Underdetermined power-law rows (some longer than the CTA), several
+    passes with restarts of the window."""
+    A, b, xs = synth.powerlaw_underdetermined(m=600, n=6000, mean_len=20, max_len=1500, seed=21)
+    A = A.astype(np.float64)
+    with plss.Context(A) as ctx:
+        for maxit, seed in ((1, 3), (7, 3), (600, 5), (2500, 5)):
+            ref, bar = oracle_with_bar(A, b, maxit, K, seed)
+            x, r = ctx.solve(b, sketch="identity", kacz_hist=K, seed=seed, tol=0.0, maxit=maxit)
+            assert r["iters"] == maxit
+            assert rel(x, ref["x"]) <= bar, (K, maxit, rel(x, ref["x"]), bar)
+
+
+def test_converges_and_matches(plss):
+    """A rank-deficient underdetermined power-law system (some rows repeat a
+    single column): the window of 32 reaches 1e-8 where plain Kaczmarz
+    stalls; both sides converge within a few passes of each other to the
+    same limit."""
+    A, b, xs = synth.powerlaw_underdetermined(m=400, n=4000, mean_len=12, max_len=600, seed=22)
+    A = A.astype(np.float64)
+    ref = oracle.kaczmarz(A, b, tol=1e-8, maxit=400 * 300, K=32, seed=9)
+    with plss.Context(A) as ctx:
+        x, r = ctx.solve(b, sketch="identity", kacz_hist=32, seed=9, tol=1e-8, maxit=400 * 300)
+    assert ref["status"] == "converged"
+    assert r["status"] == "converged" and r["relres_true"] <= 1e-8
+    assert abs(r["iters"] - ref["iters"]) <= 0.25 * ref["iters"] + 400
+    assert rel(x, ref["x"]) < 1e-4
+
+
+def test_square_overdetermined_and_x0(plss):
+    A, b, xs = synth.square_diag_dominant(n=300, per_row=5, seed=23)
+    x0 = synth.rng_for(2).standard_normal(300)
+    ref = oracle.kaczmarz(A, b, x0=x0, tol=0.0, maxit=900, K=3, seed=1)
+    with plss.Context(A) as ctx:
+        x, r = ctx.solve(b, x0, sketch="identity", kacz_hist=3, seed=1, tol=0.0, maxit=900)
+    assert rel(x, ref["x"]) < 1e-9
+
+
+def test_batched_identity(plss):
+    """One CTA per system; system s uses the row stream seeded seed + s."""
+    systems = [synth.powerlaw_underdetermined(m=100 + 37 * s, n=900 + 100 * s, mean_len=8,
+                                              max_len=120, seed=40 + s) for s in range(4)]
+    As = [A.astype(np.float64) for A, _, _ in systems]
+    bs = [b for _, b, _ in systems]
+    with plss.Context(As) as ctx:
+        xs, rs = ctx.solve_batched(bs, sketch="identity", kacz_hist=6, seed=100, tol=0.0, maxit=500)
+    for s, (A, b, x, r) in enumerate(zip(As, bs, xs, rs)):
+        ref, bar = oracle_with_bar(A, b, 500, 6, 100 + s)
+        assert r["iters"] == 500
+        assert rel(x, ref["x"]) <= bar
