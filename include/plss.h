@@ -191,37 +191,45 @@ typedef struct plss_server plss_server;
 typedef struct {
     int32_t max_slots;        /* systems resident on the device at once          */
     int32_t max_queue;        /* pending requests before plss_submit says BUSY   */
-    int64_t hbm_budget_bytes; /* admission budget (<= 0: 80% of free memory)     */
+    int64_t hbm_budget_bytes; /* device arena for matrices and vectors; <= 0:    */
+                              /* 4 GiB, capped at 80% of free memory             */
     int32_t precision;        /* PLSS_FP64 / PLSS_FP32 for every request         */
-    int32_t reserved;
+    int32_t bodies_per_poll;  /* iterations run between admission rounds (8)     */
 } plss_server_opts;
 
 void plss_server_opts_default(plss_server_opts *o);
 
-/* Starts a server: a host thread that admits queued requests into device
- * slots while memory and slots allow, and runs all admitted systems
- * together, one block-diagonal sweep per step. */
+/* Starts a server: one host thread owns a device arena sized by the budget
+ * and runs every admitted system together -- each sweep of Algorithm 1 is
+ * one launch over the tiles of all resident systems (continuous batching).
+ * Between rounds of bodies_per_poll iterations it retires finished systems
+ * (freeing their slot and arena ranges) and admits queued requests, in
+ * arrival order, while a slot and arena room for the request's matrix,
+ * transpose and vectors are free. */
 plss_status plss_server_create(const plss_server_opts *so, plss_server **out);
 
 /* Queues one solve. A, b (length A->m) and x0 (length A->n, or NULL) are host
- * arrays, copied before the call returns. o gives tol and maxit (residual
- * sketch). *ticket identifies the request. PLSS_ERR_BUSY when the queue is
- * full; PLSS_ERR_INVALID for a malformed request. */
+ * arrays, copied before the call returns. o gives tol, maxit and w_mode
+ * (residual sketch; the server always verifies convergence on b - A x).
+ * *ticket identifies the request. PLSS_ERR_BUSY when the queue is full or
+ * the request can never fit the arena; PLSS_ERR_INVALID for a malformed
+ * request. Thread-safe. */
 plss_status plss_submit(plss_server *srv, const plss_csr *A, const double *b, const double *x0,
                         const plss_opts *o, uint64_t *ticket);
 
-/* Never blocks. PLSS_PENDING while the request runs; once finished, copies
- * x (length n) to the host array x_out (may be NULL), fills *res (may be
- * NULL; res->seconds = submit-to-completion wall time) and forgets the
- * ticket, returning the solve's status. PLSS_ERR_NOT_FOUND for an unknown
- * or already collected ticket. */
+/* Never blocks. PLSS_PENDING while the request is queued or running; once
+ * finished, copies x (length n) to the host array x_out (may be NULL), fills
+ * *res (may be NULL; res->seconds = submit-to-completion wall time) and
+ * forgets the ticket, returning the solve's status. PLSS_ERR_NOT_FOUND for
+ * an unknown or already collected ticket. Thread-safe. */
 plss_status plss_poll(plss_server *srv, uint64_t ticket, double *x_out, plss_result *res);
 
-/* Counters: completed requests, queued, running, device bytes in use. */
+/* Counters: completed requests, queued, running, arena bytes in use. */
 plss_status plss_server_stats(plss_server *srv, int64_t *completed, int64_t *queued,
                               int64_t *running, int64_t *bytes_in_use);
 
-/* Stops the server thread (pending requests are dropped) and frees it. */
+/* Stops the server thread (pending and running requests are dropped) and
+ * frees its device memory. */
 void plss_server_destroy(plss_server *srv);
 
 #ifdef __cplusplus

@@ -44,9 +44,10 @@
  *     history holds at most K updates and, once full, is emptied before the
  *     next row (which then takes a plain Kaczmarz step, so every stored
  *     update lives on the union of the window's rows); a row whose projected
- *     norm delta is <= 1e-14 ||a_i||^2 is skipped, and an update with
- *     ||p|| = 0 (r_i = 0) is not stored in the history (its theta would
- *     divide by zero in the next projection).
+ *     norm delta is <= 1e-14 ||a_i||^2 is skipped; the window stores each
+ *     row's direction q = p / gamma (the same projector), so a row with
+ *     r_i = 0 still enters it and the window schedule does not depend on
+ *     rounding in b - A x.
  */
 #include <math.h>
 #include <stdint.h>
@@ -377,11 +378,14 @@ void plss_oracle_permutation(uint64_t *state, int64_t m, int32_t *perm)
 
 /*
  * PLSS Kaczmarz (eq:pkKacz): for row i = i_k,
- *   r_i = b_i - a_i^T x;  c_j = p_j^T a_i (j in the history);
+ *   r_i = b_i - a_i^T x;  c_j = q_j^T a_i (j in the history);
  *   ||d||^2 = sum_j c_j^2 / theta_j;
  *   gamma = r_i / ((||a_i|| - ||d||)(||a_i|| + ||d||));
- *   p = gamma (a_i - sum_j (c_j/theta_j) p_j);  x = x + p;
- *   append p and theta = ||p||^2 to the history.
+ *   q = a_i - sum_j (c_j/theta_j) q_j;  p = gamma q;  x = x + p;
+ *   append q and theta = ||q||^2 to the history.
+ * The history holds the directions q_j = p_j / gamma_j: P Theta^{-1} P^T is
+ * the same projector for any column scaling, so this is eq:pkKacz, and a
+ * row with r_i = 0 (p = 0) still enters the window with its direction.
  * With K = 0 (no history) this is the classical Kaczmarz step.
  * maxit caps the rows visited; after every full pass over the rows the
  * residual ||b - A x||/||b|| is tested against tol.
@@ -434,7 +438,7 @@ int plss_oracle_kaczmarz(int64_t m, int64_t n, const int64_t *row_ptr, const int
             double delta = (na - nd) * (na + nd);
             if (!(delta > 1e-14 * a2)) { skipped += 1; continue; }
             double gamma = r_i / delta;
-            /* p = gamma (a_i - sum_j (c_j/theta_j) p_j) */
+            /* q = a_i - sum_j (c_j/theta_j) q_j, p = gamma q, x = x + p */
             for (int64_t jj = 0; jj < n; ++jj) p[jj] = 0.0;
             for (int64_t q = s0; q < s1; ++q) p[col_idx[q]] = val[q];
             for (int64_t j = 0; j < nh; ++j) {
@@ -443,12 +447,10 @@ int plss_oracle_kaczmarz(int64_t m, int64_t n, const int64_t *row_ptr, const int
             }
             double thn = 0.0;
             for (int64_t jj = 0; jj < n; ++jj) {
-                p[jj] = gamma * p[jj];
                 thn += p[jj] * p[jj];
-                x[jj] += p[jj];
+                x[jj] += gamma * p[jj];
             }
             if (K > 0 && thn > 0.0) {
-                /* a zero update (r_i = 0: the row already holds) is not stored */
                 memcpy(P + nh * n, p, (size_t)n * sizeof(double));
                 th[nh] = thn;
                 nh += 1;

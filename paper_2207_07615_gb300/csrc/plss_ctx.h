@@ -71,6 +71,18 @@ struct plss_ctx {
 
 namespace plss {
 
+// Host copy of one CSR with values in double.
+struct HostCsr {
+    int64_t m = 0, n = 0, nnz = 0;
+    std::vector<int64_t> row_ptr;
+    std::vector<int32_t> col_idx;
+    std::vector<double> val;
+};
+
+// Copies and validates a caller's CSR (host or device arrays).
+plss_status fetch_csr(const plss_csr *A, HostCsr &h);
+void build_vec_tiles(int64_t begin, int64_t end, int32_t sys, int64_t chunk, std::vector<Tile> &out);
+
 plss_status fail(plss_status s, const char *fmt, ...);
 void clear_error();
 const char *last_error();

@@ -89,14 +89,6 @@ void build_vec_tiles(int64_t begin, int64_t end, int32_t sys, int64_t chunk, std
 // Validation and packing
 // ---------------------------------------------------------------------------
 
-// Host copy of one CSR with values in double.
-struct HostCsr {
-    int64_t m = 0, n = 0, nnz = 0;
-    std::vector<int64_t> row_ptr;
-    std::vector<int32_t> col_idx;
-    std::vector<double> val;
-};
-
 plss_status fetch_csr(const plss_csr *A, HostCsr &h) {
     if (!A) return fail(PLSS_ERR_INVALID, "A is NULL");
     if (A->m < 0 || A->n < 0 || A->nnz < 0)

@@ -3,7 +3,10 @@
 // For the sketch S_k = [e_{i_1} ... e_{i_k}] the update of eq:pkKacz is
 //   p = gamma (a_i - P Theta^{-1} P^T a_i),
 //   gamma = r_i / ((||a_i|| - ||d||)(||a_i|| + ||d||)),  d = Theta^{-1/2} P^T a_i,
-// with r_i = b_i - a_i^T x, P the stored updates and Theta = diag(||p_j||^2).
+// with r_i = b_i - a_i^T x, P the stored history and Theta = diag(||p_j||^2).
+// The history is kept as the directions q_j = p_j / gamma_j (the projector
+// P Theta^{-1} P^T does not depend on the column scale), so every row that
+// is not skipped enters the window, even when r_i = 0.
 // The window holds at most K updates; once full it is emptied before the
 // next row, so every stored update lives on U, the union of the supports of
 // the window's rows. P is therefore kept compactly as |U| x K (column j =
@@ -155,19 +158,16 @@ __global__ void __launch_bounds__(kKzThreads) k_kacz(KzArgs a) {
             for (int j = 0; j < nh; ++j) d2 += (sh_c[j] * sh_c[j]) / th[j];
             const double na = sqrt(a2), nd = sqrt(d2);
             const double delta = (na - nd) * (na + nd);
-            int skip = !(delta > 1e-14 * a2) ? 1 : 0;
+            const int skip = !(delta > 1e-14 * a2) ? 1 : 0;
             if (!skip) {
                 sh_gamma = ri / delta;
-                // r_i = 0: the row already holds; the zero update changes
-                // nothing and is not stored
-                if (sh_gamma == 0.0) skip = 2;
                 for (int j = 0; j < nh; ++j) sh_c[j] = sh_c[j] / th[j];
             }
             sh_skip = skip;
         }
         __syncthreads();
         if (sh_skip) {
-            skipped += sh_skip == 1;
+            ++skipped;
             continue;
         }
         const double gamma = sh_gamma;
@@ -216,22 +216,22 @@ __global__ void __launch_bounds__(kKzThreads) k_kacz(KzArgs a) {
         for (int32_t k = s0 + tid; k < s1; k += kKzThreads)
             P[int64_t(nh) * ucap + a.slot[a.col_idx[k]]] = double(val[k]);
         __syncthreads();
-        // p = gamma (a_i - sum_j (c_j/theta_j) p_j) on U; x += p; theta = ||p||^2
-        double tp = 0.0, unused = 0.0;
+        // q = a_i - sum_j (c_j/theta_j) q_j on U; x += gamma q; theta = ||q||^2.
+        // The window keeps the directions q (P Theta^{-1} P^T does not depend
+        // on their scale), so a row with r_i = 0 still enters it.
+        double tq = 0.0, unused = 0.0;
         for (int s = tid; s < nU; s += kKzThreads) {
             double v = P[int64_t(nh) * ucap + s];
             for (int j = 0; j < nh; ++j) v = __dsub_rn(v, __dmul_rn(sh_c[j], P[int64_t(j) * ucap + s]));
-            const double p = __dmul_rn(gamma, v);
-            P[int64_t(nh) * ucap + s] = p;
+            P[int64_t(nh) * ucap + s] = v;
             const int32_t c = U[s];
-            a.x[c] = __dadd_rn(a.x[c], p);
-            tp = __dadd_rn(tp, __dmul_rn(p, p));
+            a.x[c] = __dadd_rn(a.x[c], __dmul_rn(gamma, v));
+            tq = __dadd_rn(tq, __dmul_rn(v, v));
         }
-        kz_sum2(tp, unused, sh_red);
+        kz_sum2(tq, unused, sh_red);
         if (tid == 0) {
-            // a zero update (r_i = 0) is not stored
-            sh_store = tp > 0.0;
-            if (tp > 0.0) th[nh] = tp;
+            sh_store = tq > 0.0;
+            if (tq > 0.0) th[nh] = tq;
         }
         __syncthreads();
         nh += sh_store;

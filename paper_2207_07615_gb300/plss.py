@@ -58,7 +58,8 @@ class Result(C.Structure):
 
 class ServerOpts(C.Structure):
     _fields_ = [("max_slots", C.c_int32), ("max_queue", C.c_int32),
-                ("hbm_budget_bytes", C.c_int64), ("precision", C.c_int32), ("reserved", C.c_int32)]
+                ("hbm_budget_bytes", C.c_int64), ("precision", C.c_int32),
+                ("bodies_per_poll", C.c_int32)]
 
 
 _lib = None
@@ -307,11 +308,13 @@ class Context:
 class Server:
     """Continuous-batching solve server (plss_server_*)."""
 
-    def __init__(self, max_slots=64, max_queue=4096, hbm_budget_bytes=0, precision="fp64"):
+    def __init__(self, max_slots=64, max_queue=4096, hbm_budget_bytes=0, precision="fp64",
+                 bodies_per_poll=8):
         L = lib()
         so = ServerOpts()
         L.plss_server_opts_default(C.byref(so))
         so.max_slots, so.max_queue = int(max_slots), int(max_queue)
+        so.bodies_per_poll = int(bodies_per_poll)
         so.hbm_budget_bytes = int(hbm_budget_bytes)
         so.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
         self._h = C.c_void_p()

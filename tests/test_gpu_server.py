@@ -1,0 +1,124 @@
+"""Continuous-batching server (plss_submit / plss_poll) on the GPU.
+
+The key property: a request's result in the mix equals the same request
+solved alone (plss_solve with the same options). Each system's tiles,
+partial sums and reduction order do not depend on its neighbours, so the
+two agree bit for bit.
+"""
+import time
+
+import numpy as np
+import pytest
+
+from paper_2207_07615_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def plss():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+    from paper_2207_07615_gb300 import plss as P
+    return P
+
+
+def requests(count, seed=500, m_lo=300, m_hi=6000):
+    """Serving-shaped requests: m log-uniform, n/m in {0.5, 1, 2}, 8-32
+    nonzeros per row, N(0,1) values, b = A x*."""
+    out = []
+    for i in range(count):
+        rng = synth.rng_for(seed + i)
+        m = int(round(np.exp(rng.uniform(np.log(m_lo), np.log(m_hi)))))
+        n = max(1, int(round(m * (0.5, 1.0, 2.0)[int(rng.integers(0, 3))])))
+        lengths = np.minimum(rng.integers(8, 33, size=m), n).astype(np.int64)
+        cols = synth.distinct_columns(rng, lengths, n)
+        rp = np.zeros(m + 1, dtype=np.int64)
+        np.cumsum(lengths, out=rp[1:])
+        A = synth.CSR(m, n, rp, cols, rng.standard_normal(int(lengths.sum())))
+        out.append((A, synth.rhs(A, rng.standard_normal(n))))
+    return out
+
+
+def drain(srv, tickets, timeout=300.0):
+    res = {}
+    t0 = time.time()
+    while len(res) < len(tickets):
+        for t in tickets:
+            if t in res:
+                continue
+            r = srv.poll(t)
+            if r is not None:
+                res[t] = r
+        assert time.time() - t0 < timeout, "server did not finish in time"
+        time.sleep(0.001)
+    return res
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_mix_equals_alone(plss, precision):
+    reqs = requests(14)
+    kw = dict(tol=1e-6, maxit=3000, w_mode=1)
+    srv = plss.Server(max_slots=4, precision=precision, hbm_budget_bytes=256 << 20)
+    try:
+        tickets = [srv.submit(A, b, **kw) for A, b in reqs]
+        assert all(t is not None for t in tickets)
+        got = drain(srv, tickets)
+        st = srv.stats()
+        assert st["completed"] == len(reqs) and st["queued"] == 0 and st["running"] == 0
+    finally:
+        srv.close()
+    for (A, b), t in zip(reqs, tickets):
+        x_mix, r_mix = got[t]
+        with plss.Context(A, precision=precision) as ctx:
+            x_one, r_one = ctx.solve(b, stop_on_true=1, **kw)
+        assert r_mix["status"] == r_one["status"]
+        assert r_mix["iters"] == r_one["iters"]
+        np.testing.assert_array_equal(x_mix, x_one)
+        if r_mix["status"] == "converged":
+            assert r_mix["relres_true"] <= 1e-6
+        assert r_mix["seconds"] > 0
+
+
+def test_admission_by_memory(plss):
+    """A small arena: requests queue until earlier ones free room."""
+    reqs = requests(10, seed=900, m_lo=2000, m_hi=6000)
+    srv = plss.Server(max_slots=16, hbm_budget_bytes=6 << 20)
+    try:
+        tickets = [srv.submit(A, b, tol=1e-6, maxit=2000, w_mode=1) for A, b in reqs]
+        peak_running, peak_bytes = 0, 0
+        res = {}
+        t0 = time.time()
+        while len(res) < len(tickets):
+            s = srv.stats()
+            peak_running = max(peak_running, s["running"])
+            peak_bytes = max(peak_bytes, s["bytes_in_use"])
+            for t in tickets:
+                if t not in res:
+                    r = srv.poll(t)
+                    if r is not None:
+                        res[t] = r
+            assert time.time() - t0 < 300
+        assert peak_bytes <= 6 << 20
+        assert 1 <= peak_running < len(reqs)
+    finally:
+        srv.close()
+
+
+def test_busy_and_unknown_ticket(plss):
+    srv = plss.Server(max_slots=2, hbm_budget_bytes=1 << 20)
+    try:
+        big, bb = synth.overdetermined_scaled(m=200000, n=50000, per_row=8, seed=3)[:2]
+        assert srv.submit(big, bb) is None                   # can never fit: BUSY
+        with pytest.raises(plss.PlssError):
+            srv.poll(123456)                                 # unknown ticket
+        A, b = requests(1)[0]
+        t = srv.submit(A, b, tol=1e-6, maxit=3000)
+        drain(srv, [t])
+        with pytest.raises(plss.PlssError):
+            srv.poll(t)                                      # already collected
+    finally:
+        srv.close()
