@@ -325,8 +325,10 @@ def run_plss(args):
         t0 = time.perf_counter()
         xh, rh = ctx.solve(b, **kw)
         te.append(time.perf_counter() - t0)
-    e2e = {"value": float(np.mean(te)), "unit": "s", "h2d_bytes_per_step": 8 * m,
-           "d2h_bytes_per_step": 8 * n}
+    e2e = None
+    if te:
+        e2e = {"value": float(np.mean(te)), "unit": "s", "h2d_bytes_per_step": 8 * m,
+               "d2h_bytes_per_step": 8 * n}
 
     variants = {}
     if not args.no_variants and rank == 0:

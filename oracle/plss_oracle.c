@@ -36,9 +36,9 @@
  *     scalar recursion in double, x in double; the residual is recomputed as
  *     b - A x in double and the recursion restarts from it every `refine`
  *     updates and whenever rho has fallen by inner_tol^2 since the last
- *     start -- iterative refinement, which keeps the float recursion away
- *     from its rounding floor where it turns unstable (this extension is not
- *     in the paper).
+ *     start (or risen above 4x its starting value) -- iterative refinement,
+ *     which keeps the float recursion away from its rounding floor where it
+ *     turns unstable (this extension is not in the paper).
  *   - Kaczmarz order: rows are visited without replacement in a fresh
  *     permutation per pass (SplitMix64 stream + Fisher-Yates shuffle); the
  *     history holds at most K updates and, once full, is emptied before the
@@ -248,9 +248,11 @@ int plss_oracle_residual(int64_t m, int64_t n, const int64_t *row_ptr, const int
             continue;
         }
         if (k >= maxit) { status = ORC_NOT_CONVERGED; break; }
-        if (!restart && inner_tol > 0.0 && rho <= inner_tol * inner_tol * rho_start) {
+        if (!restart && inner_tol > 0.0 &&
+            (rho <= inner_tol * inner_tol * rho_start || rho > 4.0 * rho_start)) {
             /* inner solve done (residual reduced by inner_tol since the last
-             * start): refine from b - A x */
+             * start), or the float recursion has drifted above twice its
+             * starting residual: refine from b - A x */
             true_residual(m, row_ptr, col_idx, val, b, x, rt);
             for (int64_t i = 0; i < m; ++i) r[i] = rf(rt[i], f32);
             rho = dot(m, r, r);

@@ -12,8 +12,7 @@
 
 namespace plss {
 
-constexpr int64_t kTileNnz = 2048;      // target nonzeros per sweep tile
-constexpr int64_t kTileMaxSegs = 1024;  // max rows/columns per sweep tile
+constexpr int64_t kTileMaxSegs = 2048;  // max rows/columns per sweep tile
 constexpr int64_t kVecTile = 1024;      // entries per update tile
 constexpr int kCtasPerSm = 8;           // resident CTAs per SM assumed for grids
 constexpr int kMaxChunk = 64;           // bodies per graph launch (max)
@@ -82,6 +81,7 @@ struct HostCsr {
 // Copies and validates a caller's CSR (host or device arrays).
 plss_status fetch_csr(const plss_csr *A, HostCsr &h);
 void build_vec_tiles(int64_t begin, int64_t end, int32_t sys, int64_t chunk, std::vector<Tile> &out);
+int64_t tile_target(int64_t nnz, int nsm, bool f32);
 
 plss_status fail(plss_status s, const char *fmt, ...);
 void clear_error();
@@ -94,7 +94,7 @@ plss_status check_opts(const plss_opts *o);
 plss_status ensure_weights(plss_ctx *c, int32_t w_mode, cudaStream_t s);
 plss_status true_relres(plss_ctx *c, cudaStream_t s, std::vector<double> &rel);
 void build_tiles(const int32_t *ptr, int64_t begin, int64_t end, int32_t sys, int64_t target,
-                 int64_t max_segs, std::vector<Tile> &out);
+                 int64_t max_segs, bool f32, std::vector<Tile> &out);
 
 // identity sketch (plss_kaczmarz.cu)
 plss_status run_identity(plss_ctx *c, const double *b, const double *x0, double *x_out,

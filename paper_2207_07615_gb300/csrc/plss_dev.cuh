@@ -95,6 +95,7 @@ struct SweepArgs {
     void *p;
     void *u;
     const double *w;     // W = diag(w) or nullptr for W = I
+    const double *winv;  // 1/w (theta = p^T W^{-1} p), nullptr with w
 };
 
 }  // namespace plss

@@ -37,11 +37,15 @@ const char *last_error() { return g_err.c_str(); }
 // Tile schedules
 // ---------------------------------------------------------------------------
 
-// Lanes per segment: the smallest power of two >= the mean segment length,
-// clamped to [1, 32].
-static int32_t pick_group(double mean) {
+// Lanes per segment. FP64 sweeps are bound by the FP64 pipe on GB300, so
+// each lane should accumulate about 8 nonzeros (one FMA each, short
+// shuffle tree): the largest power of two <= mean/8. FP32 sweeps have FP32
+// arithmetic to spare and sum staged products from shared memory: the
+// largest power of two <= mean/4. Both within [1, 32].
+static int32_t pick_group(double mean, bool f32) {
+    const double per_lane = f32 ? 4.0 : 8.0;
     int32_t g = 1;
-    while (g < 32 && g < mean) g <<= 1;
+    while (g < 32 && 2.0 * g * per_lane <= mean) g <<= 1;
     return g;
 }
 
@@ -50,7 +54,7 @@ static int32_t pick_group(double mean) {
 // own worked by the whole CTA (group 0). An empty range still gets one
 // (empty) tile so that every system reaches its scalar step.
 void build_tiles(const int32_t *ptr, int64_t begin, int64_t end, int32_t sys, int64_t target,
-                 int64_t max_segs, std::vector<Tile> &out) {
+                 int64_t max_segs, bool f32, std::vector<Tile> &out) {
     if (begin == end) {
         out.push_back({sys, int32_t(begin), int32_t(begin), 1});
         return;
@@ -71,9 +75,19 @@ void build_tiles(const int32_t *ptr, int64_t begin, int64_t end, int32_t sys, in
             nz += l;
             ++j;
         }
-        out.push_back({sys, int32_t(i), int32_t(j), pick_group(double(nz) / double(j - i))});
+        out.push_back({sys, int32_t(i), int32_t(j), pick_group(double(nz) / double(j - i), f32)});
         i = j;
     }
+}
+
+// Nonzeros per sweep tile for a context of nnz nonzeros: about two tiles
+// per resident CTA (a balanced contiguous split), within [1,024, 16,384]
+// (4,096 for FP32 storage).
+int64_t tile_target(int64_t nnz, int nsm, bool f32) {
+    const int64_t slots = int64_t(nsm) * std::max(sweep_ctas_per_sm(0, f32), sweep_ctas_per_sm(1, f32));
+    // FP32 tiles are staged in 16 KB of shared memory (4,096 float products)
+    const int64_t cap = f32 ? 4096 : 16384;
+    return std::min<int64_t>(cap, std::max<int64_t>(1024, (nnz + 2 * slots - 1) / (2 * slots) * 21 / 20));
 }
 
 void build_vec_tiles(int64_t begin, int64_t end, int32_t sys, int64_t chunk, std::vector<Tile> &out) {
@@ -311,14 +325,14 @@ static plss_status ctx_build(const plss_csr *As, int32_t nsys, const plss_opts *
     }
     const int32_t *colp = sym ? rp.data() : cp.data();
 
-    // tile schedules
+    const int64_t target = tile_target(NNZ, c->nsm, c->f32);
     for (int32_t s = 0; s < nsys; ++s) {
         SysDesc &d = c->h_desc[size_t(s)];
         d.rt_begin = int32_t(c->h_rt.size());
-        build_tiles(rp.data(), d.row_off, d.row_off + d.m, s, kTileNnz, kTileMaxSegs, c->h_rt);
+        build_tiles(rp.data(), d.row_off, d.row_off + d.m, s, target, kTileMaxSegs, c->f32, c->h_rt);
         d.rt_count = int32_t(c->h_rt.size()) - d.rt_begin;
         d.ct_begin = int32_t(c->h_ct.size());
-        build_tiles(colp, d.col_off, d.col_off + d.n, s, kTileNnz, kTileMaxSegs, c->h_ct);
+        build_tiles(colp, d.col_off, d.col_off + d.n, s, target, kTileMaxSegs, c->f32, c->h_ct);
         d.ct_count = int32_t(c->h_ct.size()) - d.ct_begin;
         d.vt_begin = int32_t(c->h_vt.size());
         build_vec_tiles(d.col_off, d.col_off + d.n, s, kVecTile, c->h_vt);
@@ -361,7 +375,7 @@ static plss_status ctx_build(const plss_csr *As, int32_t nsys, const plss_opts *
     TRY_ST(dalloc(reinterpret_cast<void **>(&c->d_active), 16, "counter"));
     TRY_ST(dalloc(reinterpret_cast<void **>(&c->d_b), 8 * size_t(M), "b"));
     TRY_ST(dalloc(reinterpret_cast<void **>(&c->d_x), 8 * size_t(N), "x"));
-    TRY_ST(dalloc(reinterpret_cast<void **>(&c->d_w), 8 * size_t(N), "w"));
+    TRY_ST(dalloc(reinterpret_cast<void **>(&c->d_w), 16 * size_t(N), "w"));   // w, then 1/w
     TRY_ST(dalloc(&c->d_r, sb * size_t(M), "r"));
     TRY_ST(dalloc(&c->d_p, sb * size_t(N), "p"));
     TRY_ST(dalloc(&c->d_u, sb * size_t(N), "u"));
@@ -383,9 +397,9 @@ static plss_status ctx_build(const plss_csr *As, int32_t nsys, const plss_opts *
         return fail(PLSS_ERR_CUDA, "stream/event creation failed");
     }
 #undef TRY_ST
-    c->grid_r = std::max(1, std::min(int(c->h_rt.size()), c->nsm * kCtasPerSm));
-    c->grid_c = std::max(1, std::min(int(c->h_ct.size()), c->nsm * kCtasPerSm));
-    c->grid_v = std::max(1, std::min(int(c->h_vt.size()), c->nsm * kCtasPerSm));
+    c->grid_r = std::max(1, std::min(int(c->h_rt.size()), c->nsm * sweep_ctas_per_sm(0, c->f32)));
+    c->grid_c = std::max(1, std::min(int(c->h_ct.size()), c->nsm * sweep_ctas_per_sm(1, c->f32)));
+    c->grid_v = std::max(1, std::min(int(c->h_vt.size()), c->nsm * sweep_ctas_per_sm(2, c->f32)));
 
     SweepArgs &a = c->args;
     a.row_ptr = c->d_row_ptr;
@@ -412,6 +426,7 @@ static plss_status ctx_build(const plss_csr *As, int32_t nsys, const plss_opts *
     a.p = c->d_p;
     a.u = c->d_u;
     a.w = nullptr;
+    a.winv = nullptr;
     *out = c;
     return PLSS_OK;
 }
@@ -429,6 +444,7 @@ static plss_status get_graph(plss_ctx *c, int chunk, bool w_on, bool prof, cudaG
     }
     SweepArgs a = c->args;
     a.w = w_on ? c->d_w : nullptr;
+    a.winv = w_on ? c->d_w + c->n : nullptr;
     cudaGraph_t g = nullptr;
     CUDA_TRY(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaSuccess;
@@ -474,7 +490,7 @@ plss_status ensure_weights(plss_ctx *c, int32_t w_mode, cudaStream_t s) {
     if (w_mode != PLSS_W_COLNORM && w_mode != PLSS_W_COLNORM2)
         return fail(PLSS_ERR_INVALID, "unknown w_mode %d", w_mode);
     if (c->w_mode_cur == w_mode) return PLSS_OK;
-    CUDA_TRY(launch_colweights(c->d_col_ptr, c->d_cval, c->f32, c->n, w_mode, c->d_w, s));
+    CUDA_TRY(launch_colweights(c->d_col_ptr, c->d_cval, c->f32, c->n, w_mode, c->d_w, c->d_w + c->n, s));
     c->w_mode_cur = w_mode;
     return PLSS_OK;
 }

@@ -14,123 +14,169 @@
 //                 (re)start); the last tile then applies the stopping rule
 //                 sqrt(rho)/||b|| <= tol (Sec. 5) and the maxit cap.
 //
-// The sweeps are HBM-bandwidth bound (about 2 flops per 12-16 bytes), so the
-// kernels are plain CUDA-core code built for memory-level parallelism:
-//   * a tile is a run of whole rows (columns) holding at most 2,048
-//     nonzeros; its nonzeros are streamed with coalesced loads, 8 per thread
-//     issued back to back with their gathers, and the products are staged
-//     in shared memory;
-//   * the segments are then summed out of shared memory by groups of G
-//     lanes (G picked per tile from its mean segment length) with a
-//     warp-shuffle tree; a segment longer than a tile gets a tile of its own
-//     that the whole CTA streams;
-//   * each CTA owns a contiguous range of tiles; per-tile FP64 partial sums
-//     of rho / phi / theta are written to global memory and each CTA
-//     announces its tiles with one atomic per system it touched; the CTA
-//     that completes a system sums that system's partials in tile order
-//     (deterministic for a given schedule) and takes its scalar step.
+// The sweeps move ~12-16 bytes per nonzero and, on GB300, also meet the
+// FP64 pipe, which runs at a small fraction of the FP32 rate: a sweep that
+// spends more than about one FP64 operation per nonzero is bound by it
+// rather than by HBM. So the kernels are plain CUDA-core code that
+//   * cut the work into tiles of whole rows (columns) of a few thousand
+//     nonzeros; a group of G lanes works on one segment, G chosen per tile
+//     so that each lane accumulates about 8 nonzeros (one FMA per nonzero,
+//     plus log2(G) shuffle levels per segment);
+//   * issue each lane's 8 index/value loads, then their 8 gathers, before
+//     the first FMA, so every lane keeps 16-24 loads in flight;
+//   * keep per-tile FP64 partial sums of rho / phi / theta in global memory,
+//     reduced with a thread-stride fold in one warp rather than full-warp
+//     shuffle trees;
+//   * give each CTA a contiguous range of tiles, announced with one atomic
+//     per system it touched; the CTA that completes a system sums that
+//     system's partials in tile order (deterministic for a given schedule)
+//     and takes its scalar step.
 #include <cuda_runtime.h>
+
+#include <type_traits>
 
 #include "plss_dev.cuh"
 #include "plss_launch.h"
 
 namespace plss {
 
-constexpr int kUnroll = 8;                       // nonzeros per thread per tile
-constexpr int kStreamNnz = kThreads * kUnroll;   // nonzeros staged per tile
+constexpr int kBatch = 8;   // loads each lane issues before using any of them
 
 __device__ __forceinline__ double fma_t(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ float fma_t(float a, float b, float c) { return fmaf(a, b, c); }
 
-// Fixed-order sum over the CTA of N doubles. Every thread calls it; the
-// result is valid in thread 0.
+// Fixed-order sum over the CTA of N doubles, spending few FP64 operations
+// (GB300 runs FP64 at a small fraction of its FP32 rate): every thread
+// stores its values, warp 0 folds them 8 to a lane, lane 0 adds the 32 lane
+// sums. Every thread calls it; the result is valid in thread 0.
 template <int N>
 __device__ __forceinline__ void cta_sum(double (&v)[N]) {
-    __shared__ double sh[N][kWarps];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int i = 0; i < N; ++i) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
-    }
+    __shared__ double sh[N][kThreads];
+    __shared__ double sh2[N][32];
     __syncthreads();
-    if (lane == 0) {
 #pragma unroll
-        for (int i = 0; i < N; ++i) sh[i][warp] = v[i];
-    }
+    for (int i = 0; i < N; ++i) sh[i][threadIdx.x] = v[i];
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32) {
 #pragma unroll
         for (int i = 0; i < N; ++i) {
-            double s = 0.0;
+            double t = sh[i][threadIdx.x];
 #pragma unroll
-            for (int k = 0; k < kWarps; ++k) s += sh[i][k];
-            v[i] = s;
+            for (int q = 1; q < kWarps; ++q) t += sh[i][threadIdx.x + 32 * q];
+            sh2[i][threadIdx.x] = t;
+        }
+        __syncwarp();
+        if (threadIdx.x == 0) {
+#pragma unroll
+            for (int i = 0; i < N; ++i) {
+                double t = 0.0;
+                for (int l = 0; l < 32; ++l) t += sh2[i][l];
+                v[i] = t;
+            }
         }
     }
 }
 
-// Products val[z0+k] * x[idx[z0+k]] for k < nz (nz <= kStreamNnz) into
-// prod[k]: every thread issues its 8 index/value loads, then its 8 gathers,
-// before using any of them.
-template <typename VT, typename XT, typename PT>
-__device__ __forceinline__ void stage_products(const int32_t *__restrict__ idx,
-                                               const VT *__restrict__ val, int32_t z0, int32_t nz,
-                                               const XT *__restrict__ x, PT *prod) {
-    int32_t c[kUnroll];
-    VT v[kUnroll];
+// Dot product of one sparse segment (nonzeros [s, e)) with a dense vector,
+// split over the G lanes of a group (lane gl takes s+gl, s+gl+G, ...); each
+// lane issues 8 index/value loads, then their 8 gathers, then its 8 FMAs,
+// so one FMA is spent per nonzero plus log2(G) tree levels per segment. The
+// sum lands in every lane of the group. All 32 lanes of the warp must call
+// it (warp-uniform control flow around the call).
+template <int G, typename VT, typename XT, typename ACC>
+__device__ __forceinline__ ACC seg_dot(const int32_t *__restrict__ idx, const VT *__restrict__ val,
+                                       int32_t s, int32_t e, int gl, const XT *__restrict__ x) {
+    ACC acc = ACC(0);
+    for (int32_t base = s + gl; base < e; base += kBatch * G) {
+        int32_t c[kBatch];
+        VT v[kBatch];
 #pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
-        const int32_t k = threadIdx.x + u * kThreads;
-        const bool in = k < nz;
-        c[u] = in ? __ldg(idx + z0 + k) : 0;
-        v[u] = in ? __ldg(val + z0 + k) : VT(0);
-    }
-    XT g[kUnroll];
-#pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
-        const int32_t k = threadIdx.x + u * kThreads;
-        g[u] = k < nz ? __ldg(x + c[u]) : XT(0);
-    }
-#pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
-        const int32_t k = threadIdx.x + u * kThreads;
-        if (k < nz) prod[k] = PT(v[u]) * PT(g[u]);
-    }
-}
-
-// Dot product of one long segment [s, e) with a dense vector, streamed by
-// the whole CTA with 8 independent accumulators per thread; lane partials
-// combined in a fixed order in double (result in thread 0).
-template <typename VT, typename XT, typename ACC>
-__device__ __forceinline__ double cta_dot(const int32_t *__restrict__ idx,
-                                          const VT *__restrict__ val, int32_t s, int32_t e,
-                                          const XT *__restrict__ x) {
-    ACC acc[kUnroll];
-#pragma unroll
-    for (int u = 0; u < kUnroll; ++u) acc[u] = ACC(0);
-    for (int32_t base = s; base < e; base += kStreamNnz) {
-        int32_t c[kUnroll];
-        VT v[kUnroll];
-#pragma unroll
-        for (int u = 0; u < kUnroll; ++u) {
-            const int32_t k = base + threadIdx.x + u * kThreads;
+        for (int u = 0; u < kBatch; ++u) {
+            const int32_t k = base + u * G;
             const bool in = k < e;
             c[u] = in ? __ldg(idx + k) : 0;
             v[u] = in ? __ldg(val + k) : VT(0);
         }
+        XT g[kBatch];
 #pragma unroll
-        for (int u = 0; u < kUnroll; ++u) {
-            const int32_t k = base + threadIdx.x + u * kThreads;
-            if (k < e) acc[u] = fma_t(ACC(v[u]), ACC(__ldg(x + c[u])), acc[u]);
-        }
+        for (int u = 0; u < kBatch; ++u) g[u] = base + u * G < e ? __ldg(x + c[u]) : XT(0);
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u)
+            if (base + u * G < e) acc = fma_t(ACC(v[u]), ACC(g[u]), acc);
     }
-    double t = 0.0;
 #pragma unroll
-    for (int u = 0; u < kUnroll; ++u) t += double(acc[u]);
-    double v1[1] = {t};
+    for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    return acc;
+}
+
+// Dot product of one long segment [s, e) with a dense vector, streamed by
+// the whole CTA in batches of 8 loads per thread; thread partials combined
+// in a fixed order in double (result in thread 0).
+template <typename VT, typename XT, typename ACC>
+__device__ __forceinline__ double cta_dot(const int32_t *__restrict__ idx,
+                                          const VT *__restrict__ val, int32_t s, int32_t e,
+                                          const XT *__restrict__ x) {
+    ACC acc = ACC(0);
+    for (int32_t base = s + threadIdx.x; base < e; base += kBatch * kThreads) {
+        int32_t c[kBatch];
+        VT v[kBatch];
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+            const int32_t k = base + u * kThreads;
+            const bool in = k < e;
+            c[u] = in ? __ldg(idx + k) : 0;
+            v[u] = in ? __ldg(val + k) : VT(0);
+        }
+        XT g[kBatch];
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) g[u] = base + u * kThreads < e ? __ldg(x + c[u]) : XT(0);
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u)
+            if (base + u * kThreads < e) acc = fma_t(ACC(v[u]), ACC(g[u]), acc);
+    }
+    double v1[1] = {double(acc)};
     cta_sum<1>(v1);
     return v1[0];
+}
+
+// FP32 storage: a tile's products are staged in shared memory. Every thread
+// issues 8 coalesced index/value loads, then their 8 gathers, then stores 8
+// float products; the segments are summed out of shared memory afterwards.
+// FP32 arithmetic is plentiful on GB300, so this trades a few float adds for
+// coalesced loads and 16 loads in flight per thread.
+constexpr int kStageNnz = 4096;   // float products staged per tile (16 KB)
+
+__device__ __forceinline__ void stage_f32(const int32_t *__restrict__ idx,
+                                          const float *__restrict__ val, int32_t z0, int32_t nz,
+                                          const float *__restrict__ x, float *prod) {
+    for (int32_t base = threadIdx.x; base < nz; base += kBatch * kThreads) {
+        int32_t c[kBatch];
+        float v[kBatch];
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+            const int32_t k = base + u * kThreads;
+            const bool in = k < nz;
+            c[u] = in ? __ldg(idx + z0 + k) : 0;
+            v[u] = in ? __ldg(val + z0 + k) : 0.0f;
+        }
+        float g[kBatch];
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) g[u] = base + u * kThreads < nz ? __ldg(x + c[u]) : 0.0f;
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+            const int32_t k = base + u * kThreads;
+            if (k < nz) prod[k] = v[u] * g[u];
+        }
+    }
+}
+
+template <int G>
+__device__ __forceinline__ float group_sum_f32(const float *prod, int32_t s, int32_t e, int gl) {
+    float acc = 0.0f;
+    for (int32_t k = s + gl; k < e; k += G) acc += prod[k];
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    return acc;
 }
 
 // Calls body(seg, s, e, gl, valid) for each segment of the tile with groups
@@ -147,17 +193,6 @@ __device__ __forceinline__ void for_segments(const int32_t *__restrict__ ptr, co
         const int32_t e = valid ? __ldg(ptr + seg + 1) : 0;
         body(seg, s, e, gl, valid);
     }
-}
-
-// Sum of the staged products of one segment over the G lanes of a group
-// (lane-strided, then a shuffle tree); valid in every lane of the group.
-template <int G, typename PT>
-__device__ __forceinline__ PT group_sum(const PT *prod, int32_t s, int32_t e, int gl) {
-    PT acc = PT(0);
-    for (int32_t k = s + gl; k < e; k += G) acc += prod[k];
-#pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    return acc;
 }
 
 // Contiguous, balanced share of n tiles for this CTA.
@@ -200,40 +235,45 @@ __device__ __forceinline__ void finish_system(const SweepArgs &a, SysState *st, 
 
 template <int G, typename S>
 __device__ __forceinline__ void row_tile(const SweepArgs &a, const Tile &t, bool init,
-                                         double &acc_r, double &acc_b, double *smem) {
+                                         double &acc_r, double &acc_b, float *prod_sh) {
     const S *__restrict__ val = static_cast<const S *>(a.val);
     S *__restrict__ r = static_cast<S *>(a.r);
-    const int32_t z0 = __ldg(a.row_ptr + t.begin);
-    const int32_t nz = __ldg(a.row_ptr + t.end) - z0;
     if (init) {
-        stage_products<S, double, double>(a.col_idx, val, z0, nz, a.x, smem);
-        __syncthreads();
-        const double *prod = smem - z0;
         for_segments<G>(a.row_ptr, t, [&](int32_t row, int32_t s, int32_t e, int gl, bool valid) {
-            const double d = group_sum<G>(prod, s, e, gl);
+            const double d = seg_dot<G, S, double, double>(a.col_idx, val, s, e, gl, a.x);
             if (valid && gl == 0) {
                 const double bi = a.b[row];
                 const S ri = S(bi - d);
                 r[row] = ri;
-                acc_r += double(ri) * double(ri);
-                acc_b += bi * bi;
+                acc_r = fma(double(ri), double(ri), acc_r);
+                acc_b = fma(bi, bi, acc_b);
             }
         });
-    } else {
-        S *sp = reinterpret_cast<S *>(smem);
-        stage_products<S, S, S>(a.col_idx, val, z0, nz, static_cast<const S *>(a.p), sp);
+    } else if constexpr (std::is_same<S, float>::value) {
+        const int32_t z0 = __ldg(a.row_ptr + t.begin);
+        stage_f32(a.col_idx, val, z0, __ldg(a.row_ptr + t.end) - z0, static_cast<const float *>(a.p), prod_sh);
         __syncthreads();
-        const S *prod = sp - z0;
+        const float *prod = prod_sh - z0;
         for_segments<G>(a.row_ptr, t, [&](int32_t row, int32_t s, int32_t e, int gl, bool valid) {
-            const S d = group_sum<G>(prod, s, e, gl);
+            const float d = group_sum_f32<G>(prod, s, e, gl);
+            if (valid && gl == 0) {
+                const float ri = r[row] - d;
+                r[row] = ri;
+                acc_r = fma(double(ri), double(ri), acc_r);
+            }
+        });
+        __syncthreads();
+    } else {
+        const S *__restrict__ p = static_cast<const S *>(a.p);
+        for_segments<G>(a.row_ptr, t, [&](int32_t row, int32_t s, int32_t e, int gl, bool valid) {
+            const S d = seg_dot<G, S, S, S>(a.col_idx, val, s, e, gl, p);
             if (valid && gl == 0) {
                 const S ri = r[row] - d;
                 r[row] = ri;
-                acc_r += double(ri) * double(ri);
+                acc_r = fma(double(ri), double(ri), acc_r);
             }
         });
     }
-    __syncthreads();
 }
 
 template <typename S>
@@ -251,12 +291,12 @@ __device__ __forceinline__ void row_tile_cta(const SweepArgs &a, const Tile &t, 
             const double bi = a.b[row];
             const S ri = S(bi - d);
             r[row] = ri;
-            acc_r += double(ri) * double(ri);
-            acc_b += bi * bi;
+            acc_r = fma(double(ri), double(ri), acc_r);
+            acc_b = fma(bi, bi, acc_b);
         } else {
             const S ri = r[row] - S(d);
             r[row] = ri;
-            acc_r += double(ri) * double(ri);
+            acc_r = fma(double(ri), double(ri), acc_r);
         }
     }
 }
@@ -295,9 +335,11 @@ __device__ void finish_row(const SweepArgs &a, int32_t sys, bool init) {
         }
     } else if (st->iters >= st->maxit) {
         finish_system(a, st, 1);
-    } else if (!init && st->inner_tol2 > 0.0 && rho <= st->inner_tol2 * st->rho0) {
+    } else if (!init && st->inner_tol2 > 0.0 && (rho <= st->inner_tol2 * st->rho0 || rho > 4.0 * st->rho0)) {
+        // inner solve done, or the float recursion has drifted upwards:
+        // refine from b - A x
         st->since = 0;
-        st->phase = PH_SETUP;       // inner solve done: refine from b - A x
+        st->phase = PH_SETUP;
     } else {
         st->phase = init ? PH_FIRST : PH_RUN;
     }
@@ -305,7 +347,8 @@ __device__ void finish_row(const SweepArgs &a, int32_t sys, bool init) {
 
 template <typename S>
 __global__ void __launch_bounds__(kThreads) k_row_sweep(SweepArgs a) {
-    __shared__ __align__(16) double smem[kStreamNnz];
+    // staging buffer of the FP32 path (unused in FP64)
+    __shared__ __align__(16) float stage[std::is_same<S, float>::value ? kStageNnz : 4];
     int32_t t0, t1;
     tile_range(a.n_rtiles, t0, t1);
     int32_t cur = -1;
@@ -326,12 +369,12 @@ __global__ void __launch_bounds__(kThreads) k_row_sweep(SweepArgs a) {
         double acc[2] = {0.0, 0.0};
         switch (t.group) {
             case 0: row_tile_cta<S>(a, t, init, acc[0], acc[1]); break;
-            case 1: row_tile<1, S>(a, t, init, acc[0], acc[1], smem); break;
-            case 2: row_tile<2, S>(a, t, init, acc[0], acc[1], smem); break;
-            case 4: row_tile<4, S>(a, t, init, acc[0], acc[1], smem); break;
-            case 8: row_tile<8, S>(a, t, init, acc[0], acc[1], smem); break;
-            case 16: row_tile<16, S>(a, t, init, acc[0], acc[1], smem); break;
-            default: row_tile<32, S>(a, t, init, acc[0], acc[1], smem); break;
+            case 1: row_tile<1, S>(a, t, init, acc[0], acc[1], stage); break;
+            case 2: row_tile<2, S>(a, t, init, acc[0], acc[1], stage); break;
+            case 4: row_tile<4, S>(a, t, init, acc[0], acc[1], stage); break;
+            case 8: row_tile<8, S>(a, t, init, acc[0], acc[1], stage); break;
+            case 16: row_tile<16, S>(a, t, init, acc[0], acc[1], stage); break;
+            default: row_tile<32, S>(a, t, init, acc[0], acc[1], stage); break;
         }
         cta_sum<2>(acc);
         if (threadIdx.x == 0) {
@@ -351,23 +394,29 @@ template <typename S>
 __device__ __forceinline__ void col_out(const SweepArgs &a, int32_t col, double y, double &acc) {
     const S uj = a.w ? S(a.w[col] * y) : S(y);
     static_cast<S *>(a.u)[col] = uj;
-    acc += y * double(uj);
+    acc = fma(y, double(uj), acc);
 }
 
 template <int G, typename S>
-__device__ __forceinline__ void col_tile(const SweepArgs &a, const Tile &t, double &acc, double *smem) {
+__device__ __forceinline__ void col_tile(const SweepArgs &a, const Tile &t, double &acc, float *prod_sh) {
     const S *__restrict__ val = static_cast<const S *>(a.cval);
-    const int32_t z0 = __ldg(a.col_ptr + t.begin);
-    const int32_t nz = __ldg(a.col_ptr + t.end) - z0;
-    S *sp = reinterpret_cast<S *>(smem);
-    stage_products<S, S, S>(a.row_idx, val, z0, nz, static_cast<const S *>(a.r), sp);
-    __syncthreads();
-    const S *prod = sp - z0;
-    for_segments<G>(a.col_ptr, t, [&](int32_t col, int32_t s, int32_t e, int gl, bool valid) {
-        const S d = group_sum<G>(prod, s, e, gl);
-        if (valid && gl == 0) col_out<S>(a, col, double(d), acc);
-    });
-    __syncthreads();
+    const S *__restrict__ r = static_cast<const S *>(a.r);
+    if constexpr (std::is_same<S, float>::value) {
+        const int32_t z0 = __ldg(a.col_ptr + t.begin);
+        stage_f32(a.row_idx, val, z0, __ldg(a.col_ptr + t.end) - z0, r, prod_sh);
+        __syncthreads();
+        const float *prod = prod_sh - z0;
+        for_segments<G>(a.col_ptr, t, [&](int32_t col, int32_t s, int32_t e, int gl, bool valid) {
+            const float d = group_sum_f32<G>(prod, s, e, gl);
+            if (valid && gl == 0) col_out<S>(a, col, double(d), acc);
+        });
+        __syncthreads();
+    } else {
+        for_segments<G>(a.col_ptr, t, [&](int32_t col, int32_t s, int32_t e, int gl, bool valid) {
+            const S d = seg_dot<G, S, S, S>(a.row_idx, val, s, e, gl, r);
+            if (valid && gl == 0) col_out<S>(a, col, double(d), acc);
+        });
+    }
 }
 
 template <typename S>
@@ -421,7 +470,7 @@ __device__ void finish_col(const SweepArgs &a, int32_t sys) {
 
 template <typename S>
 __global__ void __launch_bounds__(kThreads) k_col_sweep(SweepArgs a) {
-    __shared__ __align__(16) double smem[kStreamNnz];
+    __shared__ __align__(16) float stage[std::is_same<S, float>::value ? kStageNnz : 4];
     int32_t t0, t1;
     tile_range(a.n_ctiles, t0, t1);
     int32_t cur = -1;
@@ -440,12 +489,12 @@ __global__ void __launch_bounds__(kThreads) k_col_sweep(SweepArgs a) {
         double acc[1] = {0.0};
         switch (t.group) {
             case 0: col_tile_cta<S>(a, t, acc[0]); break;
-            case 1: col_tile<1, S>(a, t, acc[0], smem); break;
-            case 2: col_tile<2, S>(a, t, acc[0], smem); break;
-            case 4: col_tile<4, S>(a, t, acc[0], smem); break;
-            case 8: col_tile<8, S>(a, t, acc[0], smem); break;
-            case 16: col_tile<16, S>(a, t, acc[0], smem); break;
-            default: col_tile<32, S>(a, t, acc[0], smem); break;
+            case 1: col_tile<1, S>(a, t, acc[0], stage); break;
+            case 2: col_tile<2, S>(a, t, acc[0], stage); break;
+            case 4: col_tile<4, S>(a, t, acc[0], stage); break;
+            case 8: col_tile<8, S>(a, t, acc[0], stage); break;
+            case 16: col_tile<16, S>(a, t, acc[0], stage); break;
+            default: col_tile<32, S>(a, t, acc[0], stage); break;
         }
         cta_sum<1>(acc);
         if (threadIdx.x == 0) a.part_col[ti] = acc[0];
@@ -488,37 +537,76 @@ __device__ void finish_upd(const SweepArgs &a, int32_t sys) {
     }
 }
 
+// FP32 storage: p = beta p + gamma u in float (p is stored in float; beta
+// and gamma rounded to float), theta partials in float per thread, x in
+// double -- two FP64-pipe operations per entry.
+__device__ __forceinline__ double update_tile_f32(const SweepArgs &a, const Tile &t, bool first,
+                                                  double beta, double gamma) {
+    float *__restrict__ p = static_cast<float *>(a.p);
+    const float *__restrict__ u = static_cast<const float *>(a.u);
+    double *__restrict__ x = a.x;
+    const double *__restrict__ winv = a.winv;
+    const float bf = float(beta), gf = float(gamma);
+    float acc = 0.0f;
+    constexpr int U = 4;
+    for (int32_t base = t.begin + threadIdx.x; base < t.end; base += kThreads * U) {
+        float uj[U], pj[U], wj[U];
+        double xj[U];
+#pragma unroll
+        for (int q = 0; q < U; ++q) {
+            const int32_t j = base + q * kThreads;
+            const bool in = j < t.end;
+            uj[q] = in ? u[j] : 0.0f;
+            pj[q] = in && !first ? p[j] : 0.0f;
+            xj[q] = in ? x[j] : 0.0;
+            wj[q] = in && winv ? float(winv[j]) : 1.0f;
+        }
+#pragma unroll
+        for (int q = 0; q < U; ++q) {
+            const int32_t j = base + q * kThreads;
+            if (j < t.end) {
+                const float pn = first ? gf * uj[q] : fmaf(bf, pj[q], gf * uj[q]);
+                p[j] = pn;
+                acc = fmaf(pn, pn * wj[q], acc);
+                x[j] = xj[q] + double(pn);
+            }
+        }
+    }
+    return double(acc);
+}
+
 template <typename S>
 __device__ __forceinline__ double update_tile(const SweepArgs &a, const Tile &t, bool first,
                                               double beta, double gamma) {
+    if constexpr (std::is_same<S, float>::value) return update_tile_f32(a, t, first, beta, gamma);
     S *__restrict__ p = static_cast<S *>(a.p);
     const S *__restrict__ u = static_cast<const S *>(a.u);
     double *__restrict__ x = a.x;
-    const double *__restrict__ w = a.w;
+    const double *__restrict__ winv = a.winv;
     double acc = 0.0;
     constexpr int U = 4;
-    for (int32_t base = t.begin; base < t.end; base += kThreads * U) {
+    for (int32_t base = t.begin + threadIdx.x; base < t.end; base += kThreads * U) {
         double uj[U], pj[U], xj[U], wj[U];
 #pragma unroll
         for (int q = 0; q < U; ++q) {
-            const int32_t j = base + threadIdx.x + q * kThreads;
+            const int32_t j = base + q * kThreads;
             const bool in = j < t.end;
             uj[q] = in ? double(u[j]) : 0.0;
             pj[q] = in && !first ? double(p[j]) : 0.0;
             xj[q] = in ? x[j] : 0.0;
-            wj[q] = in && w ? w[j] : 1.0;
+            wj[q] = in && winv ? winv[j] : 1.0;
         }
 #pragma unroll
         for (int q = 0; q < U; ++q) {
-            const int32_t j = base + threadIdx.x + q * kThreads;
+            const int32_t j = base + q * kThreads;
             if (j < t.end) {
-                const double pn = first ? __dmul_rn(gamma, uj[q])
-                                        : __dadd_rn(__dmul_rn(beta, pj[q]), __dmul_rn(gamma, uj[q]));
+                const double gu = gamma * uj[q];
+                const double pn = first ? gu : fma(beta, pj[q], gu);
                 const S ps = S(pn);
                 p[j] = ps;
                 const double pd = double(ps);
-                acc += w ? __ddiv_rn(__dmul_rn(pd, pd), wj[q]) : __dmul_rn(pd, pd);
-                x[j] = __dadd_rn(xj[q], pd);
+                acc = fma(pd, winv ? pd * wj[q] : pd, acc);
+                x[j] = xj[q] + pd;
             }
         }
     }
@@ -558,11 +646,11 @@ __global__ void __launch_bounds__(kThreads) k_update(SweepArgs a) {
 // Auxiliary kernels: products in double, residual norms, column weights
 // ---------------------------------------------------------------------------
 
-template <int G>
-__device__ __forceinline__ void spmv_segments(const int32_t *ptr, const Tile &t, const double *prod,
-                                              double *out) {
+template <int G, typename S>
+__device__ __forceinline__ void spmv_segments(const int32_t *ptr, const int32_t *idx, const S *val,
+                                              const Tile &t, const double *v, double *out) {
     for_segments<G>(ptr, t, [&](int32_t seg, int32_t s, int32_t e, int gl, bool valid) {
-        const double d = group_sum<G>(prod, s, e, gl);
+        const double d = seg_dot<G, S, double, double>(idx, val, s, e, gl, v);
         if (valid && gl == 0) out[seg] = d;
     });
 }
@@ -573,34 +661,29 @@ template <typename S>
 __global__ void __launch_bounds__(kThreads)
 k_spmv(const int32_t *ptr, const int32_t *idx, const void *val_, const Tile *tiles, int32_t ntiles,
        const double *v, double *out, const double *b, double *part) {
-    __shared__ __align__(16) double smem[kStreamNnz];
     const S *val = static_cast<const S *>(val_);
     for (int32_t ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
         const Tile t = tiles[ti];
-        if (t.group == 0) {
-            const int32_t s = ptr[t.begin], e = ptr[t.begin + 1];
-            const double d = cta_dot<S, double, double>(idx, val, s, e, v);
-            if (threadIdx.x == 0) out[t.begin] = d;
-        } else {
-            const int32_t z0 = ptr[t.begin];
-            stage_products<S, double, double>(idx, val, z0, ptr[t.end] - z0, v, smem);
-            __syncthreads();
-            const double *prod = smem - z0;
-            switch (t.group) {
-                case 1: spmv_segments<1>(ptr, t, prod, out); break;
-                case 2: spmv_segments<2>(ptr, t, prod, out); break;
-                case 4: spmv_segments<4>(ptr, t, prod, out); break;
-                case 8: spmv_segments<8>(ptr, t, prod, out); break;
-                case 16: spmv_segments<16>(ptr, t, prod, out); break;
-                default: spmv_segments<32>(ptr, t, prod, out); break;
+        switch (t.group) {
+            case 0: {
+                const int32_t s = ptr[t.begin], e = ptr[t.begin + 1];
+                const double d = cta_dot<S, double, double>(idx, val, s, e, v);
+                if (threadIdx.x == 0) out[t.begin] = d;
+                break;
             }
+            case 1: spmv_segments<1, S>(ptr, idx, val, t, v, out); break;
+            case 2: spmv_segments<2, S>(ptr, idx, val, t, v, out); break;
+            case 4: spmv_segments<4, S>(ptr, idx, val, t, v, out); break;
+            case 8: spmv_segments<8, S>(ptr, idx, val, t, v, out); break;
+            case 16: spmv_segments<16, S>(ptr, idx, val, t, v, out); break;
+            default: spmv_segments<32, S>(ptr, idx, val, t, v, out); break;
         }
         __syncthreads();
         if (b != nullptr) {
             double acc[1] = {0.0};
             for (int32_t i = t.begin + threadIdx.x; i < t.end; i += kThreads) {
                 const double ri = b[i] - out[i];
-                acc[0] += ri * ri;
+                acc[0] = fma(ri, ri, acc[0]);
             }
             cta_sum<1>(acc);
             if (threadIdx.x == 0) part[ti] = acc[0];
@@ -610,9 +693,11 @@ k_spmv(const int32_t *ptr, const int32_t *idx, const void *val_, const Tile *til
 }
 
 // w_j from the squared norm of column j (segments of the CSC, ascending
-// rows): mode 1 -> 1/||A_j||, mode 2 -> 1/||A_j||^2, empty column -> 1.
+// rows): mode 1 -> 1/||A_j||, mode 2 -> 1/||A_j||^2, empty column -> 1;
+// winv_j = 1/w_j for theta = p^T W^{-1} p.
 template <typename S>
-__global__ void k_colweights(const int32_t *ptr, const void *val_, int64_t n, int32_t mode, double *w) {
+__global__ void k_colweights(const int32_t *ptr, const void *val_, int64_t n, int32_t mode, double *w,
+                             double *winv) {
     const S *val = static_cast<const S *>(val_);
     for (int64_t j = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; j < n;
          j += int64_t(gridDim.x) * blockDim.x) {
@@ -621,7 +706,14 @@ __global__ void k_colweights(const int32_t *ptr, const void *val_, int64_t n, in
             const double v = double(val[k]);
             ss = __dadd_rn(ss, __dmul_rn(v, v));
         }
-        w[j] = ss == 0.0 ? 1.0 : (mode == 2 ? __ddiv_rn(1.0, ss) : __ddiv_rn(1.0, __dsqrt_rn(ss)));
+        double wj = 1.0, wi = 1.0;
+        if (ss != 0.0) {
+            const double nrm = __dsqrt_rn(ss);
+            wj = mode == 2 ? __ddiv_rn(1.0, ss) : __ddiv_rn(1.0, nrm);
+            wi = mode == 2 ? ss : nrm;
+        }
+        w[j] = wj;
+        winv[j] = wi;
     }
 }
 
@@ -629,7 +721,26 @@ __global__ void k_colweights(const int32_t *ptr, const void *val_, int64_t n, in
 // Host launchers
 // ---------------------------------------------------------------------------
 
-static_assert(kStreamNnz == 2048, "tile nonzero capacity must match the host tile builder");
+int sweep_ctas_per_sm(int which, bool f32) {
+    int n = 0;
+    cudaError_t e = cudaSuccess;
+    switch (which) {
+        case 0: e = f32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_row_sweep<float>, kThreads, 0)
+                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_row_sweep<double>, kThreads, 0);
+                break;
+        case 1: e = f32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_col_sweep<float>, kThreads, 0)
+                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_col_sweep<double>, kThreads, 0);
+                break;
+        default: e = f32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_update<float>, kThreads, 0)
+                         : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_update<double>, kThreads, 0);
+                break;
+    }
+    if (e != cudaSuccess || n < 1) {
+        cudaGetLastError();
+        return 1;
+    }
+    return n;
+}
 
 cudaError_t launch_row_sweep(const SweepArgs &a, bool f32, int grid, cudaStream_t s) {
     if (f32) k_row_sweep<float><<<grid, kThreads, 0, s>>>(a);
@@ -659,11 +770,11 @@ cudaError_t launch_spmv(const int32_t *ptr, const int32_t *idx, const void *val,
 }
 
 cudaError_t launch_colweights(const int32_t *ptr, const void *val, bool f32, int64_t n, int32_t mode,
-                              double *w, cudaStream_t s) {
+                              double *w, double *winv, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     const int grid = int((n + kThreads - 1) / kThreads);
-    if (f32) k_colweights<float><<<grid, kThreads, 0, s>>>(ptr, val, n, mode, w);
-    else k_colweights<double><<<grid, kThreads, 0, s>>>(ptr, val, n, mode, w);
+    if (f32) k_colweights<float><<<grid, kThreads, 0, s>>>(ptr, val, n, mode, w, winv);
+    else k_colweights<double><<<grid, kThreads, 0, s>>>(ptr, val, n, mode, w, winv);
     return cudaGetLastError();
 }
 

@@ -15,14 +15,18 @@ cudaError_t launch_row_sweep(const SweepArgs &a, bool f32, int grid, cudaStream_
 cudaError_t launch_col_sweep(const SweepArgs &a, bool f32, int grid, cudaStream_t s);
 cudaError_t launch_update(const SweepArgs &a, bool f32, int grid, cudaStream_t s);
 
+// Resident CTAs per SM of a sweep kernel (0 row, 1 column, 2 update).
+int sweep_ctas_per_sm(int which, bool f32);
+
 // out[seg] = (A v)[seg] over the segments of `tiles` in double; with b,
 // part[tile] = sum over the tile of (b - out)^2.
 cudaError_t launch_spmv(const int32_t *ptr, const int32_t *idx, const void *val, bool f32,
                         const Tile *tiles, int32_t ntiles, const double *v, double *out,
                         const double *b, double *part, int grid, cudaStream_t s);
 
-// Diagonal weights of Sec. 4.1 from column segments (ptr over n columns).
+// Diagonal weights of Sec. 4.1 from column segments (ptr over n columns):
+// w[j] and winv[j] = 1/w[j].
 cudaError_t launch_colweights(const int32_t *ptr, const void *val, bool f32, int64_t n,
-                              int32_t mode, double *w, cudaStream_t s);
+                              int32_t mode, double *w, double *winv, cudaStream_t s);
 
 }  // namespace plss

@@ -179,8 +179,11 @@ static void srv_prepare(plss_server *s, HostCsr &h, SrvRequest *r) {
         r->v64 = std::move(h.val);
         r->cv64 = std::move(cv);
     }
-    build_tiles(r->rp.data(), 0, h.m, 0, kTileNnz, kTileMaxSegs, r->rt);
-    build_tiles(r->cp.data(), 0, h.n, 0, kTileNnz, kTileMaxSegs, r->ct);
+    // the schedule a single-system context of this request would use, so
+    // that its arithmetic is the same alone and in the mix
+    const int64_t target = tile_target(h.nnz, s->nsm, s->f32);
+    build_tiles(r->rp.data(), 0, h.m, 0, target, kTileMaxSegs, s->f32, r->rt);
+    build_tiles(r->cp.data(), 0, h.n, 0, target, kTileMaxSegs, s->f32, r->ct);
     build_vec_tiles(0, h.n, 0, kVecTile, r->vt);
 }
 
@@ -266,9 +269,11 @@ static bool srv_upload(plss_server *s, SrvRequest *r) {
         if (r->w_mode == PLSS_W_IDENTITY) {
             std::vector<double> ones(static_cast<size_t>(r->n), 1.0);
             SRV_TRY(cudaMemcpyAsync(s->d_w + r->coff, ones.data(), 8 * size_t(r->n), cudaMemcpyHostToDevice, st));
+            SRV_TRY(cudaMemcpyAsync(s->d_w + s->Ncap + r->coff, ones.data(), 8 * size_t(r->n),
+                                    cudaMemcpyHostToDevice, st));
         } else {
             SRV_TRY(launch_colweights(s->d_col_ptr + r->coff, s->d_cval, s->f32, r->n, r->w_mode,
-                                      s->d_w + r->coff, st));
+                                      s->d_w + r->coff, s->d_w + s->Ncap + r->coff, st));
         }
     }
     SysState z;
@@ -351,6 +356,7 @@ static SweepArgs srv_args(plss_server *s) {
     a.p = s->d_p;
     a.u = s->d_u;
     a.w = s->d_w;
+    a.winv = s->d_w + s->Ncap;
     return a;
 }
 
@@ -424,9 +430,9 @@ static void srv_worker(plss_server *s) {
         // iterate
         if (ok) {
             const SweepArgs a = srv_args(s);
-            const int gr = std::max(1, std::min(a.n_rtiles, s->nsm * kCtasPerSm));
-            const int gc = std::max(1, std::min(a.n_ctiles, s->nsm * kCtasPerSm));
-            const int gv = std::max(1, std::min(a.n_vtiles, s->nsm * kCtasPerSm));
+            const int gr = std::max(1, std::min(a.n_rtiles, s->nsm * sweep_ctas_per_sm(0, s->f32)));
+            const int gc = std::max(1, std::min(a.n_ctiles, s->nsm * sweep_ctas_per_sm(1, s->f32)));
+            const int gv = std::max(1, std::min(a.n_vtiles, s->nsm * sweep_ctas_per_sm(2, s->f32)));
             for (int i = 0; i < s->so.bodies_per_poll && ok; ++i) {
                 ok = launch_col_sweep(a, s->f32, gc, s->stream) == cudaSuccess &&
                      launch_update(a, s->f32, gv, s->stream) == cudaSuccess &&
@@ -508,8 +514,8 @@ plss_status plss_server_create(const plss_server_opts *so_in, plss_server **out)
     s->Mcap = std::min<int64_t>(s->Zcap / 8 + 64 * so.max_slots, INT32_MAX / 2);
     s->Ncap = std::min<int64_t>(2 * (s->Zcap / 8) + 64 * so.max_slots, INT32_MAX / 2);
     s->Scap = so.max_slots;
-    s->Tr = 2 * (s->Zcap / kTileNnz) + s->Mcap / kTileMaxSegs + 2 * int64_t(s->Scap) + 16;
-    s->Tc = 2 * (s->Zcap / kTileNnz) + s->Ncap / kTileMaxSegs + 2 * int64_t(s->Scap) + 16;
+    s->Tr = 2 * (s->Zcap / 1024) + s->Mcap / kTileMaxSegs + 2 * int64_t(s->Scap) + 16;
+    s->Tc = 2 * (s->Zcap / 1024) + s->Ncap / kTileMaxSegs + 2 * int64_t(s->Scap) + 16;
     s->Tv = s->Ncap / kVecTile + 2 * int64_t(s->Scap) + 16;
     s->rows.init(s->Mcap);
     s->cols.init(s->Ncap);
@@ -532,7 +538,7 @@ plss_status plss_server_create(const plss_server_opts *so_in, plss_server **out)
     A(reinterpret_cast<void **>(&s->d_x), 8 * size_t(s->Ncap), "arena x");
     A(&s->d_p, size_t(sb) * size_t(s->Ncap), "arena p");
     A(&s->d_u, size_t(sb) * size_t(s->Ncap), "arena u");
-    A(reinterpret_cast<void **>(&s->d_w), 8 * size_t(s->Ncap), "arena w");
+    A(reinterpret_cast<void **>(&s->d_w), 16 * size_t(s->Ncap), "arena w");   // w, then 1/w
     A(reinterpret_cast<void **>(&s->d_part_row), 16 * size_t(s->Tr), "partials");
     A(reinterpret_cast<void **>(&s->d_part_res), 8 * size_t(s->Tr), "partials");
     A(reinterpret_cast<void **>(&s->d_part_col), 8 * size_t(s->Tc), "partials");

@@ -43,6 +43,7 @@ struct RhsArgs {
     double *X;           // n x 32
     void *R, *P, *U;     // storage type, (m|n) x 32
     const double *w;
+    const double *winv;
 };
 
 struct RhsState {
@@ -164,7 +165,10 @@ __global__ void __launch_bounds__(kThreads) k_rhs_row(RhsArgs a) {
     rhs_final_sums(a.part, gridDim.x, 1, nb2);
     if (threadIdx.x < 32 && mine && act) {
         SysState *st = a.st + lane;
-        if (init) st->nb = sqrt(nb2);
+        if (init) {
+            st->nb = sqrt(nb2);
+            st->rho0 = rho;
+        }
         const double nb = st->nb;
         st->rho = rho;
         if (nb == 0.0) {
@@ -181,6 +185,10 @@ __global__ void __launch_bounds__(kThreads) k_rhs_row(RhsArgs a) {
                 }
             } else if (st->iters >= st->maxit) {
                 rhs_done(a, st, 1);
+            } else if (!init && st->inner_tol2 > 0.0 &&
+                       (rho <= st->inner_tol2 * st->rho0 || rho > 4.0 * st->rho0)) {
+                st->since = 0;
+                st->phase = PH_SETUP;
             } else {
                 st->phase = init ? PH_FIRST : PH_RUN;
             }
@@ -271,7 +279,7 @@ __global__ void __launch_bounds__(kThreads) k_rhs_update(RhsArgs a) {
                 const S ps = S(pn);
                 P[ix] = ps;
                 const double pd = double(ps);
-                acc += a.w ? __ddiv_rn(__dmul_rn(pd, pd), a.w[j]) : __dmul_rn(pd, pd);
+                acc = fma(pd, a.winv ? pd * a.winv[j] : pd, acc);
                 a.X[ix] = __dadd_rn(a.X[ix], pd);
             }
         }
@@ -400,6 +408,7 @@ static RhsArgs rhs_args(plss_ctx *c, int32_t k, bool w_on) {
     a.P = r->d_P;
     a.U = r->d_U;
     a.w = w_on ? c->d_w : nullptr;
+    a.winv = w_on ? c->d_w + c->n : nullptr;
     return a;
 }
 

@@ -109,9 +109,9 @@ def test_admission_by_memory(plss):
 
 
 def test_busy_and_unknown_ticket(plss):
-    srv = plss.Server(max_slots=2, hbm_budget_bytes=1 << 20)
+    srv = plss.Server(max_slots=2, hbm_budget_bytes=16 << 20)
     try:
-        big, bb = synth.overdetermined_scaled(m=200000, n=50000, per_row=8, seed=3)[:2]
+        big, bb = synth.overdetermined_scaled(m=400000, n=100000, per_row=8, seed=3)[:2]
         assert srv.submit(big, bb) is None                   # can never fit: BUSY
         with pytest.raises(plss.PlssError):
             srv.poll(123456)                                 # unknown ticket
