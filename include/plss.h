@@ -169,6 +169,33 @@ plss_status plss_solve_rhs(plss_ctx *ctx, int32_t nrhs, const double *B, const d
 plss_status plss_spmv(plss_ctx *ctx, int32_t transpose, const double *v, double *out,
                       const plss_opts *o);
 
+/* r = b - A x and *norm2 = ||r||^2 for callers that cannot allocate device
+ * memory. The paper has no counterpart: this is a service of the library.
+ * Who needs it: code that has handed the whole GPU to its own memory pool
+ * (a framework's caching allocator or arena, where a library cudaMalloc would
+ * fail or fragment the pool), or a latency-critical loop that fixes its
+ * memory at start-up and forbids allocation afterwards. Every other entry
+ * point allocates its workspace in plss_create / plss_server_create; this
+ * one allocates nothing, on the device or the host: its scratch (one partial
+ * sum per block of 1,024 rows and an arrival counter) is a static device
+ * array of about 33 KB that every GPU loading the library holds until the
+ * process exits.
+ *   A: CSR with row_ptr int64 [m+1], col_idx int32 [nnz], val double [nnz];
+ *   x double [n], b double [m], r double [m] (output), norm2 one double
+ *   (output) -- all device memory of the current device, owned by the caller.
+ *   m <= 4,194,304 rows (the scratch capacity); larger m returns
+ *   PLSS_ERR_INVALID without launching anything.
+ * The call is asynchronous on `stream` (a cudaStream_t; NULL = legacy
+ * stream): r and *norm2 are valid once the stream reaches that point. The
+ * first call on a device looks up the scratch's device address (once per
+ * device); make that first call before any stream capture. All calls share
+ * the one scratch array: calls whose kernels overlap on the GPU (different
+ * streams, no ordering between them) race and give wrong sums; the arrival
+ * counter is cleared on the stream before each launch. */
+plss_status plss_residual_noalloc(int64_t m, int64_t n, int64_t nnz, const int64_t *row_ptr,
+                                  const int32_t *col_idx, const double *val, const double *x,
+                                  const double *b, double *r, double *norm2, void *stream);
+
 /* Device time of the residual-sketch sweeps accumulated over the solves of
  * this context that ran with o->profile = 1: ms[0..2] = total milliseconds
  * of the row sweep (r = r - A p, rho), the column sweep (y = A^T r, phi,

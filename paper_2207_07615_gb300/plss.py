@@ -27,7 +27,7 @@ PRECISION = {"fp64": 0, "fp32": 1}
 #: every symbol declared in include/plss.h
 EXPORTS = ["plss_opts_default", "plss_create", "plss_create_batched", "plss_destroy",
            "plss_ctx_info", "plss_solve", "plss_solve_batched", "plss_solve_rhs", "plss_spmv",
-           "plss_kernel_times", "plss_last_error", "plss_server_opts_default", "plss_server_create", "plss_submit",
+           "plss_kernel_times", "plss_residual_noalloc", "plss_last_error", "plss_server_opts_default", "plss_server_create", "plss_submit",
            "plss_poll", "plss_server_stats", "plss_server_destroy"]
 
 
@@ -89,6 +89,8 @@ def lib() -> C.CDLL:
             L.plss_solve_rhs.argtypes = [vp, i32, vp, vp, vp, vp, vp]
             L.plss_spmv.argtypes = [vp, i32, vp, vp, vp]
             L.plss_kernel_times.argtypes = [vp, vp, vp, i32]
+            L.plss_residual_noalloc.argtypes = [i64, i64, i64, vp, vp, vp, vp, vp, vp, vp, vp]
+            L.plss_residual_noalloc.restype = C.c_int32
             L.plss_last_error.argtypes = []
             L.plss_last_error.restype = C.c_char_p
             L.plss_server_opts_default.argtypes = [vp]
