@@ -390,7 +390,7 @@ def run_variants(args, A, b, xs, x_ref, ctx, b_dev, flush):
         c32 = plss.Context(A, precision="fp32")
         out["fp32_w2"] = timed(c32, b_dev, w_mode=2, **base)
         out["fp32_w1"] = timed(c32, b_dev, w_mode=1, **base)
-        out["fp32_w0"] = timed(c32, b_dev, w_mode=0, **dict(base, maxit=min(args.maxit, 400000)))
+        out["fp32_w0"] = timed(c32, b_dev, w_mode=0, **dict(base, maxit=min(args.maxit, 200000)))
         c32.close()
     return out
 

@@ -12,7 +12,9 @@
 
 namespace plss {
 
-constexpr int64_t kTileMaxSegs = 2048;  // max rows/columns per sweep tile
+constexpr int64_t kTileMaxSegs = 2048;  // max rows/columns per FP64 sweep tile
+constexpr int64_t kTileMaxSegsF32 = 1024;   // ... per FP32 tile (shared-memory staging)
+inline int64_t max_segs(bool f32) { return f32 ? kTileMaxSegsF32 : kTileMaxSegs; }
 constexpr int64_t kVecTile = 1024;      // entries per update tile
 constexpr int kCtasPerSm = 8;           // resident CTAs per SM assumed for grids
 constexpr int kMaxChunk = 64;           // bodies per graph launch (max)
@@ -45,6 +47,7 @@ struct plss_ctx {
 
     // iteration vectors
     double *d_b = nullptr, *d_x = nullptr, *d_w = nullptr;
+    float *d_wf = nullptr;   // FP32 storage: float w and 1/w
     void *d_r = nullptr, *d_p = nullptr, *d_u = nullptr;
     double *d_vin = nullptr, *d_vout = nullptr;
     double *d_hist = nullptr;

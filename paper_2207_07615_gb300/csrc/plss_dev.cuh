@@ -96,6 +96,8 @@ struct SweepArgs {
     void *u;
     const double *w;     // W = diag(w) or nullptr for W = I
     const double *winv;  // 1/w (theta = p^T W^{-1} p), nullptr with w
+    const float *wf;     // float copies for the FP32-storage sweeps
+    const float *winvf;
 };
 
 }  // namespace plss

@@ -82,11 +82,11 @@ void build_tiles(const int32_t *ptr, int64_t begin, int64_t end, int32_t sys, in
 
 // Nonzeros per sweep tile for a context of nnz nonzeros: about two tiles
 // per resident CTA (a balanced contiguous split), within [1,024, 16,384]
-// (4,096 for FP32 storage).
+// (2,048 for FP32 storage).
 int64_t tile_target(int64_t nnz, int nsm, bool f32) {
     const int64_t slots = int64_t(nsm) * std::max(sweep_ctas_per_sm(0, f32), sweep_ctas_per_sm(1, f32));
-    // FP32 tiles are staged in 16 KB of shared memory (4,096 float products)
-    const int64_t cap = f32 ? 4096 : 16384;
+    // FP32 tiles are staged in 8 KB of shared memory (2,048 float products)
+    const int64_t cap = f32 ? 2048 : 16384;
     return std::min<int64_t>(cap, std::max<int64_t>(1024, (nnz + 2 * slots - 1) / (2 * slots) * 21 / 20));
 }
 
@@ -219,7 +219,7 @@ static void ctx_free(plss_ctx *c) {
     if (c->ev1) cudaEventDestroy(c->ev1);
     void *ptrs[] = {c->d_row_ptr, c->d_col_idx, c->d_val, c->d_rt, c->d_ct, c->d_vt, c->d_desc,
                     c->d_st, c->d_part_row, c->d_part_col, c->d_part_upd, c->d_part_res, c->d_active,
-                    c->d_b, c->d_x, c->d_w, c->d_r, c->d_p, c->d_u, c->d_hist, c->d_vin, c->d_vout};
+                    c->d_b, c->d_x, c->d_w, c->d_wf, c->d_r, c->d_p, c->d_u, c->d_hist, c->d_vin, c->d_vout};
     for (void *p : ptrs) dfree(p);
     if (!c->symmetric) {
         dfree(c->d_col_ptr);
@@ -329,10 +329,10 @@ static plss_status ctx_build(const plss_csr *As, int32_t nsys, const plss_opts *
     for (int32_t s = 0; s < nsys; ++s) {
         SysDesc &d = c->h_desc[size_t(s)];
         d.rt_begin = int32_t(c->h_rt.size());
-        build_tiles(rp.data(), d.row_off, d.row_off + d.m, s, target, kTileMaxSegs, c->f32, c->h_rt);
+        build_tiles(rp.data(), d.row_off, d.row_off + d.m, s, target, max_segs(c->f32), c->f32, c->h_rt);
         d.rt_count = int32_t(c->h_rt.size()) - d.rt_begin;
         d.ct_begin = int32_t(c->h_ct.size());
-        build_tiles(colp, d.col_off, d.col_off + d.n, s, target, kTileMaxSegs, c->f32, c->h_ct);
+        build_tiles(colp, d.col_off, d.col_off + d.n, s, target, max_segs(c->f32), c->f32, c->h_ct);
         d.ct_count = int32_t(c->h_ct.size()) - d.ct_begin;
         d.vt_begin = int32_t(c->h_vt.size());
         build_vec_tiles(d.col_off, d.col_off + d.n, s, kVecTile, c->h_vt);
@@ -376,6 +376,7 @@ static plss_status ctx_build(const plss_csr *As, int32_t nsys, const plss_opts *
     TRY_ST(dalloc(reinterpret_cast<void **>(&c->d_b), 8 * size_t(M), "b"));
     TRY_ST(dalloc(reinterpret_cast<void **>(&c->d_x), 8 * size_t(N), "x"));
     TRY_ST(dalloc(reinterpret_cast<void **>(&c->d_w), 16 * size_t(N), "w"));   // w, then 1/w
+    if (c->f32) TRY_ST(dalloc(reinterpret_cast<void **>(&c->d_wf), 8 * size_t(N), "wf"));   // float copies
     TRY_ST(dalloc(&c->d_r, sb * size_t(M), "r"));
     TRY_ST(dalloc(&c->d_p, sb * size_t(N), "p"));
     TRY_ST(dalloc(&c->d_u, sb * size_t(N), "u"));
@@ -427,6 +428,8 @@ static plss_status ctx_build(const plss_csr *As, int32_t nsys, const plss_opts *
     a.u = c->d_u;
     a.w = nullptr;
     a.winv = nullptr;
+    a.wf = nullptr;
+    a.winvf = nullptr;
     *out = c;
     return PLSS_OK;
 }
@@ -445,6 +448,8 @@ static plss_status get_graph(plss_ctx *c, int chunk, bool w_on, bool prof, cudaG
     SweepArgs a = c->args;
     a.w = w_on ? c->d_w : nullptr;
     a.winv = w_on ? c->d_w + c->n : nullptr;
+    a.wf = w_on && c->d_wf ? c->d_wf : nullptr;
+    a.winvf = w_on && c->d_wf ? c->d_wf + c->n : nullptr;
     cudaGraph_t g = nullptr;
     CUDA_TRY(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaSuccess;
@@ -490,7 +495,8 @@ plss_status ensure_weights(plss_ctx *c, int32_t w_mode, cudaStream_t s) {
     if (w_mode != PLSS_W_COLNORM && w_mode != PLSS_W_COLNORM2)
         return fail(PLSS_ERR_INVALID, "unknown w_mode %d", w_mode);
     if (c->w_mode_cur == w_mode) return PLSS_OK;
-    CUDA_TRY(launch_colweights(c->d_col_ptr, c->d_cval, c->f32, c->n, w_mode, c->d_w, c->d_w + c->n, s));
+    CUDA_TRY(launch_colweights(c->d_col_ptr, c->d_cval, c->f32, c->n, w_mode, c->d_w, c->d_w + c->n,
+                               c->d_wf, c->d_wf ? c->d_wf + c->n : nullptr, s));
     c->w_mode_cur = w_mode;
     return PLSS_OK;
 }

@@ -45,34 +45,92 @@ constexpr int kBatch = 8;   // loads each lane issues before using any of them
 __device__ __forceinline__ double fma_t(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ float fma_t(float a, float b, float c) { return fmaf(a, b, c); }
 
-// Fixed-order sum over the CTA of N doubles, spending few FP64 operations
-// (GB300 runs FP64 at a small fraction of its FP32 rate): every thread
-// stores its values, warp 0 folds them 8 to a lane, lane 0 adds the 32 lane
-// sums. Every thread calls it; the result is valid in thread 0.
+// Fixed-order sum over the CTA of N doubles: a shuffle tree in every warp,
+// then one over the warp totals. On GB300 a FP64 warp-instruction costs the
+// same whether one lane or 32 are active, so full-warp trees (5 + 3
+// dependent FP64 adds) beat sequential folds. Every thread calls it; the
+// result is valid in thread 0.
 template <int N>
 __device__ __forceinline__ void cta_sum(double (&v)[N]) {
-    __shared__ double sh[N][kThreads];
-    __shared__ double sh2[N][32];
+    __shared__ double sh[N][kWarps];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
+    }
+    __syncthreads();
+    if (lane == 0) {
+#pragma unroll
+        for (int i = 0; i < N; ++i) sh[i][warp] = v[i];
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            double t = lane < kWarps ? sh[i][lane] : 0.0;
+#pragma unroll
+            for (int o = kWarps / 2; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+            v[i] = t;
+        }
+    }
+}
+
+// Double-float accumulator (an unevaluated sum hi + lo of two floats, about
+// 48 significant bits) built from FP32 operations only. The FP32-storage
+// sweeps keep their inner products in it: on GB300 every FP64
+// warp-instruction holds the SM's FP64 pipe for about twenty cycles whether
+// or not all lanes are active, so per-row FP64 epilogues would bound those
+// sweeps. Only the CTA total is converted to double.
+struct DF {
+    float hi, lo;
+};
+
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+    const float s = __fadd_rn(a.hi, b.hi);
+    const float v = __fsub_rn(s, a.hi);
+    float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, v)), __fsub_rn(b.hi, v));
+    e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+    const float h = __fadd_rn(s, e);
+    return {h, __fsub_rn(e, __fsub_rn(h, s))};
+}
+
+// a + x * y with the product split exactly (x*y = p + fma(x, y, -p)).
+__device__ __forceinline__ DF df_add_prod(DF a, float x, float y) {
+    const float p = __fmul_rn(x, y);
+    return df_add(a, DF{p, fmaf(x, y, -p)});
+}
+
+// Fixed-order CTA sum of N double-float values; the double result is valid
+// in thread 0 (three FP64 operations per value, by one thread).
+template <int N>
+__device__ __forceinline__ void cta_sum_df(const DF (&v)[N], double (&out)[N]) {
+    __shared__ float shh[N][kThreads], shl[N][kThreads];
+    __shared__ DF sh2[N][32];
     __syncthreads();
 #pragma unroll
-    for (int i = 0; i < N; ++i) sh[i][threadIdx.x] = v[i];
+    for (int i = 0; i < N; ++i) {
+        shh[i][threadIdx.x] = v[i].hi;
+        shl[i][threadIdx.x] = v[i].lo;
+    }
     __syncthreads();
     if (threadIdx.x < 32) {
 #pragma unroll
         for (int i = 0; i < N; ++i) {
-            double t = sh[i][threadIdx.x];
+            DF t = {shh[i][threadIdx.x], shl[i][threadIdx.x]};
 #pragma unroll
-            for (int q = 1; q < kWarps; ++q) t += sh[i][threadIdx.x + 32 * q];
+            for (int q = 1; q < kWarps; ++q)
+                t = df_add(t, DF{shh[i][threadIdx.x + 32 * q], shl[i][threadIdx.x + 32 * q]});
             sh2[i][threadIdx.x] = t;
         }
         __syncwarp();
-        if (threadIdx.x == 0) {
 #pragma unroll
-            for (int i = 0; i < N; ++i) {
-                double t = 0.0;
-                for (int l = 0; l < 32; ++l) t += sh2[i][l];
-                v[i] = t;
-            }
+        for (int i = 0; i < N; ++i) {
+            DF t = sh2[i][threadIdx.x];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1)
+                t = df_add(t, DF{__shfl_xor_sync(0xffffffffu, t.hi, o), __shfl_xor_sync(0xffffffffu, t.lo, o)});
+            if (threadIdx.x == 0) out[i] = double(t.hi) + double(t.lo);
         }
     }
 }
@@ -140,43 +198,87 @@ __device__ __forceinline__ double cta_dot(const int32_t *__restrict__ idx,
 }
 
 // FP32 storage: a tile's products are staged in shared memory. Every thread
-// issues 8 coalesced index/value loads, then their 8 gathers, then stores 8
-// float products; the segments are summed out of shared memory afterwards.
-// FP32 arithmetic is plentiful on GB300, so this trades a few float adds for
-// coalesced loads and 16 loads in flight per thread.
-constexpr int kStageNnz = 4096;   // float products staged per tile (16 KB)
+// issues its (up to 16) coalesced index/value loads, the tile's segment
+// offsets and (row sweep) old residuals, then its gathers, before storing
+// any float product; the segments are then summed out of shared memory and
+// only the results go back to global memory. FP32 arithmetic is plentiful
+// on GB300, so this trades a few float adds for coalesced loads and two
+// memory round trips per tile.
+constexpr int kStageNnz = 2048;                   // float products staged per tile (8 KB)
+constexpr int kStagePer = kStageNnz / kThreads;   // nonzeros per thread
+constexpr int kStageSegs = 1024;                  // segments per FP32 tile (host: kTileMaxSegsF32)
+constexpr int kStageSegPer = (kStageSegs + 1 + kThreads - 1) / kThreads;
 
-__device__ __forceinline__ void stage_f32(const int32_t *__restrict__ idx,
-                                          const float *__restrict__ val, int32_t z0, int32_t nz,
-                                          const float *__restrict__ x, float *prod) {
-    for (int32_t base = threadIdx.x; base < nz; base += kBatch * kThreads) {
-        int32_t c[kBatch];
-        float v[kBatch];
+struct StageF32 {
+    float prod[kStageNnz];
+    int32_t ptr[kStageSegs + 1];
+    float old[kStageSegs];
+};
+
+// Stages the tile [t.begin, t.end) of ptr/idx/val against x; with `vec`,
+// also old[i] = vec[t.begin + i]. All global loads (indices, values,
+// segment offsets, old values) are issued before any is used, then the
+// gathers, then the shared-memory stores. Ends with __syncthreads().
+__device__ __forceinline__ void stage_tile_f32(const Tile &t, const int32_t *__restrict__ ptr,
+                                               const int32_t *__restrict__ idx,
+                                               const float *__restrict__ val,
+                                               const float *__restrict__ x,
+                                               const float *__restrict__ vec, StageF32 &sm) {
+    const int32_t nseg = t.end - t.begin;
+    const int32_t z0 = __ldg(ptr + t.begin);
+    const int32_t nz = __ldg(ptr + t.end) - z0;
+    int32_t c[kStagePer];
+    float v[kStagePer];
 #pragma unroll
-        for (int u = 0; u < kBatch; ++u) {
-            const int32_t k = base + u * kThreads;
-            const bool in = k < nz;
-            c[u] = in ? __ldg(idx + z0 + k) : 0;
-            v[u] = in ? __ldg(val + z0 + k) : 0.0f;
-        }
-        float g[kBatch];
-#pragma unroll
-        for (int u = 0; u < kBatch; ++u) g[u] = base + u * kThreads < nz ? __ldg(x + c[u]) : 0.0f;
-#pragma unroll
-        for (int u = 0; u < kBatch; ++u) {
-            const int32_t k = base + u * kThreads;
-            if (k < nz) prod[k] = v[u] * g[u];
-        }
+    for (int u = 0; u < kStagePer; ++u) {
+        const int32_t k = threadIdx.x + u * kThreads;
+        const bool in = k < nz;
+        c[u] = in ? __ldg(idx + z0 + k) : 0;
+        v[u] = in ? __ldg(val + z0 + k) : 0.0f;
     }
+    int32_t pq[kStageSegPer];
+    float oq[kStageSegPer];
+#pragma unroll
+    for (int q = 0; q < kStageSegPer; ++q) {
+        const int32_t i = threadIdx.x + q * kThreads;
+        pq[q] = i <= nseg ? __ldg(ptr + t.begin + i) : 0;
+        oq[q] = vec && i < nseg ? vec[t.begin + i] : 0.0f;
+    }
+    float g[kStagePer];
+#pragma unroll
+    for (int u = 0; u < kStagePer; ++u) g[u] = threadIdx.x + u * kThreads < nz ? __ldg(x + c[u]) : 0.0f;
+#pragma unroll
+    for (int q = 0; q < kStageSegPer; ++q) {
+        const int32_t i = threadIdx.x + q * kThreads;
+        if (i <= nseg) sm.ptr[i] = pq[q] - z0;
+        if (i < nseg) sm.old[i] = oq[q];
+    }
+#pragma unroll
+    for (int u = 0; u < kStagePer; ++u) {
+        const int32_t k = threadIdx.x + u * kThreads;
+        if (k < nz) sm.prod[k] = v[u] * g[u];
+    }
+    __syncthreads();
 }
 
-template <int G>
-__device__ __forceinline__ float group_sum_f32(const float *prod, int32_t s, int32_t e, int gl) {
-    float acc = 0.0f;
-    for (int32_t k = s + gl; k < e; k += G) acc += prod[k];
+// Calls body(i, d, gl, valid) with d the sum over segment i of the tile
+// (tile-local index), G lanes per segment; warp-uniform loop.
+template <int G, typename F>
+__device__ __forceinline__ void staged_segments(const Tile &t, const StageF32 &sm, F &&body) {
+    constexpr int SPW = 32 / G;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int gid = lane / G, gl = lane & (G - 1);
+    const int32_t nseg = t.end - t.begin;
+    for (int32_t base = warp * SPW; base < nseg; base += kWarps * SPW) {
+        const int32_t i = base + gid;
+        const bool valid = i < nseg;
+        const int32_t s = valid ? sm.ptr[i] : 0, e = valid ? sm.ptr[i + 1] : 0;
+        float acc = 0.0f;
+        for (int32_t k = s + gl; k < e; k += G) acc += sm.prod[k];
 #pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    return acc;
+        for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        body(i, acc, gl, valid);
+    }
 }
 
 // Calls body(seg, s, e, gl, valid) for each segment of the tile with groups
@@ -194,6 +296,12 @@ __device__ __forceinline__ void for_segments(const int32_t *__restrict__ ptr, co
         body(seg, s, e, gl, valid);
     }
 }
+
+// Programmatic dependent launch: the sweeps are launched so that a kernel
+// may start while its predecessor drains; everything it reads was written
+// by that predecessor, so it first waits for the predecessor's completion
+// (griddepcontrol.wait returns at once when there is none).
+__device__ __forceinline__ void wait_prior_grid() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 // Contiguous, balanced share of n tiles for this CTA.
 __device__ __forceinline__ void tile_range(int32_t n, int32_t &t0, int32_t &t1) {
@@ -235,7 +343,7 @@ __device__ __forceinline__ void finish_system(const SweepArgs &a, SysState *st, 
 
 template <int G, typename S>
 __device__ __forceinline__ void row_tile(const SweepArgs &a, const Tile &t, bool init,
-                                         double &acc_r, double &acc_b, float *prod_sh) {
+                                         double &acc_r, double &acc_b) {
     const S *__restrict__ val = static_cast<const S *>(a.val);
     S *__restrict__ r = static_cast<S *>(a.r);
     if (init) {
@@ -249,31 +357,35 @@ __device__ __forceinline__ void row_tile(const SweepArgs &a, const Tile &t, bool
                 acc_b = fma(bi, bi, acc_b);
             }
         });
-    } else if constexpr (std::is_same<S, float>::value) {
-        const int32_t z0 = __ldg(a.row_ptr + t.begin);
-        stage_f32(a.col_idx, val, z0, __ldg(a.row_ptr + t.end) - z0, static_cast<const float *>(a.p), prod_sh);
-        __syncthreads();
-        const float *prod = prod_sh - z0;
-        for_segments<G>(a.row_ptr, t, [&](int32_t row, int32_t s, int32_t e, int gl, bool valid) {
-            const float d = group_sum_f32<G>(prod, s, e, gl);
-            if (valid && gl == 0) {
-                const float ri = r[row] - d;
-                r[row] = ri;
-                acc_r = fma(double(ri), double(ri), acc_r);
-            }
-        });
-        __syncthreads();
     } else {
         const S *__restrict__ p = static_cast<const S *>(a.p);
         for_segments<G>(a.row_ptr, t, [&](int32_t row, int32_t s, int32_t e, int gl, bool valid) {
+            const S old = valid && gl == 0 ? r[row] : S(0);   // issued before the dot's loads
             const S d = seg_dot<G, S, S, S>(a.col_idx, val, s, e, gl, p);
             if (valid && gl == 0) {
-                const S ri = r[row] - d;
+                const S ri = old - d;
                 r[row] = ri;
                 acc_r = fma(double(ri), double(ri), acc_r);
             }
         });
     }
+}
+
+// FP32 storage, r = r - A p on a staged tile; rho partial in double-float.
+template <int G>
+__device__ __forceinline__ void row_tile_f32(const SweepArgs &a, const Tile &t, DF &acc_r, float *stage) {
+    float *__restrict__ r = static_cast<float *>(a.r);
+    StageF32 &sm = *reinterpret_cast<StageF32 *>(stage);
+    stage_tile_f32(t, a.row_ptr, a.col_idx, static_cast<const float *>(a.val),
+                   static_cast<const float *>(a.p), r, sm);
+    staged_segments<G>(t, sm, [&](int32_t i, float d, int gl, bool valid) {
+        if (valid && gl == 0) {
+            const float ri = sm.old[i] - d;
+            r[t.begin + i] = ri;
+            acc_r = df_add_prod(acc_r, ri, ri);
+        }
+    });
+    __syncthreads();
 }
 
 template <typename S>
@@ -348,7 +460,8 @@ __device__ void finish_row(const SweepArgs &a, int32_t sys, bool init) {
 template <typename S>
 __global__ void __launch_bounds__(kThreads) k_row_sweep(SweepArgs a) {
     // staging buffer of the FP32 path (unused in FP64)
-    __shared__ __align__(16) float stage[std::is_same<S, float>::value ? kStageNnz : 4];
+    __shared__ __align__(16) float stage[std::is_same<S, float>::value ? sizeof(StageF32) / 4 : 4];
+    wait_prior_grid();
     int32_t t0, t1;
     tile_range(a.n_rtiles, t0, t1);
     int32_t cur = -1;
@@ -367,16 +480,31 @@ __global__ void __launch_bounds__(kThreads) k_row_sweep(SweepArgs a) {
         }
         if (!active) continue;
         double acc[2] = {0.0, 0.0};
-        switch (t.group) {
-            case 0: row_tile_cta<S>(a, t, init, acc[0], acc[1]); break;
-            case 1: row_tile<1, S>(a, t, init, acc[0], acc[1], stage); break;
-            case 2: row_tile<2, S>(a, t, init, acc[0], acc[1], stage); break;
-            case 4: row_tile<4, S>(a, t, init, acc[0], acc[1], stage); break;
-            case 8: row_tile<8, S>(a, t, init, acc[0], acc[1], stage); break;
-            case 16: row_tile<16, S>(a, t, init, acc[0], acc[1], stage); break;
-            default: row_tile<32, S>(a, t, init, acc[0], acc[1], stage); break;
+        if (std::is_same<S, float>::value && !init && t.group != 0) {
+            DF f[1] = {{0.0f, 0.0f}};
+            switch (t.group) {
+                case 1: row_tile_f32<1>(a, t, f[0], stage); break;
+                case 2: row_tile_f32<2>(a, t, f[0], stage); break;
+                case 4: row_tile_f32<4>(a, t, f[0], stage); break;
+                case 8: row_tile_f32<8>(a, t, f[0], stage); break;
+                case 16: row_tile_f32<16>(a, t, f[0], stage); break;
+                default: row_tile_f32<32>(a, t, f[0], stage); break;
+            }
+            double o[1];
+            cta_sum_df<1>(f, o);
+            acc[0] = o[0];
+        } else {
+            switch (t.group) {
+                case 0: row_tile_cta<S>(a, t, init, acc[0], acc[1]); break;
+                case 1: row_tile<1, S>(a, t, init, acc[0], acc[1]); break;
+                case 2: row_tile<2, S>(a, t, init, acc[0], acc[1]); break;
+                case 4: row_tile<4, S>(a, t, init, acc[0], acc[1]); break;
+                case 8: row_tile<8, S>(a, t, init, acc[0], acc[1]); break;
+                case 16: row_tile<16, S>(a, t, init, acc[0], acc[1]); break;
+                default: row_tile<32, S>(a, t, init, acc[0], acc[1]); break;
+            }
+            cta_sum<2>(acc);
         }
-        cta_sum<2>(acc);
         if (threadIdx.x == 0) {
             a.part_row[2 * ti] = acc[0];
             a.part_row[2 * ti + 1] = acc[1];
@@ -398,25 +526,32 @@ __device__ __forceinline__ void col_out(const SweepArgs &a, int32_t col, double 
 }
 
 template <int G, typename S>
-__device__ __forceinline__ void col_tile(const SweepArgs &a, const Tile &t, double &acc, float *prod_sh) {
+__device__ __forceinline__ void col_tile(const SweepArgs &a, const Tile &t, double &acc) {
     const S *__restrict__ val = static_cast<const S *>(a.cval);
     const S *__restrict__ r = static_cast<const S *>(a.r);
-    if constexpr (std::is_same<S, float>::value) {
-        const int32_t z0 = __ldg(a.col_ptr + t.begin);
-        stage_f32(a.row_idx, val, z0, __ldg(a.col_ptr + t.end) - z0, r, prod_sh);
-        __syncthreads();
-        const float *prod = prod_sh - z0;
-        for_segments<G>(a.col_ptr, t, [&](int32_t col, int32_t s, int32_t e, int gl, bool valid) {
-            const float d = group_sum_f32<G>(prod, s, e, gl);
-            if (valid && gl == 0) col_out<S>(a, col, double(d), acc);
-        });
-        __syncthreads();
-    } else {
-        for_segments<G>(a.col_ptr, t, [&](int32_t col, int32_t s, int32_t e, int gl, bool valid) {
-            const S d = seg_dot<G, S, S, S>(a.row_idx, val, s, e, gl, r);
-            if (valid && gl == 0) col_out<S>(a, col, double(d), acc);
-        });
-    }
+    for_segments<G>(a.col_ptr, t, [&](int32_t col, int32_t s, int32_t e, int gl, bool valid) {
+        const S d = seg_dot<G, S, S, S>(a.row_idx, val, s, e, gl, r);
+        if (valid && gl == 0) col_out<S>(a, col, double(d), acc);
+    });
+}
+
+// FP32 storage, y = A^T r on a staged tile, u = W y with float weights,
+// phi partial in double-float.
+template <int G>
+__device__ __forceinline__ void col_tile_f32(const SweepArgs &a, const Tile &t, DF &acc, float *stage) {
+    StageF32 &sm = *reinterpret_cast<StageF32 *>(stage);
+    float *__restrict__ u = static_cast<float *>(a.u);
+    stage_tile_f32(t, a.col_ptr, a.row_idx, static_cast<const float *>(a.cval),
+                   static_cast<const float *>(a.r), nullptr, sm);
+    staged_segments<G>(t, sm, [&](int32_t i, float y, int gl, bool valid) {
+        if (valid && gl == 0) {
+            const int32_t col = t.begin + i;
+            const float uj = a.wf ? __fmul_rn(a.wf[col], y) : y;
+            u[col] = uj;
+            acc = df_add_prod(acc, y, uj);
+        }
+    });
+    __syncthreads();
 }
 
 template <typename S>
@@ -470,7 +605,8 @@ __device__ void finish_col(const SweepArgs &a, int32_t sys) {
 
 template <typename S>
 __global__ void __launch_bounds__(kThreads) k_col_sweep(SweepArgs a) {
-    __shared__ __align__(16) float stage[std::is_same<S, float>::value ? kStageNnz : 4];
+    __shared__ __align__(16) float stage[std::is_same<S, float>::value ? sizeof(StageF32) / 4 : 4];
+    wait_prior_grid();
     int32_t t0, t1;
     tile_range(a.n_ctiles, t0, t1);
     int32_t cur = -1;
@@ -487,16 +623,29 @@ __global__ void __launch_bounds__(kThreads) k_col_sweep(SweepArgs a) {
         }
         if (!active) continue;
         double acc[1] = {0.0};
-        switch (t.group) {
-            case 0: col_tile_cta<S>(a, t, acc[0]); break;
-            case 1: col_tile<1, S>(a, t, acc[0], stage); break;
-            case 2: col_tile<2, S>(a, t, acc[0], stage); break;
-            case 4: col_tile<4, S>(a, t, acc[0], stage); break;
-            case 8: col_tile<8, S>(a, t, acc[0], stage); break;
-            case 16: col_tile<16, S>(a, t, acc[0], stage); break;
-            default: col_tile<32, S>(a, t, acc[0], stage); break;
+        if (std::is_same<S, float>::value && t.group != 0) {
+            DF f[1] = {{0.0f, 0.0f}};
+            switch (t.group) {
+                case 1: col_tile_f32<1>(a, t, f[0], stage); break;
+                case 2: col_tile_f32<2>(a, t, f[0], stage); break;
+                case 4: col_tile_f32<4>(a, t, f[0], stage); break;
+                case 8: col_tile_f32<8>(a, t, f[0], stage); break;
+                case 16: col_tile_f32<16>(a, t, f[0], stage); break;
+                default: col_tile_f32<32>(a, t, f[0], stage); break;
+            }
+            cta_sum_df<1>(f, acc);
+        } else {
+            switch (t.group) {
+                case 0: col_tile_cta<S>(a, t, acc[0]); break;
+                case 1: col_tile<1, S>(a, t, acc[0]); break;
+                case 2: col_tile<2, S>(a, t, acc[0]); break;
+                case 4: col_tile<4, S>(a, t, acc[0]); break;
+                case 8: col_tile<8, S>(a, t, acc[0]); break;
+                case 16: col_tile<16, S>(a, t, acc[0]); break;
+                default: col_tile<32, S>(a, t, acc[0]); break;
+            }
+            cta_sum<1>(acc);
         }
-        cta_sum<1>(acc);
         if (threadIdx.x == 0) a.part_col[ti] = acc[0];
         ++pending;
     }
@@ -540,14 +689,14 @@ __device__ void finish_upd(const SweepArgs &a, int32_t sys) {
 // FP32 storage: p = beta p + gamma u in float (p is stored in float; beta
 // and gamma rounded to float), theta partials in float per thread, x in
 // double -- two FP64-pipe operations per entry.
-__device__ __forceinline__ double update_tile_f32(const SweepArgs &a, const Tile &t, bool first,
-                                                  double beta, double gamma) {
+__device__ __forceinline__ DF update_tile_f32(const SweepArgs &a, const Tile &t, bool first, double beta,
+                                              double gamma) {
     float *__restrict__ p = static_cast<float *>(a.p);
     const float *__restrict__ u = static_cast<const float *>(a.u);
     double *__restrict__ x = a.x;
-    const double *__restrict__ winv = a.winv;
+    const float *__restrict__ winv = a.winvf;
     const float bf = float(beta), gf = float(gamma);
-    float acc = 0.0f;
+    DF acc = {0.0f, 0.0f};
     constexpr int U = 4;
     for (int32_t base = t.begin + threadIdx.x; base < t.end; base += kThreads * U) {
         float uj[U], pj[U], wj[U];
@@ -559,7 +708,7 @@ __device__ __forceinline__ double update_tile_f32(const SweepArgs &a, const Tile
             uj[q] = in ? u[j] : 0.0f;
             pj[q] = in && !first ? p[j] : 0.0f;
             xj[q] = in ? x[j] : 0.0;
-            wj[q] = in && winv ? float(winv[j]) : 1.0f;
+            wj[q] = in && winv ? winv[j] : 1.0f;
         }
 #pragma unroll
         for (int q = 0; q < U; ++q) {
@@ -567,18 +716,17 @@ __device__ __forceinline__ double update_tile_f32(const SweepArgs &a, const Tile
             if (j < t.end) {
                 const float pn = first ? gf * uj[q] : fmaf(bf, pj[q], gf * uj[q]);
                 p[j] = pn;
-                acc = fmaf(pn, pn * wj[q], acc);
+                acc = df_add_prod(acc, pn, winv ? __fmul_rn(pn, wj[q]) : pn);
                 x[j] = xj[q] + double(pn);
             }
         }
     }
-    return double(acc);
+    return acc;
 }
 
 template <typename S>
 __device__ __forceinline__ double update_tile(const SweepArgs &a, const Tile &t, bool first,
                                               double beta, double gamma) {
-    if constexpr (std::is_same<S, float>::value) return update_tile_f32(a, t, first, beta, gamma);
     S *__restrict__ p = static_cast<S *>(a.p);
     const S *__restrict__ u = static_cast<const S *>(a.u);
     double *__restrict__ x = a.x;
@@ -615,6 +763,7 @@ __device__ __forceinline__ double update_tile(const SweepArgs &a, const Tile &t,
 
 template <typename S>
 __global__ void __launch_bounds__(kThreads) k_update(SweepArgs a) {
+    wait_prior_grid();
     int32_t t0, t1;
     tile_range(a.n_vtiles, t0, t1);
     int32_t cur = -1;
@@ -634,8 +783,14 @@ __global__ void __launch_bounds__(kThreads) k_update(SweepArgs a) {
             gamma = a.st[cur].gamma;
         }
         if (!active) continue;
-        double acc[1] = {update_tile<S>(a, t, first, beta, gamma)};
-        cta_sum<1>(acc);
+        double acc[1];
+        if constexpr (std::is_same<S, float>::value) {
+            const DF f[1] = {update_tile_f32(a, t, first, beta, gamma)};
+            cta_sum_df<1>(f, acc);
+        } else {
+            acc[0] = update_tile<S>(a, t, first, beta, gamma);
+            cta_sum<1>(acc);
+        }
         if (threadIdx.x == 0) a.part_upd[ti] = acc[0];
         ++pending;
     }
@@ -697,7 +852,7 @@ k_spmv(const int32_t *ptr, const int32_t *idx, const void *val_, const Tile *til
 // winv_j = 1/w_j for theta = p^T W^{-1} p.
 template <typename S>
 __global__ void k_colweights(const int32_t *ptr, const void *val_, int64_t n, int32_t mode, double *w,
-                             double *winv) {
+                             double *winv, float *wf, float *winvf) {
     const S *val = static_cast<const S *>(val_);
     for (int64_t j = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; j < n;
          j += int64_t(gridDim.x) * blockDim.x) {
@@ -714,6 +869,10 @@ __global__ void k_colweights(const int32_t *ptr, const void *val_, int64_t n, in
         }
         w[j] = wj;
         winv[j] = wi;
+        if (wf) {
+            wf[j] = float(wj);
+            winvf[j] = float(wi);
+        }
     }
 }
 
@@ -742,22 +901,34 @@ int sweep_ctas_per_sm(int which, bool f32) {
     return n;
 }
 
+// Launch with the programmatic-stream-serialization attribute (captured as
+// programmatic edges in CUDA graphs): the next sweep's launch overlaps the
+// tail of the previous one and its CTAs wait in wait_prior_grid().
+template <typename... Args>
+static cudaError_t launch_pdl(void (*kernel)(Args...), int grid, cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(unsigned(grid));
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 cudaError_t launch_row_sweep(const SweepArgs &a, bool f32, int grid, cudaStream_t s) {
-    if (f32) k_row_sweep<float><<<grid, kThreads, 0, s>>>(a);
-    else k_row_sweep<double><<<grid, kThreads, 0, s>>>(a);
-    return cudaGetLastError();
+    return f32 ? launch_pdl(k_row_sweep<float>, grid, s, a) : launch_pdl(k_row_sweep<double>, grid, s, a);
 }
 
 cudaError_t launch_col_sweep(const SweepArgs &a, bool f32, int grid, cudaStream_t s) {
-    if (f32) k_col_sweep<float><<<grid, kThreads, 0, s>>>(a);
-    else k_col_sweep<double><<<grid, kThreads, 0, s>>>(a);
-    return cudaGetLastError();
+    return f32 ? launch_pdl(k_col_sweep<float>, grid, s, a) : launch_pdl(k_col_sweep<double>, grid, s, a);
 }
 
 cudaError_t launch_update(const SweepArgs &a, bool f32, int grid, cudaStream_t s) {
-    if (f32) k_update<float><<<grid, kThreads, 0, s>>>(a);
-    else k_update<double><<<grid, kThreads, 0, s>>>(a);
-    return cudaGetLastError();
+    return f32 ? launch_pdl(k_update<float>, grid, s, a) : launch_pdl(k_update<double>, grid, s, a);
 }
 
 cudaError_t launch_spmv(const int32_t *ptr, const int32_t *idx, const void *val, bool f32,
@@ -770,11 +941,11 @@ cudaError_t launch_spmv(const int32_t *ptr, const int32_t *idx, const void *val,
 }
 
 cudaError_t launch_colweights(const int32_t *ptr, const void *val, bool f32, int64_t n, int32_t mode,
-                              double *w, double *winv, cudaStream_t s) {
+                              double *w, double *winv, float *wf, float *winvf, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     const int grid = int((n + kThreads - 1) / kThreads);
-    if (f32) k_colweights<float><<<grid, kThreads, 0, s>>>(ptr, val, n, mode, w, winv);
-    else k_colweights<double><<<grid, kThreads, 0, s>>>(ptr, val, n, mode, w, winv);
+    if (f32) k_colweights<float><<<grid, kThreads, 0, s>>>(ptr, val, n, mode, w, winv, wf, winvf);
+    else k_colweights<double><<<grid, kThreads, 0, s>>>(ptr, val, n, mode, w, winv, wf, winvf);
     return cudaGetLastError();
 }
 

@@ -25,8 +25,9 @@ cudaError_t launch_spmv(const int32_t *ptr, const int32_t *idx, const void *val,
                         const double *b, double *part, int grid, cudaStream_t s);
 
 // Diagonal weights of Sec. 4.1 from column segments (ptr over n columns):
-// w[j] and winv[j] = 1/w[j].
+// w[j] and winv[j] = 1/w[j] (and float copies when wf is not null).
 cudaError_t launch_colweights(const int32_t *ptr, const void *val, bool f32, int64_t n,
-                              int32_t mode, double *w, double *winv, cudaStream_t s);
+                              int32_t mode, double *w, double *winv, float *wf, float *winvf,
+                              cudaStream_t s);
 
 }  // namespace plss

@@ -114,6 +114,7 @@ struct plss_server {
     int32_t *d_row_ptr = nullptr, *d_col_idx = nullptr, *d_col_ptr = nullptr, *d_row_idx = nullptr;
     void *d_val = nullptr, *d_cval = nullptr, *d_r = nullptr, *d_p = nullptr, *d_u = nullptr;
     double *d_b = nullptr, *d_x = nullptr, *d_w = nullptr, *d_vout = nullptr;
+    float *d_wf = nullptr;   // FP32 servers: float w and 1/w
     double *d_part_row = nullptr, *d_part_col = nullptr, *d_part_upd = nullptr, *d_part_res = nullptr;
     plss::Tile *d_rt = nullptr, *d_ct = nullptr, *d_vt = nullptr;
     plss::SysDesc *d_desc = nullptr;
@@ -143,7 +144,7 @@ static size_t sval(const plss_server *s) { return s->f32 ? 4 : 8; }
 
 static void srv_free_device(plss_server *s) {
     void *ptrs[] = {s->d_row_ptr, s->d_col_idx, s->d_col_ptr, s->d_row_idx, s->d_val, s->d_cval,
-                    s->d_r, s->d_p, s->d_u, s->d_b, s->d_x, s->d_w, s->d_vout, s->d_part_row,
+                    s->d_r, s->d_p, s->d_u, s->d_b, s->d_x, s->d_w, s->d_wf, s->d_vout, s->d_part_row,
                     s->d_part_col, s->d_part_upd, s->d_part_res, s->d_rt, s->d_ct, s->d_vt,
                     s->d_desc, s->d_st, s->d_active};
     for (void *p : ptrs) dfree(p);
@@ -182,8 +183,8 @@ static void srv_prepare(plss_server *s, HostCsr &h, SrvRequest *r) {
     // the schedule a single-system context of this request would use, so
     // that its arithmetic is the same alone and in the mix
     const int64_t target = tile_target(h.nnz, s->nsm, s->f32);
-    build_tiles(r->rp.data(), 0, h.m, 0, target, kTileMaxSegs, s->f32, r->rt);
-    build_tiles(r->cp.data(), 0, h.n, 0, target, kTileMaxSegs, s->f32, r->ct);
+    build_tiles(r->rp.data(), 0, h.m, 0, target, max_segs(s->f32), s->f32, r->rt);
+    build_tiles(r->cp.data(), 0, h.n, 0, target, max_segs(s->f32), s->f32, r->ct);
     build_vec_tiles(0, h.n, 0, kVecTile, r->vt);
 }
 
@@ -271,9 +272,18 @@ static bool srv_upload(plss_server *s, SrvRequest *r) {
             SRV_TRY(cudaMemcpyAsync(s->d_w + r->coff, ones.data(), 8 * size_t(r->n), cudaMemcpyHostToDevice, st));
             SRV_TRY(cudaMemcpyAsync(s->d_w + s->Ncap + r->coff, ones.data(), 8 * size_t(r->n),
                                     cudaMemcpyHostToDevice, st));
+            if (s->d_wf) {
+                std::vector<float> fones(static_cast<size_t>(2 * r->n), 1.0f);
+                SRV_TRY(cudaMemcpyAsync(s->d_wf + r->coff, fones.data(), 4 * size_t(r->n), cudaMemcpyHostToDevice, st));
+                SRV_TRY(cudaMemcpyAsync(s->d_wf + s->Ncap + r->coff, fones.data(), 4 * size_t(r->n),
+                                        cudaMemcpyHostToDevice, st));
+                SRV_TRY(cudaStreamSynchronize(st));
+            }
         } else {
             SRV_TRY(launch_colweights(s->d_col_ptr + r->coff, s->d_cval, s->f32, r->n, r->w_mode,
-                                      s->d_w + r->coff, s->d_w + s->Ncap + r->coff, st));
+                                      s->d_w + r->coff, s->d_w + s->Ncap + r->coff,
+                                      s->d_wf ? s->d_wf + r->coff : nullptr,
+                                      s->d_wf ? s->d_wf + s->Ncap + r->coff : nullptr, st));
         }
     }
     SysState z;
@@ -357,6 +367,8 @@ static SweepArgs srv_args(plss_server *s) {
     a.u = s->d_u;
     a.w = s->d_w;
     a.winv = s->d_w + s->Ncap;
+    a.wf = s->d_wf;
+    a.winvf = s->d_wf ? s->d_wf + s->Ncap : nullptr;
     return a;
 }
 
@@ -539,6 +551,7 @@ plss_status plss_server_create(const plss_server_opts *so_in, plss_server **out)
     A(&s->d_p, size_t(sb) * size_t(s->Ncap), "arena p");
     A(&s->d_u, size_t(sb) * size_t(s->Ncap), "arena u");
     A(reinterpret_cast<void **>(&s->d_w), 16 * size_t(s->Ncap), "arena w");   // w, then 1/w
+    if (s->f32) A(reinterpret_cast<void **>(&s->d_wf), 8 * size_t(s->Ncap), "arena wf");
     A(reinterpret_cast<void **>(&s->d_part_row), 16 * size_t(s->Tr), "partials");
     A(reinterpret_cast<void **>(&s->d_part_res), 8 * size_t(s->Tr), "partials");
     A(reinterpret_cast<void **>(&s->d_part_col), 8 * size_t(s->Tc), "partials");
