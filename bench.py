@@ -38,6 +38,7 @@ METRIC = "time to ||r||/||b||<=1e-8"
 # this benchmark; the reference arm scales its sampled per-update time by it).
 REF_UPDATES_TO_TOL = 183000
 L2_FLUSH_BYTES = 512 << 20
+PROFILE_PERIOD = 16
 
 
 def parse():
@@ -48,6 +49,7 @@ def parse():
     ap.add_argument("--impl", default="plss", choices=["plss", "reference"])
     ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--w-mode", type=int, default=0)
+    ap.add_argument("--layout", default="auto", choices=["auto", "csr"])
     ap.add_argument("--m", type=int, default=1_000_000)
     ap.add_argument("--n", type=int, default=200_000)
     ap.add_argument("--tol", type=float, default=1e-8)
@@ -262,7 +264,8 @@ def run_plss(args):
     A, b, xs = make_workload(args)
     m, n, nnz = A.m, A.n, A.nnz
     sv = 8 if args.prec == "fp64" else 4
-    ctx = plss.Context(A, precision=args.prec)
+    ctx = plss.Context(A, precision=args.prec, layout=args.layout)
+    ctx_layout = dict(ctx.layout(), kind=args.layout)
     b_dev = torch.from_numpy(b).to(dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     kw = dict(tol=args.tol, maxit=args.maxit, stop_on_true=1, w_mode=args.w_mode)
@@ -278,7 +281,9 @@ def run_plss(args):
     e0.record()
     results = []
     for _ in range(args.steps):
-        x, r = ctx.solve(b_dev, profile=1, **kw)
+        # CUDA events around the kernels of one chunk of updates in every
+        # PROFILE_PERIOD (timing every chunk would slow the solve)
+        x, r = ctx.solve(b_dev, profile=PROFILE_PERIOD, **kw)
         results.append(r)
         flush.zero_()
     e1.record()
@@ -353,7 +358,7 @@ def run_plss(args):
                           "relres_true": last["relres_true"], "relres_rec": last["relres_rec"],
                           "ms_per_update": ms_step / max(1, last["iters"]),
                           "rel_err_vs_xstar": err_xstar},
-                "roofline": roof, "cpu_baseline": cb, "e2e": e2e,
+                "layout": ctx_layout, "roofline": roof, "cpu_baseline": cb, "e2e": e2e,
                 "gpu_launches": int(kt["all_launches"]), "clocks": clk, "variants": variants}
         print(json.dumps(line), flush=True)
     ctx.close()

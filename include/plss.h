@@ -59,6 +59,15 @@ enum { PLSS_FP64 = 0, PLSS_FP32 = 1 };
  * (an empty column gets weight 1). */
 enum { PLSS_W_IDENTITY = 0, PLSS_W_COLNORM = 1, PLSS_W_COLNORM2 = 2 };
 
+/* Storage of the sweeps (plss_create). AUTO: tiles of short rows (columns)
+ * whose padding stays within 1/4 are also stored sliced -- 32 segments side
+ * by side, so that a warp reads 32 consecutive indices and values per load
+ * and each lane sums one row (column) -- at the cost of a second copy of
+ * those nonzeros; other tiles use the CSR (CSC). CSR: the CSR and CSC only
+ * (the layout of the serving arena; plss_submit results equal those of a
+ * context created with it). */
+enum { PLSS_LAYOUT_AUTO = 0, PLSS_LAYOUT_CSR = 1 };
+
 /* A sparse matrix in CSR form (see the conventions above). val holds nnz
  * doubles, or floats when val_f32 = 1. */
 typedef struct {
@@ -93,8 +102,9 @@ typedef struct {
                             /* theta_{k+1}) -- the scalars of Algorithm 1          */
     int64_t hist_cap;
     int32_t profile;        /* 1: time every sweep launch with CUDA events recorded */
-                            /* on the solve's stream (see plss_kernel_times)       */
-    int32_t reserved;
+                            /* on the solve's stream (see plss_kernel_times);      */
+                            /* k > 1: time one chunk of launches in k             */
+    int32_t layout;         /* create: PLSS_LAYOUT_* (storage of the sweeps' tiles) */
     double inner_tol;       /* PLSS_FP32: restart from b - A x (refinement) once   */
                             /* the recursive residual has fallen by this factor    */
                             /* since the last start (default 1e-4; 0 = off)        */
@@ -133,6 +143,12 @@ void plss_destroy(plss_ctx *ctx);
 /* Sizes of a context: systems, total rows, total columns, total nonzeros. */
 plss_status plss_ctx_info(const plss_ctx *ctx, int32_t *nsys, int64_t *m, int64_t *n,
                           int64_t *nnz);
+
+/* Tile schedule of a context's sweeps (PLSS_LAYOUT_*): out[0] row tiles,
+ * out[1] of them sliced, out[2] column tiles, out[3] of them sliced,
+ * out[4] and out[5] elements (nonzeros plus padding) of the sliced row and
+ * column copies. */
+plss_status plss_ctx_layout(const plss_ctx *ctx, int64_t out[6]);
 
 /*
  * Solves A x = b for a single-system context.

@@ -67,6 +67,9 @@ struct plss_ctx {
     int64_t prof_n[3] = {0, 0, 0};
     int64_t prof_all = 0;               // every kernel launched by profiled solves
 
+    plss::Sliced rsl{}, csl{};        // sliced copies (csl aliases rsl when symmetric)
+    int64_t sl_elems[2] = {0, 0};     // elements of the sliced row / column copies
+
     plss::KaczState *kacz = nullptr;
     plss::RhsState *rhs = nullptr;
 };
@@ -79,6 +82,13 @@ struct HostCsr {
     std::vector<int64_t> row_ptr;
     std::vector<int32_t> col_idx;
     std::vector<double> val;
+};
+
+// Host copy of a sliced side (layout in plss_dev.cuh).
+struct HostSliced {
+    std::vector<int32_t> first, ptr, seg, idx;
+    std::vector<double> v64;
+    std::vector<float> v32;
 };
 
 // Copies and validates a caller's CSR (host or device arrays).
@@ -98,6 +108,10 @@ plss_status ensure_weights(plss_ctx *c, int32_t w_mode, cudaStream_t s);
 plss_status true_relres(plss_ctx *c, cudaStream_t s, std::vector<double> &rel);
 void build_tiles(const int32_t *ptr, int64_t begin, int64_t end, int32_t sys, int64_t target,
                  int64_t max_segs, bool f32, std::vector<Tile> &out);
+void build_side(const int32_t *ptr, int64_t begin, int64_t end, int32_t sys, int64_t nnz, int nsm,
+                bool f32, bool slice, std::vector<Tile> &out);
+void fill_sliced(const int32_t *ptr, const int32_t *idx, const double *v64, const float *v32,
+                 const std::vector<Tile> &tiles, HostSliced &out);
 
 // identity sketch (plss_kaczmarz.cu)
 plss_status run_identity(plss_ctx *c, const double *b, const double *x0, double *x_out,

@@ -20,7 +20,26 @@ constexpr int kWarps = kThreads / 32;
 // One unit of sweep work: segments (rows for A p, columns for A^T r, vector
 // entries for the update) [begin, end) of system `sys`. `group` is the number
 // of lanes that share one segment (1..32, a power of two); 0 means the whole
-// CTA works on the single segment of the tile (very long rows/columns).
+// CTA works on the single segment of the tile (very long rows/columns). With
+// kSliced set, the sweeps read the tile from its sliced copy (below) instead;
+// the low bits still give the lane count for kernels that use the plain
+// CSR/CSC (products, residual norms).
+constexpr int32_t kSliced = 0x100;
+constexpr int32_t kGroupMask = 0xff;
+
+// Sliced copy of a side (rows or columns) of A. A sliced tile's segments,
+// sorted by decreasing length (ties by index), form slices of 32 slots;
+// slice s is as wide as its longest segment and stores element k of slot l
+// at ptr[s] + 32 k + l, so a warp reads 32 consecutive indices (values) per
+// load and each lane owns one segment. Padding has index -1 and value 0.
+struct Sliced {
+    const int32_t *first;   // [tiles] first slice of each tile
+    const int32_t *ptr;     // [slices + 1] element offsets (multiples of 32)
+    const int32_t *seg;     // [32 * slices] segment of each slot, -1 if none
+    const int32_t *idx;     // padded indices
+    const void *val;        // padded values (storage type)
+};
+
 struct Tile {
     int32_t sys;
     int32_t begin;
@@ -98,6 +117,8 @@ struct SweepArgs {
     const double *winv;  // 1/w (theta = p^T W^{-1} p), nullptr with w
     const float *wf;     // float copies for the FP32-storage sweeps
     const float *winvf;
+    Sliced rsl;          // sliced rows (tiles of rtiles flagged kSliced)
+    Sliced csl;          // sliced columns (tiles of ctiles flagged kSliced)
 };
 
 }  // namespace plss

@@ -90,6 +90,120 @@ int64_t tile_target(int64_t nnz, int nsm, bool f32) {
     return std::min<int64_t>(cap, std::max<int64_t>(1024, (nnz + 2 * slots - 1) / (2 * slots) * 21 / 20));
 }
 
+// Order of a tile's segments in its slices (decreasing length, ties by
+// index); returns the padded element count (32 x each slice's width).
+static int64_t slice_order(const int32_t *ptr, const Tile &t, std::vector<int32_t> &order) {
+    const int32_t nseg = t.end - t.begin;
+    order.resize(size_t(nseg));
+    for (int32_t i = 0; i < nseg; ++i) order[size_t(i)] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+        return ptr[t.begin + a + 1] - ptr[t.begin + a] > ptr[t.begin + b + 1] - ptr[t.begin + b];
+    });
+    int64_t padded = 0;
+    for (int32_t s = 0; s < nseg; s += 32) {
+        const int32_t g = t.begin + order[size_t(s)];
+        padded += 32 * int64_t(ptr[g + 1] - ptr[g]);
+    }
+    return padded;
+}
+
+// As build_tiles (FP64 sizes), but a tile ends on a multiple of 32
+// segments unless a long segment or the end of the range comes first, so
+// that only its last slice can be partly empty.
+static void cut_slice_tiles(const int32_t *ptr, int64_t begin, int64_t end, int32_t sys, int64_t target,
+                            std::vector<Tile> &out) {
+    int64_t i = begin;
+    while (i < end) {
+        if (int64_t(ptr[i + 1]) - ptr[i] > target) {
+            out.push_back({sys, int32_t(i), int32_t(i + 1), 0});
+            ++i;
+            continue;
+        }
+        int64_t j = i, nz = 0;
+        while (j < end && j - i < kTileMaxSegs) {
+            int64_t k = j, gz = 0;
+            bool stop = false;
+            for (; k < end && k < j + 32; ++k) {
+                const int64_t l = int64_t(ptr[k + 1]) - ptr[k];
+                if (l > target) {
+                    stop = true;
+                    break;
+                }
+                gz += l;
+            }
+            if (k == j || (nz > 0 && nz + gz > target)) break;
+            nz += gz;
+            j = k;
+            if (stop) break;
+        }
+        out.push_back({sys, int32_t(i), int32_t(j), pick_group(double(nz) / double(j - i), false)});
+        i = j;
+    }
+}
+
+// Tiles of segments [begin, end) of system `sys` for one side of A. With
+// `slice`, tiles are cut at the FP64 size on 32-segment boundaries first; a
+// tile of short segments whose slices pad it by at most 1/4 is flagged
+// kSliced, and the others are cut as they would be without slicing.
+void build_side(const int32_t *ptr, int64_t begin, int64_t end, int32_t sys, int64_t nnz, int nsm,
+                bool f32, bool slice, std::vector<Tile> &out) {
+    const int64_t target = tile_target(nnz, nsm, f32);
+    if (!slice || begin == end) {
+        build_tiles(ptr, begin, end, sys, target, max_segs(f32), f32, out);
+        return;
+    }
+    std::vector<Tile> big;
+    cut_slice_tiles(ptr, begin, end, sys, tile_target(nnz, nsm, false), big);
+    std::vector<int32_t> order;
+    for (const Tile &t : big) {
+        const int64_t nz = int64_t(ptr[t.end]) - ptr[t.begin];
+        if (t.group != 0 && t.end > t.begin && slice_order(ptr, t, order) * 4 <= nz * 5) {
+            out.push_back({t.sys, t.begin, t.end, t.group | kSliced});
+        } else if (f32 && t.end > t.begin) {
+            build_tiles(ptr, t.begin, t.end, sys, target, max_segs(true), true, out);
+        } else {
+            out.push_back(t);
+        }
+    }
+}
+
+// The sliced copy of the tiles flagged kSliced (values from v64 or v32).
+void fill_sliced(const int32_t *ptr, const int32_t *idx, const double *v64, const float *v32,
+                 const std::vector<Tile> &tiles, HostSliced &out) {
+    out = HostSliced();
+    out.first.resize(tiles.size());
+    out.ptr.push_back(0);
+    std::vector<int32_t> order;
+    for (size_t ti = 0; ti < tiles.size(); ++ti) {
+        const Tile &t = tiles[ti];
+        out.first[ti] = int32_t(out.ptr.size()) - 1;
+        if (!(t.group & kSliced)) continue;
+        slice_order(ptr, t, order);
+        const int32_t nseg = t.end - t.begin;
+        for (int32_t s = 0; s < nseg; s += 32) {
+            const int32_t lead = t.begin + order[size_t(s)];
+            const int32_t width = ptr[lead + 1] - ptr[lead];
+            const int32_t base = out.ptr.back();
+            out.ptr.push_back(base + 32 * width);
+            out.idx.resize(size_t(base) + 32 * size_t(width), -1);
+            if (v64) out.v64.resize(out.idx.size(), 0.0);
+            else out.v32.resize(out.idx.size(), 0.0f);
+            for (int32_t l = 0; l < 32; ++l) {
+                const int32_t seg = s + l < nseg ? t.begin + order[size_t(s + l)] : -1;
+                out.seg.push_back(seg);
+                if (seg < 0) continue;
+                for (int32_t k = 0; k < ptr[seg + 1] - ptr[seg]; ++k) {
+                    const size_t dst = size_t(base) + 32 * size_t(k) + size_t(l);
+                    const size_t src = size_t(ptr[seg]) + size_t(k);
+                    out.idx[dst] = idx[src];
+                    if (v64) out.v64[dst] = v64[src];
+                    else out.v32[dst] = v32[src];
+                }
+            }
+        }
+    }
+}
+
 void build_vec_tiles(int64_t begin, int64_t end, int32_t sys, int64_t chunk, std::vector<Tile> &out) {
     if (begin == end) {
         out.push_back({sys, int32_t(begin), int32_t(begin), 1});
@@ -190,6 +304,39 @@ plss_status upload(T **dst, const std::vector<T> &src, const char *what) {
     return PLSS_OK;
 }
 
+// Device copy of a sliced side (all pointers null when no tile is sliced).
+static plss_status upload_sliced(const HostSliced &h, Sliced &d, bool f32) {
+    d = Sliced{};
+    if (h.seg.empty()) return PLSS_OK;
+    int32_t *first = nullptr, *ptr = nullptr, *seg = nullptr, *idx = nullptr;
+    plss_status st = upload(&first, h.first, "sliced tiles");
+    d.first = first;
+    if (st == PLSS_OK) st = upload(&ptr, h.ptr, "slice offsets");
+    d.ptr = ptr;
+    if (st == PLSS_OK) st = upload(&seg, h.seg, "slice slots");
+    d.seg = seg;
+    if (st == PLSS_OK) st = upload(&idx, h.idx, "sliced indices");
+    d.idx = idx;
+    if (st == PLSS_OK) {
+        if (f32) {
+            float *v = nullptr;
+            st = upload(&v, h.v32, "sliced values");
+            d.val = v;
+        } else {
+            double *v = nullptr;
+            st = upload(&v, h.v64, "sliced values");
+            d.val = v;
+        }
+    }
+    return st;
+}
+
+static void free_sliced(Sliced &d) {
+    const void *ptrs[] = {d.first, d.ptr, d.seg, d.idx, d.val};
+    for (const void *p : ptrs) dfree(const_cast<void *>(p));
+    d = Sliced{};
+}
+
 void dfree(void *p) {
     if (p) cudaFree(p);
 }
@@ -226,6 +373,8 @@ static void ctx_free(plss_ctx *c) {
         dfree(c->d_row_idx);
         dfree(c->d_cval);
     }
+    free_sliced(c->rsl);
+    if (!c->symmetric) free_sliced(c->csl);
     if (c->h_st) cudaFreeHost(c->h_st);
     if (c->h_active) cudaFreeHost(c->h_active);
     free_extra(c);
@@ -241,6 +390,8 @@ static plss_status ctx_build(const plss_csr *As, int32_t nsys, const plss_opts *
     if (!o) o = &od;
     if (o->precision != PLSS_FP64 && o->precision != PLSS_FP32)
         return fail(PLSS_ERR_INVALID, "unknown precision %d", o->precision);
+    if (o->layout != PLSS_LAYOUT_AUTO && o->layout != PLSS_LAYOUT_CSR)
+        return fail(PLSS_ERR_INVALID, "unknown layout %d", o->layout);
 
     std::vector<HostCsr> hs(static_cast<size_t>(nsys));
     int64_t M = 0, N = 0, NNZ = 0;
@@ -325,14 +476,16 @@ static plss_status ctx_build(const plss_csr *As, int32_t nsys, const plss_opts *
     }
     const int32_t *colp = sym ? rp.data() : cp.data();
 
-    const int64_t target = tile_target(NNZ, c->nsm, c->f32);
+    // sliced copies unless the caller asks for the plain layout (or the
+    // padded copy could overflow 32-bit offsets)
+    const bool slice = o->layout == PLSS_LAYOUT_AUTO && NNZ < 1800000000;
     for (int32_t s = 0; s < nsys; ++s) {
         SysDesc &d = c->h_desc[size_t(s)];
         d.rt_begin = int32_t(c->h_rt.size());
-        build_tiles(rp.data(), d.row_off, d.row_off + d.m, s, target, max_segs(c->f32), c->f32, c->h_rt);
+        build_side(rp.data(), d.row_off, d.row_off + d.m, s, NNZ, c->nsm, c->f32, slice, c->h_rt);
         d.rt_count = int32_t(c->h_rt.size()) - d.rt_begin;
         d.ct_begin = int32_t(c->h_ct.size());
-        build_tiles(colp, d.col_off, d.col_off + d.n, s, target, max_segs(c->f32), c->f32, c->h_ct);
+        build_side(colp, d.col_off, d.col_off + d.n, s, NNZ, c->nsm, c->f32, slice, c->h_ct);
         d.ct_count = int32_t(c->h_ct.size()) - d.ct_begin;
         d.vt_begin = int32_t(c->h_vt.size());
         build_vec_tiles(d.col_off, d.col_off + d.n, s, kVecTile, c->h_vt);
@@ -361,6 +514,19 @@ static plss_status ctx_build(const plss_csr *As, int32_t nsys, const plss_opts *
         TRY_ST(upload(&c->d_row_idx, ri, "row_idx"));
         if (c->f32) TRY_ST(upload(reinterpret_cast<float **>(&c->d_cval), cv32, "cval"));
         else TRY_ST(upload(reinterpret_cast<double **>(&c->d_cval), cv64, "cval"));
+    }
+    HostSliced hsl;
+    fill_sliced(rp.data(), ci.data(), c->f32 ? nullptr : v64.data(), c->f32 ? v32.data() : nullptr, c->h_rt, hsl);
+    TRY_ST(upload_sliced(hsl, c->rsl, c->f32));
+    c->sl_elems[0] = int64_t(hsl.idx.size());
+    if (sym) {
+        c->csl = c->rsl;   // same tiles over the same arrays
+        c->sl_elems[1] = c->sl_elems[0];
+    } else {
+        fill_sliced(cp.data(), ri.data(), c->f32 ? nullptr : cv64.data(), c->f32 ? cv32.data() : nullptr,
+                    c->h_ct, hsl);
+        TRY_ST(upload_sliced(hsl, c->csl, c->f32));
+        c->sl_elems[1] = int64_t(hsl.idx.size());
     }
     TRY_ST(upload(&c->d_rt, c->h_rt, "row tiles"));
     TRY_ST(upload(&c->d_ct, c->h_ct, "col tiles"));
@@ -430,6 +596,8 @@ static plss_status ctx_build(const plss_csr *As, int32_t nsys, const plss_opts *
     a.winv = nullptr;
     a.wf = nullptr;
     a.winvf = nullptr;
+    a.rsl = c->rsl;
+    a.csl = c->csl;
     *out = c;
     return PLSS_OK;
 }
@@ -507,6 +675,7 @@ plss_status check_opts(const plss_opts *o) {
     if (o->hist_cap < 0) return fail(PLSS_ERR_INVALID, "hist_cap < 0");
     if (!(o->inner_tol >= 0.0) || !(o->inner_tol < 1.0)) return fail(PLSS_ERR_INVALID, "inner_tol must be in [0, 1)");
     if (o->hist_cap > 0 && !o->hist) return fail(PLSS_ERR_INVALID, "hist_cap > 0 with hist NULL");
+    if (o->profile < 0) return fail(PLSS_ERR_INVALID, "profile < 0");
     return PLSS_OK;
 }
 
@@ -598,11 +767,13 @@ plss_status run_residual(plss_ctx *c, const double *const *b, const double *cons
     // restarts (at most one per update), so 2 (maxit + 2) bodies suffice.
     const int64_t body_cap = 2 * (maxit_all + 2) + 8;
     const bool prof = o->profile != 0;
-    int64_t bodies = 0;
+    const int64_t period = std::max<int64_t>(1, o->profile);   // profile one chunk in `period`
+    int64_t bodies = 0, nchunk = 0;
     int chunk = 1;
     for (;;) {
+        const bool pchunk = prof && nchunk++ % period == 0;
         cudaGraphExec_t g;
-        st = get_graph(c, chunk, w_on, prof, &g);
+        st = get_graph(c, chunk, w_on, pchunk, &g);
         if (st != PLSS_OK) return st;
         CUDA_TRY(cudaGraphLaunch(g, s));
         bodies += chunk;
@@ -612,7 +783,7 @@ plss_status run_residual(plss_ctx *c, const double *const *b, const double *cons
         // time only chunks in which some system stayed active throughout
         // (after the set-up body), so that launches returning at once after
         // convergence do not enter the per-launch averages
-        if (prof && *c->h_active > 0 && bodies > 1) {
+        if (pchunk && *c->h_active > 0 && bodies > 1) {
             for (int i = 0; i < chunk; ++i) {
                 const cudaEvent_t *ev = &c->prof_ev[size_t(4 * i)];
                 float t[3] = {0.0f, 0.0f, 0.0f};
@@ -691,7 +862,7 @@ void plss_opts_default(plss_opts *o) {
     o->hist = nullptr;
     o->hist_cap = 0;
     o->profile = 0;
-    o->reserved = 0;
+    o->layout = PLSS_LAYOUT_AUTO;
     o->inner_tol = 1e-4;
 }
 
@@ -716,6 +887,21 @@ plss_status plss_ctx_info(const plss_ctx *ctx, int32_t *nsys, int64_t *m, int64_
     if (m) *m = ctx->m;
     if (n) *n = ctx->n;
     if (nnz) *nnz = ctx->nnz;
+    return PLSS_OK;
+}
+
+plss_status plss_ctx_layout(const plss_ctx *ctx, int64_t out[6]) {
+    clear_error();
+    if (!ctx || !out) return fail(PLSS_ERR_INVALID, "NULL argument");
+    int64_t sr = 0, sc = 0;
+    for (const Tile &t : ctx->h_rt) sr += (t.group & kSliced) ? 1 : 0;
+    for (const Tile &t : ctx->h_ct) sc += (t.group & kSliced) ? 1 : 0;
+    out[0] = int64_t(ctx->h_rt.size());
+    out[1] = sr;
+    out[2] = int64_t(ctx->h_ct.size());
+    out[3] = sc;
+    out[4] = ctx->sl_elems[0];
+    out[5] = ctx->sl_elems[1];
     return PLSS_OK;
 }
 

@@ -297,6 +297,49 @@ __device__ __forceinline__ void for_segments(const int32_t *__restrict__ ptr, co
     }
 }
 
+// Dot product of slot `lane` of a slice (element offset `off`, `width`
+// elements per slot) with a dense vector: the warp loads 32 consecutive
+// indices and values per step, 8 steps before their gathers, and each lane
+// sums its own segment in element order with one FMA per element. Padding
+// (index -1, value 0) gathers nothing and adds an exact zero.
+template <typename VT, typename XT, typename ACC>
+__device__ __forceinline__ ACC slice_dot(const int32_t *__restrict__ idx, const VT *__restrict__ val,
+                                         int32_t off, int32_t width, int lane, const XT *__restrict__ x) {
+    ACC acc = ACC(0);
+    for (int32_t k0 = 0; k0 < width; k0 += kBatch) {
+        int32_t c[kBatch];
+        VT v[kBatch];
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+            const bool in = k0 + u < width;
+            const int32_t e = off + 32 * (k0 + u) + lane;
+            c[u] = in ? __ldg(idx + e) : -1;
+            v[u] = in ? __ldg(val + e) : VT(0);
+        }
+        XT g[kBatch];
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) g[u] = c[u] >= 0 ? __ldg(x + c[u]) : XT(0);
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) acc = fma_t(ACC(v[u]), ACC(g[u]), acc);
+    }
+    return acc;
+}
+
+// Calls body(seg, off, width, lane) for each slot of the sliced tile `ti`
+// (one warp per slice; seg < 0 for an empty slot); warp-uniform loop.
+template <typename F>
+__device__ __forceinline__ void for_slices(const Sliced &sl, const Tile &t, int32_t ti, F &&body) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int32_t s0 = __ldg(sl.first + ti);
+    const int32_t ns = (t.end - t.begin + 31) >> 5;
+    for (int32_t s = warp; s < ns; s += kWarps) {
+        const int32_t off = __ldg(sl.ptr + s0 + s);
+        const int32_t width = (__ldg(sl.ptr + s0 + s + 1) - off) >> 5;
+        const int32_t seg = __ldg(sl.seg + 32 * (s0 + s) + lane);
+        body(seg, off, width, lane);
+    }
+}
+
 // Programmatic dependent launch: the sweeps are launched so that a kernel
 // may start while its predecessor drains; everything it reads was written
 // by that predecessor, so it first waits for the predecessor's completion
@@ -413,6 +456,38 @@ __device__ __forceinline__ void row_tile_cta(const SweepArgs &a, const Tile &t, 
     }
 }
 
+// Sliced tile of the row sweep (both storage types): r = r - A p, or
+// r = b - A x with products in double after a (re)start; one lane per row.
+template <typename S>
+__device__ __forceinline__ void row_tile_sliced(const SweepArgs &a, const Tile &t, int32_t ti, bool init,
+                                                double &acc_r, double &acc_b) {
+    const S *__restrict__ val = static_cast<const S *>(a.rsl.val);
+    S *__restrict__ r = static_cast<S *>(a.r);
+    if (init) {
+        for_slices(a.rsl, t, ti, [&](int32_t row, int32_t off, int32_t width, int lane) {
+            const double bi = row >= 0 ? a.b[row] : 0.0;
+            const double d = slice_dot<S, double, double>(a.rsl.idx, val, off, width, lane, a.x);
+            if (row >= 0) {
+                const S ri = S(bi - d);
+                r[row] = ri;
+                acc_r = fma(double(ri), double(ri), acc_r);
+                acc_b = fma(bi, bi, acc_b);
+            }
+        });
+    } else {
+        const S *__restrict__ p = static_cast<const S *>(a.p);
+        for_slices(a.rsl, t, ti, [&](int32_t row, int32_t off, int32_t width, int lane) {
+            const S old = row >= 0 ? r[row] : S(0);   // issued before the dot's loads
+            const S d = slice_dot<S, S, S>(a.rsl.idx, val, off, width, lane, p);
+            if (row >= 0) {
+                const S ri = old - d;
+                r[row] = ri;
+                acc_r = fma(double(ri), double(ri), acc_r);
+            }
+        });
+    }
+}
+
 __device__ void finish_row(const SweepArgs &a, int32_t sys, bool init) {
     const SysDesc d = a.desc[sys];
     double v[2] = {0.0, 0.0};
@@ -480,7 +555,10 @@ __global__ void __launch_bounds__(kThreads) k_row_sweep(SweepArgs a) {
         }
         if (!active) continue;
         double acc[2] = {0.0, 0.0};
-        if (std::is_same<S, float>::value && !init && t.group != 0) {
+        if (t.group & kSliced) {
+            row_tile_sliced<S>(a, t, ti, init, acc[0], acc[1]);
+            cta_sum<2>(acc);
+        } else if (std::is_same<S, float>::value && !init && t.group != 0) {
             DF f[1] = {{0.0f, 0.0f}};
             switch (t.group) {
                 case 1: row_tile_f32<1>(a, t, f[0], stage); break;
@@ -563,6 +641,26 @@ __device__ __forceinline__ void col_tile_cta(const SweepArgs &a, const Tile &t, 
     if (threadIdx.x == 0) col_out<S>(a, col, double(S(d)), acc);
 }
 
+// Sliced tile of the column sweep: y = A^T r, u = W y (float weights for
+// FP32 storage), phi partial in double; one lane per column.
+template <typename S>
+__device__ __forceinline__ void col_tile_sliced(const SweepArgs &a, const Tile &t, int32_t ti, double &acc) {
+    const S *__restrict__ val = static_cast<const S *>(a.csl.val);
+    const S *__restrict__ r = static_cast<const S *>(a.r);
+    for_slices(a.csl, t, ti, [&](int32_t col, int32_t off, int32_t width, int lane) {
+        const S y = slice_dot<S, S, S>(a.csl.idx, val, off, width, lane, r);
+        if (col >= 0) {
+            if constexpr (std::is_same<S, float>::value) {
+                const float uj = a.wf ? __fmul_rn(a.wf[col], y) : y;
+                static_cast<float *>(a.u)[col] = uj;
+                acc = fma(double(y), double(uj), acc);
+            } else {
+                col_out<S>(a, col, double(y), acc);
+            }
+        }
+    });
+}
+
 __device__ void finish_col(const SweepArgs &a, int32_t sys) {
     const SysDesc d = a.desc[sys];
     double v[1] = {0.0};
@@ -623,7 +721,10 @@ __global__ void __launch_bounds__(kThreads) k_col_sweep(SweepArgs a) {
         }
         if (!active) continue;
         double acc[1] = {0.0};
-        if (std::is_same<S, float>::value && t.group != 0) {
+        if (t.group & kSliced) {
+            col_tile_sliced<S>(a, t, ti, acc[0]);
+            cta_sum<1>(acc);
+        } else if (std::is_same<S, float>::value && t.group != 0) {
             DF f[1] = {{0.0f, 0.0f}};
             switch (t.group) {
                 case 1: col_tile_f32<1>(a, t, f[0], stage); break;
@@ -819,7 +920,7 @@ k_spmv(const int32_t *ptr, const int32_t *idx, const void *val_, const Tile *til
     const S *val = static_cast<const S *>(val_);
     for (int32_t ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
         const Tile t = tiles[ti];
-        switch (t.group) {
+        switch (t.group & kGroupMask) {
             case 0: {
                 const int32_t s = ptr[t.begin], e = ptr[t.begin + 1];
                 const double d = cta_dot<S, double, double>(idx, val, s, e, v);

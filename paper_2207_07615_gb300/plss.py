@@ -23,10 +23,11 @@ STATUS_NAMES = {0: "converged", 1: "not_converged", 2: "pending", -1: "invalid",
                 -3: "cuda", -4: "breakdown", -5: "timeout", -6: "busy", -7: "not_found"}
 SKETCH = {"residual": 0, "identity": 1}
 PRECISION = {"fp64": 0, "fp32": 1}
+LAYOUT = {"auto": 0, "csr": 1}
 
 #: every symbol declared in include/plss.h
 EXPORTS = ["plss_opts_default", "plss_create", "plss_create_batched", "plss_destroy",
-           "plss_ctx_info", "plss_solve", "plss_solve_batched", "plss_solve_rhs", "plss_spmv",
+           "plss_ctx_info", "plss_ctx_layout", "plss_solve", "plss_solve_batched", "plss_solve_rhs", "plss_spmv",
            "plss_kernel_times", "plss_residual_noalloc", "plss_last_error", "plss_server_opts_default", "plss_server_create", "plss_submit",
            "plss_poll", "plss_server_stats", "plss_server_destroy"]
 
@@ -43,7 +44,7 @@ class Opts(C.Structure):
                 ("refine_period", C.c_int64), ("kacz_hist", C.c_int64), ("seed", C.c_uint64),
                 ("io_device", C.c_int32), ("symmetric", C.c_int32), ("stream", C.c_void_p),
                 ("hist", C.c_void_p), ("hist_cap", C.c_int64), ("profile", C.c_int32),
-                ("reserved", C.c_int32), ("inner_tol", C.c_double)]
+                ("layout", C.c_int32), ("inner_tol", C.c_double)]
 
 
 class Result(C.Structure):
@@ -84,6 +85,7 @@ def lib() -> C.CDLL:
             L.plss_destroy.argtypes = [vp]
             L.plss_destroy.restype = None
             L.plss_ctx_info.argtypes = [vp, vp, vp, vp, vp]
+            L.plss_ctx_layout.argtypes = [vp, vp]
             L.plss_solve.argtypes = [vp, vp, vp, vp, vp, vp]
             L.plss_solve_batched.argtypes = [vp, vp, vp, vp, vp, vp]
             L.plss_solve_rhs.argtypes = [vp, i32, vp, vp, vp, vp, vp]
@@ -101,7 +103,8 @@ def lib() -> C.CDLL:
             L.plss_server_stats.argtypes = [vp, vp, vp, vp, vp]
             L.plss_server_destroy.argtypes = [vp]
             L.plss_server_destroy.restype = None
-            for name in ("plss_create", "plss_create_batched", "plss_ctx_info", "plss_solve",
+            for name in ("plss_create", "plss_create_batched", "plss_ctx_info", "plss_ctx_layout",
+                         "plss_solve",
                          "plss_kernel_times",
                          "plss_solve_batched", "plss_solve_rhs", "plss_spmv",
                          "plss_server_create", "plss_submit", "plss_poll", "plss_server_stats"):
@@ -176,6 +179,8 @@ def make_opts(**kw) -> Opts:
             v = SKETCH[v]
         if k == "precision" and isinstance(v, str):
             v = PRECISION[v]
+        if k == "layout" and isinstance(v, str):
+            v = LAYOUT[v]
         setattr(o, k, v)
     return o
 
@@ -203,10 +208,10 @@ class _CsrHold:
 class Context:
     """A matrix (or a batch of independent matrices) resident on the GPU."""
 
-    def __init__(self, A, precision="fp64", symmetric=False):
+    def __init__(self, A, precision="fp64", symmetric=False, layout="auto"):
         L = lib()
         self._h = C.c_void_p()
-        o = make_opts(precision=precision, symmetric=int(bool(symmetric)))
+        o = make_opts(precision=precision, symmetric=int(bool(symmetric)), layout=layout)
         if isinstance(A, (list, tuple)):
             holds = [_CsrHold(a) for a in A]
             arr = (Csr * len(holds))(*[h.c for h in holds])
@@ -219,6 +224,15 @@ class Context:
         self.nsys = len(self.shapes)
         self.m = sum(s[0] for s in self.shapes)
         self.n = sum(s[1] for s in self.shapes)
+
+    def layout(self):
+        """Tile schedule: row/column tiles, how many are sliced, and the
+        elements (nonzeros plus padding) of the sliced copies."""
+        out = (C.c_int64 * 6)()
+        _check(lib().plss_ctx_layout(self._h, out), (OK,))
+        keys = ("row_tiles", "row_sliced", "col_tiles", "col_sliced", "row_sliced_elems",
+                "col_sliced_elems")
+        return dict(zip(keys, [int(v) for v in out]))
 
     def close(self):
         if self._h:

@@ -101,18 +101,37 @@ def _shape(shape):
     return synth.powerlaw_underdetermined(m=4000, n=40000, mean_len=20, max_len=5000, seed=9)
 
 
+_ORACLE_CACHE = {}
+
+
+def _oracle_once(key, fn):
+    if key not in _ORACLE_CACHE:
+        _ORACLE_CACHE[key] = fn()
+    return _ORACLE_CACHE[key]
+
+
+@pytest.mark.parametrize("layout", ["auto", "csr"])
 @pytest.mark.parametrize("shape", ["tall", "wide", "powerlaw"])
-def test_parity_shapes(plss, shape):
+def test_parity_shapes(plss, shape, layout):
     """Overdetermined with column scales, underdetermined, and power-law rows
-    (rows longer than a tile run one CTA per row): 80 updates against the
-    oracle (calibrated bar), then the solve to 1e-8 reaches the oracle's
-    limit x0 + A^T (A A^T)^+ (b - A x0) within the accuracy the tolerance
-    allows."""
+    (rows longer than a tile run one CTA per row), with the sliced tiles
+    (auto) and with the CSR/CSC only: 80 updates against the oracle
+    (calibrated bar), then the solve to 1e-8 reaches the oracle's limit
+    x0 + A^T (A A^T)^+ (b - A x0) within the accuracy the tolerance allows."""
     A, b, xs = _shape(shape)
     A = A.astype(np.float64)
     K = 80
-    ref = _parity.reference(A, b, K)
-    with plss.Context(A) as ctx:
+    ref = _oracle_once((shape, "ref"), lambda: _parity.reference(A, b, K))
+    with plss.Context(A, layout=layout) as ctx:
+        lay = ctx.layout()
+        if layout == "csr":
+            assert lay["row_sliced"] == 0 and lay["col_sliced"] == 0
+        elif shape == "powerlaw":
+            # power-law rows pad slices too much and stay in the CSR; the
+            # short columns are sliced
+            assert lay["row_sliced"] < lay["row_tiles"] and lay["col_sliced"] > 0
+        else:
+            assert lay["row_sliced"] > 0 and lay["col_sliced"] > 0
         x, res, hist = ctx.solve(b, tol=0.0, maxit=K, hist=K)
         assert res["iters"] == K
         _parity.check_scalars(hist, ref, min_strict=10)
@@ -120,7 +139,8 @@ def test_parity_shapes(plss, shape):
         x, res = ctx.solve(b, tol=1e-8, maxit=200000, stop_on_true=1)
     assert res["status"] == "converged" and res["relres_true"] <= 1e-8
     if shape != "powerlaw":   # the oracle needs ~80k updates (a minute) there
-        fin = oracle.residual(A, b, tol=1e-8, maxit=200000, stop_on_true=True)
+        fin = _oracle_once((shape, "fin"),
+                           lambda: oracle.residual(A, b, tol=1e-8, maxit=200000, stop_on_true=True))
         assert fin["status"] == "converged"
         assert rel(x, fin["x"]) < 1e-4
 
@@ -142,7 +162,8 @@ def test_weighted_parity(plss, w_mode):
     assert rel(x, xs) < 1e-5     # full column rank: the solution is x*
 
 
-def test_fp32_storage_parity_and_accuracy(plss):
+@pytest.mark.parametrize("layout", ["auto", "csr"])
+def test_fp32_storage_parity_and_accuracy(plss, layout):
     """FP32 storage, FP64 scalars and refinement: early scalars follow the
     oracle's FP32 emulation to float rounding; with W = diag(1/||A_j||^2) the
     answer reaches the FP64 tolerance on b - A x and the FP64 oracle's x."""
@@ -150,7 +171,8 @@ def test_fp32_storage_parity_and_accuracy(plss):
     emu = oracle.residual(A, b, tol=0.0, maxit=20, prec=1, stop_on_true=True, hist=20)
     w = oracle.colweights(A, 2)
     ref = oracle.residual(A, b, w=w, tol=1e-11, maxit=5000)
-    with plss.Context(A, precision="fp32") as ctx:
+    with plss.Context(A, precision="fp32", layout=layout) as ctx:
+        assert (ctx.layout()["row_sliced"] > 0) == (layout == "auto")
         _, _, hist = ctx.solve(b, tol=0.0, maxit=20, hist=20)
         assert _parity.rel_rows(hist[:8], emu["hist_s"][:8]).max() < 1e-4
         x, res = ctx.solve(b, tol=1e-8, maxit=5000, w_mode=2)
@@ -202,14 +224,15 @@ def test_edge_cases(plss):
     assert rel(x, ref["x"]) < RTOL
 
 
-def test_ragged_tails(plss):
-    """Row counts just off the tile and group boundaries."""
+@pytest.mark.parametrize("layout", ["auto", "csr"])
+def test_ragged_tails(plss, layout):
+    """Row counts just off the tile, slice and group boundaries."""
     for m in (1, 31, 33, 255, 257, 2049):
         A, b, xs = synth.powerlaw_underdetermined(m=m, n=3 * m + 7, mean_len=6, max_len=50, seed=m)
         A = A.astype(np.float64)
         K = 12
         ref = _parity.reference(A, b, K)
-        with plss.Context(A) as ctx:
+        with plss.Context(A, layout=layout) as ctx:
             x, res, hist = ctx.solve(b, tol=0.0, maxit=K, hist=K)
         assert res["iters"] == ref["iters"], m
         _parity.check_scalars(hist, ref, min_strict=1)

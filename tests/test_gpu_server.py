@@ -73,7 +73,7 @@ def test_mix_equals_alone(plss, precision):
         srv.close()
     for (A, b), t in zip(reqs, tickets):
         x_mix, r_mix = got[t]
-        with plss.Context(A, precision=precision) as ctx:
+        with plss.Context(A, precision=precision, layout="csr") as ctx:   # the arena's layout
             x_one, r_one = ctx.solve(b, stop_on_true=1, **kw)
         assert r_mix["status"] == r_one["status"]
         assert r_mix["iters"] == r_one["iters"]
