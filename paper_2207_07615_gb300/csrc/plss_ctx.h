@@ -69,6 +69,7 @@ struct plss_ctx {
 
     plss::Sliced rsl{}, csl{};        // sliced copies (csl aliases rsl when symmetric)
     int64_t sl_elems[2] = {0, 0};     // elements of the sliced row / column copies
+    int32_t *d_rwr = nullptr, *d_cwr = nullptr;   // warp ranges (Sliced::wr) or null
 
     plss::KaczState *kacz = nullptr;
     plss::RhsState *rhs = nullptr;

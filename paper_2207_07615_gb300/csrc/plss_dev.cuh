@@ -38,6 +38,10 @@ struct Sliced {
     const int32_t *seg;     // [32 * slices] segment of each slot, -1 if none
     const int32_t *idx;     // padded indices
     const void *val;        // padded values (storage type)
+    // Single-system contexts whose every tile of this side is sliced: warp w
+    // of the sweep's grid takes slices [wr[w], wr[w + 1]) (balanced by
+    // elements); null otherwise.
+    const int32_t *wr;
 };
 
 struct Tile {

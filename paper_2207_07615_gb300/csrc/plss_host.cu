@@ -331,6 +331,28 @@ static plss_status upload_sliced(const HostSliced &h, Sliced &d, bool f32) {
     return st;
 }
 
+// Splits the slices (element offsets sptr) into nwarps contiguous ranges of
+// about equal elements and uploads the nwarps + 1 boundaries; *out stays
+// null unless every tile is sliced.
+static plss_status upload_warp_ranges(const std::vector<Tile> &tiles, const std::vector<int32_t> &sptr,
+                                      int64_t nwarps, int32_t **out) {
+    *out = nullptr;
+    if (tiles.empty() || sptr.size() < 2) return PLSS_OK;
+    for (const Tile &t : tiles)
+        if (!(t.group & kSliced)) return PLSS_OK;
+    const int64_t ns = int64_t(sptr.size()) - 1;
+    const int64_t total = sptr.back();
+    std::vector<int32_t> wr(size_t(nwarps + 1));
+    int64_t s = 0;
+    for (int64_t w = 0; w < nwarps; ++w) {
+        const int64_t goal = total * w / nwarps;   // elements before warp w's first slice
+        while (s < ns && sptr[size_t(s)] < goal) ++s;
+        wr[size_t(w)] = int32_t(s);
+    }
+    wr[size_t(nwarps)] = int32_t(ns);
+    return upload(out, wr, "warp ranges");
+}
+
 static void free_sliced(Sliced &d) {
     const void *ptrs[] = {d.first, d.ptr, d.seg, d.idx, d.val};
     for (const void *p : ptrs) dfree(const_cast<void *>(p));
@@ -375,6 +397,8 @@ static void ctx_free(plss_ctx *c) {
     }
     free_sliced(c->rsl);
     if (!c->symmetric) free_sliced(c->csl);
+    dfree(c->d_rwr);
+    dfree(c->d_cwr);
     if (c->h_st) cudaFreeHost(c->h_st);
     if (c->h_active) cudaFreeHost(c->h_active);
     free_extra(c);
@@ -519,15 +543,20 @@ static plss_status ctx_build(const plss_csr *As, int32_t nsys, const plss_opts *
     fill_sliced(rp.data(), ci.data(), c->f32 ? nullptr : v64.data(), c->f32 ? v32.data() : nullptr, c->h_rt, hsl);
     TRY_ST(upload_sliced(hsl, c->rsl, c->f32));
     c->sl_elems[0] = int64_t(hsl.idx.size());
+    const std::vector<int32_t> rsl_ptr = hsl.ptr;
+    std::vector<int32_t> csl_ptr;
     if (sym) {
         c->csl = c->rsl;   // same tiles over the same arrays
         c->sl_elems[1] = c->sl_elems[0];
+        csl_ptr = rsl_ptr;
     } else {
         fill_sliced(cp.data(), ri.data(), c->f32 ? nullptr : cv64.data(), c->f32 ? cv32.data() : nullptr,
                     c->h_ct, hsl);
         TRY_ST(upload_sliced(hsl, c->csl, c->f32));
         c->sl_elems[1] = int64_t(hsl.idx.size());
+        csl_ptr = hsl.ptr;
     }
+    hsl = HostSliced();
     TRY_ST(upload(&c->d_rt, c->h_rt, "row tiles"));
     TRY_ST(upload(&c->d_ct, c->h_ct, "col tiles"));
     TRY_ST(upload(&c->d_vt, c->h_vt, "vec tiles"));
@@ -563,10 +592,24 @@ static plss_status ctx_build(const plss_csr *As, int32_t nsys, const plss_opts *
         ctx_free(c);
         return fail(PLSS_ERR_CUDA, "stream/event creation failed");
     }
-#undef TRY_ST
     c->grid_r = std::max(1, std::min(int(c->h_rt.size()), c->nsm * sweep_ctas_per_sm(0, c->f32)));
     c->grid_c = std::max(1, std::min(int(c->h_ct.size()), c->nsm * sweep_ctas_per_sm(1, c->f32)));
     c->grid_v = std::max(1, std::min(int(c->h_vt.size()), c->nsm * sweep_ctas_per_sm(2, c->f32)));
+
+    // one system with every tile of a side sliced: warp ranges instead of
+    // tiles for that side's sweep
+    if (nsys == 1) {
+        // one partial per CTA: at most as many CTAs as tiles (the partial arrays' size)
+        const int gr = std::max(1, std::min(int(c->h_rt.size()), c->nsm * sweep_ctas_per_sm(3, c->f32)));
+        const int gc = std::max(1, std::min(int(c->h_ct.size()), c->nsm * sweep_ctas_per_sm(4, c->f32)));
+        TRY_ST(upload_warp_ranges(c->h_rt, rsl_ptr, int64_t(gr) * kWarps, &c->d_rwr));
+        TRY_ST(upload_warp_ranges(c->h_ct, csl_ptr, int64_t(gc) * kWarps, &c->d_cwr));
+        c->rsl.wr = c->d_rwr;
+        c->csl.wr = c->d_cwr;
+        if (c->d_rwr) c->grid_r = gr;
+        if (c->d_cwr) c->grid_c = gc;
+    }
+#undef TRY_ST
 
     SweepArgs &a = c->args;
     a.row_ptr = c->d_row_ptr;

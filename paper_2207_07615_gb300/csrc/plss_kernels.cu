@@ -456,44 +456,50 @@ __device__ __forceinline__ void row_tile_cta(const SweepArgs &a, const Tile &t, 
     }
 }
 
-// Sliced tile of the row sweep (both storage types): r = r - A p, or
-// r = b - A x with products in double after a (re)start; one lane per row.
+// One slot (row) of a slice in the row sweep: r = r - A p, or r = b - A x
+// with products in double after a (re)start; rho (and ||b||^2) partials in
+// double.
 template <typename S>
-__device__ __forceinline__ void row_tile_sliced(const SweepArgs &a, const Tile &t, int32_t ti, bool init,
-                                                double &acc_r, double &acc_b) {
+__device__ __forceinline__ void row_slot(const SweepArgs &a, int32_t row, int32_t off, int32_t width,
+                                         int lane, bool init, double &acc_r, double &acc_b) {
     const S *__restrict__ val = static_cast<const S *>(a.rsl.val);
     S *__restrict__ r = static_cast<S *>(a.r);
     if (init) {
-        for_slices(a.rsl, t, ti, [&](int32_t row, int32_t off, int32_t width, int lane) {
-            const double bi = row >= 0 ? a.b[row] : 0.0;
-            const double d = slice_dot<S, double, double>(a.rsl.idx, val, off, width, lane, a.x);
-            if (row >= 0) {
-                const S ri = S(bi - d);
-                r[row] = ri;
-                acc_r = fma(double(ri), double(ri), acc_r);
-                acc_b = fma(bi, bi, acc_b);
-            }
-        });
+        const double bi = row >= 0 ? a.b[row] : 0.0;
+        const double d = slice_dot<S, double, double>(a.rsl.idx, val, off, width, lane, a.x);
+        if (row >= 0) {
+            const S ri = S(bi - d);
+            r[row] = ri;
+            acc_r = fma(double(ri), double(ri), acc_r);
+            acc_b = fma(bi, bi, acc_b);
+        }
     } else {
-        const S *__restrict__ p = static_cast<const S *>(a.p);
-        for_slices(a.rsl, t, ti, [&](int32_t row, int32_t off, int32_t width, int lane) {
-            const S old = row >= 0 ? r[row] : S(0);   // issued before the dot's loads
-            const S d = slice_dot<S, S, S>(a.rsl.idx, val, off, width, lane, p);
-            if (row >= 0) {
-                const S ri = old - d;
-                r[row] = ri;
-                acc_r = fma(double(ri), double(ri), acc_r);
-            }
-        });
+        const S old = row >= 0 ? r[row] : S(0);   // issued before the dot's loads
+        const S d = slice_dot<S, S, S>(a.rsl.idx, val, off, width, lane, static_cast<const S *>(a.p));
+        if (row >= 0) {
+            const S ri = old - d;
+            r[row] = ri;
+            acc_r = fma(double(ri), double(ri), acc_r);
+        }
     }
 }
 
-__device__ void finish_row(const SweepArgs &a, int32_t sys, bool init) {
-    const SysDesc d = a.desc[sys];
+// Sliced tile of the row sweep (both storage types); one lane per row.
+template <typename S>
+__device__ __forceinline__ void row_tile_sliced(const SweepArgs &a, const Tile &t, int32_t ti, bool init,
+                                                double &acc_r, double &acc_b) {
+    for_slices(a.rsl, t, ti, [&](int32_t row, int32_t off, int32_t width, int lane) {
+        row_slot<S>(a, row, off, width, lane, init, acc_r, acc_b);
+    });
+}
+
+// Sums the row-sweep partials [pb, pb + pc) of system `sys` in a fixed order
+// and applies the stopping rule (whole CTA; the last CTA of the system).
+__device__ void finish_row(const SweepArgs &a, int32_t sys, bool init, int32_t pb, int32_t pc) {
     double v[2] = {0.0, 0.0};
-    for (int32_t i = threadIdx.x; i < d.rt_count; i += kThreads) {
-        v[0] += __ldcg(a.part_row + 2 * (d.rt_begin + i));
-        v[1] += __ldcg(a.part_row + 2 * (d.rt_begin + i) + 1);
+    for (int32_t i = threadIdx.x; i < pc; i += kThreads) {
+        v[0] += __ldcg(a.part_row + 2 * (pb + i));
+        v[1] += __ldcg(a.part_row + 2 * (pb + i) + 1);
     }
     cta_sum<2>(v);
     if (threadIdx.x != 0) return;
@@ -546,7 +552,7 @@ __global__ void __launch_bounds__(kThreads) k_row_sweep(SweepArgs a) {
         const Tile t = a.rtiles[ti];
         if (t.sys != cur) {
             if (pending && arrive(&a.st[cur].cnt_row, pending, a.desc[cur].rt_count))
-                finish_row(a, cur, init);
+                finish_row(a, cur, init, a.desc[cur].rt_begin, a.desc[cur].rt_count);
             cur = t.sys;
             pending = 0;
             const int32_t ph = load_phase(a.st + cur);
@@ -589,7 +595,35 @@ __global__ void __launch_bounds__(kThreads) k_row_sweep(SweepArgs a) {
         }
         ++pending;
     }
-    if (pending && arrive(&a.st[cur].cnt_row, pending, a.desc[cur].rt_count)) finish_row(a, cur, init);
+    if (pending && arrive(&a.st[cur].cnt_row, pending, a.desc[cur].rt_count))
+        finish_row(a, cur, init, a.desc[cur].rt_begin, a.desc[cur].rt_count);
+}
+
+// Row sweep of a single-system context whose row tiles are all sliced: warp
+// w takes slices [wr[w], wr[w + 1]), one partial per CTA, one barrier per
+// CTA (its closing sum) instead of one per tile.
+template <typename S>
+__global__ void __launch_bounds__(kThreads) k_row_sweep_w(SweepArgs a) {
+    wait_prior_grid();
+    const int32_t ph = load_phase(a.st);
+    if (ph != PH_SETUP && ph != PH_RUN) return;   // uniform over the grid
+    const bool init = ph == PH_SETUP;
+    const int lane = threadIdx.x & 31;
+    const int32_t w = int32_t(blockIdx.x) * kWarps + (threadIdx.x >> 5);
+    const int32_t s0 = __ldg(a.rsl.wr + w), s1 = __ldg(a.rsl.wr + w + 1);
+    double acc[2] = {0.0, 0.0};
+    for (int32_t s = s0; s < s1; ++s) {
+        const int32_t off = __ldg(a.rsl.ptr + s);
+        const int32_t width = (__ldg(a.rsl.ptr + s + 1) - off) >> 5;
+        const int32_t row = __ldg(a.rsl.seg + 32 * s + lane);
+        row_slot<S>(a, row, off, width, lane, init, acc[0], acc[1]);
+    }
+    cta_sum<2>(acc);
+    if (threadIdx.x == 0) {
+        a.part_row[2 * blockIdx.x] = acc[0];
+        a.part_row[2 * blockIdx.x + 1] = acc[1];
+    }
+    if (arrive(&a.st->cnt_row, 1, int32_t(gridDim.x))) finish_row(a, 0, init, 0, int32_t(gridDim.x));
 }
 
 // ---------------------------------------------------------------------------
@@ -641,31 +675,37 @@ __device__ __forceinline__ void col_tile_cta(const SweepArgs &a, const Tile &t, 
     if (threadIdx.x == 0) col_out<S>(a, col, double(S(d)), acc);
 }
 
-// Sliced tile of the column sweep: y = A^T r, u = W y (float weights for
-// FP32 storage), phi partial in double; one lane per column.
+// One slot (column) of a slice in the column sweep: y = A^T r, u = W y
+// (float weights for FP32 storage), phi partial in double.
+template <typename S>
+__device__ __forceinline__ void col_slot(const SweepArgs &a, int32_t col, int32_t off, int32_t width,
+                                         int lane, double &acc) {
+    const S y = slice_dot<S, S, S>(a.csl.idx, static_cast<const S *>(a.csl.val), off, width, lane,
+                                   static_cast<const S *>(a.r));
+    if (col >= 0) {
+        if constexpr (std::is_same<S, float>::value) {
+            const float uj = a.wf ? __fmul_rn(a.wf[col], y) : y;
+            static_cast<float *>(a.u)[col] = uj;
+            acc = fma(double(y), double(uj), acc);
+        } else {
+            col_out<S>(a, col, double(y), acc);
+        }
+    }
+}
+
+// Sliced tile of the column sweep; one lane per column.
 template <typename S>
 __device__ __forceinline__ void col_tile_sliced(const SweepArgs &a, const Tile &t, int32_t ti, double &acc) {
-    const S *__restrict__ val = static_cast<const S *>(a.csl.val);
-    const S *__restrict__ r = static_cast<const S *>(a.r);
     for_slices(a.csl, t, ti, [&](int32_t col, int32_t off, int32_t width, int lane) {
-        const S y = slice_dot<S, S, S>(a.csl.idx, val, off, width, lane, r);
-        if (col >= 0) {
-            if constexpr (std::is_same<S, float>::value) {
-                const float uj = a.wf ? __fmul_rn(a.wf[col], y) : y;
-                static_cast<float *>(a.u)[col] = uj;
-                acc = fma(double(y), double(uj), acc);
-            } else {
-                col_out<S>(a, col, double(y), acc);
-            }
-        }
+        col_slot<S>(a, col, off, width, lane, acc);
     });
 }
 
-__device__ void finish_col(const SweepArgs &a, int32_t sys) {
-    const SysDesc d = a.desc[sys];
+// Sums the column-sweep partials [pb, pb + pc) of system `sys` in a fixed
+// order and takes the scalar step (whole CTA; the last CTA of the system).
+__device__ void finish_col(const SweepArgs &a, int32_t sys, int32_t pb, int32_t pc) {
     double v[1] = {0.0};
-    for (int32_t i = threadIdx.x; i < d.ct_count; i += kThreads)
-        v[0] += __ldcg(a.part_col + d.ct_begin + i);
+    for (int32_t i = threadIdx.x; i < pc; i += kThreads) v[0] += __ldcg(a.part_col + pb + i);
     cta_sum<1>(v);
     if (threadIdx.x != 0) return;
     SysState *st = a.st + sys;
@@ -713,7 +753,8 @@ __global__ void __launch_bounds__(kThreads) k_col_sweep(SweepArgs a) {
     for (int32_t ti = t0; ti < t1; ++ti) {
         const Tile t = a.ctiles[ti];
         if (t.sys != cur) {
-            if (pending && arrive(&a.st[cur].cnt_col, pending, a.desc[cur].ct_count)) finish_col(a, cur);
+            if (pending && arrive(&a.st[cur].cnt_col, pending, a.desc[cur].ct_count))
+                finish_col(a, cur, a.desc[cur].ct_begin, a.desc[cur].ct_count);
             cur = t.sys;
             pending = 0;
             const int32_t ph = load_phase(a.st + cur);
@@ -750,7 +791,30 @@ __global__ void __launch_bounds__(kThreads) k_col_sweep(SweepArgs a) {
         if (threadIdx.x == 0) a.part_col[ti] = acc[0];
         ++pending;
     }
-    if (pending && arrive(&a.st[cur].cnt_col, pending, a.desc[cur].ct_count)) finish_col(a, cur);
+    if (pending && arrive(&a.st[cur].cnt_col, pending, a.desc[cur].ct_count))
+        finish_col(a, cur, a.desc[cur].ct_begin, a.desc[cur].ct_count);
+}
+
+// Column sweep of a single-system context whose column tiles are all
+// sliced (warp ranges as in k_row_sweep_w).
+template <typename S>
+__global__ void __launch_bounds__(kThreads) k_col_sweep_w(SweepArgs a) {
+    wait_prior_grid();
+    const int32_t ph = load_phase(a.st);
+    if (ph != PH_FIRST && ph != PH_RUN) return;   // uniform over the grid
+    const int lane = threadIdx.x & 31;
+    const int32_t w = int32_t(blockIdx.x) * kWarps + (threadIdx.x >> 5);
+    const int32_t s0 = __ldg(a.csl.wr + w), s1 = __ldg(a.csl.wr + w + 1);
+    double acc[1] = {0.0};
+    for (int32_t s = s0; s < s1; ++s) {
+        const int32_t off = __ldg(a.csl.ptr + s);
+        const int32_t width = (__ldg(a.csl.ptr + s + 1) - off) >> 5;
+        const int32_t col = __ldg(a.csl.seg + 32 * s + lane);
+        col_slot<S>(a, col, off, width, lane, acc[0]);
+    }
+    cta_sum<1>(acc);
+    if (threadIdx.x == 0) a.part_col[blockIdx.x] = acc[0];
+    if (arrive(&a.st->cnt_col, 1, int32_t(gridDim.x))) finish_col(a, 0, 0, int32_t(gridDim.x));
 }
 
 // ---------------------------------------------------------------------------
@@ -991,6 +1055,12 @@ int sweep_ctas_per_sm(int which, bool f32) {
         case 1: e = f32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_col_sweep<float>, kThreads, 0)
                         : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_col_sweep<double>, kThreads, 0);
                 break;
+        case 3: e = f32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_row_sweep_w<float>, kThreads, 0)
+                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_row_sweep_w<double>, kThreads, 0);
+                break;
+        case 4: e = f32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_col_sweep_w<float>, kThreads, 0)
+                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_col_sweep_w<double>, kThreads, 0);
+                break;
         default: e = f32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_update<float>, kThreads, 0)
                          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_update<double>, kThreads, 0);
                 break;
@@ -1021,10 +1091,14 @@ static cudaError_t launch_pdl(void (*kernel)(Args...), int grid, cudaStream_t s,
 }
 
 cudaError_t launch_row_sweep(const SweepArgs &a, bool f32, int grid, cudaStream_t s) {
+    if (a.rsl.wr)
+        return f32 ? launch_pdl(k_row_sweep_w<float>, grid, s, a) : launch_pdl(k_row_sweep_w<double>, grid, s, a);
     return f32 ? launch_pdl(k_row_sweep<float>, grid, s, a) : launch_pdl(k_row_sweep<double>, grid, s, a);
 }
 
 cudaError_t launch_col_sweep(const SweepArgs &a, bool f32, int grid, cudaStream_t s) {
+    if (a.csl.wr)
+        return f32 ? launch_pdl(k_col_sweep_w<float>, grid, s, a) : launch_pdl(k_col_sweep_w<double>, grid, s, a);
     return f32 ? launch_pdl(k_col_sweep<float>, grid, s, a) : launch_pdl(k_col_sweep<double>, grid, s, a);
 }
 

@@ -15,7 +15,8 @@ cudaError_t launch_row_sweep(const SweepArgs &a, bool f32, int grid, cudaStream_
 cudaError_t launch_col_sweep(const SweepArgs &a, bool f32, int grid, cudaStream_t s);
 cudaError_t launch_update(const SweepArgs &a, bool f32, int grid, cudaStream_t s);
 
-// Resident CTAs per SM of a sweep kernel (0 row, 1 column, 2 update).
+// Resident CTAs per SM of a sweep kernel (0 row, 1 column, 2 update, 3 row
+// and 4 column over warp ranges).
 int sweep_ctas_per_sm(int which, bool f32);
 
 // out[seg] = (A v)[seg] over the segments of `tiles` in double; with b,
