@@ -58,6 +58,11 @@ def parse():
     ap.add_argument("--oracle-updates", type=int, default=100)
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4a", "c4b", "c5"],
+                    help="c2 (default): the headline line; the others print one line each for "
+                         "the other synthetic workloads (see suite_* below)")
+    ap.add_argument("--requests", type=int, default=1000, help="c5: requests in the trace")
+    ap.add_argument("--pool", type=int, default=64, help="c5: matrices in the request pool")
     return ap.parse_args()
 
 
@@ -210,6 +215,10 @@ def cpu_baseline(A, b, args, updates_to_tol):
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
+        return
+    if args.workload != "c2":
+        print(json.dumps({"impl": "reference", "unavailable": "the oracle arm times the headline "
+                          "workload (c2) only"}), flush=True)
         return
     A, b, _ = make_workload(args)
     cpu, cores = host_info()
@@ -400,10 +409,222 @@ def run_variants(args, A, b, xs, x_ref, ctx, b_dev, flush):
     return out
 
 
+# ------------------------------------------------------- other workloads
+#
+# One JSON line per workload, same clocks and device-timing rules as the
+# headline: inputs resident in HBM (device buffers), CUDA events on the
+# solve's stream, W warm-up solves. They cover the identity sketch (c3), the
+# batched and many-right-hand-side forms (c4a, c4b) and serving (c5).
+
+def _suite_common(args):
+    import torch
+    import __graft_entry__ as g
+    from paper_2207_07615_gb300 import plss
+    g.build()
+    plss.lib()
+    torch.cuda.set_device(0)
+    return torch, plss
+
+
+def _timed(torch, fn, warmup, steps):
+    """Runs fn() warmup times, then steps times between CUDA events on the
+    current stream; returns (seconds per step, last result)."""
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    out = None
+    for _ in range(warmup):
+        out = fn()
+        flush.zero_()
+    torch.cuda.synchronize()
+    clocks = Clocks(0)
+    tot = 0.0
+    for _ in range(steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        out = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        tot += e0.elapsed_time(e1) / 1e3
+    return tot / steps, out, clocks.stop()
+
+
+def _line(metric, value, unit, args, workload, extra, hib=False, dtype="f32+f64"):
+    line = {"metric": metric, "value": value, "unit": unit, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": value * 1e3 if unit == "s" else None,
+            "higher_is_better": hib, "scaling": "weak", "vs_baseline": None, "dtype": dtype,
+            "data": "synthetic", "config": {"workload": workload}}
+    line.update(extra)
+    print(json.dumps(line), flush=True)
+
+
+def suite_c1(args):
+    """2,000 x 2,000 diagonally dominant, FP64, tol 1e-10 (L2-resident,
+    latency-bound: time per update rather than GB/s)."""
+    torch, plss = _suite_common(args)
+    import oracle
+    A, b, xs = synth.square_diag_dominant()
+    A = A.astype(np.float64)
+    ctx = plss.Context(A)
+    bd = torch.from_numpy(b).cuda()
+    t, (x, r), clk = _timed(torch, lambda: ctx.solve(bd, tol=1e-10, maxit=2000, stop_on_true=1),
+                            args.warmup, args.steps)
+    oracle.build()
+    t0 = time.perf_counter()
+    ref = oracle.residual(A, b, tol=1e-10, maxit=2000)
+    tcpu = time.perf_counter() - t0
+    err = float(np.linalg.norm(x.cpu().numpy() - ref["x"]) / np.linalg.norm(ref["x"]))
+    _line("time to ||r||/||b||<=1e-10", t, "s", args, "plss_square_2000_diagdom_nnz11", {
+        "dtype": "f64",
+        "solve": {"updates": r["iters"], "status": r["status"], "relres_true": r["relres_true"],
+                  "us_per_update": t / max(1, r["iters"]) * 1e6, "rel_err_vs_oracle": err},
+        "cpu_baseline": {"value": tcpu, "unit": "s", "cores": 1, "kind": "oracle",
+                         "sample": f"the whole solve ({ref['iters']} updates)"},
+        "clocks": clk})
+    ctx.close()
+
+
+def suite_c3(args):
+    """100,000 x 1,000,000, power-law rows (mean 20, max 5,000), U(-1,1) in
+    FP32: residual sketch (FP32 storage and FP64) and identity sketch."""
+    torch, plss = _suite_common(args)
+    A, b, xs = synth.powerlaw_underdetermined()
+    bd = torch.from_numpy(b).cuda()
+    out = {}
+    for prec in ("fp32", "fp64"):
+        Ap = A if prec == "fp32" else A.astype(np.float64)
+        ctx = plss.Context(Ap, precision=prec)
+        for w in (0, 2):
+            t, (x, r), clk = _timed(torch, lambda: ctx.solve(bd, tol=1e-8, maxit=200000, stop_on_true=1,
+                                                             w_mode=w), 1, 1)
+            out[f"residual_{prec}_w{w}"] = {"seconds": t, "updates": r["iters"], "status": r["status"],
+                                            "relres_true": r["relres_true"],
+                                            "us_per_update": t / max(1, r["iters"]) * 1e6}
+        out[f"layout_{prec}"] = ctx.layout()
+        ctx.close()
+    ctx = plss.Context(A, precision="fp64")
+    for K in (0, 8):
+        t, (x, r), clk = _timed(torch, lambda: ctx.solve(bd, sketch="identity", tol=1e-8,
+                                                         maxit=10 * A.m, kacz_hist=K, seed=7), 1, 1)
+        out[f"identity_K{K}"] = {"seconds": t, "rows_visited": r["iters"], "status": r["status"],
+                                 "relres_true": r["relres_true"],
+                                 "passes": r["iters"] / A.m}
+    ctx.close()
+    conv = [v["seconds"] for k, v in out.items() if k.startswith(("residual", "identity"))
+            and v["status"] == "converged"]
+    _line("time to ||r||/||b||<=1e-8", min(conv) if conv else None, "s", args,
+          "plss_underdetermined_1e5x1e6_zipf20_max5000",
+          {"forms": out, "clocks": clk, "value_is": "fastest converged form (null: none within the caps)"})
+
+
+def suite_c4a(args):
+    """256 independent systems (m log-uniform [1e3, 2e5], n = m or m/2, 5-50
+    nonzeros per row, N(0,1) in FP32) in one batched context."""
+    torch, plss = _suite_common(args)
+    systems = synth.batched_systems()
+    As = [A for A, _, _ in systems]
+    bs = [torch.from_numpy(b).cuda() for _, b, _ in systems]
+    nnz = sum(A.nnz for A in As)
+    out = {}
+    for prec in ("fp32", "fp64"):
+        ctx = plss.Context(As if prec == "fp32" else [A.astype(np.float64) for A in As], precision=prec)
+        t, (xs_, rs), clk = _timed(torch, lambda: ctx.solve_batched(bs, tol=1e-8, maxit=5000, stop_on_true=1,
+                                                                    w_mode=2), args.warmup, args.steps)
+        ups = sum(r["iters"] for r in rs)
+        out[prec] = {"seconds": t, "converged": sum(r["status"] == "converged" for r in rs),
+                     "systems": len(rs), "system_updates": ups, "max_updates": max(r["iters"] for r in rs),
+                     "worst_relres_true": max(r["relres_true"] for r in rs)}
+        ctx.close()
+    _line("time to ||r||/||b||<=1e-8 (all systems)", out["fp32"]["seconds"], "s", args,
+          "plss_batched_256_systems", {"forms": out, "nnz_total": int(nnz), "w_mode": 2, "maxit": 5000,
+                                       "clocks": clk})
+
+
+def suite_c4b(args):
+    """7-point Laplacian on 126^3 with 32 right-hand sides (SpMM sweeps),
+    FP32 storage with FP64 refinement, tol 1e-8."""
+    torch, plss = _suite_common(args)
+    A = synth.laplacian7()
+    B, Xs = synth.laplacian_rhs(A)
+    Bd = torch.from_numpy(B).cuda()
+    out = {}
+    for prec in ("fp32", "fp64"):
+        ctx = plss.Context(A if prec == "fp32" else A.astype(np.float64), precision=prec, symmetric=True)
+        t, (X, rs), clk = _timed(torch, lambda: ctx.solve_rhs(Bd, tol=1e-8, maxit=50000, stop_on_true=1),
+                                 1, 1)
+        Xh = X.cpu().numpy()
+        out[prec] = {"seconds": t, "converged": sum(r["status"] == "converged" for r in rs),
+                     "max_updates": max(r["iters"] for r in rs),
+                     "worst_relres_true": max(r["relres_true"] for r in rs),
+                     "rel_err_vs_xstar": float(np.linalg.norm(Xh - Xs) / np.linalg.norm(Xs))}
+        ctx.close()
+    _line("time to ||r||/||b||<=1e-8 (32 right-hand sides)", out["fp32"]["seconds"], "s", args,
+          "plss_laplacian7_126cube_32rhs", {"forms": out, "nnz": int(A.nnz), "clocks": clk})
+
+
+def suite_c5(args):
+    """Open-loop Poisson arrivals (2,000 requests/s) of random sparse
+    consistent systems (m log-uniform [1e3, 1e6], n/m in {0.5, 1, 2}, 8-32
+    nonzeros per row, N(0,1)) into the continuous-batching server, FP32 with
+    FP64 refinement, W = diag(1/||A_j||), tol 1e-6, maxit 3,000. Latency is
+    completion minus arrival and includes the upload."""
+    import threading
+    torch, plss = _suite_common(args)
+    arrivals, pool_ids, mats = synth.serving_trace(nreq=args.requests, pool=args.pool)
+    reqs = []
+    for i, pid in enumerate(pool_ids):
+        A = mats[int(pid)]
+        xs = synth.rng_for(3000 + 1_000_000 + i).standard_normal(A.n)
+        reqs.append((A, synth.rhs(A, xs)))
+    srv = plss.Server(max_slots=64, precision="fp32")
+    done = {}
+    t0 = time.perf_counter()
+    tickets = [None] * len(reqs)
+    busy = [0]
+
+    def submitter():
+        for i, (A, b) in enumerate(reqs):
+            while time.perf_counter() - t0 < arrivals[i]:
+                time.sleep(0.0002)
+            t = None
+            while t is None:
+                t = srv.submit(A, b, tol=1e-6, maxit=3000, w_mode=1)
+                if t is None:
+                    busy[0] += 1
+                    time.sleep(0.001)
+            tickets[i] = t
+
+    th = threading.Thread(target=submitter)
+    clocks = Clocks(0)
+    th.start()
+    while len(done) < len(reqs):
+        for i, t in enumerate(tickets):
+            if t is None or i in done:
+                continue
+            r = srv.poll(t)
+            if r is not None:
+                done[i] = (time.perf_counter() - t0, r[1])
+        time.sleep(0.0005)
+    th.join()
+    clk = clocks.stop()
+    srv.close()
+    lat = np.array([done[i][0] - arrivals[i] for i in range(len(reqs))])
+    span = max(v[0] for v in done.values())
+    conv = sum(v[1]["status"] == "converged" for v in done.values())
+    _line("served solves/s", len(reqs) / span, "solves/s", args, "plss_serving_poisson2000", {
+        "higher_is_better": True, "steps": 1, "warmup": 0, "ms_per_step": None,
+        "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                      "mean": float(lat.mean()), "max": float(lat.max())},
+        "requests": len(reqs), "pool": args.pool, "converged": int(conv), "makespan_s": span,
+        "busy_retries": busy[0], "clocks": clk})
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload != "c2":
+        globals()[f"suite_{args.workload}"](args)
     else:
         run_plss(args)
 

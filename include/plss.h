@@ -175,7 +175,8 @@ plss_status plss_solve_batched(plss_ctx *ctx, const double *const *b, const doub
 /* Many right-hand sides on one matrix (SpMM form): B is m x nrhs, X0 and X
  * are n x nrhs, all row-major double (X0 may be NULL). Each column is an
  * independent PLSS solve with its own scalars; converged columns freeze.
- * res[nrhs]. Residual sketch only; nrhs <= 64. */
+ * res[nrhs]. Residual sketch only; 1 <= nrhs <= 32 (one warp lane per
+ * column), else PLSS_ERR_INVALID. */
 plss_status plss_solve_rhs(plss_ctx *ctx, int32_t nrhs, const double *B, const double *X0,
                            double *X, const plss_opts *o, plss_result *res);
 

@@ -36,6 +36,7 @@
 #include <type_traits>
 
 #include "plss_dev.cuh"
+#include "plss_devfn.cuh"
 #include "plss_launch.h"
 
 namespace plss {
@@ -74,31 +75,6 @@ __device__ __forceinline__ void cta_sum(double (&v)[N]) {
             v[i] = t;
         }
     }
-}
-
-// Double-float accumulator (an unevaluated sum hi + lo of two floats, about
-// 48 significant bits) built from FP32 operations only. The FP32-storage
-// sweeps keep their inner products in it: on GB300 every FP64
-// warp-instruction holds the SM's FP64 pipe for about twenty cycles whether
-// or not all lanes are active, so per-row FP64 epilogues would bound those
-// sweeps. Only the CTA total is converted to double.
-struct DF {
-    float hi, lo;
-};
-
-__device__ __forceinline__ DF df_add(DF a, DF b) {
-    const float s = __fadd_rn(a.hi, b.hi);
-    const float v = __fsub_rn(s, a.hi);
-    float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, v)), __fsub_rn(b.hi, v));
-    e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
-    const float h = __fadd_rn(s, e);
-    return {h, __fsub_rn(e, __fsub_rn(h, s))};
-}
-
-// a + x * y with the product split exactly (x*y = p + fma(x, y, -p)).
-__device__ __forceinline__ DF df_add_prod(DF a, float x, float y) {
-    const float p = __fmul_rn(x, y);
-    return df_add(a, DF{p, fmaf(x, y, -p)});
 }
 
 // Fixed-order CTA sum of N double-float values; the double result is valid
@@ -339,12 +315,6 @@ __device__ __forceinline__ void for_slices(const Sliced &sl, const Tile &t, int3
         body(seg, off, width, lane);
     }
 }
-
-// Programmatic dependent launch: the sweeps are launched so that a kernel
-// may start while its predecessor drains; everything it reads was written
-// by that predecessor, so it first waits for the predecessor's completion
-// (griddepcontrol.wait returns at once when there is none).
-__device__ __forceinline__ void wait_prior_grid() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 // Contiguous, balanced share of n tiles for this CTA.
 __device__ __forceinline__ void tile_range(int32_t n, int32_t &t0, int32_t &t1) {
@@ -1070,24 +1040,6 @@ int sweep_ctas_per_sm(int which, bool f32) {
         return 1;
     }
     return n;
-}
-
-// Launch with the programmatic-stream-serialization attribute (captured as
-// programmatic edges in CUDA graphs): the next sweep's launch overlaps the
-// tail of the previous one and its CTAs wait in wait_prior_grid().
-template <typename... Args>
-static cudaError_t launch_pdl(void (*kernel)(Args...), int grid, cudaStream_t s, Args... args) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(unsigned(grid));
-    cfg.blockDim = dim3(kThreads);
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
 cudaError_t launch_row_sweep(const SweepArgs &a, bool f32, int grid, cudaStream_t s) {

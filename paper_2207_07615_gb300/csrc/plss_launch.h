@@ -31,4 +31,23 @@ cudaError_t launch_colweights(const int32_t *ptr, const void *val, bool f32, int
                               int32_t mode, double *w, double *winv, float *wf, float *winvf,
                               cudaStream_t s);
 
+
+// Launch with the programmatic-stream-serialization attribute (captured as
+// programmatic edges in CUDA graphs): the next sweep's launch overlaps the
+// tail of the previous one and its CTAs wait in wait_prior_grid().
+template <typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(Args...), int grid, cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(unsigned(grid));
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 }  // namespace plss

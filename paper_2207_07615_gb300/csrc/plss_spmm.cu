@@ -14,11 +14,13 @@
 #include <cmath>
 #include <cstring>
 #include <map>
+#include <type_traits>
 #include <vector>
 
 #include "plss.h"
 #include "plss_ctx.h"
 #include "plss_dev.cuh"
+#include "plss_devfn.cuh"
 #include "plss_launch.h"
 
 namespace plss {
@@ -41,14 +43,18 @@ struct RhsArgs {
     int32_t *n_active;
     const double *B;     // m x 32
     double *X;           // n x 32
+    float *dX;           // FP32 storage: n x 32 float sum of the updates since the last (re)start
     void *R, *P, *U;     // storage type, (m|n) x 32
     const double *w;
     const double *winv;
+    const float *wf;     // float copies (FP32 storage)
+    const float *winvf;
 };
 
 struct RhsState {
     int32_t k = 0;
     double *d_B = nullptr, *d_X = nullptr;
+    float *d_dX = nullptr;   // FP32 storage only
     void *d_R = nullptr, *d_P = nullptr, *d_U = nullptr;
     double *d_part = nullptr;
     SysState *d_st = nullptr;
@@ -64,6 +70,157 @@ struct RhsState {
 
 __device__ __forceinline__ double rhs_fma(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ float rhs_fma(float a, float b, float c) { return fmaf(a, b, c); }
+
+// Per-lane accumulator of a sum of squares / products: double for FP64
+// storage, double-float (FP32 operations only) for FP32 storage, so the
+// FP32 sweeps spend no FP64 operation per block entry.
+template <typename S>
+struct RhsAcc;
+template <>
+struct RhsAcc<double> {
+    double v = 0.0;
+    __device__ __forceinline__ void add(double x, double y) { v = fma(x, y, v); }
+    __device__ __forceinline__ double get() const { return v; }
+};
+template <>
+struct RhsAcc<float> {
+    DF v = {0.0f, 0.0f};
+    __device__ __forceinline__ void add(float x, float y) { v = df_add_prod(v, x, y); }
+    __device__ __forceinline__ double get() const { return double(v.hi) + double(v.lo); }
+};
+
+// Lane `lane`'s entry of (A_seg . V) for one segment [s, e) of a sparse
+// side (indices idx, values val) against a stride-32 block V: the warp
+// loads 32 index/value pairs at a time (coalesced), broadcasts them by
+// shuffle and keeps 8 gathered block rows in flight before their FMAs;
+// products are summed in segment order. `on` masks the lanes that take
+// part in the gathers (every lane takes part in the shuffles).
+template <typename VT, typename XT, typename ACC>
+__device__ __forceinline__ ACC rhs_dot(const int32_t *__restrict__ idx, const VT *__restrict__ val, int32_t s,
+                                       int32_t e, const XT *__restrict__ V, int lane, bool on) {
+    ACC d = ACC(0);
+    for (int32_t q0 = s; q0 < e; q0 += 32) {
+        const int32_t q = q0 + lane;
+        const int32_t cq = q < e ? __ldg(idx + q) : 0;
+        const VT vq = q < e ? __ldg(val + q) : VT(0);
+        const int nq = e - q0 < 32 ? int(e - q0) : 32;
+        for (int u0 = 0; u0 < nq; u0 += 8) {
+            XT g[8];
+            ACC v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int j = (u0 + u) & 31;
+                const int32_t c = __shfl_sync(0xffffffffu, cq, j);
+                v[u] = ACC(__shfl_sync(0xffffffffu, vq, j));
+                g[u] = on && u0 + u < nq ? V[int64_t(c) * kRhsStride + lane] : XT(0);
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (u0 + u < nq) d = rhs_fma(v[u], ACC(g[u]), d);
+        }
+    }
+    return d;
+}
+
+// A lane's share of a block row: V consecutive right-hand sides (16 bytes:
+// 4 floats or 2 doubles), so L = 32 / V lanes cover one block row and a
+// warp works on V matrix rows at once. Indices and values are loaded by the
+// L lanes of a row group from the same address (one request), the gathered
+// block row is one 16-byte load per lane, and each lane spends V FMAs per
+// nonzero: a few instructions per nonzero instead of one warp per nonzero.
+template <typename S>
+struct RhsVec;
+template <>
+struct RhsVec<float> {
+    static constexpr int V = 4;
+    __device__ __forceinline__ static void ld(const float *p, float (&o)[4]) {
+        const float4 t = __ldg(reinterpret_cast<const float4 *>(p));
+        o[0] = t.x, o[1] = t.y, o[2] = t.z, o[3] = t.w;
+    }
+    __device__ __forceinline__ static void ld_rw(const float *p, float (&o)[4]) {
+        const float4 t = *reinterpret_cast<const float4 *>(p);
+        o[0] = t.x, o[1] = t.y, o[2] = t.z, o[3] = t.w;
+    }
+    __device__ __forceinline__ static void st(float *p, const float (&o)[4]) {
+        *reinterpret_cast<float4 *>(p) = make_float4(o[0], o[1], o[2], o[3]);
+    }
+};
+template <>
+struct RhsVec<double> {
+    static constexpr int V = 2;
+    __device__ __forceinline__ static void ld(const double *p, double (&o)[2]) {
+        const double2 t = __ldg(reinterpret_cast<const double2 *>(p));
+        o[0] = t.x, o[1] = t.y;
+    }
+    __device__ __forceinline__ static void ld_rw(const double *p, double (&o)[2]) {
+        const double2 t = *reinterpret_cast<const double2 *>(p);
+        o[0] = t.x, o[1] = t.y;
+    }
+    __device__ __forceinline__ static void st(double *p, const double (&o)[2]) {
+        *reinterpret_cast<double2 *>(p) = make_double2(o[0], o[1]);
+    }
+};
+
+// d[v] = sum over the segment [s, e) of val * Vb[idx][off + v] for the lane's
+// V right-hand sides (off = its first one), in segment order, 8 gathers in
+// flight. `len_max` is the longest segment among the warp's row groups
+// (warp-uniform loop); `on` skips the gathers of a lane with nothing to do.
+template <typename S>
+__device__ __forceinline__ void rhs_vdot(const int32_t *__restrict__ idx, const S *__restrict__ val, int32_t s,
+                                         int32_t len, int32_t len_max, const S *__restrict__ Vb, int off, bool on,
+                                         S (&d)[RhsVec<S>::V]) {
+    constexpr int V = RhsVec<S>::V;
+#pragma unroll
+    for (int v = 0; v < V; ++v) d[v] = S(0);
+    for (int32_t q0 = 0; q0 < len_max; q0 += 8) {
+        int32_t c[8];
+        S w[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const bool in = on && q0 + u < len;
+            c[u] = in ? __ldg(idx + s + q0 + u) : -1;
+            w[u] = in ? __ldg(val + s + q0 + u) : S(0);
+        }
+        S g[8][V];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            if (c[u] >= 0) RhsVec<S>::ld(Vb + int64_t(c[u]) * kRhsStride + off, g[u]);
+            else {
+#pragma unroll
+                for (int v = 0; v < V; ++v) g[u][v] = S(0);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            if (c[u] >= 0) {
+#pragma unroll
+                for (int v = 0; v < V; ++v) d[v] = rhs_fma(w[u], g[u][v], d[v]);
+            }
+    }
+}
+
+// Per right-hand side j, the fixed-order sum over the CTA of the V-lane
+// partials (vec[v] of row group `grp`, lane group `ll`) and of the
+// lane-per-column partials (one[j] in lane j); result in out[j] (thread j).
+template <int V>
+__device__ __forceinline__ void rhs_cta_sum_v(const double (&vec)[V], double one, double *out) {
+    constexpr int G = 32 / (32 / V) * kWarps;   // row groups per CTA
+    __shared__ double shv[G][32];
+    __shared__ double sho[kWarps][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int L = 32 / V, grp = warp * V + lane / L, ll = lane % L;
+    __syncthreads();
+#pragma unroll
+    for (int v = 0; v < V; ++v) shv[grp][ll * V + v] = vec[v];
+    sho[warp][lane] = one;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double t = 0.0;
+        for (int q = 0; q < G; ++q) t += shv[q][threadIdx.x];
+        for (int w = 0; w < kWarps; ++w) t += sho[w][threadIdx.x];
+        out[threadIdx.x] = t;
+    }
+}
 
 // Per-lane sum over the CTA's warps (lane j = column j) into part[0..31]
 // of the tile, fixed order.
@@ -125,40 +282,85 @@ __device__ __forceinline__ void rhs_done(const RhsArgs &a, SysState *st, int32_t
 }
 
 template <typename S>
-__global__ void __launch_bounds__(kThreads) k_rhs_row(RhsArgs a) {
+__global__ void __launch_bounds__(kThreads, 3) k_rhs_row(RhsArgs a) {
+    constexpr int V = RhsVec<S>::V, L = 32 / V;
+    wait_prior_grid();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int sub = lane / L, ll = lane % L;
+    const S *val = static_cast<const S *>(a.val);
+    S *R = static_cast<S *>(a.R);
+    const S *P = static_cast<const S *>(a.P);
+    // phases: lane j (lane-per-column form) and the lane's V columns
     const bool mine = lane < a.k;
     const int32_t ph = mine ? *reinterpret_cast<const volatile int32_t *>(&a.st[lane].phase) : PH_DONE;
     const bool init = ph == PH_SETUP;
     const bool act = init || ph == PH_RUN;
-    const S *val = static_cast<const S *>(a.val);
-    S *R = static_cast<S *>(a.R);
-    const S *P = static_cast<const S *>(a.P);
-    double acc_r = 0.0, acc_b = 0.0;
-    for (int32_t ti = blockIdx.x; ti < a.n_rtiles; ti += gridDim.x) {
+    bool run[V], run_any = false, run_all = true;
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        const int j = ll * V + v;
+        run[v] = j < a.k && *reinterpret_cast<const volatile int32_t *>(&a.st[j].phase) == PH_RUN;
+        run_any |= run[v];
+        run_all &= run[v];
+    }
+    const bool any_init = __any_sync(0xffffffffu, init);
+    const bool any_run = __any_sync(0xffffffffu, run_any);
+    RhsAcc<S> acc[V];
+    // r = r - A p for the columns in PH_RUN: V matrix rows per warp
+    for (int32_t ti = blockIdx.x; any_run && ti < a.n_rtiles; ti += gridDim.x) {
         const Tile t = a.rtiles[ti];
-        for (int32_t row = t.begin + warp; row < t.end; row += kWarps) {
-            const int32_t s = a.row_ptr[row], e = a.row_ptr[row + 1];
-            if (init) {
-                double d = 0.0;
-                for (int32_t q = s; q < e; ++q)
-                    d = fma(double(__ldg(val + q)), a.X[int64_t(__ldg(a.col_idx + q)) * kRhsStride + lane], d);
-                const double bi = a.B[int64_t(row) * kRhsStride + lane];
-                const S ri = S(bi - d);
-                R[int64_t(row) * kRhsStride + lane] = ri;
-                acc_r += double(ri) * double(ri);
-                acc_b += bi * bi;
-            } else if (act) {
-                S d = S(0);
-                for (int32_t q = s; q < e; ++q)
-                    d = rhs_fma(S(__ldg(val + q)), P[int64_t(__ldg(a.col_idx + q)) * kRhsStride + lane], d);
-                const S ri = R[int64_t(row) * kRhsStride + lane] - d;
-                R[int64_t(row) * kRhsStride + lane] = ri;
-                acc_r += double(ri) * double(ri);
+        for (int32_t r0 = t.begin + warp * V; r0 < t.end; r0 += kWarps * V) {
+            const int32_t row = r0 + sub;
+            const bool valid = row < t.end;
+            const int32_t s = valid ? a.row_ptr[row] : 0, len = valid ? a.row_ptr[row + 1] - s : 0;
+            const int32_t len_max = __reduce_max_sync(0xffffffffu, len);
+            const int64_t ix = int64_t(row) * kRhsStride + ll * V;
+            S old[V], d[V];
+            if (valid && run_any) RhsVec<S>::ld_rw(R + ix, old);
+            rhs_vdot<S>(a.col_idx, val, s, len, len_max, P, ll * V, valid && run_any, d);
+            if (valid && run_any) {
+                S ri[V];
+#pragma unroll
+                for (int v = 0; v < V; ++v) ri[v] = old[v] - d[v];
+                if (run_all) {
+                    RhsVec<S>::st(R + ix, ri);
+                } else {
+#pragma unroll
+                    for (int v = 0; v < V; ++v)
+                        if (run[v]) R[ix + v] = ri[v];
+                }
+#pragma unroll
+                for (int v = 0; v < V; ++v)
+                    if (run[v]) acc[v].add(ri[v], ri[v]);
             }
         }
     }
-    rhs_cta_sum(acc_r, acc_b, a.part + int64_t(blockIdx.x) * 64, a.part + int64_t(blockIdx.x) * 64 + 32);
+    // r = b - A x (products in double) for the columns that (re)start:
+    // lane-per-column form, rare
+    double acc_i = 0.0, acc_b = 0.0;
+    for (int32_t ti = blockIdx.x; any_init && ti < a.n_rtiles; ti += gridDim.x) {
+        const Tile t = a.rtiles[ti];
+        for (int32_t row = t.begin + warp; row < t.end; row += kWarps) {
+            const int32_t s = a.row_ptr[row], e = a.row_ptr[row + 1];
+            const int64_t ix = int64_t(row) * kRhsStride + lane;
+            const double bi = init ? a.B[ix] : 0.0;
+            double d = rhs_dot<S, double, double>(a.col_idx, val, s, e, a.X, lane, init);
+            if (a.dX) d += rhs_dot<S, float, double>(a.col_idx, val, s, e, a.dX, lane, init);
+            if (init) {
+                const S ri = S(bi - d);
+                R[ix] = ri;
+                acc_i = fma(double(ri), double(ri), acc_i);
+                acc_b = fma(bi, bi, acc_b);
+            }
+        }
+    }
+    double vr[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) vr[v] = acc[v].get();
+    const double zero[V] = {};
+    rhs_cta_sum_v<V>(vr, acc_i, a.part + int64_t(blockIdx.x) * 64);
+    rhs_cta_sum_v<V>(zero, acc_b, a.part + int64_t(blockIdx.x) * 64 + 32);
+
     if (!rhs_arrive(&a.cnt[0], gridDim.x)) return;
     double rho, nb2;
     rhs_final_sums(a.part, gridDim.x, 0, rho);
@@ -199,29 +401,58 @@ __global__ void __launch_bounds__(kThreads) k_rhs_row(RhsArgs a) {
 
 template <typename S>
 __global__ void __launch_bounds__(kThreads) k_rhs_col(RhsArgs a) {
+    constexpr int V = RhsVec<S>::V, L = 32 / V;
+    wait_prior_grid();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int sub = lane / L, ll = lane % L;
     const bool mine = lane < a.k;
     const int32_t ph = mine ? *reinterpret_cast<const volatile int32_t *>(&a.st[lane].phase) : PH_DONE;
     const bool act = ph == PH_FIRST || ph == PH_RUN;
+    bool on[V], on_any = false;
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        const int j = ll * V + v;
+        const int32_t pj = j < a.k ? *reinterpret_cast<const volatile int32_t *>(&a.st[j].phase) : PH_DONE;
+        on[v] = pj == PH_FIRST || pj == PH_RUN;
+        on_any |= on[v];
+    }
+    const bool any_act = __any_sync(0xffffffffu, on_any);
     const S *val = static_cast<const S *>(a.cval);
     const S *R = static_cast<const S *>(a.R);
     S *U = static_cast<S *>(a.U);
-    double acc = 0.0;
-    for (int32_t ti = blockIdx.x; ti < a.n_ctiles; ti += gridDim.x) {
+    RhsAcc<S> accs[V];
+    for (int32_t ti = blockIdx.x; any_act && ti < a.n_ctiles; ti += gridDim.x) {
         const Tile t = a.ctiles[ti];
-        for (int32_t col = t.begin + warp; col < t.end; col += kWarps) {
-            if (!act) continue;
-            const int32_t s = a.col_ptr[col], e = a.col_ptr[col + 1];
-            S d = S(0);
-            for (int32_t q = s; q < e; ++q)
-                d = rhs_fma(S(__ldg(val + q)), R[int64_t(__ldg(a.row_idx + q)) * kRhsStride + lane], d);
-            const double y = double(d);
-            const S uj = a.w ? S(a.w[col] * y) : S(y);
-            U[int64_t(col) * kRhsStride + lane] = uj;
-            acc += y * double(uj);
+        for (int32_t c0 = t.begin + warp * V; c0 < t.end; c0 += kWarps * V) {
+            const int32_t col = c0 + sub;
+            const bool valid = col < t.end;
+            const int32_t s = valid ? a.col_ptr[col] : 0, len = valid ? a.col_ptr[col + 1] - s : 0;
+            const int32_t len_max = __reduce_max_sync(0xffffffffu, len);
+            S y[V];
+            rhs_vdot<S>(a.row_idx, val, s, len, len_max, R, ll * V, valid && on_any, y);
+            if (valid && on_any) {
+                S uj[V];
+                if constexpr (std::is_same<S, float>::value) {
+                    const float wj = a.wf ? a.wf[col] : 1.0f;
+#pragma unroll
+                    for (int v = 0; v < V; ++v) uj[v] = a.wf ? __fmul_rn(wj, y[v]) : y[v];
+                } else {
+                    const double wj = a.w ? a.w[col] : 1.0;
+#pragma unroll
+                    for (int v = 0; v < V; ++v) uj[v] = a.w ? wj * y[v] : y[v];
+                }
+                // U of an inactive column is recomputed before its next use
+                RhsVec<S>::st(U + int64_t(col) * kRhsStride + ll * V, uj);
+#pragma unroll
+                for (int v = 0; v < V; ++v)
+                    if (on[v]) accs[v].add(y[v], uj[v]);
+            }
         }
     }
-    rhs_cta_sum(acc, 0.0, a.part + int64_t(blockIdx.x) * 64, nullptr);
+    double vr[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) vr[v] = accs[v].get();
+    rhs_cta_sum_v<V>(vr, 0.0, a.part + int64_t(blockIdx.x) * 64);
     if (!rhs_arrive(&a.cnt[1], gridDim.x)) return;
     double phi;
     rhs_final_sums(a.part, gridDim.x, 0, phi);
@@ -257,34 +488,86 @@ __global__ void __launch_bounds__(kThreads) k_rhs_col(RhsArgs a) {
     if (threadIdx.x == 0) a.cnt[1] = 0;
 }
 
+// p = beta p + gamma u in the storage type (FP32: float beta, gamma as in
+// the single-right-hand-side update), theta partials, x = x + p in double.
+template <typename S>
+__device__ __forceinline__ S rhs_pnew(bool first, double beta, double gamma, S p, S u);
+template <>
+__device__ __forceinline__ double rhs_pnew<double>(bool first, double beta, double gamma, double p, double u) {
+    return first ? __dmul_rn(gamma, u) : __dadd_rn(__dmul_rn(beta, p), __dmul_rn(gamma, u));
+}
+template <>
+__device__ __forceinline__ float rhs_pnew<float>(bool first, double beta, double gamma, float p, float u) {
+    const float bf = float(beta), gf = float(gamma);
+    return first ? gf * u : fmaf(bf, p, gf * u);
+}
+
 template <typename S>
 __global__ void __launch_bounds__(kThreads) k_rhs_update(RhsArgs a) {
+    constexpr int V = RhsVec<S>::V, L = 32 / V;
+    wait_prior_grid();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int sub = lane / L, ll = lane % L;
     const bool mine = lane < a.k;
     const int32_t ph = mine ? *reinterpret_cast<const volatile int32_t *>(&a.st[lane].phase) : PH_DONE;
     const bool act = ph == PH_FIRST || ph == PH_RUN;
-    const bool first = ph == PH_FIRST;
-    const double beta = act ? a.st[lane].beta : 0.0, gamma = act ? a.st[lane].gamma : 0.0;
+    bool on[V], first[V], on_any = false;
+    double beta[V], gamma[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        const int j = ll * V + v;
+        const int32_t pj = j < a.k ? *reinterpret_cast<const volatile int32_t *>(&a.st[j].phase) : PH_DONE;
+        on[v] = pj == PH_FIRST || pj == PH_RUN;
+        first[v] = pj == PH_FIRST;
+        beta[v] = on[v] ? a.st[j].beta : 0.0;
+        gamma[v] = on[v] ? a.st[j].gamma : 0.0;
+        on_any |= on[v];
+    }
     S *P = static_cast<S *>(a.P);
     const S *U = static_cast<const S *>(a.U);
-    double acc = 0.0;
-    for (int32_t ti = blockIdx.x; ti < a.n_vtiles; ti += gridDim.x) {
+    RhsAcc<S> accs[V];
+    for (int32_t ti = blockIdx.x; on_any && ti < a.n_vtiles; ti += gridDim.x) {
         const Tile t = a.vtiles[ti];
-        if (act) {
-            for (int32_t j = t.begin + warp; j < t.end; j += kWarps) {
-                const int64_t ix = int64_t(j) * kRhsStride + lane;
-                const double uj = double(U[ix]);
-                const double pn = first ? __dmul_rn(gamma, uj)
-                                        : __dadd_rn(__dmul_rn(beta, double(P[ix])), __dmul_rn(gamma, uj));
-                const S ps = S(pn);
-                P[ix] = ps;
-                const double pd = double(ps);
-                acc = fma(pd, a.winv ? pd * a.winv[j] : pd, acc);
-                a.X[ix] = __dadd_rn(a.X[ix], pd);
+        for (int32_t j = t.begin + warp * V + sub; j < t.end; j += kWarps * V) {
+            const int64_t ix = int64_t(j) * kRhsStride + ll * V;
+            S uj[V], pj[V], pn[V];
+            RhsVec<S>::ld_rw(U + ix, uj);
+            RhsVec<S>::ld_rw(P + ix, pj);
+#pragma unroll
+            for (int v = 0; v < V; ++v) pn[v] = on[v] ? rhs_pnew<S>(first[v], beta[v], gamma[v], pj[v], uj[v]) : pj[v];
+            RhsVec<S>::st(P + ix, pn);
+            if constexpr (std::is_same<S, float>::value) {
+                const float wi = a.winvf ? a.winvf[j] : 1.0f;
+#pragma unroll
+                for (int v = 0; v < V; ++v)
+                    if (on[v]) accs[v].add(pn[v], a.winvf ? __fmul_rn(pn[v], wi) : pn[v]);
+                // x accumulates in the float block dX during an inner solve;
+                // the first update after a (re)start moves it into X
+                float dx[V];
+                RhsVec<float>::ld_rw(a.dX + ix, dx);
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    if (first[v]) a.X[ix + v] = __dadd_rn(a.X[ix + v], double(dx[v]));
+                    dx[v] = first[v] ? pn[v] : (on[v] ? __fadd_rn(dx[v], pn[v]) : dx[v]);
+                }
+                RhsVec<float>::st(a.dX + ix, dx);
+            } else {
+                const double wi = a.winv ? a.winv[j] : 1.0;
+                double xj[V];
+                RhsVec<double>::ld_rw(a.X + ix, xj);
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    if (on[v]) accs[v].add(pn[v], a.winv ? pn[v] * wi : pn[v]);
+                    if (on[v]) xj[v] = __dadd_rn(xj[v], pn[v]);
+                }
+                RhsVec<double>::st(a.X + ix, xj);
             }
         }
     }
-    rhs_cta_sum(acc, 0.0, a.part + int64_t(blockIdx.x) * 64, nullptr);
+    double vr[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) vr[v] = accs[v].get();
+    rhs_cta_sum_v<V>(vr, 0.0, a.part + int64_t(blockIdx.x) * 64);
     if (!rhs_arrive(&a.cnt[2], gridDim.x)) return;
     double theta;
     rhs_final_sums(a.part, gridDim.x, 0, theta);
@@ -312,6 +595,15 @@ __global__ void __launch_bounds__(kThreads) k_rhs_update(RhsArgs a) {
     if (threadIdx.x == 0) a.cnt[2] = 0;
 }
 
+// FP32 storage, end of a solve: X = X + dX, dX = 0 (the updates of the last
+// inner solve).
+__global__ void __launch_bounds__(kThreads) k_rhs_flush(double *X, float *dX, int64_t count) {
+    for (int64_t i = blockIdx.x * int64_t(kThreads) + threadIdx.x; i < count; i += int64_t(gridDim.x) * kThreads) {
+        X[i] = __dadd_rn(X[i], double(dX[i]));
+        dX[i] = 0.0f;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
@@ -320,7 +612,7 @@ void free_rhs(plss_ctx *c) {
     RhsState *r = c->rhs;
     if (!r) return;
     for (auto &kv : r->graphs) cudaGraphExecDestroy(kv.second);
-    void *ptrs[] = {r->d_B, r->d_X, r->d_R, r->d_P, r->d_U, r->d_part, r->d_st, r->d_cnt,
+    void *ptrs[] = {r->d_B, r->d_X, r->d_dX, r->d_R, r->d_P, r->d_U, r->d_part, r->d_st, r->d_cnt,
                     r->d_active, r->d_rt, r->d_ct, r->d_vt};
     for (void *p : ptrs) dfree(p);
     if (r->h_st) cudaFreeHost(r->h_st);
@@ -358,6 +650,7 @@ static plss_status rhs_prepare(plss_ctx *c) {
     };
     if ((st = dalloc(reinterpret_cast<void **>(&r->d_B), 8 * kRhsStride * size_t(c->m), "B")) != PLSS_OK ||
         (st = dalloc(reinterpret_cast<void **>(&r->d_X), 8 * kRhsStride * size_t(c->n), "X")) != PLSS_OK ||
+        (c->f32 && (st = dalloc(reinterpret_cast<void **>(&r->d_dX), 4 * kRhsStride * size_t(c->n), "dX")) != PLSS_OK) ||
         (st = dalloc(&r->d_R, sb * kRhsStride * size_t(c->m), "R")) != PLSS_OK ||
         (st = dalloc(&r->d_P, sb * kRhsStride * size_t(c->n), "P")) != PLSS_OK ||
         (st = dalloc(&r->d_U, sb * kRhsStride * size_t(c->n), "U")) != PLSS_OK ||
@@ -404,11 +697,14 @@ static RhsArgs rhs_args(plss_ctx *c, int32_t k, bool w_on) {
     a.n_active = r->d_active;
     a.B = r->d_B;
     a.X = r->d_X;
+    a.dX = r->d_dX;
     a.R = r->d_R;
     a.P = r->d_P;
     a.U = r->d_U;
     a.w = w_on ? c->d_w : nullptr;
     a.winv = w_on ? c->d_w + c->n : nullptr;
+    a.wf = w_on && c->d_wf ? c->d_wf : nullptr;
+    a.winvf = w_on && c->d_wf ? c->d_wf + c->n : nullptr;
     return a;
 }
 
@@ -416,16 +712,17 @@ static cudaError_t rhs_body(plss_ctx *c, const RhsArgs &a, cudaStream_t s) {
     const int gr = std::max(1, std::min(a.n_rtiles, c->nsm * kCtasPerSm));
     const int gc = std::max(1, std::min(a.n_ctiles, c->nsm * kCtasPerSm));
     const int gv = std::max(1, std::min(a.n_vtiles, c->nsm * kCtasPerSm));
+    cudaError_t e;
     if (c->f32) {
-        k_rhs_col<float><<<gc, kThreads, 0, s>>>(a);
-        k_rhs_update<float><<<gv, kThreads, 0, s>>>(a);
-        k_rhs_row<float><<<gr, kThreads, 0, s>>>(a);
+        if ((e = launch_pdl(k_rhs_col<float>, gc, s, a)) != cudaSuccess) return e;
+        if ((e = launch_pdl(k_rhs_update<float>, gv, s, a)) != cudaSuccess) return e;
+        e = launch_pdl(k_rhs_row<float>, gr, s, a);
     } else {
-        k_rhs_col<double><<<gc, kThreads, 0, s>>>(a);
-        k_rhs_update<double><<<gv, kThreads, 0, s>>>(a);
-        k_rhs_row<double><<<gr, kThreads, 0, s>>>(a);
+        if ((e = launch_pdl(k_rhs_col<double>, gc, s, a)) != cudaSuccess) return e;
+        if ((e = launch_pdl(k_rhs_update<double>, gv, s, a)) != cudaSuccess) return e;
+        e = launch_pdl(k_rhs_row<double>, gr, s, a);
     }
-    return cudaGetLastError();
+    return e;
 }
 
 static plss_status rhs_graph(plss_ctx *c, int chunk, int32_t k, bool w_on, cudaGraphExec_t *out) {
@@ -486,6 +783,8 @@ plss_status run_rhs(plss_ctx *c, int32_t k, const double *B, const double *X0, d
     const bool dev = o->io_device != 0;
     if ((st = rhs_put(r->d_B, B, c->m, k, dev, s)) != PLSS_OK) return st;
     if ((st = rhs_put(r->d_X, X0, c->n, k, dev, s)) != PLSS_OK) return st;
+    if (r->d_dX && c->n > 0 && cudaMemsetAsync(r->d_dX, 0, 4 * kRhsStride * size_t(c->n), s) != cudaSuccess)
+        return fail(PLSS_ERR_CUDA, "memset failed");
     if ((st = ensure_weights(c, o->w_mode, s)) != PLSS_OK) return st;
     const bool w_on = o->w_mode != PLSS_W_IDENTITY;
     if (o->hist_cap > 0 && o->hist_cap > c->hist_cap_alloc) {
@@ -532,7 +831,12 @@ plss_status run_rhs(plss_ctx *c, int32_t k, const double *B, const double *X0, d
         if (bodies > body_cap) return fail(PLSS_ERR_TIMEOUT, "iteration driver exceeded %lld bodies", (long long)body_cap);
         chunk = std::min(chunk * 4, kMaxChunk);
     }
-    if (cudaEventRecord(c->ev1, s) != cudaSuccess ||
+    if (r->d_dX && c->n > 0) {
+        const int64_t cnt = int64_t(kRhsStride) * c->n;
+        const int grid = int(std::min<int64_t>((cnt + kThreads - 1) / kThreads, int64_t(c->nsm) * kCtasPerSm));
+        k_rhs_flush<<<grid, kThreads, 0, s>>>(r->d_X, r->d_dX, cnt);
+    }
+    if (cudaGetLastError() != cudaSuccess || cudaEventRecord(c->ev1, s) != cudaSuccess ||
         cudaMemcpyAsync(r->h_st, r->d_st, sizeof(SysState) * kRhsMax, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaMemcpy2DAsync(X, 8 * size_t(k), r->d_X, 8 * kRhsStride, 8 * size_t(k), size_t(c->n),
                           dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s) != cudaSuccess ||
