@@ -39,6 +39,7 @@ struct RhsArgs {
     int64_t m, n;
     SysState *st;        // [k]
     double *part;        // [max tiles][2][32]
+    double *part_init;   // [max tiles][2][32], partials of k_rhs_row_init
     uint32_t *cnt;       // [3]
     int32_t *n_active;
     const double *B;     // m x 32
@@ -56,7 +57,7 @@ struct RhsState {
     double *d_B = nullptr, *d_X = nullptr;
     float *d_dX = nullptr;   // FP32 storage only
     void *d_R = nullptr, *d_P = nullptr, *d_U = nullptr;
-    double *d_part = nullptr;
+    double *d_part = nullptr;   // 2 x [max tiles][64]: sweeps, then the restart row sweep
     SysState *d_st = nullptr;
     SysState *h_st = nullptr;
     uint32_t *d_cnt = nullptr;
@@ -281,6 +282,41 @@ __device__ __forceinline__ void rhs_done(const RhsArgs &a, SysState *st, int32_t
     atomicSub(a.n_active, 1);
 }
 
+// Row sweep of the columns that (re)start: r = b - A x with products in
+// double, lane-per-column form; per-CTA partials of rho and ||b||^2 in
+// part_init for k_rhs_row (launched next with the same grid) to finish.
+// Returns at once when no column restarts (the usual case).
+template <typename S>
+__global__ void __launch_bounds__(kThreads) k_rhs_row_init(RhsArgs a) {
+    wait_prior_grid();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const bool mine = lane < a.k;
+    const int32_t ph = mine ? *reinterpret_cast<const volatile int32_t *>(&a.st[lane].phase) : PH_DONE;
+    const bool init = ph == PH_SETUP;
+    const bool any_init = __any_sync(0xffffffffu, init);
+    if (!any_init) return;   // uniform: every warp reads the same phases
+    const S *val = static_cast<const S *>(a.val);
+    S *R = static_cast<S *>(a.R);
+    double acc_i = 0.0, acc_b = 0.0;
+    for (int32_t ti = blockIdx.x; ti < a.n_rtiles; ti += gridDim.x) {
+        const Tile t = a.rtiles[ti];
+        for (int32_t row = t.begin + warp; row < t.end; row += kWarps) {
+            const int32_t s = a.row_ptr[row], e = a.row_ptr[row + 1];
+            const int64_t ix = int64_t(row) * kRhsStride + lane;
+            const double bi = init ? a.B[ix] : 0.0;
+            double d = rhs_dot<S, double, double>(a.col_idx, val, s, e, a.X, lane, init);
+            if (a.dX) d += rhs_dot<S, float, double>(a.col_idx, val, s, e, a.dX, lane, init);
+            if (init) {
+                const S ri = S(bi - d);
+                R[ix] = ri;
+                acc_i = fma(double(ri), double(ri), acc_i);
+                acc_b = fma(bi, bi, acc_b);
+            }
+        }
+    }
+    rhs_cta_sum(acc_i, acc_b, a.part_init + int64_t(blockIdx.x) * 64, a.part_init + int64_t(blockIdx.x) * 64 + 32);
+}
+
 template <typename S>
 __global__ void __launch_bounds__(kThreads, 3) k_rhs_row(RhsArgs a) {
     constexpr int V = RhsVec<S>::V, L = 32 / V;
@@ -303,7 +339,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_rhs_row(RhsArgs a) {
         run_any |= run[v];
         run_all &= run[v];
     }
-    const bool any_init = __any_sync(0xffffffffu, init);
+    const bool any_init = __syncthreads_or(init) != 0;   // uniform over the CTA
     const bool any_run = __any_sync(0xffffffffu, run_any);
     RhsAcc<S> acc[V];
     // r = r - A p for the columns in PH_RUN: V matrix rows per warp
@@ -335,36 +371,20 @@ __global__ void __launch_bounds__(kThreads, 3) k_rhs_row(RhsArgs a) {
             }
         }
     }
-    // r = b - A x (products in double) for the columns that (re)start:
-    // lane-per-column form, rare
-    double acc_i = 0.0, acc_b = 0.0;
-    for (int32_t ti = blockIdx.x; any_init && ti < a.n_rtiles; ti += gridDim.x) {
-        const Tile t = a.rtiles[ti];
-        for (int32_t row = t.begin + warp; row < t.end; row += kWarps) {
-            const int32_t s = a.row_ptr[row], e = a.row_ptr[row + 1];
-            const int64_t ix = int64_t(row) * kRhsStride + lane;
-            const double bi = init ? a.B[ix] : 0.0;
-            double d = rhs_dot<S, double, double>(a.col_idx, val, s, e, a.X, lane, init);
-            if (a.dX) d += rhs_dot<S, float, double>(a.col_idx, val, s, e, a.dX, lane, init);
-            if (init) {
-                const S ri = S(bi - d);
-                R[ix] = ri;
-                acc_i = fma(double(ri), double(ri), acc_i);
-                acc_b = fma(bi, bi, acc_b);
-            }
-        }
-    }
     double vr[V];
 #pragma unroll
     for (int v = 0; v < V; ++v) vr[v] = acc[v].get();
-    const double zero[V] = {};
-    rhs_cta_sum_v<V>(vr, acc_i, a.part + int64_t(blockIdx.x) * 64);
-    rhs_cta_sum_v<V>(zero, acc_b, a.part + int64_t(blockIdx.x) * 64 + 32);
+    rhs_cta_sum_v<V>(vr, 0.0, a.part + int64_t(blockIdx.x) * 64);
 
     if (!rhs_arrive(&a.cnt[0], gridDim.x)) return;
-    double rho, nb2;
-    rhs_final_sums(a.part, gridDim.x, 0, rho);
-    rhs_final_sums(a.part, gridDim.x, 1, nb2);
+    // rho of a restarting column (and ||b||^2) comes from k_rhs_row_init,
+    // which ran just before with the same grid
+    double rho, nb2 = 0.0;
+    rhs_final_sums(any_init ? a.part_init : a.part, gridDim.x, 0, rho);
+    double rho_run;
+    rhs_final_sums(a.part, gridDim.x, 0, rho_run);
+    if (any_init) rhs_final_sums(a.part_init, gridDim.x, 1, nb2);
+    if (!init) rho = rho_run;
     if (threadIdx.x < 32 && mine && act) {
         SysState *st = a.st + lane;
         if (init) {
@@ -491,14 +511,13 @@ __global__ void __launch_bounds__(kThreads) k_rhs_col(RhsArgs a) {
 // p = beta p + gamma u in the storage type (FP32: float beta, gamma as in
 // the single-right-hand-side update), theta partials, x = x + p in double.
 template <typename S>
-__device__ __forceinline__ S rhs_pnew(bool first, double beta, double gamma, S p, S u);
+__device__ __forceinline__ S rhs_pnew(bool first, S beta, S gamma, S p, S u);
 template <>
 __device__ __forceinline__ double rhs_pnew<double>(bool first, double beta, double gamma, double p, double u) {
     return first ? __dmul_rn(gamma, u) : __dadd_rn(__dmul_rn(beta, p), __dmul_rn(gamma, u));
 }
 template <>
-__device__ __forceinline__ float rhs_pnew<float>(bool first, double beta, double gamma, float p, float u) {
-    const float bf = float(beta), gf = float(gamma);
+__device__ __forceinline__ float rhs_pnew<float>(bool first, float bf, float gf, float p, float u) {
     return first ? gf * u : fmaf(bf, p, gf * u);
 }
 
@@ -512,15 +531,15 @@ __global__ void __launch_bounds__(kThreads) k_rhs_update(RhsArgs a) {
     const int32_t ph = mine ? *reinterpret_cast<const volatile int32_t *>(&a.st[lane].phase) : PH_DONE;
     const bool act = ph == PH_FIRST || ph == PH_RUN;
     bool on[V], first[V], on_any = false;
-    double beta[V], gamma[V];
+    S beta[V], gamma[V];   // rounded to the storage type once (FP32: float)
 #pragma unroll
     for (int v = 0; v < V; ++v) {
         const int j = ll * V + v;
         const int32_t pj = j < a.k ? *reinterpret_cast<const volatile int32_t *>(&a.st[j].phase) : PH_DONE;
         on[v] = pj == PH_FIRST || pj == PH_RUN;
         first[v] = pj == PH_FIRST;
-        beta[v] = on[v] ? a.st[j].beta : 0.0;
-        gamma[v] = on[v] ? a.st[j].gamma : 0.0;
+        beta[v] = S(on[v] ? a.st[j].beta : 0.0);
+        gamma[v] = S(on[v] ? a.st[j].gamma : 0.0);
         on_any |= on[v];
     }
     S *P = static_cast<S *>(a.P);
@@ -654,7 +673,7 @@ static plss_status rhs_prepare(plss_ctx *c) {
         (st = dalloc(&r->d_R, sb * kRhsStride * size_t(c->m), "R")) != PLSS_OK ||
         (st = dalloc(&r->d_P, sb * kRhsStride * size_t(c->n), "P")) != PLSS_OK ||
         (st = dalloc(&r->d_U, sb * kRhsStride * size_t(c->n), "U")) != PLSS_OK ||
-        (st = dalloc(reinterpret_cast<void **>(&r->d_part), 8 * 64 * maxt, "partials")) != PLSS_OK ||
+        (st = dalloc(reinterpret_cast<void **>(&r->d_part), 2 * 8 * 64 * maxt, "partials")) != PLSS_OK ||
         (st = dalloc(reinterpret_cast<void **>(&r->d_st), sizeof(SysState) * kRhsMax, "state")) != PLSS_OK ||
         (st = dalloc(reinterpret_cast<void **>(&r->d_cnt), 16, "counters")) != PLSS_OK ||
         (st = dalloc(reinterpret_cast<void **>(&r->d_active), 16, "active")) != PLSS_OK ||
@@ -693,6 +712,7 @@ static RhsArgs rhs_args(plss_ctx *c, int32_t k, bool w_on) {
     a.n = c->n;
     a.st = r->d_st;
     a.part = r->d_part;
+    a.part_init = r->d_part + 64 * std::max(1, c->nsm * kCtasPerSm);
     a.cnt = r->d_cnt;
     a.n_active = r->d_active;
     a.B = r->d_B;
@@ -716,10 +736,12 @@ static cudaError_t rhs_body(plss_ctx *c, const RhsArgs &a, cudaStream_t s) {
     if (c->f32) {
         if ((e = launch_pdl(k_rhs_col<float>, gc, s, a)) != cudaSuccess) return e;
         if ((e = launch_pdl(k_rhs_update<float>, gv, s, a)) != cudaSuccess) return e;
+        if ((e = launch_pdl(k_rhs_row_init<float>, gr, s, a)) != cudaSuccess) return e;
         e = launch_pdl(k_rhs_row<float>, gr, s, a);
     } else {
         if ((e = launch_pdl(k_rhs_col<double>, gc, s, a)) != cudaSuccess) return e;
         if ((e = launch_pdl(k_rhs_update<double>, gv, s, a)) != cudaSuccess) return e;
+        if ((e = launch_pdl(k_rhs_row_init<double>, gr, s, a)) != cudaSuccess) return e;
         e = launch_pdl(k_rhs_row<double>, gr, s, a);
     }
     return e;
