@@ -451,7 +451,7 @@ def _timed(torch, fn, warmup, steps):
 
 def _line(metric, value, unit, args, workload, extra, hib=False, dtype="f32+f64"):
     line = {"metric": metric, "value": value, "unit": unit, "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": value * 1e3 if unit == "s" else None,
+            "warmup": args.warmup, "ms_per_step": value * 1e3 if unit == "s" and value is not None else None,
             "higher_is_better": hib, "scaling": "weak", "vs_baseline": None, "dtype": dtype,
             "data": "synthetic", "config": {"workload": workload}}
     line.update(extra)

@@ -68,6 +68,18 @@ enum { PLSS_W_IDENTITY = 0, PLSS_W_COLNORM = 1, PLSS_W_COLNORM2 = 2 };
  * context created with it). */
 enum { PLSS_LAYOUT_AUTO = 0, PLSS_LAYOUT_CSR = 1 };
 
+/* Schedule of a residual-sketch solve. AUTO and GRID: every sweep is a
+ * grid-wide kernel over all systems of the context. SMALL: when every system
+ * is small (at most 65,536 nonzeros, and r, p, u, x within 160 KB of shared
+ * memory: about m + 3n <= 20,000 in FP64) one CTA per system runs whole
+ * iterations between block barriers with its vectors in shared memory
+ * (plss_kernel_times then records nothing); otherwise as GRID. On GB300 the
+ * one-CTA form measured slower than the grid sweeps (a 2,000 x 2,000 system:
+ * 38 vs 26 us per update; 128 systems of 1,000-4,000 rows: 75 vs 65 us per
+ * batched update), so AUTO does not pick it. The schedules reduce in
+ * different orders: their iterates agree to rounding, not bit for bit. */
+enum { PLSS_SCHED_AUTO = 0, PLSS_SCHED_GRID = 1, PLSS_SCHED_SMALL = 2 };
+
 /* A sparse matrix in CSR form (see the conventions above). val holds nnz
  * doubles, or floats when val_f32 = 1. */
 typedef struct {
@@ -108,6 +120,9 @@ typedef struct {
     double inner_tol;       /* PLSS_FP32: restart from b - A x (refinement) once   */
                             /* the recursive residual has fallen by this factor    */
                             /* since the last start (default 1e-4; 0 = off)        */
+    int32_t schedule;       /* residual sketch: PLSS_SCHED_* (how the iterations   */
+                            /* are spread over the GPU)                           */
+    int32_t reserved;
 } plss_opts;
 
 /* Outcome of one solve. relres_rec is sqrt(rho)/||b|| of the last recursive

@@ -596,6 +596,15 @@ static plss_status ctx_build(const plss_csr *As, int32_t nsys, const plss_opts *
     c->grid_c = std::max(1, std::min(int(c->h_ct.size()), c->nsm * sweep_ctas_per_sm(1, c->f32)));
     c->grid_v = std::max(1, std::min(int(c->h_vt.size()), c->nsm * sweep_ctas_per_sm(2, c->f32)));
 
+    c->small_fits = true;
+    c->small_smem = 0;
+    for (const SysDesc &d : c->h_desc) {
+        const int64_t nz = int64_t(rp[size_t(d.row_off + d.m)]) - rp[size_t(d.row_off)];
+        c->small_smem = std::max(c->small_smem, small_vec_bytes(d.m, d.n, c->f32));
+        if (nz > kSmallMaxNnz) c->small_fits = false;
+    }
+    if (c->small_smem > kSmallMaxSmem) c->small_fits = false;
+
     // one system with every tile of a side sliced: warp ranges instead of
     // tiles for that side's sweep
     if (nsys == 1) {
@@ -719,6 +728,8 @@ plss_status check_opts(const plss_opts *o) {
     if (!(o->inner_tol >= 0.0) || !(o->inner_tol < 1.0)) return fail(PLSS_ERR_INVALID, "inner_tol must be in [0, 1)");
     if (o->hist_cap > 0 && !o->hist) return fail(PLSS_ERR_INVALID, "hist_cap > 0 with hist NULL");
     if (o->profile < 0) return fail(PLSS_ERR_INVALID, "profile < 0");
+    if (o->schedule != PLSS_SCHED_AUTO && o->schedule != PLSS_SCHED_GRID && o->schedule != PLSS_SCHED_SMALL)
+        return fail(PLSS_ERR_INVALID, "unknown schedule %d", o->schedule);
     return PLSS_OK;
 }
 
@@ -813,7 +824,28 @@ plss_status run_residual(plss_ctx *c, const double *const *b, const double *cons
     const int64_t period = std::max<int64_t>(1, o->profile);   // profile one chunk in `period`
     int64_t bodies = 0, nchunk = 0;
     int chunk = 1;
-    for (;;) {
+    // the one-CTA form only on request: measured on GB300 it is slower than
+    // the grid sweeps both for a lone small system and for many of them
+    const bool small = c->small_fits && o->schedule == PLSS_SCHED_SMALL;
+    if (small) {
+        // one CTA per system, whole bodies per launch
+        SweepArgs a = c->args;
+        a.w = w_on ? c->d_w : nullptr;
+        a.winv = w_on ? c->d_w + c->n : nullptr;
+        a.wf = w_on && c->d_wf ? c->d_wf : nullptr;
+        a.winvf = w_on && c->d_wf ? c->d_wf + c->n : nullptr;
+        int32_t per = 16;
+        for (;;) {
+            CUDA_TRY(launch_small_solve(a, c->f32, c->nsys, per, c->small_smem, s));
+            bodies += per;
+            CUDA_TRY(cudaMemcpyAsync(c->h_active, c->d_active, 4, cudaMemcpyDeviceToHost, s));
+            CUDA_TRY(cudaStreamSynchronize(s));
+            if (*c->h_active <= 0) break;
+            if (bodies > body_cap) return fail(PLSS_ERR_TIMEOUT, "iteration driver exceeded %lld bodies", (long long)body_cap);
+            per = std::min(per * 4, 4096);
+        }
+    }
+    while (!small) {
         const bool pchunk = prof && nchunk++ % period == 0;
         cudaGraphExec_t g;
         st = get_graph(c, chunk, w_on, pchunk, &g);
@@ -906,6 +938,8 @@ void plss_opts_default(plss_opts *o) {
     o->hist_cap = 0;
     o->profile = 0;
     o->layout = PLSS_LAYOUT_AUTO;
+    o->schedule = PLSS_SCHED_AUTO;
+    o->reserved = 0;
     o->inner_tol = 1e-4;
 }
 

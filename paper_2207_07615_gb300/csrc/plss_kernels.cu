@@ -463,21 +463,12 @@ __device__ __forceinline__ void row_tile_sliced(const SweepArgs &a, const Tile &
     });
 }
 
-// Sums the row-sweep partials [pb, pb + pc) of system `sys` in a fixed order
-// and applies the stopping rule (whole CTA; the last CTA of the system).
-__device__ void finish_row(const SweepArgs &a, int32_t sys, bool init, int32_t pb, int32_t pc) {
-    double v[2] = {0.0, 0.0};
-    for (int32_t i = threadIdx.x; i < pc; i += kThreads) {
-        v[0] += __ldcg(a.part_row + 2 * (pb + i));
-        v[1] += __ldcg(a.part_row + 2 * (pb + i) + 1);
-    }
-    cta_sum<2>(v);
-    if (threadIdx.x != 0) return;
-    SysState *st = a.st + sys;
+// The stopping rule after a row sweep (one thread): rho = r^T r, and with
+// `init` (r = b - A x) bb = ||b||^2.
+__device__ void row_decide(const SweepArgs &a, SysState *st, bool init, double rho, double bb) {
     st->cnt_row = 0;
-    const double rho = v[0];
     if (init) {
-        st->nb = sqrt(v[1]);
+        st->nb = sqrt(bb);
         st->rho0 = rho;
     }
     const double nb = st->nb;
@@ -506,6 +497,18 @@ __device__ void finish_row(const SweepArgs &a, int32_t sys, bool init, int32_t p
     } else {
         st->phase = init ? PH_FIRST : PH_RUN;
     }
+}
+
+// Sums the row-sweep partials [pb, pb + pc) of system `sys` in a fixed order
+// and applies the stopping rule (whole CTA; the last CTA of the system).
+__device__ void finish_row(const SweepArgs &a, int32_t sys, bool init, int32_t pb, int32_t pc) {
+    double v[2] = {0.0, 0.0};
+    for (int32_t i = threadIdx.x; i < pc; i += kThreads) {
+        v[0] += __ldcg(a.part_row + 2 * (pb + i));
+        v[1] += __ldcg(a.part_row + 2 * (pb + i) + 1);
+    }
+    cta_sum<2>(v);
+    if (threadIdx.x == 0) row_decide(a, a.st + sys, init, v[0], v[1]);
 }
 
 template <typename S>
@@ -671,16 +674,11 @@ __device__ __forceinline__ void col_tile_sliced(const SweepArgs &a, const Tile &
     });
 }
 
-// Sums the column-sweep partials [pb, pb + pc) of system `sys` in a fixed
-// order and takes the scalar step (whole CTA; the last CTA of the system).
-__device__ void finish_col(const SweepArgs &a, int32_t sys, int32_t pb, int32_t pc) {
-    double v[1] = {0.0};
-    for (int32_t i = threadIdx.x; i < pc; i += kThreads) v[0] += __ldcg(a.part_col + pb + i);
-    cta_sum<1>(v);
-    if (threadIdx.x != 0) return;
-    SysState *st = a.st + sys;
+// The scalar step of Theorem 4.1 after a column sweep (one thread): phi =
+// y^T W y gives beta and gamma (or the first update's gamma = rho/phi), or a
+// breakdown.
+__device__ void col_decide(const SweepArgs &a, SysState *st, double phi) {
     st->cnt_col = 0;
-    const double phi = v[0];
     st->phi = phi;
     const double rho = st->rho;
     if (st->phase == PH_FIRST) {
@@ -709,6 +707,15 @@ __device__ void finish_col(const SweepArgs &a, int32_t sys, int32_t pb, int32_t 
         st->beta = beta;
         st->gamma = __dmul_rn(__ddiv_rn(theta, rho), beta);
     }
+}
+
+// Sums the column-sweep partials [pb, pb + pc) of system `sys` in a fixed
+// order and takes the scalar step (whole CTA; the last CTA of the system).
+__device__ void finish_col(const SweepArgs &a, int32_t sys, int32_t pb, int32_t pc) {
+    double v[1] = {0.0};
+    for (int32_t i = threadIdx.x; i < pc; i += kThreads) v[0] += __ldcg(a.part_col + pb + i);
+    cta_sum<1>(v);
+    if (threadIdx.x == 0) col_decide(a, a.st + sys, v[0]);
 }
 
 template <typename S>
@@ -791,16 +798,10 @@ __global__ void __launch_bounds__(kThreads) k_col_sweep_w(SweepArgs a) {
 // Update: p = beta p + gamma u, theta = p^T W^{-1} p, x = x + p
 // ---------------------------------------------------------------------------
 
-__device__ void finish_upd(const SweepArgs &a, int32_t sys) {
-    const SysDesc d = a.desc[sys];
-    double v[1] = {0.0};
-    for (int32_t i = threadIdx.x; i < d.vt_count; i += kThreads)
-        v[0] += __ldcg(a.part_upd + d.vt_begin + i);
-    cta_sum<1>(v);
-    if (threadIdx.x != 0) return;
-    SysState *st = a.st + sys;
+// After an update (one thread): theta = p^T W^{-1} p, the update count,
+// the optional history row and the periodic refinement.
+__device__ void upd_decide(SysState *st, double theta) {
     st->cnt_upd = 0;
-    const double theta = v[0];
     st->theta = theta;
     const int64_t k = st->iters;
     if (st->hist && k < st->hist_cap) {
@@ -819,6 +820,15 @@ __device__ void finish_upd(const SweepArgs &a, int32_t sys) {
     } else {
         st->phase = PH_RUN;
     }
+}
+
+__device__ void finish_upd(const SweepArgs &a, int32_t sys) {
+    const SysDesc d = a.desc[sys];
+    double v[1] = {0.0};
+    for (int32_t i = threadIdx.x; i < d.vt_count; i += kThreads)
+        v[0] += __ldcg(a.part_upd + d.vt_begin + i);
+    cta_sum<1>(v);
+    if (threadIdx.x == 0) upd_decide(a.st + sys, v[0]);
 }
 
 // FP32 storage: p = beta p + gamma u in float (p is stored in float; beta
@@ -930,6 +940,249 @@ __global__ void __launch_bounds__(kThreads) k_update(SweepArgs a) {
         ++pending;
     }
     if (pending && arrive(&a.st[cur].cnt_upd, pending, a.desc[cur].vt_count)) finish_upd(a, cur);
+}
+
+// ---------------------------------------------------------------------------
+// Small systems: one CTA runs the whole recursion of one system
+// ---------------------------------------------------------------------------
+//
+// For a system of a few thousand rows a body of three grid-wide launches is
+// all latency (kernel boundaries, arrivals, last-CTA reductions, global
+// round trips for every vector access). Here one CTA of kSmallThreads per
+// system runs the same body -- column sweep, scalar step, update, row
+// sweep, stopping rule, in the same order and with the same decision
+// functions -- for up to `bodies` bodies per launch, with the system's
+// vectors r, p, u, x and its SysState held in shared memory (loaded at entry,
+// written back at exit) and only A streamed from L2/HBM. Sums are
+// fixed-order block reductions (deterministic).
+
+constexpr int kSmallThreads = 512;
+constexpr int kSmallWarps = kSmallThreads / 32;
+
+template <int N>
+__device__ __forceinline__ void small_sum(double (&v)[N]) {
+    __shared__ double sh[N][kSmallWarps];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
+    }
+    __syncthreads();
+    if (lane == 0) {
+#pragma unroll
+        for (int i = 0; i < N; ++i) sh[i][warp] = v[i];
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            double t = lane < kSmallWarps ? sh[i][lane] : 0.0;
+#pragma unroll
+            for (int o = kSmallWarps / 2; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+            v[i] = t;
+        }
+    }
+}
+
+// Segment dot with G lanes per segment against a shared-memory vector xs
+// indexed from xoff (global index c reads xs[c - xoff]).
+template <int G, typename VT, typename XT, typename ACC>
+__device__ __forceinline__ ACC small_dot(const int32_t *__restrict__ idx, const VT *__restrict__ val, int32_t s,
+                                         int32_t e, int gl, const XT *xs, int32_t xoff) {
+    ACC acc = ACC(0);
+    for (int32_t base = s + gl; base < e; base += kBatch * G) {
+        int32_t c[kBatch];
+        VT v[kBatch];
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+            const int32_t k = base + u * G;
+            const bool in = k < e;
+            c[u] = in ? __ldg(idx + k) - xoff : 0;
+            v[u] = in ? __ldg(val + k) : VT(0);
+        }
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u)
+            if (base + u * G < e) acc = fma_t(ACC(v[u]), ACC(xs[c[u]]), acc);
+    }
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    return acc;
+}
+
+// Calls body(seg, s, e, gl, valid) for segments [b0, b1) with G lanes each
+// over the whole CTA (warp-uniform loop).
+template <int G, typename F>
+__device__ __forceinline__ void small_segments(const int32_t *__restrict__ ptr, int32_t b0, int32_t b1, F &&body) {
+    constexpr int SPW = 32 / G;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int gid = lane / G, gl = lane & (G - 1);
+    for (int32_t base = b0 + warp * SPW; base < b1; base += kSmallWarps * SPW) {
+        const int32_t seg = base + gid;
+        const bool valid = seg < b1;
+        const int32_t s = valid ? __ldg(ptr + seg) : 0;
+        const int32_t e = valid ? __ldg(ptr + seg + 1) : 0;
+        body(seg, s, e, gl, valid);
+    }
+}
+
+// The system's vectors in shared memory (local indices).
+template <typename S>
+struct SmallVecs {
+    double *x;   // [n]
+    S *r;        // [m]
+    S *p;        // [n]
+    S *u;        // [n]
+};
+
+template <int G, typename S>
+__device__ __forceinline__ void small_row(const SweepArgs &a, const SmallVecs<S> &v, int32_t r0, int32_t r1,
+                                          int32_t c0, bool init, double &acc_r, double &acc_b) {
+    const S *__restrict__ val = static_cast<const S *>(a.val);
+    small_segments<G>(a.row_ptr, r0, r1, [&](int32_t row, int32_t s, int32_t e, int gl, bool valid) {
+        if (init) {
+            const double d = small_dot<G, S, double, double>(a.col_idx, val, s, e, gl, v.x, c0);
+            if (valid && gl == 0) {
+                const double bi = a.b[row];
+                const S ri = S(bi - d);
+                v.r[row - r0] = ri;
+                acc_r = fma(double(ri), double(ri), acc_r);
+                acc_b = fma(bi, bi, acc_b);
+            }
+        } else {
+            const S d = small_dot<G, S, S, S>(a.col_idx, val, s, e, gl, v.p, c0);
+            if (valid && gl == 0) {
+                const S ri = v.r[row - r0] - d;
+                v.r[row - r0] = ri;
+                acc_r = fma(double(ri), double(ri), acc_r);
+            }
+        }
+    });
+}
+
+template <int G, typename S>
+__device__ __forceinline__ void small_col(const SweepArgs &a, const SmallVecs<S> &v, int32_t c0, int32_t c1,
+                                          int32_t r0, double &acc) {
+    const S *__restrict__ val = static_cast<const S *>(a.cval);
+    small_segments<G>(a.col_ptr, c0, c1, [&](int32_t col, int32_t s, int32_t e, int gl, bool valid) {
+        const S y = small_dot<G, S, S, S>(a.row_idx, val, s, e, gl, v.r, r0);
+        if (valid && gl == 0) {
+            S uj;
+            if constexpr (std::is_same<S, float>::value) uj = a.wf ? __fmul_rn(a.wf[col], y) : y;
+            else uj = a.w ? S(a.w[col] * double(y)) : y;
+            v.u[col - c0] = uj;
+            acc = fma(double(y), double(uj), acc);
+        }
+    });
+}
+
+// Lanes per segment for a mean segment length (as the host's tile groups).
+__device__ __forceinline__ int small_group(int64_t nnz, int64_t segs) {
+    int g = 1;
+    while (g < 32 && 2 * g * 8 * segs <= nnz) g <<= 1;
+    return g;
+}
+
+// Shared-memory bytes of a system's vectors (x double; r, p, u storage type).
+__host__ __device__ constexpr int64_t small_smem_bytes(int64_t m, int64_t n, int64_t sv) {
+    return ((8 * n + 15) / 16 * 16) + ((sv * m + 15) / 16 * 16) + 2 * ((sv * n + 15) / 16 * 16);
+}
+
+template <typename S>
+__global__ void __launch_bounds__(kSmallThreads) k_small_solve(SweepArgs a, int32_t bodies) {
+    extern __shared__ __align__(16) unsigned char small_smem[];
+    __shared__ SysState sst;
+    const int32_t sys = blockIdx.x;
+    const SysDesc d = a.desc[sys];
+    const int32_t r0 = int32_t(d.row_off), r1 = int32_t(d.row_off) + d.m;
+    const int32_t c0 = int32_t(d.col_off), c1 = int32_t(d.col_off) + d.n;
+    constexpr int64_t sv = sizeof(S);
+    SmallVecs<S> v;
+    v.x = reinterpret_cast<double *>(small_smem);
+    v.r = reinterpret_cast<S *>(small_smem + (8 * d.n + 15) / 16 * 16);
+    v.p = reinterpret_cast<S *>(reinterpret_cast<unsigned char *>(v.r) + (sv * d.m + 15) / 16 * 16);
+    v.u = reinterpret_cast<S *>(reinterpret_cast<unsigned char *>(v.p) + (sv * d.n + 15) / 16 * 16);
+    if (threadIdx.x == 0) sst = a.st[sys];
+    const S *gr = static_cast<const S *>(a.r), *gp = static_cast<const S *>(a.p), *gu = static_cast<const S *>(a.u);
+    for (int32_t i = threadIdx.x; i < d.m; i += kSmallThreads) v.r[i] = gr[r0 + i];
+    for (int32_t j = threadIdx.x; j < d.n; j += kSmallThreads) {
+        v.x[j] = a.x[c0 + j];
+        v.p[j] = gp[c0 + j];
+        v.u[j] = gu[c0 + j];
+    }
+    __syncthreads();
+    SysState *st = &sst;
+    const int64_t nnz = int64_t(a.row_ptr[r1]) - a.row_ptr[r0];
+    const int gr_ = small_group(nnz, d.m), gc_ = small_group(nnz, d.n);
+    for (int32_t it = 0; it < bodies; ++it) {
+        __syncthreads();
+        int32_t ph = st->phase;
+        if (ph == PH_DONE) break;
+        if (ph == PH_FIRST || ph == PH_RUN) {
+            double w1[1] = {0.0};
+            switch (gc_) {
+                case 1: small_col<1, S>(a, v, c0, c1, r0, w1[0]); break;
+                case 2: small_col<2, S>(a, v, c0, c1, r0, w1[0]); break;
+                case 4: small_col<4, S>(a, v, c0, c1, r0, w1[0]); break;
+                case 8: small_col<8, S>(a, v, c0, c1, r0, w1[0]); break;
+                case 16: small_col<16, S>(a, v, c0, c1, r0, w1[0]); break;
+                default: small_col<32, S>(a, v, c0, c1, r0, w1[0]); break;
+            }
+            small_sum<1>(w1);
+            if (threadIdx.x == 0) col_decide(a, st, w1[0]);
+            __syncthreads();
+            ph = st->phase;
+            if (ph == PH_FIRST || ph == PH_RUN) {
+                const bool first = ph == PH_FIRST;
+                const double beta = st->beta, gamma = st->gamma;
+                double acc[1] = {0.0};
+                for (int32_t j = threadIdx.x; j < d.n; j += kSmallThreads) {
+                    S ps;
+                    if constexpr (std::is_same<S, float>::value) {
+                        const float bf = float(beta), gf = float(gamma);
+                        ps = first ? gf * v.u[j] : fmaf(bf, v.p[j], gf * v.u[j]);
+                    } else {
+                        const double gu = gamma * v.u[j];
+                        ps = first ? gu : fma(beta, v.p[j], gu);
+                    }
+                    v.p[j] = ps;
+                    const double pd = double(ps);
+                    if constexpr (std::is_same<S, float>::value)
+                        acc[0] = fma(pd, a.winvf ? double(__fmul_rn(ps, a.winvf[c0 + j])) : pd, acc[0]);
+                    else
+                        acc[0] = fma(pd, a.winv ? pd * a.winv[c0 + j] : pd, acc[0]);
+                    v.x[j] = v.x[j] + pd;
+                }
+                small_sum<1>(acc);
+                if (threadIdx.x == 0) upd_decide(st, acc[0]);
+            }
+            __syncthreads();
+            ph = st->phase;
+        }
+        if (ph == PH_SETUP || ph == PH_RUN) {
+            const bool init = ph == PH_SETUP;
+            double w2[2] = {0.0, 0.0};
+            switch (gr_) {
+                case 1: small_row<1, S>(a, v, r0, r1, c0, init, w2[0], w2[1]); break;
+                case 2: small_row<2, S>(a, v, r0, r1, c0, init, w2[0], w2[1]); break;
+                case 4: small_row<4, S>(a, v, r0, r1, c0, init, w2[0], w2[1]); break;
+                case 8: small_row<8, S>(a, v, r0, r1, c0, init, w2[0], w2[1]); break;
+                case 16: small_row<16, S>(a, v, r0, r1, c0, init, w2[0], w2[1]); break;
+                default: small_row<32, S>(a, v, r0, r1, c0, init, w2[0], w2[1]); break;
+            }
+            small_sum<2>(w2);
+            if (threadIdx.x == 0) row_decide(a, st, init, w2[0], w2[1]);
+        }
+    }
+    __syncthreads();
+    S *wr = static_cast<S *>(a.r), *wp = static_cast<S *>(a.p), *wu = static_cast<S *>(a.u);
+    for (int32_t i = threadIdx.x; i < d.m; i += kSmallThreads) wr[r0 + i] = v.r[i];
+    for (int32_t j = threadIdx.x; j < d.n; j += kSmallThreads) {
+        a.x[c0 + j] = v.x[j];
+        wp[c0 + j] = v.p[j];
+        wu[c0 + j] = v.u[j];
+    }
+    if (threadIdx.x == 0) a.st[sys] = sst;
 }
 
 // ---------------------------------------------------------------------------
@@ -1056,6 +1309,20 @@ cudaError_t launch_col_sweep(const SweepArgs &a, bool f32, int grid, cudaStream_
 
 cudaError_t launch_update(const SweepArgs &a, bool f32, int grid, cudaStream_t s) {
     return f32 ? launch_pdl(k_update<float>, grid, s, a) : launch_pdl(k_update<double>, grid, s, a);
+}
+
+int64_t small_vec_bytes(int64_t m, int64_t n, bool f32) { return small_smem_bytes(m, n, f32 ? 4 : 8); }
+
+cudaError_t launch_small_solve(const SweepArgs &a, bool f32, int32_t nsys, int32_t bodies, int64_t smem,
+                               cudaStream_t s) {
+    cudaError_t e = f32 ? cudaFuncSetAttribute(k_small_solve<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               int(smem))
+                        : cudaFuncSetAttribute(k_small_solve<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               int(smem));
+    if (e != cudaSuccess) return e;
+    if (f32) k_small_solve<float><<<nsys, kSmallThreads, size_t(smem), s>>>(a, bodies);
+    else k_small_solve<double><<<nsys, kSmallThreads, size_t(smem), s>>>(a, bodies);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_spmv(const int32_t *ptr, const int32_t *idx, const void *val, bool f32,

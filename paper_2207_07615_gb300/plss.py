@@ -24,6 +24,7 @@ STATUS_NAMES = {0: "converged", 1: "not_converged", 2: "pending", -1: "invalid",
 SKETCH = {"residual": 0, "identity": 1}
 PRECISION = {"fp64": 0, "fp32": 1}
 LAYOUT = {"auto": 0, "csr": 1}
+SCHEDULE = {"auto": 0, "grid": 1, "small": 2}
 
 #: every symbol declared in include/plss.h
 EXPORTS = ["plss_opts_default", "plss_create", "plss_create_batched", "plss_destroy",
@@ -44,7 +45,8 @@ class Opts(C.Structure):
                 ("refine_period", C.c_int64), ("kacz_hist", C.c_int64), ("seed", C.c_uint64),
                 ("io_device", C.c_int32), ("symmetric", C.c_int32), ("stream", C.c_void_p),
                 ("hist", C.c_void_p), ("hist_cap", C.c_int64), ("profile", C.c_int32),
-                ("layout", C.c_int32), ("inner_tol", C.c_double)]
+                ("layout", C.c_int32), ("inner_tol", C.c_double), ("schedule", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class Result(C.Structure):
@@ -181,6 +183,8 @@ def make_opts(**kw) -> Opts:
             v = PRECISION[v]
         if k == "layout" and isinstance(v, str):
             v = LAYOUT[v]
+        if k == "schedule" and isinstance(v, str):
+            v = SCHEDULE[v]
         setattr(o, k, v)
     return o
 

@@ -33,7 +33,7 @@ def test_exports_match_header(L):
 
 
 def test_struct_layouts(L):
-    assert C.sizeof(plss.Opts) == 104
+    assert C.sizeof(plss.Opts) == 112
     assert C.sizeof(plss.Csr) == 56
     assert C.sizeof(plss.Result) == 40
     o = plss.Opts()

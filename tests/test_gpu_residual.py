@@ -51,7 +51,8 @@ def test_smoke():
     g.smoke()
 
 
-def test_square_2000_every_iterate(plss):
+@pytest.mark.parametrize("schedule", ["small", "grid"])
+def test_square_2000_every_iterate(plss, schedule):
     """The 2,000 x 2,000 diagonally dominant system, tol 1e-10: every update's
     scalars (rho, phi, beta, gamma, theta) and sampled iterates x_k against the
     oracle, at 1e-10 while the recursion's own rounding sensitivity allows it
@@ -60,14 +61,14 @@ def test_square_2000_every_iterate(plss):
     ref = _parity.reference(A, b, 2000)
     fin = oracle.residual(A, b, tol=1e-10, maxit=2000)
     with plss.Context(A) as ctx:
-        x, res, hist = ctx.solve(b, tol=1e-10, maxit=2000, hist=2000)
+        x, res, hist = ctx.solve(b, tol=1e-10, maxit=2000, hist=2000, schedule=schedule)
         assert res["status"] == "converged"
         assert abs(res["iters"] - fin["iters"]) <= 2
         strict = _parity.check_scalars(hist, ref, min_strict=20)
         assert res["relres_true"] <= 2e-10
         assert rel(x, fin["x"]) < 1e-8
         for k in (1, 2, 3, 7, 15, strict, strict + 5, res["iters"]):
-            xk, rk = ctx.solve(b, tol=0.0, maxit=k)
+            xk, rk = ctx.solve(b, tol=0.0, maxit=k, schedule=schedule)
             assert rk["iters"] == k and rk["status"] == "not_converged"
             _parity.check_x(xk, ref, k)
 
@@ -110,9 +111,12 @@ def _oracle_once(key, fn):
     return _ORACLE_CACHE[key]
 
 
-@pytest.mark.parametrize("layout", ["auto", "csr"])
+SCHEDULES = [("auto", "small"), ("auto", "grid"), ("csr", "grid")]
+
+
+@pytest.mark.parametrize("layout,schedule", SCHEDULES)
 @pytest.mark.parametrize("shape", ["tall", "wide", "powerlaw"])
-def test_parity_shapes(plss, shape, layout):
+def test_parity_shapes(plss, shape, layout, schedule):
     """Overdetermined with column scales, underdetermined, and power-law rows
     (rows longer than a tile run one CTA per row), with the sliced tiles
     (auto) and with the CSR/CSC only: 80 updates against the oracle
@@ -132,11 +136,11 @@ def test_parity_shapes(plss, shape, layout):
             assert lay["row_sliced"] < lay["row_tiles"] and lay["col_sliced"] > 0
         else:
             assert lay["row_sliced"] > 0 and lay["col_sliced"] > 0
-        x, res, hist = ctx.solve(b, tol=0.0, maxit=K, hist=K)
+        x, res, hist = ctx.solve(b, tol=0.0, maxit=K, hist=K, schedule=schedule)
         assert res["iters"] == K
         _parity.check_scalars(hist, ref, min_strict=10)
         _parity.check_x(x, ref, K)
-        x, res = ctx.solve(b, tol=1e-8, maxit=200000, stop_on_true=1)
+        x, res = ctx.solve(b, tol=1e-8, maxit=200000, stop_on_true=1, schedule=schedule)
     assert res["status"] == "converged" and res["relres_true"] <= 1e-8
     if shape != "powerlaw":   # the oracle needs ~80k updates (a minute) there
         fin = _oracle_once((shape, "fin"),
@@ -224,8 +228,8 @@ def test_edge_cases(plss):
     assert rel(x, ref["x"]) < RTOL
 
 
-@pytest.mark.parametrize("layout", ["auto", "csr"])
-def test_ragged_tails(plss, layout):
+@pytest.mark.parametrize("layout,schedule", SCHEDULES)
+def test_ragged_tails(plss, layout, schedule):
     """Row counts just off the tile, slice and group boundaries."""
     for m in (1, 31, 33, 255, 257, 2049):
         A, b, xs = synth.powerlaw_underdetermined(m=m, n=3 * m + 7, mean_len=6, max_len=50, seed=m)
@@ -233,14 +237,15 @@ def test_ragged_tails(plss, layout):
         K = 12
         ref = _parity.reference(A, b, K)
         with plss.Context(A, layout=layout) as ctx:
-            x, res, hist = ctx.solve(b, tol=0.0, maxit=K, hist=K)
+            x, res, hist = ctx.solve(b, tol=0.0, maxit=K, hist=K, schedule=schedule)
         assert res["iters"] == ref["iters"], m
         _parity.check_scalars(hist, ref, min_strict=1)
         if res["iters"]:
             _parity.check_x(x, ref, res["iters"])
 
 
-def test_batched_matches_single(plss):
+@pytest.mark.parametrize("schedule", ["small", "grid"])
+def test_batched_matches_single(plss, schedule):
     """Independent systems packed into one context: each system's trajectory
     equals the oracle's solve of that system alone, and each stops on its own."""
     systems = synth.batched_systems(nsys=6, m_lo=200, m_hi=4000, len_lo=5, len_hi=20, seed0=50)
@@ -248,12 +253,12 @@ def test_batched_matches_single(plss):
     bs = [b for _, b, _ in systems]
     K = 40
     with plss.Context(As) as ctx:
-        xs, rs = ctx.solve_batched(bs, tol=0.0, maxit=K)
+        xs, rs = ctx.solve_batched(bs, tol=0.0, maxit=K, schedule=schedule)
         for A, b, x, r in zip(As, bs, xs, rs):
             ref = _parity.reference(A, b, K)
             assert r["iters"] == K and r["status"] == "not_converged"
             _parity.check_x(x, ref, K)
-        xs, rs = ctx.solve_batched(bs, tol=1e-6, maxit=20000, stop_on_true=1)
+        xs, rs = ctx.solve_batched(bs, tol=1e-6, maxit=20000, stop_on_true=1, schedule=schedule)
     iters = set()
     for A, b, x, r in zip(As, bs, xs, rs):
         assert r["status"] == "converged" and r["relres_true"] <= 1e-6

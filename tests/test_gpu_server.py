@@ -73,8 +73,9 @@ def test_mix_equals_alone(plss, precision):
         srv.close()
     for (A, b), t in zip(reqs, tickets):
         x_mix, r_mix = got[t]
-        with plss.Context(A, precision=precision, layout="csr") as ctx:   # the arena's layout
-            x_one, r_one = ctx.solve(b, stop_on_true=1, **kw)
+        # the arena's layout and schedule
+        with plss.Context(A, precision=precision, layout="csr") as ctx:
+            x_one, r_one = ctx.solve(b, stop_on_true=1, schedule="grid", **kw)
         assert r_mix["status"] == r_one["status"]
         assert r_mix["iters"] == r_one["iters"]
         np.testing.assert_array_equal(x_mix, x_one)
