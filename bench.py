@@ -495,7 +495,8 @@ def suite_c3(args):
         Ap = A if prec == "fp32" else A.astype(np.float64)
         ctx = plss.Context(Ap, precision=prec)
         for w in (0, 2):
-            t, (x, r), clk = _timed(torch, lambda: ctx.solve(bd, tol=1e-8, maxit=200000, stop_on_true=1,
+            t, (x, r), clk = _timed(torch, lambda: ctx.solve(bd, tol=1e-8, maxit=min(200000, args.maxit),
+                                                             stop_on_true=1,
                                                              w_mode=w), 1, 1)
             out[f"residual_{prec}_w{w}"] = {"seconds": t, "updates": r["iters"], "status": r["status"],
                                             "relres_true": r["relres_true"],
@@ -505,7 +506,7 @@ def suite_c3(args):
     ctx = plss.Context(A, precision="fp64")
     for K in (0, 8):
         t, (x, r), clk = _timed(torch, lambda: ctx.solve(bd, sketch="identity", tol=1e-8,
-                                                         maxit=10 * A.m, kacz_hist=K, seed=7), 1, 1)
+                                                         maxit=min(10 * A.m, args.maxit), kacz_hist=K, seed=7), 1, 1)
         out[f"identity_K{K}"] = {"seconds": t, "rows_visited": r["iters"], "status": r["status"],
                                  "relres_true": r["relres_true"],
                                  "passes": r["iters"] / A.m}
@@ -528,7 +529,8 @@ def suite_c4a(args):
     out = {}
     for prec in ("fp32", "fp64"):
         ctx = plss.Context(As if prec == "fp32" else [A.astype(np.float64) for A in As], precision=prec)
-        t, (xs_, rs), clk = _timed(torch, lambda: ctx.solve_batched(bs, tol=1e-8, maxit=5000, stop_on_true=1,
+        t, (xs_, rs), clk = _timed(torch, lambda: ctx.solve_batched(bs, tol=1e-8, maxit=min(5000, args.maxit),
+                                                                    stop_on_true=1,
                                                                     w_mode=2), args.warmup, args.steps)
         ups = sum(r["iters"] for r in rs)
         out[prec] = {"seconds": t, "converged": sum(r["status"] == "converged" for r in rs),
@@ -550,7 +552,8 @@ def suite_c4b(args):
     out = {}
     for prec in ("fp32", "fp64"):
         ctx = plss.Context(A if prec == "fp32" else A.astype(np.float64), precision=prec, symmetric=True)
-        t, (X, rs), clk = _timed(torch, lambda: ctx.solve_rhs(Bd, tol=1e-8, maxit=50000, stop_on_true=1),
+        t, (X, rs), clk = _timed(torch, lambda: ctx.solve_rhs(Bd, tol=1e-8, maxit=min(50000, args.maxit),
+                                                              stop_on_true=1),
                                  1, 1)
         Xh = X.cpu().numpy()
         out[prec] = {"seconds": t, "converged": sum(r["status"] == "converged" for r in rs),
@@ -588,7 +591,7 @@ def suite_c5(args):
                 time.sleep(0.0002)
             t = None
             while t is None:
-                t = srv.submit(A, b, tol=1e-6, maxit=3000, w_mode=1)
+                t = srv.submit(A, b, tol=1e-6, maxit=min(3000, args.maxit), w_mode=1)
                 if t is None:
                     busy[0] += 1
                     time.sleep(0.001)
