@@ -22,9 +22,11 @@ constexpr int kWarps = kThreads / 32;
 // of lanes that share one segment (1..32, a power of two); 0 means the whole
 // CTA works on the single segment of the tile (very long rows/columns). With
 // kSliced set, the sweeps read the tile from its sliced copy (below) instead;
-// the low bits still give the lane count for kernels that use the plain
-// CSR/CSC (products, residual norms).
+// with kStaged set, they stage its products in shared memory; the low bits
+// still give the lane count for kernels that use the plain CSR/CSC
+// (products, residual norms).
 constexpr int32_t kSliced = 0x100;
+constexpr int32_t kStaged = 0x200;   // products staged in shared memory (at most 2,048 nonzeros, 1,024 segments)
 constexpr int32_t kGroupMask = 0xff;
 
 // Sliced copy of a side (rows or columns) of A. A sliced tile's segments,

@@ -75,7 +75,8 @@ void build_tiles(const int32_t *ptr, int64_t begin, int64_t end, int32_t sys, in
             nz += l;
             ++j;
         }
-        out.push_back({sys, int32_t(i), int32_t(j), pick_group(double(nz) / double(j - i), f32)});
+        // FP32 tiles (cut to the staging limits) stage their products
+        out.push_back({sys, int32_t(i), int32_t(j), pick_group(double(nz) / double(j - i), f32) | (f32 ? kStaged : 0)});
         i = j;
     }
 }
@@ -159,8 +160,11 @@ void build_side(const int32_t *ptr, int64_t begin, int64_t end, int32_t sys, int
         const int64_t nz = int64_t(ptr[t.end]) - ptr[t.begin];
         if (t.group != 0 && t.end > t.begin && slice_order(ptr, t, order) * 4 <= nz * 5) {
             out.push_back({t.sys, t.begin, t.end, t.group | kSliced});
-        } else if (f32 && t.end > t.begin) {
-            build_tiles(ptr, t.begin, t.end, sys, target, max_segs(true), true, out);
+        } else if (t.group != 0 && t.end > t.begin) {
+            // uneven segments: staged tiles (FP64 too), so that a long
+            // segment does not hold a warp through a serial gather chain
+            build_tiles(ptr, t.begin, t.end, sys, f32 ? target : tile_target(nnz, nsm, true), max_segs(true), true,
+                        out);
         } else {
             out.push_back(t);
         }

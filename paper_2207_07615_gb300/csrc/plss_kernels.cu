@@ -173,56 +173,56 @@ __device__ __forceinline__ double cta_dot(const int32_t *__restrict__ idx,
     return v1[0];
 }
 
-// FP32 storage: a tile's products are staged in shared memory. Every thread
-// issues its (up to 16) coalesced index/value loads, the tile's segment
-// offsets and (row sweep) old residuals, then its gathers, before storing
-// any float product; the segments are then summed out of shared memory and
-// only the results go back to global memory. FP32 arithmetic is plentiful
-// on GB300, so this trades a few float adds for coalesced loads and two
-// memory round trips per tile.
-constexpr int kStageNnz = 2048;                   // float products staged per tile (8 KB)
+// Staged tiles (kSliced unset, kStaged set: every FP32 tile that is not
+// sliced, and FP64 tiles of uneven segments): a tile's products are staged
+// in shared memory. Every thread issues its (up to 8) coalesced index/value
+// loads, the tile's segment offsets and (row sweep) old residuals, then its
+// gathers, before storing any product; the segments are then summed out of
+// shared memory by G lanes each, so a long segment among short ones costs
+// shared-memory adds rather than a warp's serial gather chain.
+constexpr int kStageNnz = 2048;                   // products staged per tile
 constexpr int kStagePer = kStageNnz / kThreads;   // nonzeros per thread
-constexpr int kStageSegs = 1024;                  // segments per FP32 tile (host: kTileMaxSegsF32)
+constexpr int kStageSegs = 1024;                  // segments per staged tile (host: kTileMaxSegsF32)
 constexpr int kStageSegPer = (kStageSegs + 1 + kThreads - 1) / kThreads;
 
-struct StageF32 {
-    float prod[kStageNnz];
+template <typename T>
+struct Stage {
+    T prod[kStageNnz];
     int32_t ptr[kStageSegs + 1];
-    float old[kStageSegs];
+    T old[kStageSegs];
 };
 
 // Stages the tile [t.begin, t.end) of ptr/idx/val against x; with `vec`,
 // also old[i] = vec[t.begin + i]. All global loads (indices, values,
 // segment offsets, old values) are issued before any is used, then the
 // gathers, then the shared-memory stores. Ends with __syncthreads().
-__device__ __forceinline__ void stage_tile_f32(const Tile &t, const int32_t *__restrict__ ptr,
-                                               const int32_t *__restrict__ idx,
-                                               const float *__restrict__ val,
-                                               const float *__restrict__ x,
-                                               const float *__restrict__ vec, StageF32 &sm) {
+template <typename T>
+__device__ __forceinline__ void stage_tile(const Tile &t, const int32_t *__restrict__ ptr,
+                                           const int32_t *__restrict__ idx, const T *__restrict__ val,
+                                           const T *__restrict__ x, const T *__restrict__ vec, Stage<T> &sm) {
     const int32_t nseg = t.end - t.begin;
     const int32_t z0 = __ldg(ptr + t.begin);
     const int32_t nz = __ldg(ptr + t.end) - z0;
     int32_t c[kStagePer];
-    float v[kStagePer];
+    T v[kStagePer];
 #pragma unroll
     for (int u = 0; u < kStagePer; ++u) {
         const int32_t k = threadIdx.x + u * kThreads;
         const bool in = k < nz;
         c[u] = in ? __ldg(idx + z0 + k) : 0;
-        v[u] = in ? __ldg(val + z0 + k) : 0.0f;
+        v[u] = in ? __ldg(val + z0 + k) : T(0);
     }
     int32_t pq[kStageSegPer];
-    float oq[kStageSegPer];
+    T oq[kStageSegPer];
 #pragma unroll
     for (int q = 0; q < kStageSegPer; ++q) {
         const int32_t i = threadIdx.x + q * kThreads;
         pq[q] = i <= nseg ? __ldg(ptr + t.begin + i) : 0;
-        oq[q] = vec && i < nseg ? vec[t.begin + i] : 0.0f;
+        oq[q] = vec && i < nseg ? vec[t.begin + i] : T(0);
     }
-    float g[kStagePer];
+    T g[kStagePer];
 #pragma unroll
-    for (int u = 0; u < kStagePer; ++u) g[u] = threadIdx.x + u * kThreads < nz ? __ldg(x + c[u]) : 0.0f;
+    for (int u = 0; u < kStagePer; ++u) g[u] = threadIdx.x + u * kThreads < nz ? __ldg(x + c[u]) : T(0);
 #pragma unroll
     for (int q = 0; q < kStageSegPer; ++q) {
         const int32_t i = threadIdx.x + q * kThreads;
@@ -239,8 +239,8 @@ __device__ __forceinline__ void stage_tile_f32(const Tile &t, const int32_t *__r
 
 // Calls body(i, d, gl, valid) with d the sum over segment i of the tile
 // (tile-local index), G lanes per segment; warp-uniform loop.
-template <int G, typename F>
-__device__ __forceinline__ void staged_segments(const Tile &t, const StageF32 &sm, F &&body) {
+template <int G, typename T, typename F>
+__device__ __forceinline__ void staged_segments(const Tile &t, const Stage<T> &sm, F &&body) {
     constexpr int SPW = 32 / G;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int gid = lane / G, gl = lane & (G - 1);
@@ -249,7 +249,7 @@ __device__ __forceinline__ void staged_segments(const Tile &t, const StageF32 &s
         const int32_t i = base + gid;
         const bool valid = i < nseg;
         const int32_t s = valid ? sm.ptr[i] : 0, e = valid ? sm.ptr[i + 1] : 0;
-        float acc = 0.0f;
+        T acc = T(0);
         for (int32_t k = s + gl; k < e; k += G) acc += sm.prod[k];
 #pragma unroll
         for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -273,6 +273,11 @@ __device__ __forceinline__ void for_segments(const int32_t *__restrict__ ptr, co
     }
 }
 
+// Random gathers of the sliced sweeps: cached in L2 only (L1 would only
+// take fills that are never reused).
+template <typename T>
+__device__ __forceinline__ T kGather(const T *p) { return __ldcg(p); }
+
 // Dot product of slot `lane` of a slice (element offset `off`, `width`
 // elements per slot) with a dense vector: the warp loads 32 consecutive
 // indices and values per step, 8 steps before their gathers, and each lane
@@ -294,7 +299,7 @@ __device__ __forceinline__ ACC slice_dot(const int32_t *__restrict__ idx, const 
         }
         XT g[kBatch];
 #pragma unroll
-        for (int u = 0; u < kBatch; ++u) g[u] = c[u] >= 0 ? __ldg(x + c[u]) : XT(0);
+        for (int u = 0; u < kBatch; ++u) g[u] = c[u] >= 0 ? kGather(x + c[u]) : XT(0);
 #pragma unroll
         for (int u = 0; u < kBatch; ++u) acc = fma_t(ACC(v[u]), ACC(g[u]), acc);
     }
@@ -384,18 +389,20 @@ __device__ __forceinline__ void row_tile(const SweepArgs &a, const Tile &t, bool
     }
 }
 
-// FP32 storage, r = r - A p on a staged tile; rho partial in double-float.
-template <int G>
-__device__ __forceinline__ void row_tile_f32(const SweepArgs &a, const Tile &t, DF &acc_r, float *stage) {
-    float *__restrict__ r = static_cast<float *>(a.r);
-    StageF32 &sm = *reinterpret_cast<StageF32 *>(stage);
-    stage_tile_f32(t, a.row_ptr, a.col_idx, static_cast<const float *>(a.val),
-                   static_cast<const float *>(a.p), r, sm);
-    staged_segments<G>(t, sm, [&](int32_t i, float d, int gl, bool valid) {
+// r = r - A p on a staged tile; rho partial in double-float (FP32) or
+// double (FP64).
+template <int G, typename S>
+__device__ __forceinline__ void row_tile_staged(const SweepArgs &a, const Tile &t, DF &acc_f, double &acc_d,
+                                                unsigned char *stage) {
+    S *__restrict__ r = static_cast<S *>(a.r);
+    Stage<S> &sm = *reinterpret_cast<Stage<S> *>(stage);
+    stage_tile<S>(t, a.row_ptr, a.col_idx, static_cast<const S *>(a.val), static_cast<const S *>(a.p), r, sm);
+    staged_segments<G>(t, sm, [&](int32_t i, S d, int gl, bool valid) {
         if (valid && gl == 0) {
-            const float ri = sm.old[i] - d;
+            const S ri = sm.old[i] - d;
             r[t.begin + i] = ri;
-            acc_r = df_add_prod(acc_r, ri, ri);
+            if constexpr (std::is_same<S, float>::value) acc_f = df_add_prod(acc_f, ri, ri);
+            else acc_d = fma(ri, ri, acc_d);
         }
     });
     __syncthreads();
@@ -513,8 +520,7 @@ __device__ void finish_row(const SweepArgs &a, int32_t sys, bool init, int32_t p
 
 template <typename S>
 __global__ void __launch_bounds__(kThreads) k_row_sweep(SweepArgs a) {
-    // staging buffer of the FP32 path (unused in FP64)
-    __shared__ __align__(16) float stage[std::is_same<S, float>::value ? sizeof(StageF32) / 4 : 4];
+    __shared__ __align__(16) unsigned char stage[sizeof(Stage<S>)];   // staged tiles
     wait_prior_grid();
     int32_t t0, t1;
     tile_range(a.n_rtiles, t0, t1);
@@ -537,21 +543,25 @@ __global__ void __launch_bounds__(kThreads) k_row_sweep(SweepArgs a) {
         if (t.group & kSliced) {
             row_tile_sliced<S>(a, t, ti, init, acc[0], acc[1]);
             cta_sum<2>(acc);
-        } else if (std::is_same<S, float>::value && !init && t.group != 0) {
+        } else if ((t.group & kStaged) && !init) {
             DF f[1] = {{0.0f, 0.0f}};
-            switch (t.group) {
-                case 1: row_tile_f32<1>(a, t, f[0], stage); break;
-                case 2: row_tile_f32<2>(a, t, f[0], stage); break;
-                case 4: row_tile_f32<4>(a, t, f[0], stage); break;
-                case 8: row_tile_f32<8>(a, t, f[0], stage); break;
-                case 16: row_tile_f32<16>(a, t, f[0], stage); break;
-                default: row_tile_f32<32>(a, t, f[0], stage); break;
+            switch (t.group & kGroupMask) {
+                case 1: row_tile_staged<1, S>(a, t, f[0], acc[0], stage); break;
+                case 2: row_tile_staged<2, S>(a, t, f[0], acc[0], stage); break;
+                case 4: row_tile_staged<4, S>(a, t, f[0], acc[0], stage); break;
+                case 8: row_tile_staged<8, S>(a, t, f[0], acc[0], stage); break;
+                case 16: row_tile_staged<16, S>(a, t, f[0], acc[0], stage); break;
+                default: row_tile_staged<32, S>(a, t, f[0], acc[0], stage); break;
             }
-            double o[1];
-            cta_sum_df<1>(f, o);
-            acc[0] = o[0];
+            if constexpr (std::is_same<S, float>::value) {
+                double o[1];
+                cta_sum_df<1>(f, o);
+                acc[0] = o[0];
+            } else {
+                cta_sum<2>(acc);
+            }
         } else {
-            switch (t.group) {
+            switch (t.group & kGroupMask) {
                 case 0: row_tile_cta<S>(a, t, init, acc[0], acc[1]); break;
                 case 1: row_tile<1, S>(a, t, init, acc[0], acc[1]); break;
                 case 2: row_tile<2, S>(a, t, init, acc[0], acc[1]); break;
@@ -620,20 +630,24 @@ __device__ __forceinline__ void col_tile(const SweepArgs &a, const Tile &t, doub
     });
 }
 
-// FP32 storage, y = A^T r on a staged tile, u = W y with float weights,
-// phi partial in double-float.
-template <int G>
-__device__ __forceinline__ void col_tile_f32(const SweepArgs &a, const Tile &t, DF &acc, float *stage) {
-    StageF32 &sm = *reinterpret_cast<StageF32 *>(stage);
-    float *__restrict__ u = static_cast<float *>(a.u);
-    stage_tile_f32(t, a.col_ptr, a.row_idx, static_cast<const float *>(a.cval),
-                   static_cast<const float *>(a.r), nullptr, sm);
-    staged_segments<G>(t, sm, [&](int32_t i, float y, int gl, bool valid) {
+// y = A^T r on a staged tile, u = W y (float weights for FP32 storage), phi
+// partial in double-float (FP32) or double (FP64).
+template <int G, typename S>
+__device__ __forceinline__ void col_tile_staged(const SweepArgs &a, const Tile &t, DF &acc_f, double &acc_d,
+                                                unsigned char *stage) {
+    Stage<S> &sm = *reinterpret_cast<Stage<S> *>(stage);
+    S *__restrict__ u = static_cast<S *>(a.u);
+    stage_tile<S>(t, a.col_ptr, a.row_idx, static_cast<const S *>(a.cval), static_cast<const S *>(a.r), nullptr, sm);
+    staged_segments<G>(t, sm, [&](int32_t i, S y, int gl, bool valid) {
         if (valid && gl == 0) {
             const int32_t col = t.begin + i;
-            const float uj = a.wf ? __fmul_rn(a.wf[col], y) : y;
-            u[col] = uj;
-            acc = df_add_prod(acc, y, uj);
+            if constexpr (std::is_same<S, float>::value) {
+                const float uj = a.wf ? __fmul_rn(a.wf[col], y) : y;
+                u[col] = uj;
+                acc_f = df_add_prod(acc_f, y, uj);
+            } else {
+                col_out<S>(a, col, y, acc_d);
+            }
         }
     });
     __syncthreads();
@@ -720,7 +734,7 @@ __device__ void finish_col(const SweepArgs &a, int32_t sys, int32_t pb, int32_t 
 
 template <typename S>
 __global__ void __launch_bounds__(kThreads) k_col_sweep(SweepArgs a) {
-    __shared__ __align__(16) float stage[std::is_same<S, float>::value ? sizeof(StageF32) / 4 : 4];
+    __shared__ __align__(16) unsigned char stage[sizeof(Stage<S>)];   // staged tiles
     wait_prior_grid();
     int32_t t0, t1;
     tile_range(a.n_ctiles, t0, t1);
@@ -742,19 +756,20 @@ __global__ void __launch_bounds__(kThreads) k_col_sweep(SweepArgs a) {
         if (t.group & kSliced) {
             col_tile_sliced<S>(a, t, ti, acc[0]);
             cta_sum<1>(acc);
-        } else if (std::is_same<S, float>::value && t.group != 0) {
+        } else if (t.group & kStaged) {
             DF f[1] = {{0.0f, 0.0f}};
-            switch (t.group) {
-                case 1: col_tile_f32<1>(a, t, f[0], stage); break;
-                case 2: col_tile_f32<2>(a, t, f[0], stage); break;
-                case 4: col_tile_f32<4>(a, t, f[0], stage); break;
-                case 8: col_tile_f32<8>(a, t, f[0], stage); break;
-                case 16: col_tile_f32<16>(a, t, f[0], stage); break;
-                default: col_tile_f32<32>(a, t, f[0], stage); break;
+            switch (t.group & kGroupMask) {
+                case 1: col_tile_staged<1, S>(a, t, f[0], acc[0], stage); break;
+                case 2: col_tile_staged<2, S>(a, t, f[0], acc[0], stage); break;
+                case 4: col_tile_staged<4, S>(a, t, f[0], acc[0], stage); break;
+                case 8: col_tile_staged<8, S>(a, t, f[0], acc[0], stage); break;
+                case 16: col_tile_staged<16, S>(a, t, f[0], acc[0], stage); break;
+                default: col_tile_staged<32, S>(a, t, f[0], acc[0], stage); break;
             }
-            cta_sum_df<1>(f, acc);
+            if constexpr (std::is_same<S, float>::value) cta_sum_df<1>(f, acc);
+            else cta_sum<1>(acc);
         } else {
-            switch (t.group) {
+            switch (t.group & kGroupMask) {
                 case 0: col_tile_cta<S>(a, t, acc[0]); break;
                 case 1: col_tile<1, S>(a, t, acc[0]); break;
                 case 2: col_tile<2, S>(a, t, acc[0]); break;

@@ -530,7 +530,7 @@ __global__ void __launch_bounds__(kThreads) k_rhs_update(RhsArgs a) {
     const bool mine = lane < a.k;
     const int32_t ph = mine ? *reinterpret_cast<const volatile int32_t *>(&a.st[lane].phase) : PH_DONE;
     const bool act = ph == PH_FIRST || ph == PH_RUN;
-    bool on[V], first[V], on_any = false;
+    bool on[V], first[V], on_any = false, first_any = false;
     S beta[V], gamma[V];   // rounded to the storage type once (FP32: float)
 #pragma unroll
     for (int v = 0; v < V; ++v) {
@@ -541,7 +541,12 @@ __global__ void __launch_bounds__(kThreads) k_rhs_update(RhsArgs a) {
         beta[v] = S(on[v] ? a.st[j].beta : 0.0);
         gamma[v] = S(on[v] ? a.st[j].gamma : 0.0);
         on_any |= on[v];
+        first_any |= first[v];
     }
+    // the first update after a (re)start is rare: keep its FP64 flush of dX
+    // out of the common path (predicated-off FP64 instructions still occupy
+    // the FP64 pipe)
+    first_any = __syncthreads_or(first_any) != 0;
     S *P = static_cast<S *>(a.P);
     const S *U = static_cast<const S *>(a.U);
     RhsAcc<S> accs[V];
@@ -564,11 +569,13 @@ __global__ void __launch_bounds__(kThreads) k_rhs_update(RhsArgs a) {
                 // the first update after a (re)start moves it into X
                 float dx[V];
                 RhsVec<float>::ld_rw(a.dX + ix, dx);
+                if (first_any) {
 #pragma unroll
-                for (int v = 0; v < V; ++v) {
-                    if (first[v]) a.X[ix + v] = __dadd_rn(a.X[ix + v], double(dx[v]));
-                    dx[v] = first[v] ? pn[v] : (on[v] ? __fadd_rn(dx[v], pn[v]) : dx[v]);
+                    for (int v = 0; v < V; ++v)
+                        if (first[v]) a.X[ix + v] = __dadd_rn(a.X[ix + v], double(dx[v]));
                 }
+#pragma unroll
+                for (int v = 0; v < V; ++v) dx[v] = first[v] ? pn[v] : (on[v] ? __fadd_rn(dx[v], pn[v]) : dx[v]);
                 RhsVec<float>::st(a.dX + ix, dx);
             } else {
                 const double wi = a.winv ? a.winv[j] : 1.0;
