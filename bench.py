@@ -75,6 +75,17 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(value, dist, device=None):
+    """The slowest rank's value (replicas: every rank solves its own copy of
+    the workload; the job's time per step is the last one to finish)."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def host_info():
     cpu = "unknown"
     try:
@@ -300,11 +311,7 @@ def run_plss(args):
     clk = clocks.stop()
     ms_total = e0.elapsed_time(e1)
     kt = ctx.kernel_times(reset=True)
-    ms_step = ms_total / args.steps
-    if dist is not None:
-        t = torch.tensor([ms_step], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
+    ms_step = max_over_ranks(ms_total / args.steps, dist, dev)
     last = results[-1]
     x_np = x.cpu().numpy()
     err_xstar = float(np.linalg.norm(x_np - xs) / np.linalg.norm(xs))

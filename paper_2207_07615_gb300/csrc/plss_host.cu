@@ -543,8 +543,28 @@ static plss_status ctx_build(const plss_csr *As, int32_t nsys, const plss_opts *
         if (c->f32) TRY_ST(upload(reinterpret_cast<float **>(&c->d_cval), cv32, "cval"));
         else TRY_ST(upload(reinterpret_cast<double **>(&c->d_cval), cv64, "cval"));
     }
+    // A single system whose side is sliced throughout runs that side's sweep
+    // over warp ranges of slices, where tiles play no part: its slices are
+    // then cut from all segments sorted by length (less padding than
+    // tile-local sorting).
+    auto all_sliced = [](const std::vector<Tile> &ts) {
+        if (ts.empty()) return false;
+        for (const Tile &t : ts)
+            if (!(t.group & kSliced)) return false;
+        return true;
+    };
+    auto fill_side = [&](const int32_t *ptr, const int32_t *idx, const double *vd, const float *vf,
+                         const std::vector<Tile> &ts, int64_t nseg, HostSliced &out) {
+        if (nsys == 1 && all_sliced(ts) && nseg > 0) {
+            const std::vector<Tile> whole = {Tile{0, 0, int32_t(nseg), ts[0].group}};
+            fill_sliced(ptr, idx, vd, vf, whole, out);
+            out.first.assign(ts.size(), 0);
+        } else {
+            fill_sliced(ptr, idx, vd, vf, ts, out);
+        }
+    };
     HostSliced hsl;
-    fill_sliced(rp.data(), ci.data(), c->f32 ? nullptr : v64.data(), c->f32 ? v32.data() : nullptr, c->h_rt, hsl);
+    fill_side(rp.data(), ci.data(), c->f32 ? nullptr : v64.data(), c->f32 ? v32.data() : nullptr, c->h_rt, M, hsl);
     TRY_ST(upload_sliced(hsl, c->rsl, c->f32));
     c->sl_elems[0] = int64_t(hsl.idx.size());
     const std::vector<int32_t> rsl_ptr = hsl.ptr;
@@ -554,8 +574,8 @@ static plss_status ctx_build(const plss_csr *As, int32_t nsys, const plss_opts *
         c->sl_elems[1] = c->sl_elems[0];
         csl_ptr = rsl_ptr;
     } else {
-        fill_sliced(cp.data(), ri.data(), c->f32 ? nullptr : cv64.data(), c->f32 ? cv32.data() : nullptr,
-                    c->h_ct, hsl);
+        fill_side(cp.data(), ri.data(), c->f32 ? nullptr : cv64.data(), c->f32 ? cv32.data() : nullptr, c->h_ct, N,
+                  hsl);
         TRY_ST(upload_sliced(hsl, c->csl, c->f32));
         c->sl_elems[1] = int64_t(hsl.idx.size());
         csl_ptr = hsl.ptr;
