@@ -159,10 +159,11 @@ void plss_destroy(plss_ctx *ctx);
 plss_status plss_ctx_info(const plss_ctx *ctx, int32_t *nsys, int64_t *m, int64_t *n,
                           int64_t *nnz);
 
-/* Tile schedule of a context's sweeps (PLSS_LAYOUT_*): out[0] row tiles,
- * out[1] of them sliced, out[2] column tiles, out[3] of them sliced,
- * out[4] and out[5] elements (nonzeros plus padding) of the sliced row and
- * column copies. */
+/* Tile schedule of a context's sweeps (PLSS_LAYOUT_*; an inspection call
+ * with no counterpart in the paper): out[0] row tiles, out[1] of them
+ * sliced, out[2] column tiles, out[3] of them sliced, out[4] and out[5]
+ * elements (nonzeros plus padding) of the sliced row and column copies.
+ * PLSS_ERR_INVALID on a NULL argument. */
 plss_status plss_ctx_layout(const plss_ctx *ctx, int64_t out[6]);
 
 /*
@@ -229,13 +230,15 @@ plss_status plss_residual_noalloc(int64_t m, int64_t n, int64_t nnz, const int64
                                   const double *b, double *r, double *norm2, void *stream);
 
 /* Device time of the residual-sketch sweeps accumulated over the solves of
- * this context that ran with o->profile = 1: ms[0..2] = total milliseconds
- * of the row sweep (r = r - A p, rho), the column sweep (y = A^T r, phi,
- * scalar step) and the update (p, theta, x), over the graph launches in
- * which a system stayed active throughout; launches[0..2] = the launches
- * those totals cover; launches[3] = every kernel the profiled solves
- * launched. reset = 1 clears the totals after reading. Either array may be
- * NULL (ms has 3 entries, launches 4). */
+ * this context that ran with o->profile = k > 0 (GRID schedule): ms[0..2] =
+ * total milliseconds of the row sweep (r = r - A p, rho), the column sweep
+ * (y = A^T r, phi, scalar step) and the update (p, theta, x), between CUDA
+ * events recorded around each kernel of one graph launch in k, over the
+ * launches in which a system stayed active throughout; launches[0..2] = the
+ * kernel launches those totals cover; launches[3] = every kernel the
+ * profiled solves launched. reset = 1 clears the totals after reading.
+ * Either array may be NULL (ms has 3 entries, launches 4). A diagnostic
+ * with no counterpart in the paper. */
 plss_status plss_kernel_times(plss_ctx *ctx, double *ms, int64_t *launches, int32_t reset);
 
 /* Message of the last error on the calling thread ("" when none). */
