@@ -88,7 +88,7 @@ struct SysState {
     int32_t phase;
     int32_t status;     // plss_status once phase == PH_DONE
     int32_t stop_on_true;
-    int32_t pad0;
+    int32_t upd;        // update due in this body: 0 none, 1 p = beta p + gamma u, 2 p = gamma u (first)
     uint32_t cnt_row, cnt_col, cnt_upd, pad1;
 };
 

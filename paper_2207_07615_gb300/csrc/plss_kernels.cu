@@ -506,16 +506,43 @@ __device__ void row_decide(const SweepArgs &a, SysState *st, bool init, double r
     }
 }
 
+// After an update (one thread, in the row sweep's finishing CTA, before the
+// stopping rule): theta = p^T W^{-1} p, the optional history row, the update
+// count and the refinement counter.
+__device__ void upd_done(SysState *st, double theta) {
+    st->theta = theta;
+    const int64_t k = st->iters;
+    if (st->hist && k < st->hist_cap) {
+        double *h = st->hist + 5 * k;
+        h[0] = st->rho;
+        h[1] = st->phi;
+        h[2] = st->beta;
+        h[3] = st->gamma;
+        h[4] = theta;
+    }
+    st->iters = k + 1;
+    st->since = st->phase == PH_SETUP ? 0 : st->since + 1;
+    st->upd = 0;
+}
+
 // Sums the row-sweep partials [pb, pb + pc) of system `sys` in a fixed order
 // and applies the stopping rule (whole CTA; the last CTA of the system).
 __device__ void finish_row(const SweepArgs &a, int32_t sys, bool init, int32_t pb, int32_t pc) {
-    double v[2] = {0.0, 0.0};
+    const SysDesc d = a.desc[sys];
+    const bool upd = reinterpret_cast<const volatile int32_t *>(&a.st[sys].upd)[0] != 0;
+    double v[3] = {0.0, 0.0, 0.0};
     for (int32_t i = threadIdx.x; i < pc; i += kThreads) {
         v[0] += __ldcg(a.part_row + 2 * (pb + i));
         v[1] += __ldcg(a.part_row + 2 * (pb + i) + 1);
     }
-    cta_sum<2>(v);
-    if (threadIdx.x == 0) row_decide(a, a.st + sys, init, v[0], v[1]);
+    if (upd)   // theta of the update this row sweep followed
+        for (int32_t i = threadIdx.x; i < d.vt_count; i += kThreads) v[2] += __ldcg(a.part_upd + d.vt_begin + i);
+    cta_sum<3>(v);
+    if (threadIdx.x == 0) {
+        SysState *st = a.st + sys;
+        if (upd) upd_done(st, v[2]);
+        row_decide(a, st, init, v[0], v[1]);
+    }
 }
 
 template <typename S>
@@ -695,7 +722,8 @@ __device__ void col_decide(const SweepArgs &a, SysState *st, double phi) {
     st->cnt_col = 0;
     st->phi = phi;
     const double rho = st->rho;
-    if (st->phase == PH_FIRST) {
+    const bool first = st->phase == PH_FIRST;
+    if (first) {
         // Algorithm 1 initialisation: p = (rho/phi) W y
         if (!(phi > 0.0) || !isfinite(phi)) { finish_system(a, st, -4); return; }
         st->beta = 0.0;
@@ -721,6 +749,10 @@ __device__ void col_decide(const SweepArgs &a, SysState *st, double phi) {
         st->beta = beta;
         st->gamma = __dmul_rn(__ddiv_rn(theta, rho), beta);
     }
+    // the update of this body is due; the row sweep that follows it sees
+    // PH_RUN, or PH_SETUP when the periodic refinement restarts from b - A x
+    st->upd = first ? 2 : 1;
+    st->phase = (st->refine > 0 && st->since + 1 >= st->refine) ? PH_SETUP : PH_RUN;
 }
 
 // Sums the column-sweep partials [pb, pb + pc) of system `sys` in a fixed
@@ -813,39 +845,6 @@ __global__ void __launch_bounds__(kThreads) k_col_sweep_w(SweepArgs a) {
 // Update: p = beta p + gamma u, theta = p^T W^{-1} p, x = x + p
 // ---------------------------------------------------------------------------
 
-// After an update (one thread): theta = p^T W^{-1} p, the update count,
-// the optional history row and the periodic refinement.
-__device__ void upd_decide(SysState *st, double theta) {
-    st->cnt_upd = 0;
-    st->theta = theta;
-    const int64_t k = st->iters;
-    if (st->hist && k < st->hist_cap) {
-        double *h = st->hist + 5 * k;
-        h[0] = st->rho;
-        h[1] = st->phi;
-        h[2] = st->beta;
-        h[3] = st->gamma;
-        h[4] = theta;
-    }
-    st->iters = k + 1;
-    st->since += 1;
-    if (st->refine > 0 && st->since >= st->refine) {
-        st->since = 0;
-        st->phase = PH_SETUP;   // periodic refinement: restart from b - A x
-    } else {
-        st->phase = PH_RUN;
-    }
-}
-
-__device__ void finish_upd(const SweepArgs &a, int32_t sys) {
-    const SysDesc d = a.desc[sys];
-    double v[1] = {0.0};
-    for (int32_t i = threadIdx.x; i < d.vt_count; i += kThreads)
-        v[0] += __ldcg(a.part_upd + d.vt_begin + i);
-    cta_sum<1>(v);
-    if (threadIdx.x == 0) upd_decide(a.st + sys, v[0]);
-}
-
 // FP32 storage: p = beta p + gamma u in float (p is stored in float; beta
 // and gamma rounded to float), theta partials in float per thread, x in
 // double -- two FP64-pipe operations per entry.
@@ -921,24 +920,25 @@ __device__ __forceinline__ double update_tile(const SweepArgs &a, const Tile &t,
     return acc;
 }
 
+// The update writes one theta partial per tile and finishes nothing: the
+// row sweep that follows sums them (it has to wait for the whole update
+// anyway), which takes the arrival and the last-CTA reduction off this
+// short kernel's critical path.
 template <typename S>
 __global__ void __launch_bounds__(kThreads) k_update(SweepArgs a) {
     wait_prior_grid();
     int32_t t0, t1;
     tile_range(a.n_vtiles, t0, t1);
     int32_t cur = -1;
-    uint32_t pending = 0;
     bool active = false, first = false;
     double beta = 0.0, gamma = 0.0;
     for (int32_t ti = t0; ti < t1; ++ti) {
         const Tile t = a.vtiles[ti];
         if (t.sys != cur) {
-            if (pending && arrive(&a.st[cur].cnt_upd, pending, a.desc[cur].vt_count)) finish_upd(a, cur);
             cur = t.sys;
-            pending = 0;
-            const int32_t ph = load_phase(a.st + cur);
-            active = ph == PH_FIRST || ph == PH_RUN;
-            first = ph == PH_FIRST;
+            const int32_t upd = reinterpret_cast<const volatile int32_t *>(&a.st[cur].upd)[0];
+            active = upd != 0;
+            first = upd == 2;
             beta = a.st[cur].beta;
             gamma = a.st[cur].gamma;
         }
@@ -952,9 +952,7 @@ __global__ void __launch_bounds__(kThreads) k_update(SweepArgs a) {
             cta_sum<1>(acc);
         }
         if (threadIdx.x == 0) a.part_upd[ti] = acc[0];
-        ++pending;
     }
-    if (pending && arrive(&a.st[cur].cnt_upd, pending, a.desc[cur].vt_count)) finish_upd(a, cur);
 }
 
 // ---------------------------------------------------------------------------
@@ -1146,9 +1144,9 @@ __global__ void __launch_bounds__(kSmallThreads) k_small_solve(SweepArgs a, int3
             small_sum<1>(w1);
             if (threadIdx.x == 0) col_decide(a, st, w1[0]);
             __syncthreads();
-            ph = st->phase;
-            if (ph == PH_FIRST || ph == PH_RUN) {
-                const bool first = ph == PH_FIRST;
+            const int32_t upd = st->upd;
+            if (upd != 0) {
+                const bool first = upd == 2;
                 const double beta = st->beta, gamma = st->gamma;
                 double acc[1] = {0.0};
                 for (int32_t j = threadIdx.x; j < d.n; j += kSmallThreads) {
@@ -1169,7 +1167,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_small_solve(SweepArgs a, int3
                     v.x[j] = v.x[j] + pd;
                 }
                 small_sum<1>(acc);
-                if (threadIdx.x == 0) upd_decide(st, acc[0]);
+                if (threadIdx.x == 0) upd_done(st, acc[0]);
             }
             __syncthreads();
             ph = st->phase;
