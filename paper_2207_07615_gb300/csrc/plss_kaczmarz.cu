@@ -243,6 +243,74 @@ __global__ void __launch_bounds__(kKzThreads) k_kacz(KzArgs a) {
     }
 }
 
+// Classical Kaczmarz (window K = 0): a row step is a dot product, one
+// division and a scatter of at most a few dozen entries, so a whole CTA
+// spends its time in barriers. Here one warp walks one system: the row's
+// entries are spread over the lanes, sums are butterfly shuffles (the same
+// fixed order in every lane), and the scatter is made visible to the next
+// row by __syncwarp. Everything of the next row that does not depend on x
+// (its place in the permutation, offsets, b_i and its first 32 indices and
+// values) is loaded while the current row is processed, and the scatter
+// reuses the x values the dot product gathered, so a row costs about one
+// memory round trip (the gather of x).
+template <typename S>
+__global__ void __launch_bounds__(kKzThreads) k_kacz0(KzArgs a, int32_t nsys) {
+    const int lane = threadIdx.x & 31;
+    const int32_t sys = int32_t(blockIdx.x) * kKzWarps + (threadIdx.x >> 5);
+    if (sys >= nsys) return;   // whole warp
+    const SysDesc d = a.desc[sys];
+    const KzSys ks = a.ks[sys];
+    const S *__restrict__ val = static_cast<const S *>(a.val);
+    const int32_t *perm = a.perm + d.row_off;
+    int64_t skipped = ks.skipped;
+    // row t: i, [s0, s1), b_i, and the lane's entry of the first 32
+    const bool any = ks.rows_todo > 0;
+    int32_t i = any ? int32_t(d.row_off) + perm[0] : 0;
+    int32_t s0 = any ? a.row_ptr[i] : 0, s1 = any ? a.row_ptr[i + 1] : 0;
+    double bi = any ? a.b[i] : 0.0;
+    int32_t cq = s0 + lane < s1 ? a.col_idx[s0 + lane] : -1;
+    double vq = cq >= 0 ? double(val[s0 + lane]) : 0.0;
+    for (int64_t t = 0; t < ks.rows_todo; ++t) {
+        const bool more = t + 1 < ks.rows_todo;
+        const int32_t in = more ? int32_t(d.row_off) + perm[t + 1] : i;
+        const double xq = cq >= 0 ? a.x[cq] : 0.0;
+        double ax = fma(vq, xq, 0.0), a2 = fma(vq, vq, 0.0);
+        for (int32_t k = s0 + 32 + lane; k < s1; k += 32) {
+            const double v = double(val[k]);
+            ax = fma(v, a.x[a.col_idx[k]], ax);
+            a2 = fma(v, v, a2);
+        }
+        const int32_t s0n = more ? a.row_ptr[in] : 0, s1n = more ? a.row_ptr[in + 1] : 0;
+        const double bin = more ? a.b[in] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            ax += __shfl_xor_sync(0xffffffffu, ax, o);
+            a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+        }
+        const double ri = bi - ax;
+        const double na = sqrt(a2), nd = sqrt(0.0);
+        const double delta = (na - nd) * (na + nd);
+        if (!(delta > 1e-14 * a2)) {
+            ++skipped;
+        } else {
+            const double gamma = ri / delta;
+            if (cq >= 0) a.x[cq] = __dadd_rn(xq, __dmul_rn(gamma, vq));
+            for (int32_t k = s0 + 32 + lane; k < s1; k += 32) {
+                const int32_t c = a.col_idx[k];
+                a.x[c] = __dadd_rn(a.x[c], __dmul_rn(gamma, double(val[k])));
+            }
+        }
+        __syncwarp();
+        i = in;
+        s0 = s0n;
+        s1 = s1n;
+        bi = bin;
+        cq = more && s0 + lane < s1 ? a.col_idx[s0 + lane] : -1;
+        vq = cq >= 0 ? double(val[s0 + lane]) : 0.0;
+    }
+    if (lane == 0) a.ks[sys].skipped = skipped;
+}
+
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
@@ -426,8 +494,15 @@ plss_status run_identity_multi(plss_ctx *c, const double *const *b, const double
         if (cudaMemcpyAsync(kz->d_perm, kz->h_perm, 4 * size_t(c->m), cudaMemcpyHostToDevice, s) != cudaSuccess ||
             cudaMemcpyAsync(kz->d_sys, kz->h_sys, sizeof(KzSys) * size_t(n), cudaMemcpyHostToDevice, s) != cudaSuccess)
             return fail(PLSS_ERR_CUDA, "upload of the row order failed");
-        if (c->f32) k_kacz<float><<<n, kKzThreads, 0, s>>>(ka);
-        else k_kacz<double><<<n, kKzThreads, 0, s>>>(ka);
+        if (K == 0) {
+            const int grid = (n + kKzWarps - 1) / kKzWarps;
+            if (c->f32) k_kacz0<float><<<grid, kKzThreads, 0, s>>>(ka, n);
+            else k_kacz0<double><<<grid, kKzThreads, 0, s>>>(ka, n);
+        } else if (c->f32) {
+            k_kacz<float><<<n, kKzThreads, 0, s>>>(ka);
+        } else {
+            k_kacz<double><<<n, kKzThreads, 0, s>>>(ka);
+        }
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return fail(PLSS_ERR_CUDA, "kaczmarz kernel: %s", cudaGetErrorString(e));
         if (cudaMemcpyAsync(kz->h_sys, kz->d_sys, sizeof(KzSys) * size_t(n), cudaMemcpyDeviceToHost, s) != cudaSuccess)
