@@ -345,10 +345,16 @@ __global__ void __launch_bounds__(kThreads, 3) k_rhs_row(RhsArgs a) {
     // r = r - A p for the columns in PH_RUN: V matrix rows per warp
     for (int32_t ti = blockIdx.x; any_run && ti < a.n_rtiles; ti += gridDim.x) {
         const Tile t = a.rtiles[ti];
+        // the row offsets of the next step are loaded one step ahead
+        int32_t sn = t.begin + warp * V + sub < t.end ? a.row_ptr[t.begin + warp * V + sub] : 0;
+        int32_t en = t.begin + warp * V + sub < t.end ? a.row_ptr[t.begin + warp * V + sub + 1] : 0;
         for (int32_t r0 = t.begin + warp * V; r0 < t.end; r0 += kWarps * V) {
             const int32_t row = r0 + sub;
             const bool valid = row < t.end;
-            const int32_t s = valid ? a.row_ptr[row] : 0, len = valid ? a.row_ptr[row + 1] - s : 0;
+            const int32_t s = sn, len = en - sn;
+            const int32_t rn = row + kWarps * V;
+            sn = rn < t.end ? a.row_ptr[rn] : 0;
+            en = rn < t.end ? a.row_ptr[rn + 1] : 0;
             const int32_t len_max = __reduce_max_sync(0xffffffffu, len);
             const int64_t ix = int64_t(row) * kRhsStride + ll * V;
             S old[V], d[V];
@@ -443,10 +449,16 @@ __global__ void __launch_bounds__(kThreads) k_rhs_col(RhsArgs a) {
     RhsAcc<S> accs[V];
     for (int32_t ti = blockIdx.x; any_act && ti < a.n_ctiles; ti += gridDim.x) {
         const Tile t = a.ctiles[ti];
+        // the column offsets of the next step are loaded one step ahead
+        int32_t sn = t.begin + warp * V + sub < t.end ? a.col_ptr[t.begin + warp * V + sub] : 0;
+        int32_t en = t.begin + warp * V + sub < t.end ? a.col_ptr[t.begin + warp * V + sub + 1] : 0;
         for (int32_t c0 = t.begin + warp * V; c0 < t.end; c0 += kWarps * V) {
             const int32_t col = c0 + sub;
             const bool valid = col < t.end;
-            const int32_t s = valid ? a.col_ptr[col] : 0, len = valid ? a.col_ptr[col + 1] - s : 0;
+            const int32_t s = sn, len = en - sn;
+            const int32_t cn = col + kWarps * V;
+            sn = cn < t.end ? a.col_ptr[cn] : 0;
+            en = cn < t.end ? a.col_ptr[cn + 1] : 0;
             const int32_t len_max = __reduce_max_sync(0xffffffffu, len);
             S y[V];
             rhs_vdot<S>(a.row_idx, val, s, len, len_max, R, ll * V, valid && on_any, y);
@@ -735,10 +747,26 @@ static RhsArgs rhs_args(plss_ctx *c, int32_t k, bool w_on) {
     return a;
 }
 
+// Resident CTAs per SM of a kernel (at most kCtasPerSm: the partials hold
+// one entry per CTA of nsm * kCtasPerSm).
+template <typename K>
+static int rhs_occupancy(K kernel) {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, kThreads, 0) != cudaSuccess || n < 1) {
+        cudaGetLastError();
+        return 1;
+    }
+    return std::min(n, kCtasPerSm);
+}
+
 static cudaError_t rhs_body(plss_ctx *c, const RhsArgs &a, cudaStream_t s) {
-    const int gr = std::max(1, std::min(a.n_rtiles, c->nsm * kCtasPerSm));
-    const int gc = std::max(1, std::min(a.n_ctiles, c->nsm * kCtasPerSm));
-    const int gv = std::max(1, std::min(a.n_vtiles, c->nsm * kCtasPerSm));
+    // grids of one wave: every CTA resident at once
+    const int orow = c->f32 ? rhs_occupancy(k_rhs_row<float>) : rhs_occupancy(k_rhs_row<double>);
+    const int ocol = c->f32 ? rhs_occupancy(k_rhs_col<float>) : rhs_occupancy(k_rhs_col<double>);
+    const int oupd = c->f32 ? rhs_occupancy(k_rhs_update<float>) : rhs_occupancy(k_rhs_update<double>);
+    const int gr = std::max(1, std::min(a.n_rtiles, c->nsm * orow));
+    const int gc = std::max(1, std::min(a.n_ctiles, c->nsm * ocol));
+    const int gv = std::max(1, std::min(a.n_vtiles, c->nsm * oupd));
     cudaError_t e;
     if (c->f32) {
         if ((e = launch_pdl(k_rhs_col<float>, gc, s, a)) != cudaSuccess) return e;
