@@ -91,6 +91,7 @@ struct HostCsr {
 
 // Host copy of a sliced side (layout in plss_dev.cuh).
 struct HostSliced {
+    int32_t g = 1;   // lanes per segment
     std::vector<int32_t> first, ptr, seg, idx;
     std::vector<double> v64;
     std::vector<float> v32;
@@ -114,9 +115,10 @@ plss_status true_relres(plss_ctx *c, cudaStream_t s, std::vector<double> &rel);
 void build_tiles(const int32_t *ptr, int64_t begin, int64_t end, int32_t sys, int64_t target,
                  int64_t max_segs, bool f32, std::vector<Tile> &out);
 void build_side(const int32_t *ptr, int64_t begin, int64_t end, int32_t sys, int64_t nnz, int nsm,
-                bool f32, bool slice, std::vector<Tile> &out);
+                bool f32, bool slice, int32_t g, std::vector<Tile> &out);
 void fill_sliced(const int32_t *ptr, const int32_t *idx, const double *v64, const float *v32,
-                 const std::vector<Tile> &tiles, HostSliced &out);
+                 const std::vector<Tile> &tiles, int32_t g, HostSliced &out);
+int32_t slice_lanes(int64_t nnz, int64_t segs);
 
 // identity sketch (plss_kaczmarz.cu)
 plss_status run_identity(plss_ctx *c, const double *b, const double *x0, double *x_out,

@@ -30,11 +30,14 @@ constexpr int32_t kStaged = 0x200;   // products staged in shared memory (at mos
 constexpr int32_t kGroupMask = 0xff;
 
 // Sliced copy of a side (rows or columns) of A. A sliced tile's segments,
-// sorted by decreasing length (ties by index), form slices of 32 slots;
-// slice s is as wide as its longest segment and stores element k of slot l
-// at ptr[s] + 32 k + l, so a warp reads 32 consecutive indices (values) per
-// load and each lane owns one segment. Padding has index -1 and value 0.
+// sorted by decreasing length (ties by index), form slices of 32 / g
+// segments with g lanes each (slots q g .. q g + g - 1 hold segment q);
+// slice s is as wide as ceil(longest segment / g) and stores the segment's
+// element k in lane q g + (k mod g) at ptr[s] + 32 (k / g) + lane, so a warp
+// reads 32 consecutive indices (values) per load. Padding has index -1 and
+// value 0.
 struct Sliced {
+    int32_t g;              // lanes per segment (power of two, 1..32)
     const int32_t *first;   // [tiles] first slice of each tile
     const int32_t *ptr;     // [slices + 1] element offsets (multiples of 32)
     const int32_t *seg;     // [32 * slices] segment of each slot, -1 if none

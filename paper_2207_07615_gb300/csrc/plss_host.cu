@@ -92,20 +92,31 @@ int64_t tile_target(int64_t nnz, int nsm, bool f32) {
 }
 
 // Order of a tile's segments in its slices (decreasing length, ties by
-// index); returns the padded element count (32 x each slice's width).
-static int64_t slice_order(const int32_t *ptr, const Tile &t, std::vector<int32_t> &order) {
-    const int32_t nseg = t.end - t.begin;
+// index); returns the padded element count (32 x each slice's width) for
+// slices of 32 / g segments with g lanes each.
+static int64_t slice_order(const int32_t *ptr, const Tile &t, std::vector<int32_t> &order, int32_t g) {
+    const int32_t nseg = t.end - t.begin, per = 32 / g;
     order.resize(size_t(nseg));
     for (int32_t i = 0; i < nseg; ++i) order[size_t(i)] = i;
     std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
         return ptr[t.begin + a + 1] - ptr[t.begin + a] > ptr[t.begin + b + 1] - ptr[t.begin + b];
     });
     int64_t padded = 0;
-    for (int32_t s = 0; s < nseg; s += 32) {
-        const int32_t g = t.begin + order[size_t(s)];
-        padded += 32 * int64_t(ptr[g + 1] - ptr[g]);
+    for (int32_t s = 0; s < nseg; s += per) {
+        const int32_t lead = t.begin + order[size_t(s)];
+        padded += 32 * int64_t((ptr[lead + 1] - ptr[lead] + g - 1) / g);
     }
     return padded;
+}
+
+// Lanes per segment of a side's slices: the largest power of two g with
+// 8 g <= mean segment length (at most 32), so that a lane keeps about 8
+// elements and wide sides (C2 columns: 40 per column) give every warp
+// several slices.
+int32_t slice_lanes(int64_t nnz, int64_t segs) {
+    int32_t g = 1;
+    while (g < 32 && 16 * g * segs <= nnz) g <<= 1;
+    return g;
 }
 
 // As build_tiles (FP64 sizes), but a tile ends on a multiple of 32
@@ -147,7 +158,7 @@ static void cut_slice_tiles(const int32_t *ptr, int64_t begin, int64_t end, int3
 // tile of short segments whose slices pad it by at most 1/4 is flagged
 // kSliced, and the others are cut as they would be without slicing.
 void build_side(const int32_t *ptr, int64_t begin, int64_t end, int32_t sys, int64_t nnz, int nsm,
-                bool f32, bool slice, std::vector<Tile> &out) {
+                bool f32, bool slice, int32_t g, std::vector<Tile> &out) {
     const int64_t target = tile_target(nnz, nsm, f32);
     if (!slice || begin == end) {
         build_tiles(ptr, begin, end, sys, target, max_segs(f32), f32, out);
@@ -158,7 +169,7 @@ void build_side(const int32_t *ptr, int64_t begin, int64_t end, int32_t sys, int
     std::vector<int32_t> order;
     for (const Tile &t : big) {
         const int64_t nz = int64_t(ptr[t.end]) - ptr[t.begin];
-        if (t.group != 0 && t.end > t.begin && slice_order(ptr, t, order) * 4 <= nz * 5) {
+        if (t.group != 0 && t.end > t.begin && slice_order(ptr, t, order, g) * 4 <= nz * 5) {
             out.push_back({t.sys, t.begin, t.end, t.group | kSliced});
         } else if (t.group != 0 && t.end > t.begin) {
             // uneven segments: staged tiles (FP64 too), so that a long
@@ -171,33 +182,38 @@ void build_side(const int32_t *ptr, int64_t begin, int64_t end, int32_t sys, int
     }
 }
 
-// The sliced copy of the tiles flagged kSliced (values from v64 or v32).
+// The sliced copy of the tiles flagged kSliced (values from v64 or v32),
+// g lanes per segment: element k of the segment in slot group q of a slice
+// lies in lane q g + (k mod g), row k / g.
 void fill_sliced(const int32_t *ptr, const int32_t *idx, const double *v64, const float *v32,
-                 const std::vector<Tile> &tiles, HostSliced &out) {
+                 const std::vector<Tile> &tiles, int32_t g, HostSliced &out) {
     out = HostSliced();
+    out.g = g;
     out.first.resize(tiles.size());
     out.ptr.push_back(0);
     std::vector<int32_t> order;
+    const int32_t per = 32 / g;
     for (size_t ti = 0; ti < tiles.size(); ++ti) {
         const Tile &t = tiles[ti];
         out.first[ti] = int32_t(out.ptr.size()) - 1;
         if (!(t.group & kSliced)) continue;
-        slice_order(ptr, t, order);
+        slice_order(ptr, t, order, g);
         const int32_t nseg = t.end - t.begin;
-        for (int32_t s = 0; s < nseg; s += 32) {
+        for (int32_t s = 0; s < nseg; s += per) {
             const int32_t lead = t.begin + order[size_t(s)];
-            const int32_t width = ptr[lead + 1] - ptr[lead];
+            const int32_t width = (ptr[lead + 1] - ptr[lead] + g - 1) / g;
             const int32_t base = out.ptr.back();
             out.ptr.push_back(base + 32 * width);
             out.idx.resize(size_t(base) + 32 * size_t(width), -1);
             if (v64) out.v64.resize(out.idx.size(), 0.0);
             else out.v32.resize(out.idx.size(), 0.0f);
             for (int32_t l = 0; l < 32; ++l) {
-                const int32_t seg = s + l < nseg ? t.begin + order[size_t(s + l)] : -1;
+                const int32_t q = l / g, r = l % g;
+                const int32_t seg = s + q < nseg ? t.begin + order[size_t(s + q)] : -1;
                 out.seg.push_back(seg);
                 if (seg < 0) continue;
-                for (int32_t k = 0; k < ptr[seg + 1] - ptr[seg]; ++k) {
-                    const size_t dst = size_t(base) + 32 * size_t(k) + size_t(l);
+                for (int32_t k = r; k < ptr[seg + 1] - ptr[seg]; k += g) {
+                    const size_t dst = size_t(base) + 32 * size_t(k / g) + size_t(l);
                     const size_t src = size_t(ptr[seg]) + size_t(k);
                     out.idx[dst] = idx[src];
                     if (v64) out.v64[dst] = v64[src];
@@ -311,6 +327,7 @@ plss_status upload(T **dst, const std::vector<T> &src, const char *what) {
 // Device copy of a sliced side (all pointers null when no tile is sliced).
 static plss_status upload_sliced(const HostSliced &h, Sliced &d, bool f32) {
     d = Sliced{};
+    d.g = h.g;
     if (h.seg.empty()) return PLSS_OK;
     int32_t *first = nullptr, *ptr = nullptr, *seg = nullptr, *idx = nullptr;
     plss_status st = upload(&first, h.first, "sliced tiles");
@@ -507,13 +524,14 @@ static plss_status ctx_build(const plss_csr *As, int32_t nsys, const plss_opts *
     // sliced copies unless the caller asks for the plain layout (or the
     // padded copy could overflow 32-bit offsets)
     const bool slice = o->layout == PLSS_LAYOUT_AUTO && NNZ < 1800000000;
+    const int32_t g_r = slice_lanes(NNZ, M), g_c = sym ? g_r : slice_lanes(NNZ, N);
     for (int32_t s = 0; s < nsys; ++s) {
         SysDesc &d = c->h_desc[size_t(s)];
         d.rt_begin = int32_t(c->h_rt.size());
-        build_side(rp.data(), d.row_off, d.row_off + d.m, s, NNZ, c->nsm, c->f32, slice, c->h_rt);
+        build_side(rp.data(), d.row_off, d.row_off + d.m, s, NNZ, c->nsm, c->f32, slice, g_r, c->h_rt);
         d.rt_count = int32_t(c->h_rt.size()) - d.rt_begin;
         d.ct_begin = int32_t(c->h_ct.size());
-        build_side(colp, d.col_off, d.col_off + d.n, s, NNZ, c->nsm, c->f32, slice, c->h_ct);
+        build_side(colp, d.col_off, d.col_off + d.n, s, NNZ, c->nsm, c->f32, slice, g_c, c->h_ct);
         d.ct_count = int32_t(c->h_ct.size()) - d.ct_begin;
         d.vt_begin = int32_t(c->h_vt.size());
         build_vec_tiles(d.col_off, d.col_off + d.n, s, kVecTile, c->h_vt);
@@ -554,17 +572,18 @@ static plss_status ctx_build(const plss_csr *As, int32_t nsys, const plss_opts *
         return true;
     };
     auto fill_side = [&](const int32_t *ptr, const int32_t *idx, const double *vd, const float *vf,
-                         const std::vector<Tile> &ts, int64_t nseg, HostSliced &out) {
+                         const std::vector<Tile> &ts, int64_t nseg, int32_t g, HostSliced &out) {
         if (nsys == 1 && all_sliced(ts) && nseg > 0) {
             const std::vector<Tile> whole = {Tile{0, 0, int32_t(nseg), ts[0].group}};
-            fill_sliced(ptr, idx, vd, vf, whole, out);
+            fill_sliced(ptr, idx, vd, vf, whole, g, out);
             out.first.assign(ts.size(), 0);
         } else {
-            fill_sliced(ptr, idx, vd, vf, ts, out);
+            fill_sliced(ptr, idx, vd, vf, ts, g, out);
         }
     };
     HostSliced hsl;
-    fill_side(rp.data(), ci.data(), c->f32 ? nullptr : v64.data(), c->f32 ? v32.data() : nullptr, c->h_rt, M, hsl);
+    fill_side(rp.data(), ci.data(), c->f32 ? nullptr : v64.data(), c->f32 ? v32.data() : nullptr, c->h_rt, M, g_r,
+              hsl);
     TRY_ST(upload_sliced(hsl, c->rsl, c->f32));
     c->sl_elems[0] = int64_t(hsl.idx.size());
     const std::vector<int32_t> rsl_ptr = hsl.ptr;
@@ -575,7 +594,7 @@ static plss_status ctx_build(const plss_csr *As, int32_t nsys, const plss_opts *
         csl_ptr = rsl_ptr;
     } else {
         fill_side(cp.data(), ri.data(), c->f32 ? nullptr : cv64.data(), c->f32 ? cv32.data() : nullptr, c->h_ct, N,
-                  hsl);
+                  g_c, hsl);
         TRY_ST(upload_sliced(hsl, c->csl, c->f32));
         c->sl_elems[1] = int64_t(hsl.idx.size());
         csl_ptr = hsl.ptr;

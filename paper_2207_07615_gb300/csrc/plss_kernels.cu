@@ -306,13 +306,22 @@ __device__ __forceinline__ ACC slice_dot(const int32_t *__restrict__ idx, const 
     return acc;
 }
 
+// Sum over the g lanes of a segment (g a power of two; every lane takes
+// part; the same fixed order in every lane of the group).
+template <typename T>
+__device__ __forceinline__ T group_sum(T v, int g) {
+    for (int o = g >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
 // Calls body(seg, off, width, lane) for each slot of the sliced tile `ti`
 // (one warp per slice; seg < 0 for an empty slot); warp-uniform loop.
 template <typename F>
 __device__ __forceinline__ void for_slices(const Sliced &sl, const Tile &t, int32_t ti, F &&body) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int32_t s0 = __ldg(sl.first + ti);
-    const int32_t ns = (t.end - t.begin + 31) >> 5;
+    const int32_t per = 32 / sl.g;   // segments per slice
+    const int32_t ns = (t.end - t.begin + per - 1) / per;
     for (int32_t s = warp; s < ns; s += kWarps) {
         const int32_t off = __ldg(sl.ptr + s0 + s);
         const int32_t width = (__ldg(sl.ptr + s0 + s + 1) - off) >> 5;
@@ -441,19 +450,21 @@ __device__ __forceinline__ void row_slot(const SweepArgs &a, int32_t row, int32_
                                          int lane, bool init, double &acc_r, double &acc_b) {
     const S *__restrict__ val = static_cast<const S *>(a.rsl.val);
     S *__restrict__ r = static_cast<S *>(a.r);
+    const int g = a.rsl.g;
+    const bool lead = row >= 0 && (lane & (g - 1)) == 0;   // first lane of the row's group
     if (init) {
-        const double bi = row >= 0 ? a.b[row] : 0.0;
-        const double d = slice_dot<S, double, double>(a.rsl.idx, val, off, width, lane, a.x);
-        if (row >= 0) {
+        const double bi = lead ? a.b[row] : 0.0;
+        const double d = group_sum(slice_dot<S, double, double>(a.rsl.idx, val, off, width, lane, a.x), g);
+        if (lead) {
             const S ri = S(bi - d);
             r[row] = ri;
             acc_r = fma(double(ri), double(ri), acc_r);
             acc_b = fma(bi, bi, acc_b);
         }
     } else {
-        const S old = row >= 0 ? r[row] : S(0);   // issued before the dot's loads
-        const S d = slice_dot<S, S, S>(a.rsl.idx, val, off, width, lane, static_cast<const S *>(a.p));
-        if (row >= 0) {
+        const S old = lead ? r[row] : S(0);   // issued before the dot's loads
+        const S d = group_sum(slice_dot<S, S, S>(a.rsl.idx, val, off, width, lane, static_cast<const S *>(a.p)), g);
+        if (lead) {
             const S ri = old - d;
             r[row] = ri;
             acc_r = fma(double(ri), double(ri), acc_r);
@@ -694,9 +705,10 @@ __device__ __forceinline__ void col_tile_cta(const SweepArgs &a, const Tile &t, 
 template <typename S>
 __device__ __forceinline__ void col_slot(const SweepArgs &a, int32_t col, int32_t off, int32_t width,
                                          int lane, double &acc) {
-    const S y = slice_dot<S, S, S>(a.csl.idx, static_cast<const S *>(a.csl.val), off, width, lane,
-                                   static_cast<const S *>(a.r));
-    if (col >= 0) {
+    const int g = a.csl.g;
+    const S y = group_sum(slice_dot<S, S, S>(a.csl.idx, static_cast<const S *>(a.csl.val), off, width, lane,
+                                             static_cast<const S *>(a.r)), g);
+    if (col >= 0 && (lane & (g - 1)) == 0) {
         if constexpr (std::is_same<S, float>::value) {
             const float uj = a.wf ? __fmul_rn(a.wf[col], y) : y;
             static_cast<float *>(a.u)[col] = uj;

@@ -342,6 +342,7 @@ static bool srv_rebuild(plss_server *s) {
 static SweepArgs srv_args(plss_server *s) {
     SweepArgs a;
     std::memset(&a, 0, sizeof a);
+    a.rsl.g = a.csl.g = 1;   // no sliced tiles in the arena
     a.row_ptr = s->d_row_ptr;
     a.col_idx = s->d_col_idx;
     a.val = s->d_val;
