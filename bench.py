@@ -107,10 +107,21 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
+def kernels_hash(path):
+    """sha256[:16] of the kernel source with comments and blank lines removed
+    (a comment edit does not invalidate recorded counters)."""
+    import hashlib
+    import re
+    text = open(path, encoding="utf-8").read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    lines = [re.sub(r"//.*$", "", ln).rstrip() for ln in text.splitlines()]
+    code = "\n".join(ln for ln in lines if ln.strip())
+    return hashlib.sha256(code.encode()).hexdigest()[:16]
+
+
 def ncu_traffic(kernel):
     """Per-launch DRAM bytes of `kernel` from the committed ncu summary, or
     None when absent or taken on a different version of the kernel source."""
-    import hashlib
     path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
     src = os.path.join(ROOT, "paper_2207_07615_gb300", "csrc", "plss_kernels.cu")
     try:
@@ -120,7 +131,7 @@ def ncu_traffic(kernel):
                 if ":" in line and not line.startswith("#"):
                     k, v = line.split(":", 1)
                     kv[k.strip()] = v.strip()
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        sha = kernels_hash(src)
         if kv.get("kernels_sha256_16") != sha:
             return None
         return float(kv[f"{kernel}_dram_bytes_per_launch"])

@@ -14,23 +14,26 @@
 //                 (re)start); the last tile then applies the stopping rule
 //                 sqrt(rho)/||b|| <= tol (Sec. 5) and the maxit cap.
 //
-// The sweeps move ~12-16 bytes per nonzero and, on GB300, also meet the
-// FP64 pipe, which runs at a small fraction of the FP32 rate: a sweep that
-// spends more than about one FP64 operation per nonzero is bound by it
-// rather than by HBM. So the kernels are plain CUDA-core code that
-//   * cut the work into tiles of whole rows (columns) of a few thousand
-//     nonzeros; a group of G lanes works on one segment, G chosen per tile
-//     so that each lane accumulates about 8 nonzeros (one FMA per nonzero,
-//     plus log2(G) shuffle levels per segment);
-//   * issue each lane's 8 index/value loads, then their 8 gathers, before
-//     the first FMA, so every lane keeps 16-24 loads in flight;
-//   * keep per-tile FP64 partial sums of rho / phi / theta in global memory,
-//     reduced with a thread-stride fold in one warp rather than full-warp
-//     shuffle trees;
-//   * give each CTA a contiguous range of tiles, announced with one atomic
-//     per system it touched; the CTA that completes a system sums that
-//     system's partials in tile order (deterministic for a given schedule)
-//     and takes its scalar step.
+// The update leaves its theta partials to the row sweep that follows: that
+// sweep's finishing CTA sums them, records the update and then applies the
+// stopping rule.
+//
+// Every nonzero of a sweep is one random gather of the dense operand, and
+// on GB300 those gathers (about 250 G sectors/s) rather than HBM bytes set
+// the time; the FP64 pipe runs at a small fraction of the FP32 rate, so FP64
+// sweeps spend one FMA per nonzero and FP32 sweeps none. The kernels are
+// plain CUDA-core code:
+//   * sliced tiles (tiles of short segments, stored 32 slots wide, g lanes
+//     per segment): the warp loads 32 consecutive indices and values per
+//     step, 8 steps before their 8 gathers; a single system whose side is
+//     sliced throughout runs that side over balanced warp ranges of slices
+//     (k_row_sweep_w, k_col_sweep_w) with one partial per CTA;
+//   * staged tiles (FP32, and FP64 tiles of uneven segments): products
+//     staged in shared memory, summed there by G lanes per segment;
+//   * CSR/CSC tiles (G lanes per segment, long segments one CTA each);
+//   * per-tile (or per-CTA) FP64 partial sums of rho / phi / theta, summed in
+//     a fixed order by the CTA that completes a system (deterministic for a
+//     given schedule), which then takes the scalar step.
 #include <cuda_runtime.h>
 
 #include <type_traits>
