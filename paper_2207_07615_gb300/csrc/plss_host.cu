@@ -353,21 +353,25 @@ static plss_status upload_sliced(const HostSliced &h, Sliced &d, bool f32) {
 }
 
 // Splits the slices (element offsets sptr) into nwarps contiguous ranges of
-// about equal elements and uploads the nwarps + 1 boundaries; *out stays
-// null unless every tile is sliced.
+// about equal cost and uploads the nwarps + 1 boundaries; *out stays null
+// unless every tile is sliced.
 static plss_status upload_warp_ranges(const std::vector<Tile> &tiles, const std::vector<int32_t> &sptr,
                                       int64_t nwarps, int32_t **out) {
     *out = nullptr;
     if (tiles.empty() || sptr.size() < 2) return PLSS_OK;
     for (const Tile &t : tiles)
         if (!(t.group & kSliced)) return PLSS_OK;
+    // cost of a slice: its elements plus a fixed part (offsets, slot map,
+    // results) worth kSliceFixed elements, so that runs of empty slices
+    // (empty rows or columns, sorted last) are spread over the warps too
+    constexpr int64_t kSliceFixed = 256;
     const int64_t ns = int64_t(sptr.size()) - 1;
-    const int64_t total = sptr.back();
+    const int64_t total = sptr.back() + kSliceFixed * ns;
     std::vector<int32_t> wr(size_t(nwarps + 1));
     int64_t s = 0;
     for (int64_t w = 0; w < nwarps; ++w) {
-        const int64_t goal = total * w / nwarps;   // elements before warp w's first slice
-        while (s < ns && sptr[size_t(s)] < goal) ++s;
+        const int64_t goal = total * w / nwarps;   // cost before warp w's first slice
+        while (s < ns && sptr[size_t(s)] + kSliceFixed * s < goal) ++s;
         wr[size_t(w)] = int32_t(s);
     }
     wr[size_t(nwarps)] = int32_t(ns);

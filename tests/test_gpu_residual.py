@@ -264,3 +264,28 @@ def test_batched_matches_single(plss, schedule):
         assert r["status"] == "converged" and r["relres_true"] <= 1e-6
         iters.add(r["iters"])
     assert len(iters) > 1     # systems stopped independently
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_symmetric_reuses_the_csr(plss, precision):
+    """A symmetric matrix declared symmetric (A^T r reads the CSR and its
+    sliced copy; no transpose stored) gives bit for bit the iterates of the
+    same matrix with its transpose stored (the transpose is the same array),
+    and those follow the oracle."""
+    A = synth.laplacian7(N=18, dtype=np.float64)
+    xs = synth.rng_for(31).standard_normal(A.n)
+    b = synth.rhs(A, xs)
+    K = 30
+    Ap = A if precision == "fp64" else A.astype(np.float32)
+    with plss.Context(Ap, precision=precision, symmetric=True) as cs, \
+            plss.Context(Ap, precision=precision) as cg:
+        assert cs.layout()["row_sliced"] > 0
+        xa, ra = cs.solve(b, tol=0.0, maxit=K)
+        xb, rb = cg.solve(b, tol=0.0, maxit=K)
+        np.testing.assert_array_equal(xa, xb)
+        if precision == "fp64":
+            ref = _parity.reference(A, b, K)
+            _parity.check_x(xa, ref, K)
+        xa, ra = cs.solve(b, tol=1e-8, maxit=20000, stop_on_true=1)
+    assert ra["status"] == "converged" and ra["relres_true"] <= 1e-8
+    assert rel(xa, xs) < 1e-5      # nonsingular: the solution is x*
