@@ -9,12 +9,10 @@
 
 #include "plss.h"
 #include "plss_dev.cuh"
+#include "plss_plan.h"
 
 namespace plss {
 
-constexpr int64_t kTileMaxSegs = 2048;  // max rows/columns per FP64 sweep tile
-constexpr int64_t kTileMaxSegsF32 = 1024;   // ... per FP32 tile (shared-memory staging)
-inline int64_t max_segs(bool f32) { return f32 ? kTileMaxSegsF32 : kTileMaxSegs; }
 constexpr int64_t kVecTile = 1024;      // entries per update tile
 constexpr int kCtasPerSm = 8;           // resident CTAs per SM assumed for grids
 constexpr int kMaxChunk = 64;           // bodies per graph launch (max)
@@ -89,18 +87,8 @@ struct HostCsr {
     std::vector<double> val;
 };
 
-// Host copy of a sliced side (layout in plss_dev.cuh).
-struct HostSliced {
-    int32_t g = 1;   // lanes per segment
-    std::vector<int32_t> first, ptr, seg, idx;
-    std::vector<double> v64;
-    std::vector<float> v32;
-};
-
 // Copies and validates a caller's CSR (host or device arrays).
 plss_status fetch_csr(const plss_csr *A, HostCsr &h);
-void build_vec_tiles(int64_t begin, int64_t end, int32_t sys, int64_t chunk, std::vector<Tile> &out);
-int64_t tile_target(int64_t nnz, int nsm, bool f32);
 
 plss_status fail(plss_status s, const char *fmt, ...);
 void clear_error();
@@ -112,13 +100,8 @@ plss_status get_vec(double *dst, const double *src, int64_t len, bool dev, cudaS
 plss_status check_opts(const plss_opts *o);
 plss_status ensure_weights(plss_ctx *c, int32_t w_mode, cudaStream_t s);
 plss_status true_relres(plss_ctx *c, cudaStream_t s, std::vector<double> &rel);
-void build_tiles(const int32_t *ptr, int64_t begin, int64_t end, int32_t sys, int64_t target,
-                 int64_t max_segs, bool f32, std::vector<Tile> &out);
-void build_side(const int32_t *ptr, int64_t begin, int64_t end, int32_t sys, int64_t nnz, int nsm,
-                bool f32, bool slice, int32_t g, std::vector<Tile> &out);
-void fill_sliced(const int32_t *ptr, const int32_t *idx, const double *v64, const float *v32,
-                 const std::vector<Tile> &tiles, int32_t g, HostSliced &out);
-int32_t slice_lanes(int64_t nnz, int64_t segs);
+// Resident CTA slots of the sweeps on this device (plan sizes).
+PlanSlots plan_slots(int nsm);
 
 // identity sketch (plss_kaczmarz.cu)
 plss_status run_identity(plss_ctx *c, const double *b, const double *x0, double *x_out,

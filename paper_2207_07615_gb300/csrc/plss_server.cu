@@ -182,7 +182,8 @@ static void srv_prepare(plss_server *s, HostCsr &h, SrvRequest *r) {
     }
     // the schedule a single-system context of this request would use, so
     // that its arithmetic is the same alone and in the mix
-    const int64_t target = tile_target(h.nnz, s->nsm, s->f32);
+    const PlanSlots slots = plan_slots(s->nsm);
+    const int64_t target = tile_target(h.nnz, s->f32 ? slots.f32 : slots.f64, s->f32);
     build_tiles(r->rp.data(), 0, h.m, 0, target, max_segs(s->f32), s->f32, r->rt);
     build_tiles(r->cp.data(), 0, h.n, 0, target, max_segs(s->f32), s->f32, r->ct);
     build_vec_tiles(0, h.n, 0, kVecTile, r->vt);
