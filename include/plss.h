@@ -59,13 +59,14 @@ enum { PLSS_FP64 = 0, PLSS_FP32 = 1 };
  * (an empty column gets weight 1). */
 enum { PLSS_W_IDENTITY = 0, PLSS_W_COLNORM = 1, PLSS_W_COLNORM2 = 2 };
 
-/* Storage of the sweeps (plss_create). AUTO: tiles of short rows (columns)
- * whose padding stays within 1/4 are also stored sliced -- 32 segments side
- * by side, so that a warp reads 32 consecutive indices and values per load
- * and each lane sums one row (column) -- at the cost of a second copy of
- * those nonzeros; other tiles use the CSR (CSC). CSR: the CSR and CSC only
- * (the layout of the serving arena; plss_submit results equal those of a
- * context created with it). */
+/* Storage of the sweeps (plss_create, plss_server_create). AUTO: tiles of
+ * short rows (columns) whose padding stays within 1/4 are also stored
+ * sliced -- 32 lanes side by side, so that a warp reads 32 consecutive
+ * indices and values per load and g lanes sum one row (column) -- at the
+ * cost of a second copy of those nonzeros; other tiles use the CSR (CSC).
+ * CSR: the CSR and CSC only. A server with the CSR layout gives each request
+ * the results of a context created with it (GRID schedule); with AUTO, the
+ * results of the same request served alone. */
 enum { PLSS_LAYOUT_AUTO = 0, PLSS_LAYOUT_CSR = 1 };
 
 /* Schedule of a residual-sketch solve. AUTO and GRID: every sweep is a
@@ -257,6 +258,9 @@ typedef struct {
                               /* 4 GiB, capped at 80% of free memory             */
     int32_t precision;        /* PLSS_FP64 / PLSS_FP32 for every request         */
     int32_t bodies_per_poll;  /* iterations run between admission rounds (8)     */
+    int32_t layout;           /* PLSS_LAYOUT_AUTO (sliced tiles where they pay,   */
+                              /* one lane per segment) or PLSS_LAYOUT_CSR        */
+    int32_t reserved;
 } plss_server_opts;
 
 void plss_server_opts_default(plss_server_opts *o);

@@ -87,6 +87,8 @@ struct SrvRequest {
     std::vector<double> v64, cv64;
     std::vector<float> v32, cv32;
     std::vector<Tile> rt, ct, vt;   // local segment indices, sys = 0
+    HostSliced hr, hc;              // sliced copies of the rows / columns (local indices)
+    int64_t nsl = 0, nel = 0;       // slice slots and elements they take in the arena
     std::vector<double> b, x0;
     double tol = 1e-8;
     int64_t maxit = -1;
@@ -94,7 +96,7 @@ struct SrvRequest {
     std::chrono::steady_clock::time_point t_submit;
     // placement
     int32_t slot = -1;
-    int64_t roff = 0, coff = 0, zoff = 0;
+    int64_t roff = 0, coff = 0, zoff = 0, sloff = 0, eloff = 0;
     int32_t rt_begin = 0, ct_begin = 0, vt_begin = 0;
     // outcome
     std::vector<double> x;
@@ -110,6 +112,12 @@ struct plss_server {
     int64_t Mcap = 0, Ncap = 0, Zcap = 0, Tr = 0, Tc = 0, Tv = 0;
     int32_t Scap = 0;
     plss::RangeAlloc rows, cols, nnzs;
+    bool sliced = false;                 // PLSS_LAYOUT_AUTO: sliced copies in the arena
+    int64_t SLcap = 0, ELcap = 0;        // slice slots, sliced elements
+    plss::RangeAlloc slcs, els;
+    int32_t *d_sl_ptr = nullptr, *d_sl_seg = nullptr, *d_sl_idx = nullptr, *d_rfirst = nullptr,
+            *d_cfirst = nullptr;
+    void *d_sl_val = nullptr;
     int64_t tiles_r = 0, tiles_c = 0, tiles_v = 0;   // tiles of resident systems
     int32_t *d_row_ptr = nullptr, *d_col_idx = nullptr, *d_col_ptr = nullptr, *d_row_idx = nullptr;
     void *d_val = nullptr, *d_cval = nullptr, *d_r = nullptr, *d_p = nullptr, *d_u = nullptr;
@@ -146,7 +154,8 @@ static void srv_free_device(plss_server *s) {
     void *ptrs[] = {s->d_row_ptr, s->d_col_idx, s->d_col_ptr, s->d_row_idx, s->d_val, s->d_cval,
                     s->d_r, s->d_p, s->d_u, s->d_b, s->d_x, s->d_w, s->d_wf, s->d_vout, s->d_part_row,
                     s->d_part_col, s->d_part_upd, s->d_part_res, s->d_rt, s->d_ct, s->d_vt,
-                    s->d_desc, s->d_st, s->d_active};
+                    s->d_desc, s->d_st, s->d_active, s->d_sl_ptr, s->d_sl_seg, s->d_sl_idx,
+                    s->d_sl_val, s->d_rfirst, s->d_cfirst};
     for (void *p : ptrs) dfree(p);
     if (s->h_st) cudaFreeHost(s->h_st);
     if (s->stream) cudaStreamDestroy(s->stream);
@@ -180,12 +189,25 @@ static void srv_prepare(plss_server *s, HostCsr &h, SrvRequest *r) {
         r->v64 = std::move(h.val);
         r->cv64 = std::move(cv);
     }
-    // the schedule a single-system context of this request would use, so
-    // that its arithmetic is the same alone and in the mix
+    // the request's own schedule (it does not depend on its neighbours, so
+    // its arithmetic is the same alone and in the mix): as a single-system
+    // context would cut it (CSR layout), or with sliced tiles, one lane per
+    // segment (AUTO)
     const PlanSlots slots = plan_slots(s->nsm);
-    const int64_t target = tile_target(h.nnz, s->f32 ? slots.f32 : slots.f64, s->f32);
-    build_tiles(r->rp.data(), 0, h.m, 0, target, max_segs(s->f32), s->f32, r->rt);
-    build_tiles(r->cp.data(), 0, h.n, 0, target, max_segs(s->f32), s->f32, r->ct);
+    if (s->sliced) {
+        build_side(r->rp.data(), 0, h.m, 0, h.nnz, slots, s->f32, true, 1, r->rt);
+        build_side(r->cp.data(), 0, h.n, 0, h.nnz, slots, s->f32, true, 1, r->ct);
+        const double *v = s->f32 ? nullptr : r->v64.data(), *cvv = s->f32 ? nullptr : r->cv64.data();
+        const float *vf = s->f32 ? r->v32.data() : nullptr, *cvf = s->f32 ? r->cv32.data() : nullptr;
+        fill_sliced(r->rp.data(), r->ci.data(), v, vf, r->rt, 1, r->hr);
+        fill_sliced(r->cp.data(), r->ri.data(), cvv, cvf, r->ct, 1, r->hc);
+        r->nsl = int64_t(r->hr.ptr.size() + r->hc.ptr.size());
+        r->nel = int64_t(r->hr.idx.size() + r->hc.idx.size());
+    } else {
+        const int64_t target = tile_target(h.nnz, s->f32 ? slots.f32 : slots.f64, s->f32);
+        build_tiles(r->rp.data(), 0, h.m, 0, target, max_segs(s->f32), s->f32, r->rt);
+        build_tiles(r->cp.data(), 0, h.n, 0, target, max_segs(s->f32), s->f32, r->ct);
+    }
     build_vec_tiles(0, h.n, 0, kVecTile, r->vt);
 }
 
@@ -212,6 +234,22 @@ static bool srv_place(plss_server *s, SrvRequest *r) {
         s->cols.release(co, r->n + 1);
         return false;
     }
+    int64_t so = 0, eo = 0;
+    if (r->nsl > 0 && !s->slcs.alloc(r->nsl, so)) {
+        s->rows.release(ro, r->m + 1);
+        s->cols.release(co, r->n + 1);
+        s->nnzs.release(zo, r->nnz);
+        return false;
+    }
+    if (r->nel > 0 && !s->els.alloc(r->nel, eo)) {
+        s->rows.release(ro, r->m + 1);
+        s->cols.release(co, r->n + 1);
+        s->nnzs.release(zo, r->nnz);
+        if (r->nsl > 0) s->slcs.release(so, r->nsl);
+        return false;
+    }
+    r->sloff = so;
+    r->eloff = eo;
     r->slot = slot;
     r->roff = ro;
     r->coff = co;
@@ -227,6 +265,8 @@ static void srv_unplace(plss_server *s, SrvRequest *r) {
     s->rows.release(r->roff, r->m + 1);
     s->cols.release(r->coff, r->n + 1);
     s->nnzs.release(r->zoff, r->nnz);
+    if (r->nsl > 0) s->slcs.release(r->sloff, r->nsl);
+    if (r->nel > 0) s->els.release(r->eloff, r->nel);
     s->tiles_r -= int64_t(r->rt.size());
     s->tiles_c -= int64_t(r->ct.size());
     s->tiles_v -= int64_t(r->vt.size());
@@ -263,6 +303,32 @@ static bool srv_upload(plss_server *s, SrvRequest *r) {
                                 cudaMemcpyHostToDevice, st));
         SRV_TRY(cudaMemcpyAsync(static_cast<char *>(s->d_cval) + sb * size_t(r->zoff), cv, sb * size_t(r->nnz),
                                 cudaMemcpyHostToDevice, st));
+    }
+    if (r->nsl > 0) {
+        // the sliced copies with arena offsets: element offsets, segment ids
+        // and indices become global; rows' slices first, then columns'
+        const HostSliced *side[2] = {&r->hr, &r->hc};
+        const int64_t seg_off[2] = {r->roff, r->coff}, idx_off[2] = {r->coff, r->roff};
+        int64_t so = r->sloff, eo = r->eloff;
+        for (int q = 0; q < 2; ++q) {
+            const HostSliced &h = *side[q];
+            std::vector<int32_t> ptr(h.ptr.size()), seg(h.seg.size()), idx(h.idx.size());
+            for (size_t i = 0; i < ptr.size(); ++i) ptr[i] = int32_t(eo + h.ptr[i]);
+            for (size_t i = 0; i < seg.size(); ++i) seg[i] = h.seg[i] < 0 ? -1 : int32_t(seg_off[q] + h.seg[i]);
+            for (size_t i = 0; i < idx.size(); ++i) idx[i] = h.idx[i] < 0 ? -1 : int32_t(idx_off[q] + h.idx[i]);
+            SRV_TRY(cudaMemcpyAsync(s->d_sl_ptr + so, ptr.data(), 4 * ptr.size(), cudaMemcpyHostToDevice, st));
+            if (!seg.empty())
+                SRV_TRY(cudaMemcpyAsync(s->d_sl_seg + 32 * so, seg.data(), 4 * seg.size(), cudaMemcpyHostToDevice, st));
+            if (!idx.empty()) {
+                SRV_TRY(cudaMemcpyAsync(s->d_sl_idx + eo, idx.data(), 4 * idx.size(), cudaMemcpyHostToDevice, st));
+                const void *v = s->f32 ? static_cast<const void *>(h.v32.data()) : static_cast<const void *>(h.v64.data());
+                SRV_TRY(cudaMemcpyAsync(static_cast<char *>(s->d_sl_val) + sb * size_t(eo), v, sb * idx.size(),
+                                        cudaMemcpyHostToDevice, st));
+            }
+            SRV_TRY(cudaStreamSynchronize(st));   // the host staging vectors go out of scope
+            so += int64_t(h.ptr.size());
+            eo += int64_t(h.idx.size());
+        }
     }
     if (r->m > 0) SRV_TRY(cudaMemcpyAsync(s->d_b + r->roff, r->b.data(), 8 * size_t(r->m), cudaMemcpyHostToDevice, st));
     if (r->n > 0) {
@@ -304,6 +370,7 @@ static bool srv_upload(plss_server *s, SrvRequest *r) {
 // with the per-slot descriptors.
 static bool srv_rebuild(plss_server *s) {
     std::vector<Tile> rt, ct, vt;
+    std::vector<int32_t> rfirst, cfirst;   // global first slice of each sliced tile
     for (int32_t i = 0; i < s->Scap; ++i) {
         SrvRequest *r = s->slot_req[size_t(i)];
         SysDesc &d = s->h_desc[size_t(i)];
@@ -314,10 +381,19 @@ static bool srv_rebuild(plss_server *s) {
         d.m = int32_t(r->m);
         d.n = int32_t(r->n);
         d.rt_begin = int32_t(rt.size());
-        for (Tile t : r->rt) rt.push_back({i, t.begin + int32_t(r->roff), t.end + int32_t(r->roff), t.group});
+        for (size_t k = 0; k < r->rt.size(); ++k) {
+            const Tile t = r->rt[k];
+            rt.push_back({i, t.begin + int32_t(r->roff), t.end + int32_t(r->roff), t.group});
+            rfirst.push_back(r->hr.first.empty() ? 0 : int32_t(r->sloff) + r->hr.first[k]);
+        }
         d.rt_count = int32_t(rt.size()) - d.rt_begin;
         d.ct_begin = int32_t(ct.size());
-        for (Tile t : r->ct) ct.push_back({i, t.begin + int32_t(r->coff), t.end + int32_t(r->coff), t.group});
+        for (size_t k = 0; k < r->ct.size(); ++k) {
+            const Tile t = r->ct[k];
+            ct.push_back({i, t.begin + int32_t(r->coff), t.end + int32_t(r->coff), t.group});
+            cfirst.push_back(r->hc.first.empty() ? 0
+                                                 : int32_t(r->sloff + int64_t(r->hr.ptr.size())) + r->hc.first[k]);
+        }
         d.ct_count = int32_t(ct.size()) - d.ct_begin;
         d.vt_begin = int32_t(vt.size());
         for (Tile t : r->vt) vt.push_back({i, t.begin + int32_t(r->coff), t.end + int32_t(r->coff), t.group});
@@ -328,6 +404,10 @@ static bool srv_rebuild(plss_server *s) {
     if (!rt.empty()) SRV_TRY(cudaMemcpyAsync(s->d_rt, rt.data(), sizeof(Tile) * rt.size(), cudaMemcpyHostToDevice, st));
     if (!ct.empty()) SRV_TRY(cudaMemcpyAsync(s->d_ct, ct.data(), sizeof(Tile) * ct.size(), cudaMemcpyHostToDevice, st));
     if (!vt.empty()) SRV_TRY(cudaMemcpyAsync(s->d_vt, vt.data(), sizeof(Tile) * vt.size(), cudaMemcpyHostToDevice, st));
+    if (s->sliced && !rfirst.empty())
+        SRV_TRY(cudaMemcpyAsync(s->d_rfirst, rfirst.data(), 4 * rfirst.size(), cudaMemcpyHostToDevice, st));
+    if (s->sliced && !cfirst.empty())
+        SRV_TRY(cudaMemcpyAsync(s->d_cfirst, cfirst.data(), 4 * cfirst.size(), cudaMemcpyHostToDevice, st));
     SRV_TRY(cudaMemcpyAsync(s->d_desc, s->h_desc.data(), sizeof(SysDesc) * size_t(s->Scap), cudaMemcpyHostToDevice, st));
     int32_t nact = 0;
     for (int32_t i = 0; i < s->Scap; ++i)
@@ -343,7 +423,15 @@ static bool srv_rebuild(plss_server *s) {
 static SweepArgs srv_args(plss_server *s) {
     SweepArgs a;
     std::memset(&a, 0, sizeof a);
-    a.rsl.g = a.csl.g = 1;   // no sliced tiles in the arena
+    a.rsl.g = a.csl.g = 1;   // one lane per segment in the arena's slices
+    if (s->sliced) {
+        a.rsl.first = s->d_rfirst;
+        a.csl.first = s->d_cfirst;
+        a.rsl.ptr = a.csl.ptr = s->d_sl_ptr;
+        a.rsl.seg = a.csl.seg = s->d_sl_seg;
+        a.rsl.idx = a.csl.idx = s->d_sl_idx;
+        a.rsl.val = a.csl.val = s->d_sl_val;
+    }
     a.row_ptr = s->d_row_ptr;
     a.col_idx = s->d_col_idx;
     a.val = s->d_val;
@@ -492,6 +580,8 @@ void plss_server_opts_default(plss_server_opts *o) {
     o->hbm_budget_bytes = 0;
     o->precision = PLSS_FP64;
     o->bodies_per_poll = 8;
+    o->layout = PLSS_LAYOUT_AUTO;
+    o->reserved = 0;
 }
 
 plss_status plss_server_create(const plss_server_opts *so_in, plss_server **out) {
@@ -504,9 +594,11 @@ plss_status plss_server_create(const plss_server_opts *so_in, plss_server **out)
     if (so.max_slots < 1 || so.max_queue < 1 || so.bodies_per_poll < 1)
         return fail(PLSS_ERR_INVALID, "max_slots, max_queue and bodies_per_poll must be positive");
     if (so.precision != PLSS_FP64 && so.precision != PLSS_FP32) return fail(PLSS_ERR_INVALID, "unknown precision");
+    if (so.layout != PLSS_LAYOUT_AUTO && so.layout != PLSS_LAYOUT_CSR) return fail(PLSS_ERR_INVALID, "unknown layout");
     plss_server *s = new plss_server();
     s->so = so;
     s->f32 = so.precision == PLSS_FP32;
+    s->sliced = so.layout == PLSS_LAYOUT_AUTO;
     if (cudaGetDevice(&s->device) != cudaSuccess) {
         delete s;
         return fail(PLSS_ERR_CUDA, "no CUDA device");
@@ -523,6 +615,13 @@ plss_status plss_server_create(const plss_server_opts *so_in, plss_server **out)
     s->bytes_per_nnz = 2 * (4 + sb);
     s->bytes_per_row = 4 + 8 + sb + 8 + 24;
     s->bytes_per_col = 4 + 8 + 2 * sb + 8 + 8;
+    // sliced copies (AUTO): at most 5/4 of the nonzeros per side, and one
+    // slice slot (offset + 32 slot ids) per 32 rows or columns
+    if (s->sliced) {
+        s->bytes_per_nnz += 2 * (4 + sb) * 5 / 4;
+        s->bytes_per_row += 4;
+        s->bytes_per_col += 4;
+    }
     const double per_nnz = double(s->bytes_per_nnz) + double(s->bytes_per_row) / 8.0 + 2.0 * double(s->bytes_per_col) / 8.0;
     s->Zcap = std::min<int64_t>(int64_t(double(budget) / per_nnz), INT32_MAX / 2);
     s->Mcap = std::min<int64_t>(s->Zcap / 8 + 64 * so.max_slots, INT32_MAX / 2);
@@ -534,6 +633,14 @@ plss_status plss_server_create(const plss_server_opts *so_in, plss_server **out)
     s->rows.init(s->Mcap);
     s->cols.init(s->Ncap);
     s->nnzs.init(s->Zcap);
+    if (s->sliced) {
+        // a request's slices take (m + 31)/32 + (n + 31)/32 + 2 slots and its
+        // elements at most 5/4 of 2 nnz plus one slice row of 32 per tile
+        s->SLcap = (s->Mcap + s->Ncap) / 32 + 4 * int64_t(so.max_slots) + 64;
+        s->ELcap = s->Zcap * 5 / 2 + 32 * (s->Tr + s->Tc) + 1024;
+        s->slcs.init(s->SLcap);
+        s->els.init(s->ELcap);
+    }
     s->h_desc.assign(size_t(s->Scap), SysDesc{});
     s->slot_req.assign(size_t(s->Scap), nullptr);
     plss_status st = PLSS_OK;
@@ -564,6 +671,14 @@ plss_status plss_server_create(const plss_server_opts *so_in, plss_server **out)
     A(reinterpret_cast<void **>(&s->d_desc), sizeof(SysDesc) * size_t(s->Scap), "desc");
     A(reinterpret_cast<void **>(&s->d_st), sizeof(SysState) * size_t(s->Scap), "state");
     A(reinterpret_cast<void **>(&s->d_active), 16, "active");
+    if (s->sliced) {
+        A(reinterpret_cast<void **>(&s->d_sl_ptr), 4 * size_t(s->SLcap), "arena slice offsets");
+        A(reinterpret_cast<void **>(&s->d_sl_seg), 128 * size_t(s->SLcap), "arena slice slots");
+        A(reinterpret_cast<void **>(&s->d_sl_idx), 4 * size_t(s->ELcap), "arena sliced indices");
+        A(&s->d_sl_val, size_t(sb) * size_t(s->ELcap), "arena sliced values");
+        A(reinterpret_cast<void **>(&s->d_rfirst), 4 * size_t(s->Tr), "arena sliced tiles");
+        A(reinterpret_cast<void **>(&s->d_cfirst), 4 * size_t(s->Tc), "arena sliced tiles");
+    }
     if (st == PLSS_OK && (cudaMallocHost(reinterpret_cast<void **>(&s->h_st), sizeof(SysState) * size_t(s->Scap)) != cudaSuccess ||
                           cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess ||
                           cudaMemset(s->d_st, 0, sizeof(SysState) * size_t(s->Scap)) != cudaSuccess ||
@@ -602,7 +717,8 @@ plss_status plss_submit(plss_server *s, const plss_csr *A, const double *b, cons
     r->maxit = o->maxit;
     r->w_mode = o->w_mode;
     if (r->m + 1 > s->Mcap || r->n + 1 > s->Ncap || r->nnz > s->Zcap || int64_t(r->rt.size()) > s->Tr ||
-        int64_t(r->ct.size()) > s->Tc || int64_t(r->vt.size()) > s->Tv) {
+        int64_t(r->ct.size()) > s->Tc || int64_t(r->vt.size()) > s->Tv || r->nsl > s->SLcap ||
+        r->nel > s->ELcap) {
         delete r;
         return fail(PLSS_ERR_BUSY, "request larger than the server arena");
     }

@@ -62,7 +62,7 @@ class Result(C.Structure):
 class ServerOpts(C.Structure):
     _fields_ = [("max_slots", C.c_int32), ("max_queue", C.c_int32),
                 ("hbm_budget_bytes", C.c_int64), ("precision", C.c_int32),
-                ("bodies_per_poll", C.c_int32)]
+                ("bodies_per_poll", C.c_int32), ("layout", C.c_int32), ("reserved", C.c_int32)]
 
 
 _lib = None
@@ -329,7 +329,7 @@ class Server:
     """Continuous-batching solve server (plss_server_*)."""
 
     def __init__(self, max_slots=64, max_queue=4096, hbm_budget_bytes=0, precision="fp64",
-                 bodies_per_poll=8):
+                 bodies_per_poll=8, layout="auto"):
         L = lib()
         so = ServerOpts()
         L.plss_server_opts_default(C.byref(so))
@@ -337,6 +337,7 @@ class Server:
         so.bodies_per_poll = int(bodies_per_poll)
         so.hbm_budget_bytes = int(hbm_budget_bytes)
         so.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
+        so.layout = LAYOUT[layout] if isinstance(layout, str) else int(layout)
         self._h = C.c_void_p()
         _check(L.plss_server_create(C.byref(so), C.byref(self._h)), (OK,))
         self._n = {}

@@ -36,6 +36,7 @@ def test_struct_layouts(L):
     assert C.sizeof(plss.Opts) == 112
     assert C.sizeof(plss.Csr) == 56
     assert C.sizeof(plss.Result) == 40
+    assert C.sizeof(plss.ServerOpts) == 32
     o = plss.Opts()
     L.plss_opts_default(C.byref(o))
     assert o.tol == 1e-8 and o.maxit == -1 and o.sketch == 0 and o.precision == 0

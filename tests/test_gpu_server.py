@@ -58,11 +58,15 @@ def drain(srv, tickets, timeout=300.0):
     return res
 
 
+@pytest.mark.parametrize("layout", ["auto", "csr"])
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_mix_equals_alone(plss, precision):
+def test_mix_equals_alone(plss, precision, layout):
+    """Each request in the mix gets bit for bit what it gets alone: with the
+    CSR layout, what a context created with it computes; with sliced tiles,
+    what the same request served alone computes."""
     reqs = requests(14)
     kw = dict(tol=1e-6, maxit=3000, w_mode=1)
-    srv = plss.Server(max_slots=4, precision=precision, hbm_budget_bytes=256 << 20)
+    srv = plss.Server(max_slots=4, precision=precision, hbm_budget_bytes=256 << 20, layout=layout)
     try:
         tickets = [srv.submit(A, b, **kw) for A, b in reqs]
         assert all(t is not None for t in tickets)
@@ -71,23 +75,37 @@ def test_mix_equals_alone(plss, precision):
         assert st["completed"] == len(reqs) and st["queued"] == 0 and st["running"] == 0
     finally:
         srv.close()
-    for (A, b), t in zip(reqs, tickets):
-        x_mix, r_mix = got[t]
-        # the arena's layout and schedule
-        with plss.Context(A, precision=precision, layout="csr") as ctx:
-            x_one, r_one = ctx.solve(b, stop_on_true=1, schedule="grid", **kw)
-        assert r_mix["status"] == r_one["status"]
-        assert r_mix["iters"] == r_one["iters"]
-        np.testing.assert_array_equal(x_mix, x_one)
-        if r_mix["status"] == "converged":
-            assert r_mix["relres_true"] <= 1e-6
-        assert r_mix["seconds"] > 0
+    alone = None
+    if layout == "auto":
+        alone = plss.Server(max_slots=1, precision=precision, hbm_budget_bytes=256 << 20, layout=layout)
+    try:
+        for (A, b), t in zip(reqs, tickets):
+            x_mix, r_mix = got[t]
+            if alone is not None:
+                t1 = alone.submit(A, b, **kw)
+                x_one, r_one = drain(alone, [t1])[t1]
+            else:
+                with plss.Context(A, precision=precision, layout="csr") as ctx:
+                    x_one, r_one = ctx.solve(b, stop_on_true=1, schedule="grid", **kw)
+            _check_same(r_mix, r_one, x_mix, x_one)
+    finally:
+        if alone is not None:
+            alone.close()
+
+
+def _check_same(r_mix, r_one, x_mix, x_one):
+    assert r_mix["status"] == r_one["status"]
+    assert r_mix["iters"] == r_one["iters"]
+    np.testing.assert_array_equal(x_mix, x_one)
+    if r_mix["status"] == "converged":
+        assert r_mix["relres_true"] <= 1e-6
+    assert r_mix["seconds"] > 0
 
 
 def test_admission_by_memory(plss):
     """A small arena: requests queue until earlier ones free room."""
     reqs = requests(10, seed=900, m_lo=2000, m_hi=6000)
-    srv = plss.Server(max_slots=16, hbm_budget_bytes=6 << 20)
+    srv = plss.Server(max_slots=16, hbm_budget_bytes=6 << 20, layout="csr")
     try:
         tickets = [srv.submit(A, b, tol=1e-6, maxit=2000, w_mode=1) for A, b in reqs]
         peak_running, peak_bytes = 0, 0
