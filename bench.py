@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--w-mode", type=int, default=0)
     ap.add_argument("--layout", default="auto", choices=["auto", "csr"])
+    ap.add_argument("--server-layout", default="csr", choices=["auto", "csr"], help="c5: arena layout")
     ap.add_argument("--m", type=int, default=1_000_000)
     ap.add_argument("--n", type=int, default=200_000)
     ap.add_argument("--tol", type=float, default=1e-8)
@@ -588,7 +589,10 @@ def suite_c5(args):
     consistent systems (m log-uniform [1e3, 1e6], n/m in {0.5, 1, 2}, 8-32
     nonzeros per row, N(0,1)) into the continuous-batching server, FP32 with
     FP64 refinement, W = diag(1/||A_j||), tol 1e-6, maxit 3,000. Latency is
-    completion minus arrival and includes the upload."""
+    completion minus arrival and includes the host-side preparation and the
+    upload. Eight client threads submit (plss_submit prepares the request on
+    the calling thread), each taking every eighth request at its arrival
+    time."""
     import threading
     torch, plss = _suite_common(args)
     arrivals, pool_ids, mats = synth.serving_trace(nreq=args.requests, pool=args.pool)
@@ -597,36 +601,46 @@ def suite_c5(args):
         A = mats[int(pid)]
         xs = synth.rng_for(3000 + 1_000_000 + i).standard_normal(A.n)
         reqs.append((A, synth.rhs(A, xs)))
-    srv = plss.Server(max_slots=64, precision="fp32")
+    srv = plss.Server(max_slots=64, precision="fp32", layout=args.server_layout)
     done = {}
+    nthreads = 8
     t0 = time.perf_counter()
     tickets = [None] * len(reqs)
+    submit_s = [0.0] * len(reqs)
     busy = [0]
 
-    def submitter():
-        for i, (A, b) in enumerate(reqs):
+    def submitter(k):
+        for i in range(k, len(reqs), nthreads):
+            A, b = reqs[i]
             while time.perf_counter() - t0 < arrivals[i]:
                 time.sleep(0.0002)
+            ts = time.perf_counter()
             t = None
             while t is None:
                 t = srv.submit(A, b, tol=1e-6, maxit=min(3000, args.maxit), w_mode=1)
                 if t is None:
                     busy[0] += 1
                     time.sleep(0.001)
+            submit_s[i] = time.perf_counter() - ts
             tickets[i] = t
 
-    th = threading.Thread(target=submitter)
+    ths = [threading.Thread(target=submitter, args=(k,)) for k in range(nthreads)]
     clocks = Clocks(0)
-    th.start()
-    while len(done) < len(reqs):
-        for i, t in enumerate(tickets):
-            if t is None or i in done:
+    for th in ths:
+        th.start()
+    pending = set(range(len(reqs)))
+    while pending:
+        for i in list(pending):
+            t = tickets[i]
+            if t is None:
                 continue
             r = srv.poll(t)
             if r is not None:
                 done[i] = (time.perf_counter() - t0, r[1])
-        time.sleep(0.0005)
-    th.join()
+                pending.discard(i)
+        time.sleep(0.002)
+    for th in ths:
+        th.join()
     clk = clocks.stop()
     srv.close()
     lat = np.array([done[i][0] - arrivals[i] for i in range(len(reqs))])
@@ -637,6 +651,8 @@ def suite_c5(args):
         "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                       "mean": float(lat.mean()), "max": float(lat.max())},
         "requests": len(reqs), "pool": args.pool, "converged": int(conv), "makespan_s": span,
+        "server_layout": args.server_layout, "client_threads": nthreads,
+        "submit_s": {"total": float(sum(submit_s)), "max": float(max(submit_s))},
         "busy_retries": busy[0], "clocks": clk})
 
 

@@ -258,8 +258,9 @@ typedef struct {
                               /* 4 GiB, capped at 80% of free memory             */
     int32_t precision;        /* PLSS_FP64 / PLSS_FP32 for every request         */
     int32_t bodies_per_poll;  /* iterations run between admission rounds (8)     */
-    int32_t layout;           /* PLSS_LAYOUT_AUTO (sliced tiles where they pay,   */
-                              /* one lane per segment) or PLSS_LAYOUT_CSR        */
+    int32_t layout;           /* PLSS_LAYOUT_CSR (default) or PLSS_LAYOUT_AUTO   */
+                              /* (sliced tiles, one lane per segment; measured   */
+                              /* slower for serving: mixed batches of tiles)     */
     int32_t reserved;
 } plss_server_opts;
 

@@ -329,7 +329,7 @@ class Server:
     """Continuous-batching solve server (plss_server_*)."""
 
     def __init__(self, max_slots=64, max_queue=4096, hbm_budget_bytes=0, precision="fp64",
-                 bodies_per_poll=8, layout="auto"):
+                 bodies_per_poll=8, layout="csr"):
         L = lib()
         so = ServerOpts()
         L.plss_server_opts_default(C.byref(so))
