@@ -69,16 +69,16 @@ enum { PLSS_W_IDENTITY = 0, PLSS_W_COLNORM = 1, PLSS_W_COLNORM2 = 2 };
  * results of the same request served alone. */
 enum { PLSS_LAYOUT_AUTO = 0, PLSS_LAYOUT_CSR = 1 };
 
-/* Schedule of a residual-sketch solve. AUTO and GRID: every sweep is a
- * grid-wide kernel over all systems of the context. SMALL: when every system
- * is small (at most 65,536 nonzeros, and r, p, u, x within 160 KB of shared
- * memory: about m + 3n <= 20,000 in FP64) one CTA per system runs whole
- * iterations between block barriers with its vectors in shared memory
- * (plss_kernel_times then records nothing); otherwise as GRID. On GB300 the
- * one-CTA form measured slower than the grid sweeps (a 2,000 x 2,000 system:
- * 38 vs 26 us per update; 128 systems of 1,000-4,000 rows: 75 vs 65 us per
- * batched update), so AUTO does not pick it. The schedules reduce in
- * different orders: their iterates agree to rounding, not bit for bit. */
+/* Schedule of a residual-sketch solve. GRID: every sweep is a grid-wide
+ * kernel over all systems of the context. SMALL: when every system has at
+ * most 2^20 nonzeros, one thread-block cluster of 8 CTAs per system runs
+ * whole iterations, its CTAs meeting at cluster barriers and exchanging
+ * partial sums through distributed shared memory (no kernel boundaries
+ * between the sweeps; plss_kernel_times then records nothing); otherwise as
+ * GRID. AUTO: SMALL when it fits and every system has at most 65,536
+ * nonzeros or the systems are at least 1/8 as many as the SMs; else GRID.
+ * The schedules reduce in different orders: their iterates agree to
+ * rounding, not bit for bit. */
 enum { PLSS_SCHED_AUTO = 0, PLSS_SCHED_GRID = 1, PLSS_SCHED_SMALL = 2 };
 
 /* A sparse matrix in CSR form (see the conventions above). val holds nnz

@@ -16,8 +16,8 @@ namespace plss {
 constexpr int64_t kVecTile = 1024;      // entries per update tile
 constexpr int kCtasPerSm = 8;           // resident CTAs per SM assumed for grids
 constexpr int kMaxChunk = 64;           // bodies per graph launch (max)
-constexpr int64_t kSmallMaxSmem = 160 * 1024;   // one-CTA-per-system schedule: vectors in shared memory
-constexpr int64_t kSmallMaxNnz = 65536;         // ... and at most this many nonzeros per system
+constexpr int64_t kSmallMaxNnz = 1 << 20;       // cluster schedule: nonzeros per system at most
+constexpr int64_t kSmallAutoNnz = 1 << 16;      // ... chosen by AUTO up to this size (or for many systems)
 
 struct KaczState;   // identity-sketch buffers (plss_kaczmarz.cu)
 struct RhsState;    // multi-right-hand-side buffers (plss_spmm.cu)
@@ -70,8 +70,8 @@ struct plss_ctx {
     plss::Sliced rsl{}, csl{};        // sliced copies (csl aliases rsl when symmetric)
     int64_t sl_elems[2] = {0, 0};     // elements of the sliced row / column copies
     int32_t *d_rwr = nullptr, *d_cwr = nullptr;   // warp ranges (Sliced::wr) or null
-    bool small_fits = false;                      // every system fits the one-CTA schedule
-    int64_t small_smem = 0;                       // its shared-memory bytes (largest system)
+    bool small_fits = false;                      // every system fits the cluster schedule
+    bool small_auto = false;                      // ... and AUTO picks it
 
     plss::KaczState *kacz = nullptr;
     plss::RhsState *rhs = nullptr;

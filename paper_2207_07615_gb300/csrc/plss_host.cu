@@ -440,13 +440,17 @@ static plss_status ctx_build(const plss_csr *As, int32_t nsys, const plss_opts *
     c->grid_v = std::max(1, std::min(int(c->h_vt.size()), c->nsm * sweep_ctas_per_sm(2, c->f32)));
 
     c->small_fits = true;
-    c->small_smem = 0;
+    int64_t max_nz = 0;
     for (const SysDesc &d : c->h_desc) {
         const int64_t nz = int64_t(rp[size_t(d.row_off + d.m)]) - rp[size_t(d.row_off)];
-        c->small_smem = std::max(c->small_smem, small_vec_bytes(d.m, d.n, c->f32));
+        max_nz = std::max(max_nz, nz);
         if (nz > kSmallMaxNnz) c->small_fits = false;
     }
-    if (c->small_smem > kSmallMaxSmem) c->small_fits = false;
+    // AUTO picks the cluster form where it measured faster: systems of at
+    // most 65,536 nonzeros (a lone 2,000 x 2,000 system: 16 vs 25 us per
+    // update), or enough of them to give every SM a CTA (128 systems of
+    // 1,000-4,000 rows: 14 % faster)
+    c->small_auto = c->small_fits && (max_nz <= kSmallAutoNnz || int64_t(c->nsys) * 8 >= int64_t(c->nsm));
 
     // one system with every tile of a side sliced: warp ranges instead of
     // tiles for that side's sweep
@@ -667,11 +671,10 @@ plss_status run_residual(plss_ctx *c, const double *const *b, const double *cons
     const int64_t period = std::max<int64_t>(1, o->profile);   // profile one chunk in `period`
     int64_t bodies = 0, nchunk = 0;
     int chunk = 1;
-    // the one-CTA form only on request: measured on GB300 it is slower than
-    // the grid sweeps both for a lone small system and for many of them
-    const bool small = c->small_fits && o->schedule == PLSS_SCHED_SMALL;
+    const bool small = o->schedule == PLSS_SCHED_SMALL ? c->small_fits
+                                                        : (o->schedule == PLSS_SCHED_AUTO && c->small_auto);
     if (small) {
-        // one CTA per system, whole bodies per launch
+        // one cluster per system, whole bodies per launch
         SweepArgs a = c->args;
         a.w = w_on ? c->d_w : nullptr;
         a.winv = w_on ? c->d_w + c->n : nullptr;
@@ -679,7 +682,7 @@ plss_status run_residual(plss_ctx *c, const double *const *b, const double *cons
         a.winvf = w_on && c->d_wf ? c->d_wf + c->n : nullptr;
         int32_t per = 16;
         for (;;) {
-            CUDA_TRY(launch_small_solve(a, c->f32, c->nsys, per, c->small_smem, s));
+            CUDA_TRY(launch_cluster_solve(a, c->f32, c->nsys, per, s));
             bodies += per;
             CUDA_TRY(cudaMemcpyAsync(c->h_active, c->d_active, 4, cudaMemcpyDeviceToHost, s));
             CUDA_TRY(cudaStreamSynchronize(s));

@@ -971,25 +971,30 @@ __global__ void __launch_bounds__(kThreads) k_update(SweepArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// Small systems: one CTA runs the whole recursion of one system
+// Small systems: one thread-block cluster runs the whole recursion
 // ---------------------------------------------------------------------------
 //
 // For a system of a few thousand rows a body of three grid-wide launches is
-// all latency (kernel boundaries, arrivals, last-CTA reductions, global
-// round trips for every vector access). Here one CTA of kSmallThreads per
-// system runs the same body -- column sweep, scalar step, update, row
-// sweep, stopping rule, in the same order and with the same decision
-// functions -- for up to `bodies` bodies per launch, with the system's
-// vectors r, p, u, x and its SysState held in shared memory (loaded at entry,
-// written back at exit) and only A streamed from L2/HBM. Sums are
-// fixed-order block reductions (deterministic).
+// all latency (kernel boundaries, arrivals, last-CTA reductions). Here a
+// cluster of kClusterCtas CTAs per system runs the same body -- column sweep,
+// scalar step, update, row sweep, stopping rule, in the same order and with
+// the same decision functions -- for up to `bodies` bodies per launch. Each
+// CTA owns a contiguous share of the rows and of the columns (balanced by
+// nonzeros); after each phase it puts its fixed-order partial sum in its
+// shared memory and the cluster meets at a hardware barrier
+// (barrier.cluster, release/acquire: the phase's vector writes are then
+// visible to the whole cluster); every CTA then reads the kClusterCtas
+// partials through distributed shared memory in rank order and takes the
+// same scalar decisions on its own copy of the system state, so no
+// broadcast is needed. The vectors stay in global memory (L2-resident).
 
-constexpr int kSmallThreads = 512;
-constexpr int kSmallWarps = kSmallThreads / 32;
+constexpr int kClusterCtas = 8;
+constexpr int kClusterThreads = 512;
+constexpr int kClusterWarps = kClusterThreads / 32;
 
 template <int N>
-__device__ __forceinline__ void small_sum(double (&v)[N]) {
-    __shared__ double sh[N][kSmallWarps];
+__device__ __forceinline__ void clu_block_sum(double (&v)[N]) {
+    __shared__ double sh[N][kClusterWarps];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int i = 0; i < N; ++i) {
@@ -1005,47 +1010,56 @@ __device__ __forceinline__ void small_sum(double (&v)[N]) {
     if (warp == 0) {
 #pragma unroll
         for (int i = 0; i < N; ++i) {
-            double t = lane < kSmallWarps ? sh[i][lane] : 0.0;
+            double t = lane < kClusterWarps ? sh[i][lane] : 0.0;
 #pragma unroll
-            for (int o = kSmallWarps / 2; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+            for (int o = kClusterWarps / 2; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
             v[i] = t;
         }
     }
 }
 
-// Segment dot with G lanes per segment against a shared-memory vector xs
-// indexed from xoff (global index c reads xs[c - xoff]).
-template <int G, typename VT, typename XT, typename ACC>
-__device__ __forceinline__ ACC small_dot(const int32_t *__restrict__ idx, const VT *__restrict__ val, int32_t s,
-                                         int32_t e, int gl, const XT *xs, int32_t xoff) {
-    ACC acc = ACC(0);
-    for (int32_t base = s + gl; base < e; base += kBatch * G) {
-        int32_t c[kBatch];
-        VT v[kBatch];
-#pragma unroll
-        for (int u = 0; u < kBatch; ++u) {
-            const int32_t k = base + u * G;
-            const bool in = k < e;
-            c[u] = in ? __ldg(idx + k) - xoff : 0;
-            v[u] = in ? __ldg(val + k) : VT(0);
-        }
-#pragma unroll
-        for (int u = 0; u < kBatch; ++u)
-            if (base + u * G < e) acc = fma_t(ACC(v[u]), ACC(xs[c[u]]), acc);
-    }
-#pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    return acc;
+// Cluster-wide barrier (hardware; release/acquire at cluster scope).
+__device__ __forceinline__ void cluster_barrier() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
-// Calls body(seg, s, e, gl, valid) for segments [b0, b1) with G lanes each
-// over the whole CTA (warp-uniform loop).
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+// Reads a double from the shared memory of CTA `rank` of this cluster.
+__device__ __forceinline__ double dsmem_load(const double *p, uint32_t rank) {
+    uint32_t local = static_cast<uint32_t>(__cvta_generic_to_shared(p)), remote;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(local), "r"(rank));
+    double v;
+    asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(remote) : "memory");
+    return v;
+}
+
+// First segment of share k of [b0, b1) when the shares hold about equal
+// nonzeros (offsets in ptr).
+__device__ __forceinline__ int32_t clu_split(const int32_t *ptr, int32_t b0, int32_t b1, int k) {
+    if (k <= 0) return b0;
+    if (k >= kClusterCtas) return b1;
+    const int64_t z0 = ptr[b0], z1 = ptr[b1];
+    const int64_t goal = z0 + (z1 - z0) * k / kClusterCtas;
+    int32_t lo = b0, hi = b1;   // first segment whose start is >= goal
+    while (lo < hi) {
+        const int32_t mid = lo + (hi - lo) / 2;
+        if (ptr[mid] < goal) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
 template <int G, typename F>
-__device__ __forceinline__ void small_segments(const int32_t *__restrict__ ptr, int32_t b0, int32_t b1, F &&body) {
+__device__ __forceinline__ void clu_segments(const int32_t *__restrict__ ptr, int32_t b0, int32_t b1, F &&body) {
     constexpr int SPW = 32 / G;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int gid = lane / G, gl = lane & (G - 1);
-    for (int32_t base = b0 + warp * SPW; base < b1; base += kSmallWarps * SPW) {
+    for (int32_t base = b0 + warp * SPW; base < b1; base += kClusterWarps * SPW) {
         const int32_t seg = base + gid;
         const bool valid = seg < b1;
         const int32_t s = valid ? __ldg(ptr + seg) : 0;
@@ -1054,34 +1068,54 @@ __device__ __forceinline__ void small_segments(const int32_t *__restrict__ ptr, 
     }
 }
 
-// The system's vectors in shared memory (local indices).
-template <typename S>
-struct SmallVecs {
-    double *x;   // [n]
-    S *r;        // [m]
-    S *p;        // [n]
-    S *u;        // [n]
-};
+// Segment dot with G lanes against a vector written within this kernel
+// (coherent loads).
+template <int G, typename VT, typename XT, typename ACC>
+__device__ __forceinline__ ACC clu_dot(const int32_t *__restrict__ idx, const VT *__restrict__ val, int32_t s,
+                                       int32_t e, int gl, const XT *x) {
+    ACC acc = ACC(0);
+    for (int32_t base = s + gl; base < e; base += kBatch * G) {
+        int32_t c[kBatch];
+        VT v[kBatch];
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+            const int32_t k = base + u * G;
+            const bool in = k < e;
+            c[u] = in ? __ldg(idx + k) : 0;
+            v[u] = in ? __ldg(val + k) : VT(0);
+        }
+        XT g[kBatch];
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) g[u] = base + u * G < e ? __ldcg(x + c[u]) : XT(0);
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u)
+            if (base + u * G < e) acc = fma_t(ACC(v[u]), ACC(g[u]), acc);
+    }
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    return acc;
+}
 
 template <int G, typename S>
-__device__ __forceinline__ void small_row(const SweepArgs &a, const SmallVecs<S> &v, int32_t r0, int32_t r1,
-                                          int32_t c0, bool init, double &acc_r, double &acc_b) {
+__device__ __forceinline__ void clu_row(const SweepArgs &a, int32_t r0, int32_t r1, bool init, double &acc_r,
+                                        double &acc_b) {
     const S *__restrict__ val = static_cast<const S *>(a.val);
-    small_segments<G>(a.row_ptr, r0, r1, [&](int32_t row, int32_t s, int32_t e, int gl, bool valid) {
+    S *r = static_cast<S *>(a.r);
+    clu_segments<G>(a.row_ptr, r0, r1, [&](int32_t row, int32_t s, int32_t e, int gl, bool valid) {
         if (init) {
-            const double d = small_dot<G, S, double, double>(a.col_idx, val, s, e, gl, v.x, c0);
+            const double d = clu_dot<G, S, double, double>(a.col_idx, val, s, e, gl, a.x);
             if (valid && gl == 0) {
                 const double bi = a.b[row];
                 const S ri = S(bi - d);
-                v.r[row - r0] = ri;
+                r[row] = ri;
                 acc_r = fma(double(ri), double(ri), acc_r);
                 acc_b = fma(bi, bi, acc_b);
             }
         } else {
-            const S d = small_dot<G, S, S, S>(a.col_idx, val, s, e, gl, v.p, c0);
+            const S d = clu_dot<G, S, S, S>(a.col_idx, val, s, e, gl, static_cast<const S *>(a.p));
             if (valid && gl == 0) {
-                const S ri = v.r[row - r0] - d;
-                v.r[row - r0] = ri;
+                const S ri = r[row] - d;
+                r[row] = ri;
                 acc_r = fma(double(ri), double(ri), acc_r);
             }
         }
@@ -1089,100 +1123,108 @@ __device__ __forceinline__ void small_row(const SweepArgs &a, const SmallVecs<S>
 }
 
 template <int G, typename S>
-__device__ __forceinline__ void small_col(const SweepArgs &a, const SmallVecs<S> &v, int32_t c0, int32_t c1,
-                                          int32_t r0, double &acc) {
+__device__ __forceinline__ void clu_col(const SweepArgs &a, int32_t c0, int32_t c1, double &acc) {
     const S *__restrict__ val = static_cast<const S *>(a.cval);
-    small_segments<G>(a.col_ptr, c0, c1, [&](int32_t col, int32_t s, int32_t e, int gl, bool valid) {
-        const S y = small_dot<G, S, S, S>(a.row_idx, val, s, e, gl, v.r, r0);
+    clu_segments<G>(a.col_ptr, c0, c1, [&](int32_t col, int32_t s, int32_t e, int gl, bool valid) {
+        const S y = clu_dot<G, S, S, S>(a.row_idx, val, s, e, gl, static_cast<const S *>(a.r));
         if (valid && gl == 0) {
-            S uj;
-            if constexpr (std::is_same<S, float>::value) uj = a.wf ? __fmul_rn(a.wf[col], y) : y;
-            else uj = a.w ? S(a.w[col] * double(y)) : y;
-            v.u[col - c0] = uj;
-            acc = fma(double(y), double(uj), acc);
+            if constexpr (std::is_same<S, float>::value) {
+                const float uj = a.wf ? __fmul_rn(a.wf[col], y) : y;
+                static_cast<float *>(a.u)[col] = uj;
+                acc = fma(double(y), double(uj), acc);
+            } else {
+                col_out<S>(a, col, double(y), acc);
+            }
         }
     });
 }
 
 // Lanes per segment for a mean segment length (as the host's tile groups).
-__device__ __forceinline__ int small_group(int64_t nnz, int64_t segs) {
+__device__ __forceinline__ int clu_group(int64_t nnz, int64_t segs) {
     int g = 1;
     while (g < 32 && 2 * g * 8 * segs <= nnz) g <<= 1;
     return g;
 }
 
-// Shared-memory bytes of a system's vectors (x double; r, p, u storage type).
-__host__ __device__ constexpr int64_t small_smem_bytes(int64_t m, int64_t n, int64_t sv) {
-    return ((8 * n + 15) / 16 * 16) + ((sv * m + 15) / 16 * 16) + 2 * ((sv * n + 15) / 16 * 16);
-}
-
 template <typename S>
-__global__ void __launch_bounds__(kSmallThreads) k_small_solve(SweepArgs a, int32_t bodies) {
-    extern __shared__ __align__(16) unsigned char small_smem[];
-    __shared__ SysState sst;
-    const int32_t sys = blockIdx.x;
+__global__ void __launch_bounds__(kClusterThreads) k_cluster_solve(SweepArgs a, int32_t bodies) {
+    __shared__ SysState sst;           // this CTA's copy of the system state
+    // this CTA's partials (phi, theta, rho, ||b||^2), one set per parity of
+    // the body: a CTA rewrites a set only after a barrier that every CTA
+    // reaches after reading it
+    __shared__ double parts[2][4];
+    __shared__ int32_t done_local;     // stands in for the active count in CTAs other than rank 0
+    const uint32_t rank = cluster_rank();
+    const int32_t sys = int32_t(blockIdx.x) / kClusterCtas;
     const SysDesc d = a.desc[sys];
-    const int32_t r0 = int32_t(d.row_off), r1 = int32_t(d.row_off) + d.m;
-    const int32_t c0 = int32_t(d.col_off), c1 = int32_t(d.col_off) + d.n;
-    constexpr int64_t sv = sizeof(S);
-    SmallVecs<S> v;
-    v.x = reinterpret_cast<double *>(small_smem);
-    v.r = reinterpret_cast<S *>(small_smem + (8 * d.n + 15) / 16 * 16);
-    v.p = reinterpret_cast<S *>(reinterpret_cast<unsigned char *>(v.r) + (sv * d.m + 15) / 16 * 16);
-    v.u = reinterpret_cast<S *>(reinterpret_cast<unsigned char *>(v.p) + (sv * d.n + 15) / 16 * 16);
-    if (threadIdx.x == 0) sst = a.st[sys];
-    const S *gr = static_cast<const S *>(a.r), *gp = static_cast<const S *>(a.p), *gu = static_cast<const S *>(a.u);
-    for (int32_t i = threadIdx.x; i < d.m; i += kSmallThreads) v.r[i] = gr[r0 + i];
-    for (int32_t j = threadIdx.x; j < d.n; j += kSmallThreads) {
-        v.x[j] = a.x[c0 + j];
-        v.p[j] = gp[c0 + j];
-        v.u[j] = gu[c0 + j];
+    const int32_t R0 = int32_t(d.row_off), R1 = R0 + d.m, C0 = int32_t(d.col_off), C1 = C0 + d.n;
+    const int32_t r0 = clu_split(a.row_ptr, R0, R1, int(rank)), r1 = clu_split(a.row_ptr, R0, R1, int(rank) + 1);
+    const int32_t c0 = clu_split(a.col_ptr, C0, C1, int(rank)), c1 = clu_split(a.col_ptr, C0, C1, int(rank) + 1);
+    const int64_t nnz = int64_t(a.row_ptr[R1]) - a.row_ptr[R0];
+    const int gr = clu_group(nnz, d.m), gc = clu_group(nnz, d.n);
+    // only rank 0 changes global state (the active count, the history)
+    SweepArgs al = a;
+    if (threadIdx.x == 0) {
+        sst = a.st[sys];
+        done_local = 0;
+        if (rank != 0) sst.hist = nullptr;
     }
+    if (rank != 0) al.n_active = &done_local;
     __syncthreads();
     SysState *st = &sst;
-    const int64_t nnz = int64_t(a.row_ptr[r1]) - a.row_ptr[r0];
-    const int gr_ = small_group(nnz, d.m), gc_ = small_group(nnz, d.n);
+    // sum of partial q over the cluster, in rank order (the same in every CTA)
+    auto cluster_total = [&](const double *part, int q) {
+        double t = 0.0;
+        for (uint32_t k = 0; k < uint32_t(kClusterCtas); ++k) t += dsmem_load(&part[q], k);
+        return t;
+    };
     for (int32_t it = 0; it < bodies; ++it) {
         __syncthreads();
+        double *part = parts[it & 1];
         int32_t ph = st->phase;
-        if (ph == PH_DONE) break;
+        if (ph == PH_DONE) break;   // the same in every CTA of the cluster
         if (ph == PH_FIRST || ph == PH_RUN) {
             double w1[1] = {0.0};
-            switch (gc_) {
-                case 1: small_col<1, S>(a, v, c0, c1, r0, w1[0]); break;
-                case 2: small_col<2, S>(a, v, c0, c1, r0, w1[0]); break;
-                case 4: small_col<4, S>(a, v, c0, c1, r0, w1[0]); break;
-                case 8: small_col<8, S>(a, v, c0, c1, r0, w1[0]); break;
-                case 16: small_col<16, S>(a, v, c0, c1, r0, w1[0]); break;
-                default: small_col<32, S>(a, v, c0, c1, r0, w1[0]); break;
+            switch (gc) {
+                case 1: clu_col<1, S>(al, c0, c1, w1[0]); break;
+                case 2: clu_col<2, S>(al, c0, c1, w1[0]); break;
+                case 4: clu_col<4, S>(al, c0, c1, w1[0]); break;
+                case 8: clu_col<8, S>(al, c0, c1, w1[0]); break;
+                case 16: clu_col<16, S>(al, c0, c1, w1[0]); break;
+                default: clu_col<32, S>(al, c0, c1, w1[0]); break;
             }
-            small_sum<1>(w1);
-            if (threadIdx.x == 0) col_decide(a, st, w1[0]);
+            clu_block_sum<1>(w1);
+            if (threadIdx.x == 0) part[0] = w1[0];
+            cluster_barrier();   // u, phi partials complete
+            if (threadIdx.x == 0) col_decide(al, st, cluster_total(part, 0));
             __syncthreads();
-            const int32_t upd = st->upd;
-            if (upd != 0) {
-                const bool first = upd == 2;
+            if (st->upd != 0) {
+                const bool first = st->upd == 2;
                 const double beta = st->beta, gamma = st->gamma;
                 double acc[1] = {0.0};
-                for (int32_t j = threadIdx.x; j < d.n; j += kSmallThreads) {
+                S *p = static_cast<S *>(a.p);
+                const S *u = static_cast<const S *>(a.u);
+                for (int32_t j = c0 + threadIdx.x; j < c1; j += kClusterThreads) {
                     S ps;
                     if constexpr (std::is_same<S, float>::value) {
                         const float bf = float(beta), gf = float(gamma);
-                        ps = first ? gf * v.u[j] : fmaf(bf, v.p[j], gf * v.u[j]);
+                        ps = first ? gf * u[j] : fmaf(bf, p[j], gf * u[j]);
                     } else {
-                        const double gu = gamma * v.u[j];
-                        ps = first ? gu : fma(beta, v.p[j], gu);
+                        const double gu = gamma * u[j];
+                        ps = first ? gu : fma(beta, p[j], gu);
                     }
-                    v.p[j] = ps;
+                    p[j] = ps;
                     const double pd = double(ps);
                     if constexpr (std::is_same<S, float>::value)
-                        acc[0] = fma(pd, a.winvf ? double(__fmul_rn(ps, a.winvf[c0 + j])) : pd, acc[0]);
+                        acc[0] = fma(pd, a.winvf ? double(__fmul_rn(ps, a.winvf[j])) : pd, acc[0]);
                     else
-                        acc[0] = fma(pd, a.winv ? pd * a.winv[c0 + j] : pd, acc[0]);
-                    v.x[j] = v.x[j] + pd;
+                        acc[0] = fma(pd, a.winv ? pd * a.winv[j] : pd, acc[0]);
+                    a.x[j] = a.x[j] + pd;
                 }
-                small_sum<1>(acc);
-                if (threadIdx.x == 0) upd_done(st, acc[0]);
+                clu_block_sum<1>(acc);
+                if (threadIdx.x == 0) part[1] = acc[0];
+                cluster_barrier();   // p, x, theta partials complete
+                if (threadIdx.x == 0) upd_done(st, cluster_total(part, 1));
             }
             __syncthreads();
             ph = st->phase;
@@ -1190,27 +1232,27 @@ __global__ void __launch_bounds__(kSmallThreads) k_small_solve(SweepArgs a, int3
         if (ph == PH_SETUP || ph == PH_RUN) {
             const bool init = ph == PH_SETUP;
             double w2[2] = {0.0, 0.0};
-            switch (gr_) {
-                case 1: small_row<1, S>(a, v, r0, r1, c0, init, w2[0], w2[1]); break;
-                case 2: small_row<2, S>(a, v, r0, r1, c0, init, w2[0], w2[1]); break;
-                case 4: small_row<4, S>(a, v, r0, r1, c0, init, w2[0], w2[1]); break;
-                case 8: small_row<8, S>(a, v, r0, r1, c0, init, w2[0], w2[1]); break;
-                case 16: small_row<16, S>(a, v, r0, r1, c0, init, w2[0], w2[1]); break;
-                default: small_row<32, S>(a, v, r0, r1, c0, init, w2[0], w2[1]); break;
+            switch (gr) {
+                case 1: clu_row<1, S>(al, r0, r1, init, w2[0], w2[1]); break;
+                case 2: clu_row<2, S>(al, r0, r1, init, w2[0], w2[1]); break;
+                case 4: clu_row<4, S>(al, r0, r1, init, w2[0], w2[1]); break;
+                case 8: clu_row<8, S>(al, r0, r1, init, w2[0], w2[1]); break;
+                case 16: clu_row<16, S>(al, r0, r1, init, w2[0], w2[1]); break;
+                default: clu_row<32, S>(al, r0, r1, init, w2[0], w2[1]); break;
             }
-            small_sum<2>(w2);
-            if (threadIdx.x == 0) row_decide(a, st, init, w2[0], w2[1]);
+            clu_block_sum<2>(w2);
+            if (threadIdx.x == 0) {
+                part[2] = w2[0];
+                part[3] = w2[1];
+            }
+            cluster_barrier();   // r, rho partials complete
+            if (threadIdx.x == 0) row_decide(al, st, init, cluster_total(part, 2), cluster_total(part, 3));
         }
     }
     __syncthreads();
-    S *wr = static_cast<S *>(a.r), *wp = static_cast<S *>(a.p), *wu = static_cast<S *>(a.u);
-    for (int32_t i = threadIdx.x; i < d.m; i += kSmallThreads) wr[r0 + i] = v.r[i];
-    for (int32_t j = threadIdx.x; j < d.n; j += kSmallThreads) {
-        a.x[c0 + j] = v.x[j];
-        wp[c0 + j] = v.p[j];
-        wu[c0 + j] = v.u[j];
-    }
-    if (threadIdx.x == 0) a.st[sys] = sst;
+    // no CTA may exit while another can still read its shared memory
+    cluster_barrier();
+    if (rank == 0 && threadIdx.x == 0) a.st[sys] = sst;
 }
 
 // ---------------------------------------------------------------------------
@@ -1339,18 +1381,20 @@ cudaError_t launch_update(const SweepArgs &a, bool f32, int grid, cudaStream_t s
     return f32 ? launch_pdl(k_update<float>, grid, s, a) : launch_pdl(k_update<double>, grid, s, a);
 }
 
-int64_t small_vec_bytes(int64_t m, int64_t n, bool f32) { return small_smem_bytes(m, n, f32 ? 4 : 8); }
-
-cudaError_t launch_small_solve(const SweepArgs &a, bool f32, int32_t nsys, int32_t bodies, int64_t smem,
-                               cudaStream_t s) {
-    cudaError_t e = f32 ? cudaFuncSetAttribute(k_small_solve<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               int(smem))
-                        : cudaFuncSetAttribute(k_small_solve<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               int(smem));
-    if (e != cudaSuccess) return e;
-    if (f32) k_small_solve<float><<<nsys, kSmallThreads, size_t(smem), s>>>(a, bodies);
-    else k_small_solve<double><<<nsys, kSmallThreads, size_t(smem), s>>>(a, bodies);
-    return cudaGetLastError();
+cudaError_t launch_cluster_solve(const SweepArgs &a, bool f32, int32_t nsys, int32_t bodies, cudaStream_t s) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(unsigned(nsys) * kClusterCtas);
+    cfg.blockDim = dim3(kClusterThreads);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = kClusterCtas;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return f32 ? cudaLaunchKernelEx(&cfg, k_cluster_solve<float>, a, bodies)
+               : cudaLaunchKernelEx(&cfg, k_cluster_solve<double>, a, bodies);
 }
 
 cudaError_t launch_spmv(const int32_t *ptr, const int32_t *idx, const void *val, bool f32,

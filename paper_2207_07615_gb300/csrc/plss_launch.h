@@ -15,13 +15,9 @@ cudaError_t launch_row_sweep(const SweepArgs &a, bool f32, int grid, cudaStream_
 cudaError_t launch_col_sweep(const SweepArgs &a, bool f32, int grid, cudaStream_t s);
 cudaError_t launch_update(const SweepArgs &a, bool f32, int grid, cudaStream_t s);
 
-// Small systems: one CTA of 512 threads per system of the context runs up
-// to `bodies` bodies of the recursion (column sweep, update, row sweep) with
-// the system's vectors in `smem` bytes of shared memory (at least
-// small_vec_bytes of the largest system).
-cudaError_t launch_small_solve(const SweepArgs &a, bool f32, int32_t nsys, int32_t bodies, int64_t smem,
-                               cudaStream_t s);
-int64_t small_vec_bytes(int64_t m, int64_t n, bool f32);
+// Small systems: one cluster of 8 CTAs per system of the context runs up to
+// `bodies` bodies of the recursion (column sweep, update, row sweep).
+cudaError_t launch_cluster_solve(const SweepArgs &a, bool f32, int32_t nsys, int32_t bodies, cudaStream_t s);
 
 // Resident CTAs per SM of a sweep kernel (0 row, 1 column, 2 update, 3 row
 // and 4 column over warp ranges).
