@@ -260,7 +260,7 @@ def run_reference(args):
             "impl": "reference",
             "config": {"workload": WORKLOAD, "m": args.m, "n": args.n, "nnz": int(A.nnz),
                        "tol": args.tol, "w_mode": args.w_mode, "precision": args.prec,
-                       "l2": "n/a (CPU)"},
+                       "parallelism": "single", "l2": "n/a (CPU)"},
             "cpu_baseline": {"value": v, "unit": "s", "cores": 1, "kind": "oracle",
                              "sample": cb["sample"]},
             "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
