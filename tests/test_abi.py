@@ -112,3 +112,27 @@ def test_last_error_is_per_thread(L):
     t.join()
     assert seen["err"] == ""
     assert "negative" in L.plss_last_error().decode()
+
+
+def test_sizes_beyond_int32_rejected(L):
+    """Indices are int32 on the device: larger sizes are refused before any
+    array is read (the pointers here are NULL)."""
+    for m, n, nnz in ((2**31, 2, 0), (2, 2**31, 0), (2, 2, 2**31)):
+        c = plss.Csr(m, n, nnz, None, None, None, 0, 0)
+        code, err, h = _create(L, c)
+        assert code == plss.ERR_INVALID and "2^31" in err and not h.value
+
+
+def test_unknown_options_rejected(L):
+    """Option values outside their enums are refused at create."""
+    rp = np.array([0, 1], dtype=np.int64)
+    ci = np.array([0], dtype=np.int32)
+    val = np.array([1.0])
+    c = plss.Csr(1, 1, 1, rp.ctypes.data, ci.ctypes.data, val.ctypes.data, 0, 0)
+    for field, bad in (("precision", 7), ("layout", 5)):
+        o = plss.Opts()
+        L.plss_opts_default(C.byref(o))
+        setattr(o, field, bad)
+        h = C.c_void_p()
+        assert L.plss_create(C.byref(c), C.byref(o), C.byref(h)) == plss.ERR_INVALID
+        assert not h.value
