@@ -204,6 +204,39 @@ def sweep_bytes(kind, m, n, nnz, sv):
     raise KeyError(kind)
 
 
+def gather_reference(torch, A, sv, dev, flush, reps=5):
+    """PyTorch's own gather (index_select, library code) over the same index
+    streams as the two sweeps: the column indices of A into a vector of n and
+    the row indices of A^T into a vector of m, each nnz gathers with the
+    indices read and the gathered values written once. Timed alone with CUDA
+    events, L2 flushed before each repetition; the median is reported beside
+    the sweeps, which do the same gathers plus the values, products, sums and
+    vector writes."""
+    dt = torch.float64 if sv == 8 else torch.float32
+    order = np.argsort(A.col_idx, kind="stable")
+    rows = np.repeat(np.arange(A.m, dtype=np.int32), np.diff(A.row_ptr).astype(np.int64))[order]
+    out = {}
+    for side, idx_np, length in (("row_sweep", A.col_idx, A.n), ("col_sweep", rows, A.m)):
+        idx = torch.from_numpy(np.ascontiguousarray(idx_np, dtype=np.int32)).to(dev)
+        vec = torch.rand(length, dtype=dt, device=dev)
+        dst = torch.empty(idx.numel(), dtype=dt, device=dev)
+        ts = []
+        for _ in range(reps + 1):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch.index_select(vec, 0, idx, out=dst)
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1) * 1e3)
+        us = float(np.median(ts[1:]))
+        out[side] = {"us": us, "gathers_per_s": idx.numel() / (us * 1e-6)}
+        del idx, vec, dst
+    out["kernel"] = "torch.index_select (int32 indices), median of %d" % reps
+    return out
+
+
 def make_workload(args):
     A, b, xs = synth.overdetermined_scaled(m=args.m, n=args.n, per_row=8, seed=1)
     if args.prec == "fp64":
@@ -348,6 +381,14 @@ def run_plss(args):
                 "traffic": ncu_traffic(dom), "peak_source": f"{peak_src} hbm_gbs (copy)",
                 "algorithmic_bytes_per_launch": per[dom]["bytes_per_launch"],
                 "us_per_launch": per[dom]["us_per_launch"], "sweeps": per}
+
+    if roof is not None and rank == 0:
+        gref = gather_reference(torch, A, sv, dev, flush)
+        for k in ("row_sweep", "col_sweep"):
+            if k in per:
+                gref[k]["sweep_us"] = per[k]["us_per_launch"]
+                gref[k]["sweep_vs_index_select"] = gref[k]["us"] / per[k]["us_per_launch"]
+        roof["gather_reference"] = gref
 
     # end to end through the C ABI with host buffers
     torch.cuda.synchronize()
