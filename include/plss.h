@@ -123,7 +123,9 @@ typedef struct {
                             /* since the last start (default 1e-4; 0 = off)        */
     int32_t schedule;       /* residual sketch: PLSS_SCHED_* (how the iterations   */
                             /* are spread over the GPU)                           */
-    int32_t reserved;
+    int32_t tile_shift;     /* create: sweep tiles of 2^tile_shift times the       */
+                            /* default nonzeros, -2..2 (0 = default; the knob     */
+                            /* plss_tune measures)                                */
 } plss_opts;
 
 /* Outcome of one solve. relres_rec is sqrt(rho)/||b|| of the last recursive
@@ -155,6 +157,37 @@ plss_status plss_create_batched(const plss_csr *As, int32_t nsys, const plss_opt
                                 plss_ctx **out);
 
 void plss_destroy(plss_ctx *ctx);
+
+/* One candidate plan measured by plss_tune. */
+typedef struct {
+    int32_t layout;         /* PLSS_LAYOUT_*                                        */
+    int32_t tile_shift;     /* as in plss_opts                                      */
+    int32_t schedule;       /* PLSS_SCHED_GRID or PLSS_SCHED_SMALL                  */
+    int32_t status;         /* PLSS_OK, or the error that ruled the candidate out   */
+    double us_per_update;   /* wall time of the timed solve / its updates (0 if not */
+                            /* measured)                                          */
+} plss_tune_entry;
+
+/*
+ * Autotuner of the sweep plan (the paper has none: the plan is this library's).
+ * For each candidate -- layout AUTO and CSR, tile_shift -1, 0 and 1, and
+ * schedule GRID, plus SMALL where every system fits the cluster schedule --
+ * it builds a context of As[0..nsys-1] with o's precision and symmetric flag,
+ * computes the consistent right-hand sides b = A 1 on the device, runs one
+ * untimed and one timed solve of exactly `updates` updates of the residual
+ * sketch (tol 0, o's w_mode), and measures the timed one on the host clock
+ * (wall time, launches and synchronisation included). Only one candidate
+ * context exists at a time.
+ *   best: *o with layout, tile_shift and schedule of the fastest candidate.
+ *   entries[0 .. min(cap, *count)): every candidate in the order tried;
+ *   *count = the number of candidates. entries may be NULL when cap is 0.
+ * A candidate that cannot be built for lack of device memory is recorded
+ * with PLSS_ERR_NOMEM and skipped; any other failure is returned.
+ * PLSS_ERR_INVALID for NULL As/best/count, nsys <= 0, updates outside
+ * [1, 100000], cap < 0, or entries NULL with cap > 0.
+ */
+plss_status plss_tune(const plss_csr *As, int32_t nsys, const plss_opts *o, int32_t updates,
+                      plss_opts *best, plss_tune_entry *entries, int32_t cap, int32_t *count);
 
 /* Sizes of a context: systems, total rows, total columns, total nonzeros. */
 plss_status plss_ctx_info(const plss_ctx *ctx, int32_t *nsys, int64_t *m, int64_t *n,

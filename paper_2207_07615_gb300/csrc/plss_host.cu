@@ -236,6 +236,8 @@ static plss_status ctx_build(const plss_csr *As, int32_t nsys, const plss_opts *
         return fail(PLSS_ERR_INVALID, "unknown precision %d", o->precision);
     if (o->layout != PLSS_LAYOUT_AUTO && o->layout != PLSS_LAYOUT_CSR)
         return fail(PLSS_ERR_INVALID, "unknown layout %d", o->layout);
+    if (o->tile_shift < -2 || o->tile_shift > 2)
+        return fail(PLSS_ERR_INVALID, "tile_shift %d outside [-2, 2]", o->tile_shift);
 
     std::vector<HostCsr> hs(static_cast<size_t>(nsys));
     int64_t M = 0, N = 0, NNZ = 0;
@@ -324,7 +326,8 @@ static plss_status ctx_build(const plss_csr *As, int32_t nsys, const plss_opts *
     // padded copy could overflow 32-bit offsets)
     const bool slice = o->layout == PLSS_LAYOUT_AUTO && NNZ < 1800000000;
     const int32_t g_r = slice_lanes(NNZ, M), g_c = sym ? g_r : slice_lanes(NNZ, N);
-    const PlanSlots slots = plan_slots(c->nsm);
+    PlanSlots slots = plan_slots(c->nsm);
+    slots.shift = o->tile_shift;
     for (int32_t s = 0; s < nsys; ++s) {
         SysDesc &d = c->h_desc[size_t(s)];
         d.rt_begin = int32_t(c->h_rt.size());
@@ -785,7 +788,7 @@ void plss_opts_default(plss_opts *o) {
     o->profile = 0;
     o->layout = PLSS_LAYOUT_AUTO;
     o->schedule = PLSS_SCHED_AUTO;
-    o->reserved = 0;
+    o->tile_shift = 0;
     o->inner_tol = 1e-4;
 }
 

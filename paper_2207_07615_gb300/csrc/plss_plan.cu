@@ -55,11 +55,13 @@ void build_tiles(const int32_t *ptr, int64_t begin, int64_t end, int32_t sys, in
 
 // Nonzeros per sweep tile for a context of nnz nonzeros: about two tiles
 // per resident CTA (a balanced contiguous split), within [1,024, 16,384]
-// (2,048 for FP32 storage).
-int64_t tile_target(int64_t nnz, int64_t slots, bool f32) {
+// (2,048 for FP32 storage); then scaled by 2^shift within [256, cap].
+int64_t tile_target(int64_t nnz, int64_t slots, bool f32, int32_t shift) {
     // FP32 tiles are staged in 8 KB of shared memory (2,048 float products)
     const int64_t cap = f32 ? 2048 : 16384;
-    return std::min<int64_t>(cap, std::max<int64_t>(1024, (nnz + 2 * slots - 1) / (2 * slots) * 21 / 20));
+    int64_t t = std::min<int64_t>(cap, std::max<int64_t>(1024, (nnz + 2 * slots - 1) / (2 * slots) * 21 / 20));
+    t = shift >= 0 ? t << shift : t >> -shift;
+    return std::min<int64_t>(cap, std::max<int64_t>(256, t));
 }
 
 // Order of a tile's segments in its slices (decreasing length, ties by
@@ -130,13 +132,13 @@ static void cut_slice_tiles(const int32_t *ptr, int64_t begin, int64_t end, int3
 // kSliced, and the others are cut as they would be without slicing.
 void build_side(const int32_t *ptr, int64_t begin, int64_t end, int32_t sys, int64_t nnz, const PlanSlots &slots,
                 bool f32, bool slice, int32_t g, std::vector<Tile> &out) {
-    const int64_t target = tile_target(nnz, f32 ? slots.f32 : slots.f64, f32);
+    const int64_t target = tile_target(nnz, f32 ? slots.f32 : slots.f64, f32, slots.shift);
     if (!slice || begin == end) {
         build_tiles(ptr, begin, end, sys, target, max_segs(f32), f32, out);
         return;
     }
     std::vector<Tile> big;
-    cut_slice_tiles(ptr, begin, end, sys, tile_target(nnz, slots.f64, false), big);
+    cut_slice_tiles(ptr, begin, end, sys, tile_target(nnz, slots.f64, false, slots.shift), big);
     std::vector<int32_t> order;
     for (const Tile &t : big) {
         const int64_t nz = int64_t(ptr[t.end]) - ptr[t.begin];
@@ -145,8 +147,8 @@ void build_side(const int32_t *ptr, int64_t begin, int64_t end, int32_t sys, int
         } else if (t.group != 0 && t.end > t.begin) {
             // uneven segments: staged tiles (FP64 too), so that a long
             // segment does not hold a warp through a serial gather chain
-            build_tiles(ptr, t.begin, t.end, sys, f32 ? target : tile_target(nnz, slots.f32, true), max_segs(true), true,
-                        out);
+            build_tiles(ptr, t.begin, t.end, sys, f32 ? target : tile_target(nnz, slots.f32, true, slots.shift),
+                        max_segs(true), true, out);
         } else {
             out.push_back(t);
         }

@@ -13,9 +13,11 @@ constexpr int64_t kTileMaxSegsF32 = 1024;   // ... per staged tile (shared-memor
 inline int64_t max_segs(bool f32) { return f32 ? kTileMaxSegsF32 : kTileMaxSegs; }
 
 // Resident CTA slots of the sweeps on the device (SMs x CTAs per SM) for
-// FP64 and FP32 storage; sizes the tiles.
+// FP64 and FP32 storage; sizes the tiles. `shift` scales the tiles' target
+// nonzeros by 2^shift (the autotuner's knob; 0 = the default plan).
 struct PlanSlots {
     int64_t f64 = 1, f32 = 1;
+    int32_t shift = 0;
 };
 
 // Host copy of a sliced side (layout in plss_dev.cuh).
@@ -28,7 +30,7 @@ struct HostSliced {
 
 void build_tiles(const int32_t *ptr, int64_t begin, int64_t end, int32_t sys, int64_t target,
                  int64_t max_segs, bool f32, std::vector<Tile> &out);
-int64_t tile_target(int64_t nnz, int64_t slots, bool f32);
+int64_t tile_target(int64_t nnz, int64_t slots, bool f32, int32_t shift = 0);
 void build_vec_tiles(int64_t begin, int64_t end, int32_t sys, int64_t chunk, std::vector<Tile> &out);
 int32_t slice_lanes(int64_t nnz, int64_t segs);
 void build_side(const int32_t *ptr, int64_t begin, int64_t end, int32_t sys, int64_t nnz, const PlanSlots &slots,

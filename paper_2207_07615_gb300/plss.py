@@ -29,8 +29,9 @@ SCHEDULE = {"auto": 0, "grid": 1, "small": 2}
 #: every symbol declared in include/plss.h
 EXPORTS = ["plss_opts_default", "plss_create", "plss_create_batched", "plss_destroy",
            "plss_ctx_info", "plss_ctx_layout", "plss_solve", "plss_solve_batched", "plss_solve_rhs", "plss_spmv",
-           "plss_kernel_times", "plss_residual_noalloc", "plss_last_error", "plss_server_opts_default", "plss_server_create", "plss_submit",
-           "plss_poll", "plss_server_stats", "plss_server_destroy"]
+           "plss_kernel_times", "plss_residual_noalloc", "plss_last_error", "plss_server_opts_default",
+           "plss_server_create", "plss_submit", "plss_poll", "plss_server_stats", "plss_server_destroy",
+           "plss_tune"]
 
 
 class Csr(C.Structure):
@@ -46,7 +47,12 @@ class Opts(C.Structure):
                 ("io_device", C.c_int32), ("symmetric", C.c_int32), ("stream", C.c_void_p),
                 ("hist", C.c_void_p), ("hist_cap", C.c_int64), ("profile", C.c_int32),
                 ("layout", C.c_int32), ("inner_tol", C.c_double), ("schedule", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("tile_shift", C.c_int32)]
+
+
+class TuneEntry(C.Structure):
+    _fields_ = [("layout", C.c_int32), ("tile_shift", C.c_int32), ("schedule", C.c_int32),
+                ("status", C.c_int32), ("us_per_update", C.c_double)]
 
 
 class Result(C.Structure):
@@ -105,11 +111,12 @@ def lib() -> C.CDLL:
             L.plss_server_stats.argtypes = [vp, vp, vp, vp, vp]
             L.plss_server_destroy.argtypes = [vp]
             L.plss_server_destroy.restype = None
+            L.plss_tune.argtypes = [vp, i32, vp, i32, vp, vp, i32, vp]
             for name in ("plss_create", "plss_create_batched", "plss_ctx_info", "plss_ctx_layout",
                          "plss_solve",
                          "plss_kernel_times",
                          "plss_solve_batched", "plss_solve_rhs", "plss_spmv",
-                         "plss_server_create", "plss_submit", "plss_poll", "plss_server_stats"):
+                         "plss_server_create", "plss_submit", "plss_poll", "plss_server_stats", "plss_tune"):
                 getattr(L, name).restype = C.c_int32
             _lib = L
     return _lib
@@ -209,13 +216,41 @@ class _CsrHold:
         self.c = Csr(int(A.m), int(A.n), int(A.nnz), _ptr(rp), _ptr(ci), _ptr(v), int(f32), dev)
 
 
+_LAYOUT_NAMES = {v: k for k, v in LAYOUT.items()}
+_SCHEDULE_NAMES = {v: k for k, v in SCHEDULE.items()}
+
+
+def tune(A, updates=20, precision="fp64", symmetric=False, w_mode=0, stream=None):
+    """plss_tune: measures the candidate sweep plans of A (a CSR, or a list of
+    them for a batched context) and returns (best, table). `best` holds the
+    Context and solve keywords of the fastest plan ({"layout", "tile_shift"}
+    for Context, {"schedule"} for solve); `table` lists every candidate with
+    its wall time per update in microseconds."""
+    L = lib()
+    As = list(A) if isinstance(A, (list, tuple)) else [A]
+    holds = [_CsrHold(a) for a in As]
+    arr = (Csr * len(holds))(*[h.c for h in holds])
+    o = make_opts(precision=precision, symmetric=int(bool(symmetric)), w_mode=w_mode, stream=stream)
+    best = Opts()
+    cap = 32
+    ent = (TuneEntry * cap)()
+    cnt = C.c_int32()
+    _check(L.plss_tune(arr, len(holds), C.byref(o), int(updates), C.byref(best), ent, cap, C.byref(cnt)), (OK,))
+    table = [dict(layout=_LAYOUT_NAMES[e.layout], tile_shift=int(e.tile_shift),
+                  schedule=_SCHEDULE_NAMES[e.schedule],
+                  status="ok" if e.status == OK else STATUS_NAMES.get(e.status, e.status),
+                  us_per_update=float(e.us_per_update)) for e in ent[:min(cap, cnt.value)]]
+    return (dict(layout=_LAYOUT_NAMES[best.layout], tile_shift=int(best.tile_shift),
+                 schedule=_SCHEDULE_NAMES[best.schedule]), table)
+
+
 class Context:
     """A matrix (or a batch of independent matrices) resident on the GPU."""
 
-    def __init__(self, A, precision="fp64", symmetric=False, layout="auto"):
+    def __init__(self, A, precision="fp64", symmetric=False, layout="auto", tile_shift=0):
         L = lib()
         self._h = C.c_void_p()
-        o = make_opts(precision=precision, symmetric=int(bool(symmetric)), layout=layout)
+        o = make_opts(precision=precision, symmetric=int(bool(symmetric)), layout=layout, tile_shift=tile_shift)
         if isinstance(A, (list, tuple)):
             holds = [_CsrHold(a) for a in A]
             arr = (Csr * len(holds))(*[h.c for h in holds])

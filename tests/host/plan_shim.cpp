@@ -21,16 +21,20 @@ extern "C" {
 
 int32_t shim_slice_lanes(int64_t nnz, int64_t segs) { return slice_lanes(nnz, segs); }
 
-int64_t shim_tile_target(int64_t nnz, int64_t slots, int32_t f32) { return tile_target(nnz, slots, f32 != 0); }
+int64_t shim_tile_target(int64_t nnz, int64_t slots, int32_t f32, int32_t shift) {
+    return tile_target(nnz, slots, f32 != 0, shift);
+}
 
 // One side of a single system: segments [0, nseg) with offsets ptr[nseg+1]
 // (int32), indices idx and double values val.
 void *shim_plan(const int32_t *ptr, const int32_t *idx, const double *val, int64_t nseg, int64_t nnz,
-                int64_t slots64, int64_t slots32, int32_t f32, int32_t slice, int32_t g, int64_t nwarps) {
+                int64_t slots64, int64_t slots32, int32_t f32, int32_t slice, int32_t g, int64_t nwarps,
+                int32_t shift) {
     Plan *p = new Plan();
     PlanSlots s;
     s.f64 = slots64;
     s.f32 = slots32;
+    s.shift = shift;
     build_side(ptr, 0, nseg, 0, nnz, s, f32 != 0, slice != 0, g, p->tiles);
     fill_sliced(ptr, idx, val, nullptr, p->tiles, g, p->sl);
     p->wr = warp_ranges(p->tiles, p->sl.ptr, nwarps);

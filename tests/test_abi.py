@@ -37,10 +37,11 @@ def test_struct_layouts(L):
     assert C.sizeof(plss.Csr) == 56
     assert C.sizeof(plss.Result) == 40
     assert C.sizeof(plss.ServerOpts) == 32
+    assert C.sizeof(plss.TuneEntry) == 24
     o = plss.Opts()
     L.plss_opts_default(C.byref(o))
     assert o.tol == 1e-8 and o.maxit == -1 and o.sketch == 0 and o.precision == 0
-    assert o.inner_tol == 1e-4
+    assert o.inner_tol == 1e-4 and o.tile_shift == 0
 
 
 def _create(L, csr):
@@ -129,10 +130,31 @@ def test_unknown_options_rejected(L):
     ci = np.array([0], dtype=np.int32)
     val = np.array([1.0])
     c = plss.Csr(1, 1, 1, rp.ctypes.data, ci.ctypes.data, val.ctypes.data, 0, 0)
-    for field, bad in (("precision", 7), ("layout", 5)):
+    for field, bad in (("precision", 7), ("layout", 5), ("tile_shift", 3), ("tile_shift", -3)):
         o = plss.Opts()
         L.plss_opts_default(C.byref(o))
         setattr(o, field, bad)
         h = C.c_void_p()
         assert L.plss_create(C.byref(c), C.byref(o), C.byref(h)) == plss.ERR_INVALID
         assert not h.value
+
+
+def test_tune_rejects_bad_arguments(L):
+    """plss_tune validates its arguments before it builds anything."""
+    rp = np.array([0, 1], dtype=np.int64)
+    ci = np.array([0], dtype=np.int32)
+    val = np.array([1.0])
+    c = plss.Csr(1, 1, 1, rp.ctypes.data, ci.ctypes.data, val.ctypes.data, 0, 0)
+    best = plss.Opts()
+    cnt = C.c_int32()
+    ent = (plss.TuneEntry * 4)()
+    cases = [(None, 1, 5, C.byref(best), ent, 4, C.byref(cnt)),
+             (C.byref(c), 0, 5, C.byref(best), ent, 4, C.byref(cnt)),
+             (C.byref(c), 1, 0, C.byref(best), ent, 4, C.byref(cnt)),
+             (C.byref(c), 1, 100001, C.byref(best), ent, 4, C.byref(cnt)),
+             (C.byref(c), 1, 5, None, ent, 4, C.byref(cnt)),
+             (C.byref(c), 1, 5, C.byref(best), None, 4, C.byref(cnt)),
+             (C.byref(c), 1, 5, C.byref(best), ent, -1, C.byref(cnt)),
+             (C.byref(c), 1, 5, C.byref(best), ent, 4, None)]
+    for As, nsys, upd, b, e, cap, n in cases:
+        assert L.plss_tune(As, nsys, None, upd, b, e, cap, n) == plss.ERR_INVALID

@@ -28,7 +28,7 @@ def shim(tmp_path_factory):
     L = C.CDLL(out)
     L.shim_plan.restype = C.c_void_p
     L.shim_plan.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_int64, C.c_int64,
-                            C.c_int32, C.c_int32, C.c_int32, C.c_int64]
+                            C.c_int32, C.c_int32, C.c_int32, C.c_int64, C.c_int32]
     L.shim_count.restype = C.c_int64
     L.shim_count.argtypes = [C.c_void_p, C.c_int32]
     L.shim_copy.argtypes = [C.c_void_p, C.c_int32, C.c_void_p]
@@ -36,16 +36,16 @@ def shim(tmp_path_factory):
     L.shim_slice_lanes.restype = C.c_int32
     L.shim_slice_lanes.argtypes = [C.c_int64, C.c_int64]
     L.shim_tile_target.restype = C.c_int64
-    L.shim_tile_target.argtypes = [C.c_int64, C.c_int64, C.c_int32]
+    L.shim_tile_target.argtypes = [C.c_int64, C.c_int64, C.c_int32, C.c_int32]
     return L
 
 
-def plan(L, ptr, idx, val, f32, slice, g, nwarps=64, slots=(4864, 6080)):
+def plan(L, ptr, idx, val, f32, slice, g, nwarps=64, slots=(4864, 6080), shift=0):
     ptr = np.ascontiguousarray(ptr, dtype=np.int32)
     idx = np.ascontiguousarray(idx, dtype=np.int32)
     val = np.ascontiguousarray(val, dtype=np.float64)
     h = L.shim_plan(ptr.ctypes.data, idx.ctypes.data, val.ctypes.data, len(ptr) - 1, int(ptr[-1]),
-                    slots[0], slots[1], int(f32), int(slice), int(g), nwarps)
+                    slots[0], slots[1], int(f32), int(slice), int(g), nwarps, int(shift))
     try:
         def get(which, dtype, width=1):
             n = L.shim_count(h, which if which != 6 else 4)
@@ -81,19 +81,20 @@ CASES = cases()
 @pytest.mark.parametrize("name", sorted(CASES))
 @pytest.mark.parametrize("f32", [0, 1])
 @pytest.mark.parametrize("slice_", [0, 1])
-def test_plan_invariants(shim, name, f32, slice_):
+@pytest.mark.parametrize("shift", [-1, 0, 1])
+def test_plan_invariants(shim, name, f32, slice_, shift):
     ptr, idx, val = (np.asarray(a) for a in CASES[name])
     nseg, nnz = len(ptr) - 1, int(ptr[-1])
     g = shim.shim_slice_lanes(max(nnz, 1), max(nseg, 1)) if slice_ else 1
-    p = plan(shim, ptr, idx, val, f32, slice_, g)
+    p = plan(shim, ptr, idx, val, f32, slice_, g, shift=shift)
     tiles = p["tiles"]
     lens = np.diff(ptr)
     # tiles partition [0, nseg) in order
     assert len(tiles) >= 1
     assert tiles[0, 1] == 0 and tiles[-1, 2] == nseg
     assert np.all(tiles[1:, 1] == tiles[:-1, 2]) and np.all(tiles[:, 2] >= tiles[:, 1])
-    target = shim.shim_tile_target(max(nnz, 1), 6080 if f32 else 4864, f32)
-    assert 1024 <= target <= (2048 if f32 else 16384)
+    target = shim.shim_tile_target(max(nnz, 1), 6080 if f32 else 4864, f32, shift)
+    assert (256 if shift < 0 else 1024) <= target <= (2048 if f32 else 16384)
     for sys, b, e, grp in tiles:
         tnz = int(ptr[e] - ptr[b])
         if (grp & K_MASK) == 0 and e > b:                    # one segment for the whole CTA
@@ -154,3 +155,15 @@ def test_slice_lanes(shim):
     assert shim.shim_slice_lanes(8_000_000, 1_000_000) == 1      # 8 per row
     assert shim.shim_slice_lanes(8_000_000, 200_000) == 4        # 40 per column
     assert shim.shim_slice_lanes(10**9, 1000) == 32              # capped
+
+
+def test_tile_shift_scales_the_target(shim):
+    """The autotuner's knob: 2^shift times the default target, clamped to
+    [256, 16,384] (FP64) or [256, 2,048] (FP32, the staging limit)."""
+    for nnz, slots in ((8_000_000, 4864), (40_000, 4864), (2_600_000, 608)):
+        for f32 in (0, 1):
+            base = shim.shim_tile_target(nnz, slots, f32, 0)
+            cap = 2048 if f32 else 16384
+            for shift in (-2, -1, 1, 2):
+                want = base * 2 ** shift if shift > 0 else base >> -shift
+                assert shim.shim_tile_target(nnz, slots, f32, shift) == min(cap, max(256, want))
