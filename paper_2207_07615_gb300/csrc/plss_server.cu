@@ -29,55 +29,12 @@
 #include <vector>
 
 #include "plss.h"
+#include "plss_arena.h"
 #include "plss_ctx.h"
 #include "plss_dev.cuh"
 #include "plss_launch.h"
 
 namespace plss {
-
-// First-fit allocator of [0, cap) ranges with coalescing on release.
-struct RangeAlloc {
-    int64_t cap = 0, used = 0;
-    std::map<int64_t, int64_t> free_;
-    void init(int64_t c) {
-        cap = c;
-        used = 0;
-        free_.clear();
-        if (c > 0) free_[0] = c;
-    }
-    bool alloc(int64_t len, int64_t &off) {
-        off = 0;
-        if (len <= 0) return true;
-        for (auto it = free_.begin(); it != free_.end(); ++it) {
-            if (it->second >= len) {
-                off = it->first;
-                const int64_t rest = it->second - len;
-                free_.erase(it);
-                if (rest) free_[off + len] = rest;
-                used += len;
-                return true;
-            }
-        }
-        return false;
-    }
-    void release(int64_t off, int64_t len) {
-        if (len <= 0) return;
-        used -= len;
-        auto it = free_.emplace(off, len).first;
-        auto nx = std::next(it);
-        if (nx != free_.end() && it->first + it->second == nx->first) {
-            it->second += nx->second;
-            free_.erase(nx);
-        }
-        if (it != free_.begin()) {
-            auto pv = std::prev(it);
-            if (pv->first + pv->second == it->first) {
-                pv->second += it->second;
-                free_.erase(it);
-            }
-        }
-    }
-};
 
 struct SrvRequest {
     uint64_t ticket = 0;
@@ -101,6 +58,29 @@ struct SrvRequest {
     // outcome
     std::vector<double> x;
     plss_result res{};
+
+    ArenaNeed need() const {
+        ArenaNeed q;
+        q.m = m;
+        q.n = n;
+        q.nnz = nnz;
+        q.nsl = nsl;
+        q.nel = nel;
+        q.tr = int64_t(rt.size());
+        q.tc = int64_t(ct.size());
+        q.tv = int64_t(vt.size());
+        return q;
+    }
+    ArenaPlace place() const {
+        ArenaPlace p;
+        p.slot = slot;
+        p.roff = roff;
+        p.coff = coff;
+        p.zoff = zoff;
+        p.sloff = sloff;
+        p.eloff = eloff;
+        return p;
+    }
 };
 
 }  // namespace plss
@@ -111,14 +91,12 @@ struct plss_server {
     int device = 0, nsm = 1;
     int64_t Mcap = 0, Ncap = 0, Zcap = 0, Tr = 0, Tc = 0, Tv = 0;
     int32_t Scap = 0;
-    plss::RangeAlloc rows, cols, nnzs;
     bool sliced = false;                 // PLSS_LAYOUT_AUTO: sliced copies in the arena
     int64_t SLcap = 0, ELcap = 0;        // slice slots, sliced elements
-    plss::RangeAlloc slcs, els;
+    plss::Arena arena;                   // placement of the resident systems
     int32_t *d_sl_ptr = nullptr, *d_sl_seg = nullptr, *d_sl_idx = nullptr, *d_rfirst = nullptr,
             *d_cfirst = nullptr;
     void *d_sl_val = nullptr;
-    int64_t tiles_r = 0, tiles_c = 0, tiles_v = 0;   // tiles of resident systems
     int32_t *d_row_ptr = nullptr, *d_col_idx = nullptr, *d_col_ptr = nullptr, *d_row_idx = nullptr;
     void *d_val = nullptr, *d_cval = nullptr, *d_r = nullptr, *d_p = nullptr, *d_u = nullptr;
     double *d_b = nullptr, *d_x = nullptr, *d_w = nullptr, *d_vout = nullptr;
@@ -213,63 +191,20 @@ static void srv_prepare(plss_server *s, HostCsr &h, SrvRequest *r) {
 
 // Arena ranges and a slot for r; false (nothing taken) when they do not fit.
 static bool srv_place(plss_server *s, SrvRequest *r) {
-    int32_t slot = -1;
-    for (int32_t i = 0; i < s->Scap; ++i)
-        if (!s->slot_req[size_t(i)]) {
-            slot = i;
-            break;
-        }
-    if (slot < 0) return false;
-    if (s->tiles_r + int64_t(r->rt.size()) > s->Tr || s->tiles_c + int64_t(r->ct.size()) > s->Tc ||
-        s->tiles_v + int64_t(r->vt.size()) > s->Tv)
-        return false;
-    int64_t ro, co, zo;
-    if (!s->rows.alloc(r->m + 1, ro)) return false;
-    if (!s->cols.alloc(r->n + 1, co)) {
-        s->rows.release(ro, r->m + 1);
-        return false;
-    }
-    if (!s->nnzs.alloc(r->nnz, zo)) {
-        s->rows.release(ro, r->m + 1);
-        s->cols.release(co, r->n + 1);
-        return false;
-    }
-    int64_t so = 0, eo = 0;
-    if (r->nsl > 0 && !s->slcs.alloc(r->nsl, so)) {
-        s->rows.release(ro, r->m + 1);
-        s->cols.release(co, r->n + 1);
-        s->nnzs.release(zo, r->nnz);
-        return false;
-    }
-    if (r->nel > 0 && !s->els.alloc(r->nel, eo)) {
-        s->rows.release(ro, r->m + 1);
-        s->cols.release(co, r->n + 1);
-        s->nnzs.release(zo, r->nnz);
-        if (r->nsl > 0) s->slcs.release(so, r->nsl);
-        return false;
-    }
-    r->sloff = so;
-    r->eloff = eo;
-    r->slot = slot;
-    r->roff = ro;
-    r->coff = co;
-    r->zoff = zo;
-    s->slot_req[size_t(slot)] = r;
-    s->tiles_r += int64_t(r->rt.size());
-    s->tiles_c += int64_t(r->ct.size());
-    s->tiles_v += int64_t(r->vt.size());
+    ArenaPlace at;
+    if (!s->arena.place(r->need(), at)) return false;
+    r->slot = at.slot;
+    r->roff = at.roff;
+    r->coff = at.coff;
+    r->zoff = at.zoff;
+    r->sloff = at.sloff;
+    r->eloff = at.eloff;
+    s->slot_req[size_t(at.slot)] = r;
     return true;
 }
 
 static void srv_unplace(plss_server *s, SrvRequest *r) {
-    s->rows.release(r->roff, r->m + 1);
-    s->cols.release(r->coff, r->n + 1);
-    s->nnzs.release(r->zoff, r->nnz);
-    if (r->nsl > 0) s->slcs.release(r->sloff, r->nsl);
-    if (r->nel > 0) s->els.release(r->eloff, r->nel);
-    s->tiles_r -= int64_t(r->rt.size());
-    s->tiles_c -= int64_t(r->ct.size());
-    s->tiles_v -= int64_t(r->vt.size());
+    s->arena.release(r->need(), r->place());
     s->slot_req[size_t(r->slot)] = nullptr;
 }
 
@@ -414,9 +349,6 @@ static bool srv_rebuild(plss_server *s) {
         if (s->slot_req[size_t(i)]) ++nact;
     SRV_TRY(cudaMemcpyAsync(s->d_active, &nact, 4, cudaMemcpyHostToDevice, st));
     SRV_TRY(cudaStreamSynchronize(st));
-    s->tiles_r = int64_t(rt.size());
-    s->tiles_c = int64_t(ct.size());
-    s->tiles_v = int64_t(vt.size());
     return true;
 }
 
@@ -441,9 +373,9 @@ static SweepArgs srv_args(plss_server *s) {
     a.rtiles = s->d_rt;
     a.ctiles = s->d_ct;
     a.vtiles = s->d_vt;
-    a.n_rtiles = int32_t(s->tiles_r);
-    a.n_ctiles = int32_t(s->tiles_c);
-    a.n_vtiles = int32_t(s->tiles_v);
+    a.n_rtiles = int32_t(s->arena.tiles_r);
+    a.n_ctiles = int32_t(s->arena.tiles_c);
+    a.n_vtiles = int32_t(s->arena.tiles_v);
     a.desc = s->d_desc;
     a.st = s->d_st;
     a.part_row = s->d_part_row;
@@ -500,7 +432,7 @@ static void srv_fail_all(plss_server *s) {
         r->x.assign(size_t(r->n), 0.0);
         s->done[r->ticket] = r;
         s->live.erase(r->ticket);
-        s->slot_req[size_t(i)] = nullptr;
+        srv_unplace(s, r);
         s->running -= 1;
     }
 }
@@ -630,17 +562,13 @@ plss_status plss_server_create(const plss_server_opts *so_in, plss_server **out)
     s->Tr = 2 * (s->Zcap / 1024) + s->Mcap / kTileMaxSegs + 2 * int64_t(s->Scap) + 16;
     s->Tc = 2 * (s->Zcap / 1024) + s->Ncap / kTileMaxSegs + 2 * int64_t(s->Scap) + 16;
     s->Tv = s->Ncap / kVecTile + 2 * int64_t(s->Scap) + 16;
-    s->rows.init(s->Mcap);
-    s->cols.init(s->Ncap);
-    s->nnzs.init(s->Zcap);
     if (s->sliced) {
         // a request's slices take (m + 31)/32 + (n + 31)/32 + 2 slots and its
         // elements at most 5/4 of 2 nnz plus one slice row of 32 per tile
         s->SLcap = (s->Mcap + s->Ncap) / 32 + 4 * int64_t(so.max_slots) + 64;
         s->ELcap = s->Zcap * 5 / 2 + 32 * (s->Tr + s->Tc) + 1024;
-        s->slcs.init(s->SLcap);
-        s->els.init(s->ELcap);
     }
+    s->arena.init(s->Scap, s->Mcap, s->Ncap, s->Zcap, s->SLcap, s->ELcap, s->Tr, s->Tc, s->Tv);
     s->h_desc.assign(size_t(s->Scap), SysDesc{});
     s->slot_req.assign(size_t(s->Scap), nullptr);
     plss_status st = PLSS_OK;
@@ -716,9 +644,7 @@ plss_status plss_submit(plss_server *s, const plss_csr *A, const double *b, cons
     r->tol = o->tol;
     r->maxit = o->maxit;
     r->w_mode = o->w_mode;
-    if (r->m + 1 > s->Mcap || r->n + 1 > s->Ncap || r->nnz > s->Zcap || int64_t(r->rt.size()) > s->Tr ||
-        int64_t(r->ct.size()) > s->Tc || int64_t(r->vt.size()) > s->Tv || r->nsl > s->SLcap ||
-        r->nel > s->ELcap) {
+    if (!s->arena.ever_fits(r->need())) {
         delete r;
         return fail(PLSS_ERR_BUSY, "request larger than the server arena");
     }
@@ -770,8 +696,8 @@ plss_status plss_server_stats(plss_server *s, int64_t *completed, int64_t *queue
     if (queued) *queued = int64_t(s->queue.size());
     if (running) *running = s->running;
     if (bytes_in_use)
-        *bytes_in_use = s->nnzs.used * s->bytes_per_nnz + s->rows.used * s->bytes_per_row +
-                        s->cols.used * s->bytes_per_col;
+        *bytes_in_use = s->arena.nnzs.used * s->bytes_per_nnz + s->arena.rows.used * s->bytes_per_row +
+                        s->arena.cols.used * s->bytes_per_col;
     return PLSS_OK;
 }
 
