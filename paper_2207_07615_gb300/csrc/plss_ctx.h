@@ -72,6 +72,7 @@ struct plss_ctx {
     int32_t *d_rwr = nullptr, *d_cwr = nullptr;   // warp ranges (Sliced::wr) or null
     bool small_fits = false;                      // every system fits the cluster schedule
     bool small_auto = false;                      // ... and AUTO picks it
+    int32_t clu_vec_bytes = 0;                    // cluster schedule: shared-memory vector copies (0: none)
 
     plss::KaczState *kacz = nullptr;
     plss::RhsState *rhs = nullptr;

@@ -454,6 +454,12 @@ static plss_status ctx_build(const plss_csr *As, int32_t nsys, const plss_opts *
     // update), or enough of them to give every SM a CTA (128 systems of
     // 1,000-4,000 rows: 14 % faster)
     c->small_auto = c->small_fits && (max_nz <= kSmallAutoNnz || int64_t(c->nsys) * 8 >= int64_t(c->nsm));
+    // the cluster form keeps whole copies of r and p in each CTA's shared
+    // memory when the largest system's (m + n) entries fit
+    int64_t max_mn = 0;
+    for (const SysDesc &d : c->h_desc) max_mn = std::max<int64_t>(max_mn, int64_t(d.m) + int64_t(d.n));
+    const int64_t vec_bytes = (max_mn * (c->f32 ? 4 : 8) + 15) / 16 * 16;
+    c->clu_vec_bytes = c->small_fits && vec_bytes > 0 && vec_bytes <= kClusterVecBytes ? int32_t(vec_bytes) : 0;
 
     // one system with every tile of a side sliced: warp ranges instead of
     // tiles for that side's sweep
@@ -685,7 +691,7 @@ plss_status run_residual(plss_ctx *c, const double *const *b, const double *cons
         a.winvf = w_on && c->d_wf ? c->d_wf + c->n : nullptr;
         int32_t per = 16;
         for (;;) {
-            CUDA_TRY(launch_cluster_solve(a, c->f32, c->nsys, per, s));
+            CUDA_TRY(launch_cluster_solve(a, c->f32, c->nsys, per, c->clu_vec_bytes, s));
             bodies += per;
             CUDA_TRY(cudaMemcpyAsync(c->h_active, c->d_active, 4, cudaMemcpyDeviceToHost, s));
             CUDA_TRY(cudaStreamSynchronize(s));

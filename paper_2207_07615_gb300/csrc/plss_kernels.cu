@@ -986,7 +986,13 @@ __global__ void __launch_bounds__(kThreads) k_update(SweepArgs a) {
 // visible to the whole cluster); every CTA then reads the kClusterCtas
 // partials through distributed shared memory in rank order and takes the
 // same scalar decisions on its own copy of the system state, so no
-// broadcast is needed. The vectors stay in global memory (L2-resident).
+// broadcast is needed. The vectors live in global memory (L2-resident);
+// when the system is small enough (RES), every CTA also keeps whole copies
+// of the two gathered vectors -- r for the column sweep, p for the row
+// sweep -- in its shared memory, and the CTA that produces an entry writes it
+// into all the cluster's copies (st.shared::cluster) before the phase's
+// barrier, so that every gather is a shared-memory load instead of an L2
+// round trip. The arithmetic and its order are the same in both forms.
 
 constexpr int kClusterCtas = 8;
 constexpr int kClusterThreads = 512;
@@ -1038,6 +1044,22 @@ __device__ __forceinline__ double dsmem_load(const double *p, uint32_t rank) {
     return v;
 }
 
+// Writes v to the element `p` (this CTA's shared memory) of every CTA of
+// the cluster, this one included.
+template <typename T>
+__device__ __forceinline__ void dsmem_store_all(T *p, T v) {
+    const uint32_t local = static_cast<uint32_t>(__cvta_generic_to_shared(p));
+#pragma unroll
+    for (uint32_t k = 0; k < uint32_t(kClusterCtas); ++k) {
+        uint32_t remote;
+        asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(local), "r"(k));
+        if constexpr (sizeof(T) == 8)
+            asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(remote), "d"(double(v)) : "memory");
+        else
+            asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(remote), "f"(float(v)) : "memory");
+    }
+}
+
 // First segment of share k of [b0, b1) when the shares hold about equal
 // nonzeros (offsets in ptr).
 __device__ __forceinline__ int32_t clu_split(const int32_t *ptr, int32_t b0, int32_t b1, int k) {
@@ -1068,11 +1090,12 @@ __device__ __forceinline__ void clu_segments(const int32_t *__restrict__ ptr, in
     }
 }
 
-// Segment dot with G lanes against a vector written within this kernel
-// (coherent loads).
-template <int G, typename VT, typename XT, typename ACC>
+// Segment dot with G lanes against a vector written within this kernel:
+// x[c - off] from this CTA's shared-memory copy (SH), else coherent loads
+// of x[c] from global memory.
+template <int G, typename VT, typename XT, typename ACC, bool SH = false>
 __device__ __forceinline__ ACC clu_dot(const int32_t *__restrict__ idx, const VT *__restrict__ val, int32_t s,
-                                       int32_t e, int gl, const XT *x) {
+                                       int32_t e, int gl, const XT *x, int32_t off = 0) {
     ACC acc = ACC(0);
     for (int32_t base = s + gl; base < e; base += kBatch * G) {
         int32_t c[kBatch];
@@ -1086,7 +1109,10 @@ __device__ __forceinline__ ACC clu_dot(const int32_t *__restrict__ idx, const VT
         }
         XT g[kBatch];
 #pragma unroll
-        for (int u = 0; u < kBatch; ++u) g[u] = base + u * G < e ? __ldcg(x + c[u]) : XT(0);
+        for (int u = 0; u < kBatch; ++u) {
+            if constexpr (SH) g[u] = base + u * G < e ? x[c[u] - off] : XT(0);
+            else g[u] = base + u * G < e ? __ldcg(x + c[u]) : XT(0);
+        }
 #pragma unroll
         for (int u = 0; u < kBatch; ++u)
             if (base + u * G < e) acc = fma_t(ACC(v[u]), ACC(g[u]), acc);
@@ -1096,9 +1122,17 @@ __device__ __forceinline__ ACC clu_dot(const int32_t *__restrict__ idx, const VT
     return acc;
 }
 
-template <int G, typename S>
+// The shared-memory copies of the RES form: r of the system's rows (offset
+// R0) and p of its columns (offset C0); null pointers in the plain form.
+template <typename S>
+struct CluVecs {
+    S *r = nullptr, *p = nullptr;
+    int32_t R0 = 0, C0 = 0;
+};
+
+template <int G, typename S, bool RES>
 __device__ __forceinline__ void clu_row(const SweepArgs &a, int32_t r0, int32_t r1, bool init, double &acc_r,
-                                        double &acc_b) {
+                                        double &acc_b, const CluVecs<S> &sv) {
     const S *__restrict__ val = static_cast<const S *>(a.val);
     S *r = static_cast<S *>(a.r);
     clu_segments<G>(a.row_ptr, r0, r1, [&](int32_t row, int32_t s, int32_t e, int gl, bool valid) {
@@ -1108,25 +1142,32 @@ __device__ __forceinline__ void clu_row(const SweepArgs &a, int32_t r0, int32_t 
                 const double bi = a.b[row];
                 const S ri = S(bi - d);
                 r[row] = ri;
+                if constexpr (RES) dsmem_store_all(sv.r + (row - sv.R0), ri);
                 acc_r = fma(double(ri), double(ri), acc_r);
                 acc_b = fma(bi, bi, acc_b);
             }
         } else {
-            const S d = clu_dot<G, S, S, S>(a.col_idx, val, s, e, gl, static_cast<const S *>(a.p));
+            S d;
+            if constexpr (RES) d = clu_dot<G, S, S, S, true>(a.col_idx, val, s, e, gl, sv.p, sv.C0);
+            else d = clu_dot<G, S, S, S>(a.col_idx, val, s, e, gl, static_cast<const S *>(a.p));
             if (valid && gl == 0) {
-                const S ri = r[row] - d;
+                const S ri = (RES ? sv.r[row - sv.R0] : r[row]) - d;
                 r[row] = ri;
+                if constexpr (RES) dsmem_store_all(sv.r + (row - sv.R0), ri);
                 acc_r = fma(double(ri), double(ri), acc_r);
             }
         }
     });
 }
 
-template <int G, typename S>
-__device__ __forceinline__ void clu_col(const SweepArgs &a, int32_t c0, int32_t c1, double &acc) {
+template <int G, typename S, bool RES>
+__device__ __forceinline__ void clu_col(const SweepArgs &a, int32_t c0, int32_t c1, double &acc,
+                                        const CluVecs<S> &sv) {
     const S *__restrict__ val = static_cast<const S *>(a.cval);
     clu_segments<G>(a.col_ptr, c0, c1, [&](int32_t col, int32_t s, int32_t e, int gl, bool valid) {
-        const S y = clu_dot<G, S, S, S>(a.row_idx, val, s, e, gl, static_cast<const S *>(a.r));
+        S y;
+        if constexpr (RES) y = clu_dot<G, S, S, S, true>(a.row_idx, val, s, e, gl, sv.r, sv.R0);
+        else y = clu_dot<G, S, S, S>(a.row_idx, val, s, e, gl, static_cast<const S *>(a.r));
         if (valid && gl == 0) {
             if constexpr (std::is_same<S, float>::value) {
                 const float uj = a.wf ? __fmul_rn(a.wf[col], y) : y;
@@ -1146,8 +1187,9 @@ __device__ __forceinline__ int clu_group(int64_t nnz, int64_t segs) {
     return g;
 }
 
-template <typename S>
+template <typename S, bool RES>
 __global__ void __launch_bounds__(kClusterThreads) k_cluster_solve(SweepArgs a, int32_t bodies) {
+    extern __shared__ __align__(16) unsigned char clu_dyn[];   // RES: r copy, then p copy
     __shared__ SysState sst;           // this CTA's copy of the system state
     // this CTA's partials (phi, theta, rho, ||b||^2), one set per parity of
     // the body: a CTA rewrites a set only after a barrier that every CTA
@@ -1170,6 +1212,19 @@ __global__ void __launch_bounds__(kClusterThreads) k_cluster_solve(SweepArgs a, 
         if (rank != 0) sst.hist = nullptr;
     }
     if (rank != 0) al.n_active = &done_local;
+    CluVecs<S> sv;
+    if constexpr (RES) {
+        sv.r = reinterpret_cast<S *>(clu_dyn);
+        sv.p = sv.r + d.m;
+        sv.R0 = R0;
+        sv.C0 = C0;
+        const S *gr_ = static_cast<const S *>(a.r);
+        const S *gp_ = static_cast<const S *>(a.p);
+        for (int32_t i = threadIdx.x; i < d.m; i += kClusterThreads) sv.r[i] = __ldcg(gr_ + R0 + i);
+        for (int32_t j = threadIdx.x; j < d.n; j += kClusterThreads) sv.p[j] = __ldcg(gp_ + C0 + j);
+        // no CTA writes into another's copies before that one has loaded them
+        cluster_barrier();
+    }
     __syncthreads();
     SysState *st = &sst;
     // sum of partial q over the cluster, in rank order (the same in every CTA)
@@ -1186,12 +1241,12 @@ __global__ void __launch_bounds__(kClusterThreads) k_cluster_solve(SweepArgs a, 
         if (ph == PH_FIRST || ph == PH_RUN) {
             double w1[1] = {0.0};
             switch (gc) {
-                case 1: clu_col<1, S>(al, c0, c1, w1[0]); break;
-                case 2: clu_col<2, S>(al, c0, c1, w1[0]); break;
-                case 4: clu_col<4, S>(al, c0, c1, w1[0]); break;
-                case 8: clu_col<8, S>(al, c0, c1, w1[0]); break;
-                case 16: clu_col<16, S>(al, c0, c1, w1[0]); break;
-                default: clu_col<32, S>(al, c0, c1, w1[0]); break;
+                case 1: clu_col<1, S, RES>(al, c0, c1, w1[0], sv); break;
+                case 2: clu_col<2, S, RES>(al, c0, c1, w1[0], sv); break;
+                case 4: clu_col<4, S, RES>(al, c0, c1, w1[0], sv); break;
+                case 8: clu_col<8, S, RES>(al, c0, c1, w1[0], sv); break;
+                case 16: clu_col<16, S, RES>(al, c0, c1, w1[0], sv); break;
+                default: clu_col<32, S, RES>(al, c0, c1, w1[0], sv); break;
             }
             clu_block_sum<1>(w1);
             if (threadIdx.x == 0) part[0] = w1[0];
@@ -1206,14 +1261,16 @@ __global__ void __launch_bounds__(kClusterThreads) k_cluster_solve(SweepArgs a, 
                 const S *u = static_cast<const S *>(a.u);
                 for (int32_t j = c0 + threadIdx.x; j < c1; j += kClusterThreads) {
                     S ps;
+                    const S pj = first ? S(0) : (RES ? sv.p[j - C0] : p[j]);
                     if constexpr (std::is_same<S, float>::value) {
                         const float bf = float(beta), gf = float(gamma);
-                        ps = first ? gf * u[j] : fmaf(bf, p[j], gf * u[j]);
+                        ps = first ? gf * u[j] : fmaf(bf, pj, gf * u[j]);
                     } else {
                         const double gu = gamma * u[j];
-                        ps = first ? gu : fma(beta, p[j], gu);
+                        ps = first ? gu : fma(beta, pj, gu);
                     }
                     p[j] = ps;
+                    if constexpr (RES) dsmem_store_all(sv.p + (j - C0), ps);
                     const double pd = double(ps);
                     if constexpr (std::is_same<S, float>::value)
                         acc[0] = fma(pd, a.winvf ? double(__fmul_rn(ps, a.winvf[j])) : pd, acc[0]);
@@ -1233,12 +1290,12 @@ __global__ void __launch_bounds__(kClusterThreads) k_cluster_solve(SweepArgs a, 
             const bool init = ph == PH_SETUP;
             double w2[2] = {0.0, 0.0};
             switch (gr) {
-                case 1: clu_row<1, S>(al, r0, r1, init, w2[0], w2[1]); break;
-                case 2: clu_row<2, S>(al, r0, r1, init, w2[0], w2[1]); break;
-                case 4: clu_row<4, S>(al, r0, r1, init, w2[0], w2[1]); break;
-                case 8: clu_row<8, S>(al, r0, r1, init, w2[0], w2[1]); break;
-                case 16: clu_row<16, S>(al, r0, r1, init, w2[0], w2[1]); break;
-                default: clu_row<32, S>(al, r0, r1, init, w2[0], w2[1]); break;
+                case 1: clu_row<1, S, RES>(al, r0, r1, init, w2[0], w2[1], sv); break;
+                case 2: clu_row<2, S, RES>(al, r0, r1, init, w2[0], w2[1], sv); break;
+                case 4: clu_row<4, S, RES>(al, r0, r1, init, w2[0], w2[1], sv); break;
+                case 8: clu_row<8, S, RES>(al, r0, r1, init, w2[0], w2[1], sv); break;
+                case 16: clu_row<16, S, RES>(al, r0, r1, init, w2[0], w2[1], sv); break;
+                default: clu_row<32, S, RES>(al, r0, r1, init, w2[0], w2[1], sv); break;
             }
             clu_block_sum<2>(w2);
             if (threadIdx.x == 0) {
@@ -1381,10 +1438,12 @@ cudaError_t launch_update(const SweepArgs &a, bool f32, int grid, cudaStream_t s
     return f32 ? launch_pdl(k_update<float>, grid, s, a) : launch_pdl(k_update<double>, grid, s, a);
 }
 
-cudaError_t launch_cluster_solve(const SweepArgs &a, bool f32, int32_t nsys, int32_t bodies, cudaStream_t s) {
+cudaError_t launch_cluster_solve(const SweepArgs &a, bool f32, int32_t nsys, int32_t bodies, int32_t vec_bytes,
+                                 cudaStream_t s) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(unsigned(nsys) * kClusterCtas);
     cfg.blockDim = dim3(kClusterThreads);
+    cfg.dynamicSmemBytes = size_t(vec_bytes > 0 ? vec_bytes : 0);
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -1393,8 +1452,16 @@ cudaError_t launch_cluster_solve(const SweepArgs &a, bool f32, int32_t nsys, int
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return f32 ? cudaLaunchKernelEx(&cfg, k_cluster_solve<float>, a, bodies)
-               : cudaLaunchKernelEx(&cfg, k_cluster_solve<double>, a, bodies);
+    if (vec_bytes <= 0)
+        return f32 ? cudaLaunchKernelEx(&cfg, k_cluster_solve<float, false>, a, bodies)
+                   : cudaLaunchKernelEx(&cfg, k_cluster_solve<double, false>, a, bodies);
+    cudaError_t e = f32 ? cudaFuncSetAttribute(k_cluster_solve<float, true>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, vec_bytes)
+                        : cudaFuncSetAttribute(k_cluster_solve<double, true>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, vec_bytes);
+    if (e != cudaSuccess) return e;
+    return f32 ? cudaLaunchKernelEx(&cfg, k_cluster_solve<float, true>, a, bodies)
+               : cudaLaunchKernelEx(&cfg, k_cluster_solve<double, true>, a, bodies);
 }
 
 cudaError_t launch_spmv(const int32_t *ptr, const int32_t *idx, const void *val, bool f32,

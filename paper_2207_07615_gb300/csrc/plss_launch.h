@@ -17,7 +17,12 @@ cudaError_t launch_update(const SweepArgs &a, bool f32, int grid, cudaStream_t s
 
 // Small systems: one cluster of 8 CTAs per system of the context runs up to
 // `bodies` bodies of the recursion (column sweep, update, row sweep).
-cudaError_t launch_cluster_solve(const SweepArgs &a, bool f32, int32_t nsys, int32_t bodies, cudaStream_t s);
+// vec_bytes > 0: every CTA keeps copies of r and p in that many bytes of
+// shared memory (at least (m + n) x the storage size of the largest system;
+// at most kClusterVecBytes); 0: the vectors are read from global memory.
+constexpr int32_t kClusterVecBytes = 128 * 1024;
+cudaError_t launch_cluster_solve(const SweepArgs &a, bool f32, int32_t nsys, int32_t bodies, int32_t vec_bytes,
+                                 cudaStream_t s);
 
 // Resident CTAs per SM of a sweep kernel (0 row, 1 column, 2 update, 3 row
 // and 4 column over warp ranges).
