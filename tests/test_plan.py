@@ -147,6 +147,13 @@ def test_plan_invariants(shim, name, f32, slice_, shift):
     if len(tiles) and np.all(tiles[:, 3] & K_SLICED):
         assert len(wr) == 64 + 1 and wr[0] == 0 and wr[-1] == len(sl_ptr) - 1
         assert np.all(np.diff(wr) >= 0)
+        # balance: a slice costs its elements plus 256 (offsets, slot map,
+        # results); no warp gets more than an equal share plus one slice
+        cost = np.diff(sl_ptr).astype(np.int64) + 256
+        prefix = np.concatenate([[0], np.cumsum(cost)])
+        share = -(-int(prefix[-1]) // 64)
+        per_warp = prefix[wr[1:]] - prefix[wr[:-1]]
+        assert per_warp.max() <= share + (cost.max() if len(cost) else 0)
     else:
         assert len(wr) == 0
 
