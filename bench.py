@@ -109,15 +109,29 @@ def measured_peaks():
 
 
 def kernels_hash(path):
-    """sha256[:16] of the kernel source with comments and blank lines removed
-    (a comment edit does not invalidate recorded counters)."""
+    """sha256[:16] of the code of the grid-wide sweeps in plss_kernels.cu:
+    the file with comments and blank lines removed (a comment edit does not
+    invalidate recorded counters), cut to the lines before the cluster
+    solver (the sweeps, the update and their helpers) plus the launchers from
+    sweep_ctas_per_sm up to the cluster launcher -- everything the C2 sweeps
+    and update are built and launched from, and nothing else. The whole
+    file's code when those markers are missing."""
     import hashlib
     import re
     text = open(path, encoding="utf-8").read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     lines = [re.sub(r"//.*$", "", ln).rstrip() for ln in text.splitlines()]
-    code = "\n".join(ln for ln in lines if ln.strip())
-    return hashlib.sha256(code.encode()).hexdigest()[:16]
+    lines = [ln for ln in lines if ln.strip()]
+    try:
+        a = next(i for i, ln in enumerate(lines) if "kClusterCtas" in ln)
+        b = next(i for i, ln in enumerate(lines) if "int sweep_ctas_per_sm(int which" in ln)
+        c = next(i for i, ln in enumerate(lines)
+                 if ln.startswith("cudaError_t launch_cluster_solve("))
+        if a < b < c:
+            lines = lines[:a] + lines[b:c]
+    except StopIteration:
+        pass
+    return hashlib.sha256("\n".join(lines).encode()).hexdigest()[:16]
 
 
 def ncu_traffic(kernel):
