@@ -44,7 +44,8 @@ typedef enum {
     PLSS_ERR_NOMEM = -2,      /* device or host allocation failed           */
     PLSS_ERR_CUDA = -3,       /* a CUDA runtime call failed                 */
     PLSS_ERR_BREAKDOWN = -4,  /* recursion broke down (see plss_solve)      */
-    PLSS_ERR_TIMEOUT = -5,    /* a bounded device wait expired              */
+    PLSS_ERR_TIMEOUT = -5,    /* the iteration driver ran more bodies than  */
+                              /* 2 (maxit + 2) + 8 allow (a safety bound)  */
     PLSS_ERR_BUSY = -6,       /* server queue full / admission refused      */
     PLSS_ERR_NOT_FOUND = -7   /* unknown ticket                             */
 } plss_status;
@@ -74,8 +75,10 @@ enum { PLSS_LAYOUT_AUTO = 0, PLSS_LAYOUT_CSR = 1 };
  * most 2^20 nonzeros, one thread-block cluster of 8 CTAs per system runs
  * whole iterations, its CTAs meeting at cluster barriers and exchanging
  * partial sums through distributed shared memory (no kernel boundaries
- * between the sweeps; plss_kernel_times then records nothing); otherwise as
- * GRID. AUTO: SMALL when it fits and every system has at most 65,536
+ * between the sweeps; plss_kernel_times then records nothing); when the
+ * largest system's m + n vector entries take at most 128 KB in the storage
+ * type, every CTA also keeps copies of r and p in its shared memory for the
+ * sweeps' gathers (same arithmetic); otherwise as GRID. AUTO: SMALL when it fits and every system has at most 65,536
  * nonzeros or the systems are at least 1/8 as many as the SMs; else GRID.
  * The schedules reduce in different orders: their iterates agree to
  * rounding, not bit for bit. */
@@ -146,8 +149,10 @@ typedef struct plss_ctx plss_ctx;
 void plss_opts_default(plss_opts *o);
 
 /* Copies A to the device, validates it, builds its transpose (unless
- * o->symmetric) and the tile schedule of the sparse sweeps. The storage
- * precision is o->precision. On error *out is NULL. */
+ * o->symmetric) and the tile schedule of the sparse sweeps (o->layout,
+ * o->tile_shift). The storage precision is o->precision. A malformed CSR,
+ * an unknown precision or layout, or tile_shift outside [-2, 2] returns
+ * PLSS_ERR_INVALID before any device work. On error *out is NULL. */
 plss_status plss_create(const plss_csr *A, const plss_opts *o, plss_ctx **out);
 
 /* As plss_create for nsys independent systems As[0..nsys-1], packed into one
