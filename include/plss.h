@@ -152,7 +152,8 @@ void plss_opts_default(plss_opts *o);
  * o->symmetric) and the tile schedule of the sparse sweeps (o->layout,
  * o->tile_shift). The storage precision is o->precision. A malformed CSR,
  * an unknown precision or layout, or tile_shift outside [-2, 2] returns
- * PLSS_ERR_INVALID before any device work. On error *out is NULL. */
+ * PLSS_ERR_INVALID with nothing allocated on the device. On error *out is
+ * NULL. */
 plss_status plss_create(const plss_csr *A, const plss_opts *o, plss_ctx **out);
 
 /* As plss_create for nsys independent systems As[0..nsys-1], packed into one
