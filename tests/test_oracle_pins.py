@@ -340,3 +340,49 @@ def test_fp32_storage_with_refinement_reaches_1e8():
     assert out["status"] == "converged"
     assert out["relres_true"] <= 1e-8
     assert rel(out["x"], ref["x"]) < 1e-5
+
+
+def test_fp32_first_update_within_float_error_bounds():
+    """The FP32-storage mode (an extension, not in the paper) against the
+    FP64 mode on the first update, with the textbook error bounds of float
+    arithmetic (unit roundoff u = 2^-24; a float sum of k products of floats
+    is within gamma_k = k u / (1 - k u) times the sum of their magnitudes):
+    r_0 = fl(b) changes rho_0 by at most 2u(1+u) rho_0; each y_j = (A^T r_0)_j
+    summed in float is within (gamma_{n_j} (1 + u) + u) sum_i |a_ij b_i| of
+    the exact value; phi_1 = y^T y, gamma_1 = rho_0 / phi_1 and
+    theta_1 = ||fl(gamma_1 y)||^2 follow with their first-order bounds. The
+    differences must also be well above double rounding, so that a mode
+    that kept everything in double fails."""
+    A, b, xs = synth.overdetermined_scaled(m=3000, n=600, per_row=8, seed=21, scale_decades=1.0)
+    A = A.astype(np.float64)                        # values already float-exact
+    assert np.array_equal(A.val, A.val.astype(np.float32).astype(np.float64))
+    r64 = oracle.residual(A, b, tol=0.0, maxit=1, hist=1)
+    r32 = oracle.residual(A, b, tol=0.0, maxit=1, prec=1, hist=1)
+    rho64, phi64, _, gam64, th64 = r64["hist_s"][0]
+    rho32, phi32, _, gam32, th32 = r32["hist_s"][0]
+    u = 2.0 ** -24
+    S = A.scipy()
+    nj = np.diff(S.tocsc().indptr)                  # products summed per column
+    g = nj * u / (1 - nj * u)
+    absAb = abs(S).T @ np.abs(b)                    # sum_i |a_ij| |b_i|
+    y = S.T @ b                                     # exact to double rounding
+    E = (g * (1 + u) + u) * absAb + 1e-12 * absAb   # |y32_j - y_j|, plus double slack
+    # rho_0
+    assert abs(rho32 - rho64) <= (2 * u * (1 + u) + 1e-12) * rho64
+    # phi_1 = sum y_j^2 (u = W y = y)
+    dphi = float(np.sum(E * (2 * np.abs(y) + E)))
+    assert abs(phi32 - phi64) <= dphi * (1 + 1e-6) + 1e-12 * phi64
+    # gamma_1 = rho_0 / phi_1
+    rel_rho = 2 * u * (1 + u) + 1e-12
+    rel_phi = dphi / (phi64 - dphi)
+    rel_gam = rel_rho + rel_phi + rel_rho * rel_phi + 1e-12
+    assert abs(gam32 - gam64) <= rel_gam * abs(gam64)
+    # theta_1 = sum fl(gamma_1 y_j)^2 against sum (gamma_1 y_j)^2
+    dp = abs(gam32 - gam64) * (np.abs(y) + E) + abs(gam64) * E
+    p64 = gam64 * y
+    dp = dp + u * (np.abs(p64) + dp)                # the float rounding of p
+    dth = float(np.sum(dp * (2 * np.abs(p64) + dp)))
+    assert abs(th32 - th64) <= dth * (1 + 1e-6) + 1e-12 * th64
+    # float arithmetic, not double, was used
+    for a32, a64 in ((rho32, rho64), (phi32, phi64), (gam32, gam64), (th32, th64)):
+        assert abs(a32 - a64) > 1e-4 * u * abs(a64)
