@@ -158,3 +158,18 @@ def test_tune_rejects_bad_arguments(L):
              (C.byref(c), 1, 5, C.byref(best), ent, 4, None)]
     for As, nsys, upd, b, e, cap, n in cases:
         assert L.plss_tune(As, nsys, None, upd, b, e, cap, n) == plss.ERR_INVALID
+
+
+def test_binding_marshals_names_and_vectors(L):
+    """The binding only translates: enum names to the header's values, host
+    vectors to contiguous float64 of the stated length (else ValueError)."""
+    o = plss.make_opts(sketch="identity", precision="fp32", layout="csr", schedule="small", tile_shift=-1,
+                       tol=1e-6)
+    assert (o.sketch, o.precision, o.layout, o.schedule, o.tile_shift, o.tol) == (1, 1, 1, 2, -1, 1e-6)
+    assert o.inner_tol == 1e-4 and o.maxit == -1                 # untouched fields keep their defaults
+    v = plss._vec_in([1, 2, 3], 3, "b", False)
+    assert v.dtype == np.float64 and v.flags.c_contiguous and list(v) == [1.0, 2.0, 3.0]
+    with pytest.raises(ValueError):
+        plss._vec_in(np.zeros(4), 3, "b", False)
+    r = plss.Result(status=-4, iters=7, relres_rec=0.5, relres_true=0.25, seconds=1.0).as_dict()
+    assert r["status"] == "breakdown" and r["code"] == -4 and r["iters"] == 7
