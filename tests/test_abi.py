@@ -173,3 +173,25 @@ def test_binding_marshals_names_and_vectors(L):
         plss._vec_in(np.zeros(4), 3, "b", False)
     r = plss.Result(status=-4, iters=7, relres_rec=0.5, relres_true=0.25, seconds=1.0).as_dict()
     assert r["status"] == "breakdown" and r["code"] == -4 and r["iters"] == 7
+
+
+def test_server_rejects_bad_arguments(L):
+    """Server entry points refuse bad arguments before touching a device."""
+    so = plss.ServerOpts()
+    L.plss_server_opts_default(C.byref(so))
+    assert (so.max_slots, so.max_queue, so.bodies_per_poll, so.layout) == (64, 4096, 8, plss.LAYOUT["csr"])
+    h = C.c_void_p()
+    assert L.plss_server_create(C.byref(so), None) == plss.ERR_INVALID
+    for field, bad in (("max_slots", 0), ("max_queue", 0), ("bodies_per_poll", 0), ("precision", 9),
+                       ("layout", 4)):
+        o = plss.ServerOpts()
+        L.plss_server_opts_default(C.byref(o))
+        setattr(o, field, bad)
+        assert L.plss_server_create(C.byref(o), C.byref(h)) == plss.ERR_INVALID, field
+        assert not h.value
+    t = C.c_uint64()
+    res = plss.Result()
+    assert L.plss_submit(None, None, None, None, None, C.byref(t)) == plss.ERR_INVALID
+    assert L.plss_poll(None, 1, None, C.byref(res)) == plss.ERR_INVALID
+    assert L.plss_server_stats(None, None, None, None, None) == plss.ERR_INVALID
+    L.plss_server_destroy(None)                                   # a no-op
