@@ -195,3 +195,13 @@ def test_server_rejects_bad_arguments(L):
     assert L.plss_poll(None, 1, None, C.byref(res)) == plss.ERR_INVALID
     assert L.plss_server_stats(None, None, None, None, None) == plss.ERR_INVALID
     L.plss_server_destroy(None)                                   # a no-op
+
+
+def test_context_calls_refuse_a_null_context(L):
+    assert L.plss_solve_rhs(None, 1, None, None, None, None, None) == plss.ERR_INVALID
+    assert L.plss_solve_batched(None, None, None, None, None, None) == plss.ERR_INVALID
+    assert L.plss_spmv(None, 0, None, None, None) == plss.ERR_INVALID
+    assert L.plss_kernel_times(None, None, None, 0) == plss.ERR_INVALID
+    assert L.plss_ctx_info(None, None, None, None, None) == plss.ERR_INVALID
+    assert L.plss_ctx_layout(None, None) == plss.ERR_INVALID
+    L.plss_destroy(None)                                          # a no-op
