@@ -205,3 +205,17 @@ def test_context_calls_refuse_a_null_context(L):
     assert L.plss_ctx_info(None, None, None, None, None) == plss.ERR_INVALID
     assert L.plss_ctx_layout(None, None) == plss.ERR_INVALID
     L.plss_destroy(None)                                          # a no-op
+
+
+def test_noalloc_residual_checks_sizes_first(L):
+    """plss_residual_noalloc refuses negative sizes, more rows than its static
+    scratch covers, and NULL arrays, with nothing launched."""
+    n2 = (C.c_double * 1)()
+    rp = np.zeros(2, dtype=np.int64)
+    f = L.plss_residual_noalloc
+    assert f(-1, 1, 0, rp.ctypes.data, None, None, None, None, None, n2, None) == plss.ERR_INVALID
+    assert f(4_194_305, 1, 0, rp.ctypes.data, None, None, None, None, None, n2, None) == plss.ERR_INVALID
+    assert "4194304" in L.plss_last_error().decode()
+    assert f(1, 1, 0, None, None, None, None, None, None, n2, None) == plss.ERR_INVALID
+    assert f(1, 1, 0, rp.ctypes.data, None, None, None, None, None, None, None) == plss.ERR_INVALID
+    assert f(1, 1, 1, rp.ctypes.data, None, None, None, None, None, n2, None) == plss.ERR_INVALID
