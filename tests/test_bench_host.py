@@ -56,7 +56,3 @@ def test_counters_follow_the_sweep_code(tmp_path, monkeypatch):
     # no record: None
     shutil.rmtree(os.path.join(str(tmp_path / "d"), "profiles"))
     assert bench.ncu_traffic("col_sweep") is None
-
-
-def test_single_process_max_over_ranks_is_the_value():
-    assert bench.max_over_ranks(3.5, None) == 3.5
