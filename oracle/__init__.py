@@ -51,7 +51,7 @@ def _load():
                                                  vp]
             lib.plss_oracle_kaczmarz.restype = i32
             lib.plss_oracle_kaczmarz.argtypes = [i64, i64, vp, vp, vp, vp, vp, d, i64, i64, u64,
-                                                 vp, vp, vp, vp]
+                                                 i32, vp, vp, vp, vp]
             lib.plss_oracle_spmv.restype = None
             lib.plss_oracle_spmv.argtypes = [i64, vp, vp, vp, vp, vp]
             lib.plss_oracle_spmvt.restype = i32
@@ -122,11 +122,13 @@ def permutation(state: int, m: int):
 
 
 def residual(A, b, x0=None, w=None, tol=1e-10, maxit=None, prec=0, refine=0, inner_tol=0.0,
-             stop_on_true=False, gamma_form=0, hist=0):
+             stop_on_true=False, gamma_form=0, hist=0, plant=0):
     """PLSS residual sketch (Algorithm 1). Returns a dict with x, iters,
     status, relres_rec, relres_true and, when hist > 0, the per-update
     history: s[k] = (rho_k, phi_{k+1}, beta_k, gamma_k, theta_{k+1}),
-    x[k] = x_{k+1}, p[k] = p_{k+1}, y[k] = A^T r_k, r[k] = r_k."""
+    x[k] = x_{k+1}, p[k] = p_{k+1}, y[k] = A^T r_k, r[k] = r_k.
+    gamma_form=1 (same as plant=1) and plant=2/3 plant a defect for the
+    tests that show the pins reject it (see plss_oracle.c)."""
     lib = _load()
     rp, ci, val = _csr(A)
     b = _vec(b, A.m, "b")
@@ -146,7 +148,8 @@ def residual(A, b, x0=None, w=None, tol=1e-10, maxit=None, prec=0, refine=0, inn
     hr = np.zeros((H + 1, A.m)) if H else None
     st = lib.plss_oracle_residual(A.m, A.n, _p(rp), _p(ci), _p(val), _p(b), _p(x0), _p(w),
                                   float(tol), int(maxit), int(prec), int(refine), float(inner_tol),
-                                  int(bool(stop_on_true)), int(gamma_form), _p(x), _p(it),
+                                  int(bool(stop_on_true)), 1 if gamma_form == 1 else int(plant),
+                                  _p(x), _p(it),
                                   _p(rr), _p(rt), H, _p(hs), _p(hx), _p(hp), _p(hy), _p(hr))
     if st == -2:
         raise MemoryError("oracle residual")
@@ -159,8 +162,10 @@ def residual(A, b, x0=None, w=None, tol=1e-10, maxit=None, prec=0, refine=0, inn
     return out
 
 
-def kaczmarz(A, b, x0=None, tol=1e-8, maxit=None, K=0, seed=0):
-    """PLSS Kaczmarz (identity sketch, eq:pkKacz) with history cap K."""
+def kaczmarz(A, b, x0=None, tol=1e-8, maxit=None, K=0, seed=0, plant=0):
+    """PLSS Kaczmarz (identity sketch, eq:pkKacz) with history cap K.
+    plant=1/2/3 plants a wrong window reset (late, early, never) for the
+    tests that show the pins reject it (see plss_oracle.c)."""
     lib = _load()
     rp, ci, val = _csr(A)
     b = _vec(b, A.m, "b")
@@ -172,7 +177,8 @@ def kaczmarz(A, b, x0=None, tol=1e-8, maxit=None, K=0, seed=0):
     sk = np.zeros(1, dtype=np.int64)
     rt = np.zeros(1)
     st = lib.plss_oracle_kaczmarz(A.m, A.n, _p(rp), _p(ci), _p(val), _p(b), _p(x0), float(tol),
-                                  int(maxit), int(K), int(seed) & (2**64 - 1), _p(x), _p(it),
+                                  int(maxit), int(K), int(seed) & (2**64 - 1), int(plant),
+                                  _p(x), _p(it),
                                   _p(sk), _p(rt))
     if st == -2:
         raise MemoryError("oracle kaczmarz")

@@ -19,8 +19,7 @@
  * Readings where the paper is silent or inconsistent (all listed in the
  * design notes of the repository):
  *   - gamma: Algorithm 1's gamma = (theta/rho) * beta. The closed form in the
- *     statement of Theorem 4.1 differs by a factor rho; gamma_form = 1 plants
- *     that statement form, for tests that show the pins reject it.
+ *     statement of Theorem 4.1 differs by a factor rho.
  *   - stopping: stop when sqrt(rho)/||b|| <= tol, tested right after rho is
  *     formed (Sec. 5 suggests sqrt(rho)/||b|| < tau); maxit caps the number
  *     of updates p applied to x; the residual of the returned x is always
@@ -48,6 +47,14 @@
  *     row's direction q = p / gamma (the same projector), so a row with
  *     r_i = 0 still enters it and the window schedule does not depend on
  *     rounding in b - A x.
+ *
+ * Planted defects (argument `plant`, 0 in every real use): the pins of the
+ * test suite must reject each of them, which shows that they can see such a
+ * mistake. Residual sketch: 1 = the statement form of gamma, 2 = the drift
+ * restart at 2x instead of 4x the starting rho, 3 = the inner-solve restart
+ * at inner_tol instead of inner_tol^2. Identity sketch: 1 = the window is
+ * emptied one row late (K + 1 directions), 2 = one row early (K - 1),
+ * 3 = never (the whole history is kept).
  */
 #include <math.h>
 #include <stdint.h>
@@ -185,7 +192,7 @@ static void true_residual(int64_t m, const int64_t *row_ptr, const int32_t *col_
  * restart from b - A x once rho has fallen by inner_tol^2 since the last
  * start (the inner solve of iterative refinement; 0 = never), stop_on_true:
  * the stop decision uses the residual b - A x recomputed in double,
- * gamma_form 0 = Algorithm 1, 1 = the statement form (planted defect).
+ * plant = a planted defect (see the file header; 0 = none).
  * Outputs: x_out[n], *iters (updates applied), *relres_rec (sqrt(rho)/||b||
  * of the last rho), *relres_true (||b - A x||/||b||), return value = status.
  * Optional history (any pointer may be NULL; hist_cap rows):
@@ -197,7 +204,7 @@ static void true_residual(int64_t m, const int64_t *row_ptr, const int32_t *col_
 int plss_oracle_residual(int64_t m, int64_t n, const int64_t *row_ptr, const int32_t *col_idx,
                          const double *val_in, const double *b, const double *x0, const double *w,
                          double tol, int64_t maxit, int prec, int64_t refine, double inner_tol,
-                         int stop_on_true, int gamma_form, double *x_out, int64_t *iters_out,
+                         int stop_on_true, int plant, double *x_out, int64_t *iters_out,
                          double *relres_rec,
                          double *relres_true, int64_t hist_cap, double *hist_s, double *hist_x,
                          double *hist_p, double *hist_y, double *hist_r)
@@ -249,7 +256,8 @@ int plss_oracle_residual(int64_t m, int64_t n, const int64_t *row_ptr, const int
         }
         if (k >= maxit) { status = ORC_NOT_CONVERGED; break; }
         if (!restart && inner_tol > 0.0 &&
-            (rho <= inner_tol * inner_tol * rho_start || rho > 4.0 * rho_start)) {
+            (rho <= (plant == 3 ? inner_tol : inner_tol * inner_tol) * rho_start ||
+             rho > (plant == 2 ? 2.0 : 4.0) * rho_start)) {
             /* inner solve done (residual reduced by inner_tol since the last
              * start), or the float recursion has drifted above twice its
              * starting residual: refine from b - A x */
@@ -296,7 +304,7 @@ int plss_oracle_residual(int64_t m, int64_t n, const int64_t *row_ptr, const int
                 continue;
             }
             beta = 1.0 / d;
-            if (gamma_form == 1)
+            if (plant == 1)
                 gamma = theta / (theta * phi - rho * rho);   /* statement form */
             else
                 gamma = (theta / rho) * beta;                /* Algorithm 1 */
@@ -390,18 +398,24 @@ void plss_oracle_permutation(uint64_t *state, int64_t m, int32_t *perm)
  * row with r_i = 0 (p = 0) still enters the window with its direction.
  * With K = 0 (no history) this is the classical Kaczmarz step.
  * maxit caps the rows visited; after every full pass over the rows the
- * residual ||b - A x||/||b|| is tested against tol.
+ * residual ||b - A x||/||b|| is tested against tol. `plant` != 0 plants a
+ * wrong window reset (see the file header).
  * Outputs: x_out, *iters (rows visited), *n_skipped, *relres_true; returns status.
  */
 int plss_oracle_kaczmarz(int64_t m, int64_t n, const int64_t *row_ptr, const int32_t *col_idx,
                          const double *val, const double *b, const double *x0, double tol,
-                         int64_t maxit, int64_t K, uint64_t seed, double *x_out,
+                         int64_t maxit, int64_t K, uint64_t seed, int plant, double *x_out,
                          int64_t *iters_out, int64_t *n_skipped, double *relres_true)
 {
     double *x = x_out;
-    double *P = (double *)malloc((size_t)((K > 0 ? K : 1) * (n ? n : 1)) * sizeof(double));
-    double *th = (double *)malloc((size_t)(K > 0 ? K : 1) * sizeof(double));
-    double *c = (double *)malloc((size_t)(K > 0 ? K : 1) * sizeof(double));
+    /* window capacity: K, or the planted wrong one */
+    int64_t cap = K;
+    if (K > 0 && plant == 1) cap = K + 1;
+    if (K > 1 && plant == 2) cap = K - 1;
+    if (K > 0 && plant == 3) cap = maxit > 0 ? maxit : 1;
+    double *P = (double *)malloc((size_t)((cap > 0 ? cap : 1) * (n ? n : 1)) * sizeof(double));
+    double *th = (double *)malloc((size_t)(cap > 0 ? cap : 1) * sizeof(double));
+    double *c = (double *)malloc((size_t)(cap > 0 ? cap : 1) * sizeof(double));
     double *p = (double *)malloc((size_t)(n ? n : 1) * sizeof(double));
     double *rt = (double *)malloc((size_t)(m ? m : 1) * sizeof(double));
     int32_t *perm = (int32_t *)malloc((size_t)(m ? m : 1) * sizeof(int32_t));
@@ -422,7 +436,7 @@ int plss_oracle_kaczmarz(int64_t m, int64_t n, const int64_t *row_ptr, const int
         for (int64_t t = 0; t < m && k < maxit; ++t, ++k) {
             int64_t i = perm[t];
             int64_t s0 = row_ptr[i], s1 = row_ptr[i + 1];
-            if (K > 0 && nh == K) nh = 0;   /* window full: restart it empty */
+            if (cap > 0 && nh == cap) nh = 0;   /* window full: restart it empty */
             /* r_i = b_i - a_i^T x */
             double ax = 0.0, a2 = 0.0;
             for (int64_t q = s0; q < s1; ++q) ax += val[q] * x[col_idx[q]];
@@ -452,7 +466,7 @@ int plss_oracle_kaczmarz(int64_t m, int64_t n, const int64_t *row_ptr, const int
                 thn += p[jj] * p[jj];
                 x[jj] += gamma * p[jj];
             }
-            if (K > 0 && thn > 0.0) {
+            if (cap > 0 && thn > 0.0) {
                 memcpy(P + nh * n, p, (size_t)n * sizeof(double));
                 th[nh] = thn;
                 nh += 1;

@@ -8,6 +8,14 @@ Nothing here shares code with the oracle or the CUDA library:
                      (Paige & Saunders 1982, Sec. 7.2), as used by Thm 6.1
   limit_solution()   x0 + W A^T (A W A^T)^+ (b - A x0) (Thm 3.1, Cor. 3.3)
   kaczmarz_classic() x += (r_i/||a_i||^2) a_i
+  window_projection_exact()
+                     the identity sketch with a window of K rows, in exact
+                     rational arithmetic: each step projects x onto the
+                     intersection of the hyperplanes of the window's rows
+                     (eq:pkLong with S = the window's identity columns)
+  projection_run_restarted()
+                     projection_run whose residual sketch starts afresh
+                     (S = [b - A x]) whenever a given restart rule fires
 """
 from __future__ import annotations
 
@@ -100,6 +108,73 @@ def kaczmarz_classic(A, b, x0, order):
         a = A[i]
         x = x + ((b[i] - a @ x) / (a @ a)) * a
     return x
+
+
+def _solve_exact(G, rhs):
+    """Gauss-Jordan elimination over the rationals (G square, nonsingular)."""
+    k = len(G)
+    M = [list(G[i]) + [rhs[i]] for i in range(k)]
+    for c in range(k):
+        piv = next(i for i in range(c, k) if M[i][c] != 0)
+        M[c], M[piv] = M[piv], M[c]
+        for i in range(k):
+            if i != c and M[i][c] != 0:
+                f = M[i][c] / M[c][c]
+                M[i] = [a - f * b for a, b in zip(M[i], M[c])]
+    return [M[i][k] / M[i][i] for i in range(k)]
+
+
+def window_projection_exact(D, b, order, K):
+    """Identity sketch with a window of at most K rows, exactly: before a
+    row is taken, a full window (K rows) is emptied; the row is added to the
+    window and x is projected onto {x : a_j^T x = b_j for every row j of the
+    window}, x <- x + A_S^T (A_S A_S^T)^{-1} (b_S - A_S x). K = 0 keeps no
+    window (classical Kaczmarz). D, b hold integers or Fractions; the rows of
+    each window must be linearly independent. Returns the list of iterates."""
+    D = [[Fraction(v) for v in row] for row in np.asarray(D).tolist()]
+    b = [Fraction(v) for v in np.asarray(b).tolist()]
+    n = len(D[0])
+    x = [Fraction(0)] * n
+    win, out = [], []
+    for i in order:
+        if K > 0 and len(win) == K:
+            win = []
+        rows = win + [int(i)]
+        AS = [D[j] for j in rows]
+        G = [[sum(a * c for a, c in zip(ra, rc)) for rc in AS] for ra in AS]
+        res = [b[j] - sum(a * c for a, c in zip(D[j], x)) for j in rows]
+        z = _solve_exact(G, res)
+        x = [x[t] + sum(z[q] * AS[q][t] for q in range(len(rows))) for t in range(n)]
+        if K > 0:
+            win = rows
+        out.append(list(x))
+    return out
+
+
+def projection_run_restarted(A, b, x0, Wd, K, restart):
+    """K steps of x_k = x_{k-1} + p_k, p_k from pk_long with the residual
+    sketch S = [r_s, r_{s+1}, ..., r_{k-1}] that starts afresh at the last
+    restart s. After update k the rule restart(rho_k, rho_s, k - s) (rho_k =
+    ||b - A x_k||^2, exact to double rounding; rho_s at the last restart)
+    says whether the sketch restarts from r_k. Returns (xs, rhos, restarts)
+    with restarts = the update indices k after which the sketch restarted."""
+    x = np.array(x0, dtype=np.float64)
+    r = b - A @ x
+    rho_s = float(r @ r)
+    s = 0
+    cols, xs, rhos, restarts = [], [], [], []
+    for k in range(1, K + 1):
+        cols.append(r)
+        S = np.stack(cols, axis=1)
+        x = x + pk_long(A, Wd, S, r)
+        xs.append(x.copy())
+        r = b - A @ x
+        rho = float(r @ r)
+        rhos.append(rho)
+        if restart(rho, rho_s, k - s):
+            restarts.append(k)
+            cols, rho_s, s = [], rho, k
+    return xs, rhos, restarts
 
 
 def load_golden(name):
