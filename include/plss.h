@@ -148,7 +148,10 @@ typedef struct plss_ctx plss_ctx;
 
 void plss_opts_default(plss_opts *o);
 
-/* Copies A to the device, validates it, builds its transpose (unless
+/* The problem of the paper's Sec. 1: A x = b with A in R^{m x n} of any
+ * shape and rank and b in range(A) (a consistent system); a context holds
+ * one such A for any number of solves with it.
+ * Copies A to the device, validates it, builds its transpose (unless
  * o->symmetric) and the tile schedule of the sparse sweeps (o->layout,
  * o->tile_shift). The storage precision is o->precision. A malformed CSR,
  * an unknown precision or layout, or tile_shift outside [-2, 2] returns
@@ -250,21 +253,31 @@ plss_status plss_spmv(plss_ctx *ctx, int32_t transpose, const double *v, double 
  * memory at start-up and forbids allocation afterwards. Every other entry
  * point allocates its workspace in plss_create / plss_server_create; this
  * one allocates nothing, on the device or the host: its scratch (one partial
- * sum per block of 1,024 rows and an arrival counter) is a static device
- * array of about 33 KB that every GPU loading the library holds until the
- * process exits.
+ * sum per block of 1,024 rows, an arrival counter and an invalid-input flag)
+ * is a static device array of about 33 KB that every GPU loading the library
+ * holds until the process exits. It runs a row-group kernel of its own, so
+ * its r and *norm2 agree with b - plss_spmv(A, x) to rounding, not bit for
+ * bit.
  *   A: CSR with row_ptr int64 [m+1], col_idx int32 [nnz], val double [nnz];
  *   x double [n], b double [m], r double [m] (output), norm2 one double
- *   (output) -- all device memory of the current device, owned by the caller.
+ *   (output) -- all device memory of the current device (or managed
+ *   memory), owned by the caller; another GPU's memory is refused.
  *   m <= 4,194,304 rows (the scratch capacity); larger m returns
- *   PLSS_ERR_INVALID without launching anything.
+ *   PLSS_ERR_INVALID without launching anything. m = 0 gives *norm2 = 0.
+ * The CSR's contents are not checked on the host (that would need a copy):
+ * the kernel skips a row whose [row_ptr[i], row_ptr[i+1]) is not inside
+ * [0, nnz] and every entry whose column is outside [0, n), so it never reads
+ * out of bounds, and then sets *norm2 to NaN to say the input broke the
+ * contract (r is then meaningless).
  * The call is asynchronous on `stream` (a cudaStream_t; NULL = legacy
  * stream): r and *norm2 are valid once the stream reaches that point. The
  * first call on a device looks up the scratch's device address (once per
- * device); make that first call before any stream capture. All calls share
- * the one scratch array: calls whose kernels overlap on the GPU (different
- * streams, no ordering between them) race and give wrong sums; the arrival
- * counter is cleared on the stream before each launch. */
+ * device, in the device's primary context; the cached address does not
+ * survive a cudaDeviceReset); make that first call before any stream
+ * capture. All calls share the one scratch array: calls whose kernels
+ * overlap on the GPU (different streams, no ordering between them) race and
+ * give wrong sums; the arrival counter and the flag are cleared on the
+ * stream before each launch. */
 plss_status plss_residual_noalloc(int64_t m, int64_t n, int64_t nnz, const int64_t *row_ptr,
                                   const int32_t *col_idx, const double *val, const double *x,
                                   const double *b, double *r, double *norm2, void *stream);
@@ -280,6 +293,22 @@ plss_status plss_residual_noalloc(int64_t m, int64_t n, int64_t nnz, const int64
  * Either array may be NULL (ms has 3 entries, launches 4). A diagnostic
  * with no counterpart in the paper. */
 plss_status plss_kernel_times(plss_ctx *ctx, double *ms, int64_t *launches, int32_t reset);
+
+/* The gather floor of a sweep, measured on the device: a kernel that walks
+ * the sweep's own sliced index stream with the sweep's grid and warp ranges
+ * and gathers the sweep's dense vector (side 0: the row sweep's p, one
+ * entry per nonzero of A p; side 1: the column sweep's r, one per nonzero
+ * of A^T r) and does nothing else. Each of `reps` timed runs (1..1000) is
+ * preceded by a write of 256 MB that evicts L2 and a read of the vector
+ * (which the solve finds in L2, just written); *us_median and *us_min
+ * (either may be NULL) receive the device times in microseconds between
+ * CUDA events around the kernel. The contents of p and r are read, not
+ * changed. Single-system contexts whose side is sliced throughout
+ * (plss_ctx_layout reports it); otherwise PLSS_ERR_INVALID. A diagnostic
+ * with no counterpart in the paper: every nonzero of Algorithm 1's A p and
+ * A^T r is one such gather, and on GB300 their rate, not HBM bytes, bounds
+ * the sweeps. Allocates and frees 256 MB for the eviction. */
+plss_status plss_gather_bound(plss_ctx *ctx, int32_t side, int32_t reps, double *us_median, double *us_min);
 
 /* Message of the last error on the calling thread ("" when none). */
 const char *plss_last_error(void);

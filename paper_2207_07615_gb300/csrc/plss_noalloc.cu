@@ -5,12 +5,13 @@
 // running: a framework that has handed every byte of the device to its own
 // pool (a cudaMalloc from a library would fail or fragment it), or a
 // latency-critical loop whose memory is fixed at start-up. For them this file
-// offers one entry point that allocates nothing. It is the residual mode of
-// the library's tiled product kernel (the per-tile partial sums of ||b-Ax||^2
-// that plss_solve uses for its true residual), with the scratch that kernel
-// takes from a context -- per-block partial sums and an arrival counter --
-// kept instead in one file-scope static device array of fixed size. Every
-// GPU that loads the library holds that array (about 33 KB) until the
+// offers one entry point that allocates nothing: a row-group kernel of its
+// own (8 lanes per row, blocks of 1,024 rows) that forms the same quantity
+// as plss_spmv's product followed by b - A x, with its own summation order,
+// so the two agree to rounding, not bit for bit. Its scratch -- one partial
+// sum per block, an arrival counter and a flag for an invalid CSR -- is one
+// file-scope static device array of fixed size instead of context memory.
+// Every GPU that loads the library holds that array (about 33 KB) until the
 // process exits.
 #include <cuda_runtime.h>
 
@@ -31,6 +32,7 @@ constexpr int kNaMaxDevices = 64;
 struct NaScratch {
     double part[kNaMaxBlocks];   // one partial sum of r_i^2 per block of 1,024 rows
     unsigned int arrivals;       // blocks finished in the current call
+    unsigned int bad;            // set when the CSR broke its contract in this call
 };
 
 // The scratch. Host code must not pass &g_na_scratch to a kernel: on the
@@ -39,7 +41,8 @@ struct NaScratch {
 static __device__ __align__(256) NaScratch g_na_scratch;
 
 __global__ void __launch_bounds__(kNaThreads)
-k_residual_noalloc(int64_t m, const int64_t *__restrict__ row_ptr, const int32_t *__restrict__ col_idx,
+k_residual_noalloc(int64_t m, int64_t n, int64_t nnz, const int64_t *__restrict__ row_ptr,
+                   const int32_t *__restrict__ col_idx,
                    const double *__restrict__ val, const double *__restrict__ x,
                    const double *__restrict__ b, double *__restrict__ r, double *norm2,
                    NaScratch *scr) {
@@ -50,14 +53,29 @@ k_residual_noalloc(int64_t m, const int64_t *__restrict__ row_ptr, const int32_t
     const int64_t row0 = int64_t(blockIdx.x) * kNaRowsPerBlock;
     const int64_t row1 = row0 + kNaRowsPerBlock < m ? row0 + kNaRowsPerBlock : m;
     double acc = 0.0;
-    // warp-uniform loop: each pass covers kNaThreads / kNaLanes rows
+    bool bad = false;
+    // warp-uniform loop: each pass covers kNaThreads / kNaLanes rows. The CSR
+    // is not validated on the host (that would need a copy of it), so every
+    // access is guarded here: a row range outside [0, nnz] is skipped and a
+    // column outside [0, n) is not gathered; either marks the call invalid.
     for (int64_t base = row0; base < row1; base += kNaThreads / kNaLanes) {
         const int64_t row = base + grp;
         const bool ok = row < row1;
         double d = 0.0;
         if (ok) {
-            const int64_t s = row_ptr[row], e = row_ptr[row + 1];
-            for (int64_t k = s + gl; k < e; k += kNaLanes) d = fma(val[k], x[col_idx[k]], d);
+            int64_t s = row_ptr[row], e = row_ptr[row + 1];
+            if (s < 0 || e > nnz || s > e) {
+                bad = true;
+                s = e = 0;
+            }
+            for (int64_t k = s + gl; k < e; k += kNaLanes) {
+                const int64_t c = col_idx[k];
+                if (c < 0 || c >= n) {
+                    bad = true;
+                    continue;
+                }
+                d = fma(val[k], x[c], d);
+            }
         }
 #pragma unroll
         for (int o = kNaLanes / 2; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
@@ -66,6 +84,10 @@ k_residual_noalloc(int64_t m, const int64_t *__restrict__ row_ptr, const int32_t
             r[row] = ri;
             acc += ri * ri;
         }
+    }
+    if (bad) {
+        atomicOr(&scr->bad, 1u);
+        __threadfence();
     }
     // fixed-order block sum
 #pragma unroll
@@ -92,21 +114,26 @@ k_residual_noalloc(int64_t m, const int64_t *__restrict__ row_ptr, const int32_t
     if (threadIdx.x == 0) {
         double s = 0.0;
         for (int w = 0; w < kNaThreads / 32; ++w) s += sh[w];
-        *norm2 = s;
+        *norm2 = __ldcg(&scr->bad) ? __longlong_as_double(0x7ff8000000000000ll) : s;   // NaN: invalid CSR
         scr->arrivals = 0;
+        scr->bad = 0;
     }
 }
 
 static std::mutex g_na_mu;
 static NaScratch *g_na_addr[kNaMaxDevices] = {};
 
-static bool is_device_ptr(const void *p) {
+// Device (or managed) memory that the current device `dev` can load from
+// with plain loads: device memory must belong to `dev` itself (another
+// GPU's buffer would need peer access).
+static bool is_device_ptr(const void *p, int dev) {
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    if (at.type == cudaMemoryTypeDevice) return at.device == dev;
+    return at.type == cudaMemoryTypeManaged;
 }
 
 }  // namespace plss
@@ -123,6 +150,11 @@ extern "C" plss_status plss_residual_noalloc(int64_t m, int64_t n, int64_t nnz, 
                     "plss_residual_noalloc covers", (long long)m, (long long)kNaMaxRows);
     if (!row_ptr || !norm2 || (m > 0 && (!b || !r)) || (nnz > 0 && (!col_idx || !val || !x)))
         return fail(PLSS_ERR_INVALID, "NULL array");
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNaMaxDevices) {
+        cudaGetLastError();
+        return fail(PLSS_ERR_CUDA, "no usable current device");
+    }
     const void *rp = row_ptr;
     const void *ptrs[] = {rp, norm2, m > 0 ? static_cast<const void *>(b) : rp,
                           m > 0 ? static_cast<const void *>(r) : rp,
@@ -130,15 +162,15 @@ extern "C" plss_status plss_residual_noalloc(int64_t m, int64_t n, int64_t nnz, 
                           nnz > 0 ? static_cast<const void *>(val) : rp,
                           nnz > 0 ? static_cast<const void *>(x) : rp};
     for (const void *p : ptrs)
-        if (!is_device_ptr(p)) return fail(PLSS_ERR_INVALID, "every array must be device memory");
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNaMaxDevices)
-        return fail(PLSS_ERR_CUDA, "no usable current device");
+        if (!is_device_ptr(p, dev))
+            return fail(PLSS_ERR_INVALID, "every array must be device memory of the current device");
     NaScratch *scr = nullptr;
     {
         std::lock_guard<std::mutex> lk(g_na_mu);
         if (!g_na_addr[dev]) {
-            // first call on this device: the scratch's device address
+            // first call on this device: the scratch's device address (in the
+            // device's primary context, which the runtime uses; a
+            // cudaDeviceReset makes this cached address stale)
             void *p = nullptr;
             const cudaError_t e = cudaGetSymbolAddress(&p, g_na_scratch);
             if (e != cudaSuccess) {
@@ -150,13 +182,14 @@ extern "C" plss_status plss_residual_noalloc(int64_t m, int64_t n, int64_t nnz, 
         scr = g_na_addr[dev];
     }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    cudaError_t e = cudaMemsetAsync(&scr->arrivals, 0, sizeof(unsigned int), s);
+    cudaError_t e = cudaMemsetAsync(&scr->arrivals, 0, 2 * sizeof(unsigned int), s);   // arrivals, bad
     if (e != cudaSuccess) {
         cudaGetLastError();
         return fail(PLSS_ERR_CUDA, "clearing the scratch counter: %s", cudaGetErrorString(e));
     }
     const int64_t blocks = m > 0 ? (m + kNaRowsPerBlock - 1) / kNaRowsPerBlock : 1;
-    k_residual_noalloc<<<unsigned(blocks), kNaThreads, 0, s>>>(m, row_ptr, col_idx, val, x, b, r, norm2, scr);
+    k_residual_noalloc<<<unsigned(blocks), kNaThreads, 0, s>>>(m, n, nnz, row_ptr, col_idx, val, x, b, r, norm2,
+                                                                scr);
     e = cudaGetLastError();
     if (e != cudaSuccess) return fail(PLSS_ERR_CUDA, "launch: %s", cudaGetErrorString(e));
     return PLSS_OK;
