@@ -31,7 +31,7 @@ EXPORTS = ["plss_opts_default", "plss_create", "plss_create_batched", "plss_dest
            "plss_ctx_info", "plss_ctx_layout", "plss_solve", "plss_solve_batched", "plss_solve_rhs", "plss_spmv",
            "plss_kernel_times", "plss_residual_noalloc", "plss_last_error", "plss_server_opts_default",
            "plss_server_create", "plss_submit", "plss_poll", "plss_server_stats", "plss_server_destroy",
-           "plss_tune"]
+           "plss_tune", "plss_gather_bound"]
 
 
 class Csr(C.Structure):
@@ -112,11 +112,13 @@ def lib() -> C.CDLL:
             L.plss_server_destroy.argtypes = [vp]
             L.plss_server_destroy.restype = None
             L.plss_tune.argtypes = [vp, i32, vp, i32, vp, vp, i32, vp]
+            L.plss_gather_bound.argtypes = [vp, i32, i32, vp, vp]
             for name in ("plss_create", "plss_create_batched", "plss_ctx_info", "plss_ctx_layout",
                          "plss_solve",
                          "plss_kernel_times",
                          "plss_solve_batched", "plss_solve_rhs", "plss_spmv",
-                         "plss_server_create", "plss_submit", "plss_poll", "plss_server_stats", "plss_tune"):
+                         "plss_server_create", "plss_submit", "plss_poll", "plss_server_stats", "plss_tune",
+                         "plss_gather_bound"):
                 getattr(L, name).restype = C.c_int32
             _lib = L
     return _lib
@@ -348,6 +350,14 @@ class Context:
         out = {k: (float(ms[i]), int(n[i])) for i, k in enumerate(names)}
         out["all_launches"] = int(n[3])
         return out
+
+    def gather_bound(self, side, reps=5):
+        """Device time (us: median, min) of gathering the sweep's vector along
+        the sweep's own index stream and nothing else (side 0 = rows, A p;
+        1 = columns, A^T r): the floor set by the sweep's random gathers."""
+        med, mn = C.c_double(), C.c_double()
+        _check(lib().plss_gather_bound(self._h, int(side), int(reps), C.byref(med), C.byref(mn)), (OK,))
+        return med.value, mn.value
 
     def spmv(self, v, transpose=False, stream=None):
         m, n = self.shapes[0]

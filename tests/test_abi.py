@@ -204,6 +204,7 @@ def test_context_calls_refuse_a_null_context(L):
     assert L.plss_kernel_times(None, None, None, 0) == plss.ERR_INVALID
     assert L.plss_ctx_info(None, None, None, None, None) == plss.ERR_INVALID
     assert L.plss_ctx_layout(None, None) == plss.ERR_INVALID
+    assert L.plss_gather_bound(None, 0, 1, None, None) == plss.ERR_INVALID
     L.plss_destroy(None)                                          # a no-op
 
 
