@@ -7,6 +7,8 @@ or calls anything here, and this package never imports the CUDA library.
 Functions follow the paper step by step (see plss_oracle.c):
   residual()    Algorithm 1 / Theorem 4.1, optional diagonal W (Sec. 4.1)
   kaczmarz()    identity sketch, eq:pkKacz (Sec. 7)
+  general()     general sketch of random sign columns, Theorem 2.1 and
+                Corollary 2.2 (Sec. 2.4); sketch_entry() gives its columns
   spmv(), spmvt(), colweights(), permutation()  plain building blocks
 """
 from __future__ import annotations
@@ -58,6 +60,11 @@ def _load():
             lib.plss_oracle_spmvt.argtypes = [i64, i64, vp, vp, vp, vp, vp]
             lib.plss_oracle_colweights.restype = None
             lib.plss_oracle_colweights.argtypes = [i64, i64, vp, vp, vp, i32, vp]
+            lib.plss_oracle_general.restype = i32
+            lib.plss_oracle_general.argtypes = [i64, i64, vp, vp, vp, vp, vp, d, i64, i64, u64, i32,
+                                                vp, vp, vp, vp, i64, vp]
+            lib.plss_oracle_sketch_entry.restype = d
+            lib.plss_oracle_sketch_entry.argtypes = [u64, i64, i64, i64]
             lib.plss_oracle_permutation.restype = None
             lib.plss_oracle_permutation.argtypes = [vp, i64, vp]
             _lib = lib
@@ -184,3 +191,36 @@ def kaczmarz(A, b, x0=None, tol=1e-8, maxit=None, K=0, seed=0, plant=0):
         raise MemoryError("oracle kaczmarz")
     return dict(x=x, iters=int(it[0]), skipped=int(sk[0]), status=STATUS.get(st, st),
                 relres_true=float(rt[0]))
+
+
+def sketch_entry(seed: int, m: int, k: int, i: int) -> float:
+    """Entry i of general-sketch column k (0-based): +1 or -1."""
+    return float(_load().plss_oracle_sketch_entry(int(seed) & (2**64 - 1), int(m), int(k), int(i)))
+
+
+def general(A, b, x0=None, tol=1e-8, maxit=None, K=0, seed=0, hist=0, plant=0):
+    """PLSS with a general sketch of random sign columns (Theorem 2.1,
+    Corollary 2.2), history of at most K columns. hist > 0 returns the
+    iterate after each of the first `hist` columns as hist_x."""
+    lib = _load()
+    rp, ci, val = _csr(A)
+    b = _vec(b, A.m, "b")
+    x0 = _vec(x0, A.n, "x0")
+    if maxit is None:
+        maxit = A.n
+    x = np.empty(A.n)
+    it = np.zeros(1, dtype=np.int64)
+    sk = np.zeros(1, dtype=np.int64)
+    rt = np.zeros(1)
+    H = int(hist)
+    hx = np.zeros((H, A.n)) if H else None
+    st = lib.plss_oracle_general(A.m, A.n, _p(rp), _p(ci), _p(val), _p(b), _p(x0), float(tol),
+                                 int(maxit), int(K), int(seed) & (2**64 - 1), int(plant),
+                                 _p(x), _p(it), _p(sk), _p(rt), H, _p(hx))
+    if st == -2:
+        raise MemoryError("oracle general")
+    out = dict(x=x, iters=int(it[0]), skipped=int(sk[0]), status=STATUS.get(st, st),
+               relres_true=float(rt[0]))
+    if H:
+        out["hist_x"] = hx[:min(H, out["iters"])]
+    return out

@@ -15,6 +15,10 @@
  *   - plss_oracle_kaczmarz: the identity sketch of Sec. 7 (eq:pkKacz),
  *     with a dense history P (n x K) and Theta = diag(||p_j||^2).
  *   - plss_oracle_colweights: W = diag(1/||A_{:,j}||) of Sec. 4.1.
+ *   - plss_oracle_general: a general sketch S_k = [s_1 ... s_k] (eq:genS)
+ *     with random sign columns, through the update of the inverse
+ *     N_k = (Y_k^T Y_k)^{-1} of Theorem 2.1 (eq:Nkrec) and the update
+ *     p_k of Corollary 2.2 (eq:compute-pk-alpha1), Sec. 2.4.
  *
  * Readings where the paper is silent or inconsistent (all listed in the
  * design notes of the repository):
@@ -54,7 +58,15 @@
  * restart at 2x instead of 4x the starting rho, 3 = the inner-solve restart
  * at inner_tol instead of inner_tol^2. Identity sketch: 1 = the window is
  * emptied one row late (K + 1 directions), 2 = one row early (K - 1),
- * 3 = never (the whole history is kept).
+ * 3 = never (the whole history is kept). General sketch: 1 = the rank-one
+ * term t t^T / delta is left out of the update of N (eq:Nkrec).
+ *
+ * General-sketch columns (a reading: the paper leaves the sketch open and
+ * draws random normal sketches for its comparisons): s_k has entries +1 or
+ * -1, entry i of the k-th column (k = 0, 1, ... counting every column drawn)
+ * being the sign bit of output number k*m + i of the SplitMix64 stream
+ * seeded with `seed` (output j = mix(seed + (j + 1) * golden gamma), so any
+ * entry is computed directly from (seed, k, i)); bit 63 set gives -1.
  */
 #include <math.h>
 #include <stdint.h>
@@ -486,5 +498,134 @@ kdone:
         *relres_true = nb > 0.0 ? sqrt(dot(m, rt, rt)) / nb : 0.0;
     }
     free(P); free(th); free(c); free(p); free(rt); free(perm);
+    return status;
+}
+
+/* ------------------------------------------------------------------ */
+/* General sketch: Theorem 2.1 / Corollary 2.2 (Sec. 2.4)              */
+/* ------------------------------------------------------------------ */
+
+/* Output number j (0-based) of the SplitMix64 stream seeded with `seed`:
+ * the state after j + 1 increments by the golden gamma, mixed. */
+static uint64_t splitmix_at(uint64_t seed, uint64_t j)
+{
+    uint64_t z = seed + (j + 1) * 0x9e3779b97f4a7c15ULL;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+    return z ^ (z >> 31);
+}
+
+/* Entry i of sketch column k (0-based, counting every column drawn). */
+double plss_oracle_sketch_entry(uint64_t seed, int64_t m, int64_t k, int64_t i)
+{
+    return (splitmix_at(seed, (uint64_t)k * (uint64_t)m + (uint64_t)i) >> 63) ? -1.0 : 1.0;
+}
+
+/*
+ * PLSS with a general sketch S_k = [s_1 ... s_k] (eq:genS), one random
+ * sign column appended per step, computed as Sec. 2.4 does:
+ *   y_k = A^T s_k (eq:yk), Y_k = [Y_{k-1} y_k];
+ *   t_k = N_{k-1} Y_{k-1}^T y_k,  delta_k = y_k^T y_k - y_k^T Y_{k-1} t_k;
+ *   p_k = (s_k^T r_{k-1} / delta_k) (y_k - Y_{k-1} t_k)   (Corollary 2.2);
+ *   N_k = [[N_{k-1} + t t^T/delta, -t/delta], [-t^T/delta, 1/delta]]
+ *                                                      (Theorem 2.1, eq:Nkrec);
+ * with N_1 = 1/(y_1^T y_1) and r_k = b - A x_k formed from its definition
+ * (Sec. 1: x_k = x_{k-1} + p_k). The history holds at most K columns
+ * (the memory of Sec. 2.3-2.4 grows with k); a full history is emptied
+ * before the next column, which then starts a new N. A column whose delta
+ * is <= 1e-14 y^T y (y in the span of the history, or y = 0) is skipped
+ * and not appended (its column index is still used up). maxit caps the
+ * columns drawn; after each step ||r||/||b|| <= tol stops.
+ * Outputs: x_out[n], *iters (columns drawn), *n_skipped, *relres_true;
+ * hist_x[k*n] = x after column k (k < hist_cap) when hist_x != NULL.
+ */
+int plss_oracle_general(int64_t m, int64_t n, const int64_t *row_ptr, const int32_t *col_idx,
+                        const double *val, const double *b, const double *x0, double tol,
+                        int64_t maxit, int64_t K, uint64_t seed, int plant, double *x_out,
+                        int64_t *iters_out, int64_t *n_skipped, double *relres_true,
+                        int64_t hist_cap, double *hist_x)
+{
+    int64_t Kc = K > 0 ? K : 1;
+    double *x = x_out;
+    double *Y = (double *)malloc((size_t)(Kc * (n ? n : 1)) * sizeof(double));  /* column j at Y + j*n */
+    double *N = (double *)malloc((size_t)(Kc * Kc) * sizeof(double));          /* N[a*Kc + c] */
+    double *N2 = (double *)malloc((size_t)(Kc * Kc) * sizeof(double));
+    double *Yty = (double *)malloc((size_t)Kc * sizeof(double));
+    double *t = (double *)malloc((size_t)Kc * sizeof(double));
+    double *y = (double *)malloc((size_t)(n ? n : 1) * sizeof(double));
+    double *p = (double *)malloc((size_t)(n ? n : 1) * sizeof(double));
+    double *r = (double *)malloc((size_t)(m ? m : 1) * sizeof(double));
+    int status = ORC_NOT_CONVERGED;
+    int64_t k = 0, nh = 0, skipped = 0;
+    double nb;
+    if (!Y || !N || !N2 || !Yty || !t || !y || !p || !r) { status = ORC_NOMEM; goto gdone; }
+
+    for (int64_t j = 0; j < n; ++j) x[j] = x0 ? x0[j] : 0.0;
+    nb = sqrt(dot(m, b, b));
+    true_residual(m, row_ptr, col_idx, val, b, x, r);
+    if (nb == 0.0 || sqrt(dot(m, r, r)) / nb <= tol) { status = ORC_CONVERGED; goto gdone; }
+
+    for (k = 0; k < maxit; ) {
+        if (K > 0 && nh == K) nh = 0;          /* history full: start a new one */
+        /* y = A^T s_k, rho = s_k^T r_{k-1} */
+        double rho = 0.0;
+        for (int64_t j = 0; j < n; ++j) y[j] = 0.0;
+        for (int64_t i = 0; i < m; ++i) {
+            double si = plss_oracle_sketch_entry(seed, m, k, i);
+            rho += si * r[i];
+            for (int64_t q = row_ptr[i]; q < row_ptr[i + 1]; ++q) y[col_idx[q]] += si * val[q];
+        }
+        double yy = dot(n, y, y);
+        /* Y^T y, t = N Y^T y, delta */
+        for (int64_t a = 0; a < nh; ++a) Yty[a] = dot(n, Y + a * n, y);
+        for (int64_t a = 0; a < nh; ++a) {
+            double sacc = 0.0;
+            for (int64_t c = 0; c < nh; ++c) sacc += N[a * Kc + c] * Yty[c];
+            t[a] = sacc;
+        }
+        double delta = yy;
+        for (int64_t a = 0; a < nh; ++a) delta -= Yty[a] * t[a];
+        k += 1;
+        if (!(delta > 1e-14 * yy)) {
+            skipped += 1;
+        } else {
+            /* p = (rho/delta) (y - Y t) */
+            for (int64_t j = 0; j < n; ++j) {
+                double v = y[j];
+                for (int64_t a = 0; a < nh; ++a) v -= Y[a * n + j] * t[a];
+                p[j] = (rho / delta) * v;
+            }
+            for (int64_t j = 0; j < n; ++j) x[j] += p[j];
+            if (K > 0) {
+                /* N_k from N_{k-1} (eq:Nkrec), Y_k = [Y_{k-1} y] */
+                for (int64_t a = 0; a < nh; ++a)
+                    for (int64_t c = 0; c < nh; ++c)
+                        N2[a * Kc + c] = plant == 1 ? N[a * Kc + c]
+                                                    : N[a * Kc + c] + (t[a] * t[c]) / delta;
+                for (int64_t a = 0; a < nh; ++a) {
+                    N2[a * Kc + nh] = -t[a] / delta;
+                    N2[nh * Kc + a] = -t[a] / delta;
+                }
+                N2[nh * Kc + nh] = 1.0 / delta;
+                for (int64_t a = 0; a <= nh; ++a)
+                    for (int64_t c = 0; c <= nh; ++c) N[a * Kc + c] = N2[a * Kc + c];
+                memcpy(Y + nh * n, y, (size_t)n * sizeof(double));
+                nh += 1;
+            }
+        }
+        if (hist_x && k - 1 < hist_cap) memcpy(hist_x + (k - 1) * n, x, (size_t)n * sizeof(double));
+        true_residual(m, row_ptr, col_idx, val, b, x, r);
+        if (sqrt(dot(m, r, r)) / nb <= tol) { status = ORC_CONVERGED; break; }
+    }
+
+gdone:
+    if (status != ORC_NOMEM) {
+        *iters_out = k;
+        *n_skipped = skipped;
+        nb = sqrt(dot(m, b, b));
+        true_residual(m, row_ptr, col_idx, val, b, x, r);
+        *relres_true = nb > 0.0 ? sqrt(dot(m, r, r)) / nb : 0.0;
+    }
+    free(Y); free(N); free(N2); free(Yty); free(t); free(y); free(p); free(r);
     return status;
 }
