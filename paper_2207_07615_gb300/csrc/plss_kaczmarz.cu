@@ -13,11 +13,15 @@
 // p_j restricted to U) with a column -> slot map, and one row costs
 // O(nnz(a_i) K + |U| K) instead of O(n K).
 //
-// The loop over rows is sequential by nature; one CTA runs one system, and
-// a batch of systems runs as one launch with one CTA per system. Rows are
-// visited without replacement in a fresh permutation per pass (SplitMix64
-// stream + Fisher-Yates shuffle, drawn on the host); ||b - A x|| is tested
-// after every pass.
+// The loop over rows is sequential by nature; for windows of up to 64
+// updates one CTA runs one system, and a batch of systems runs as one launch
+// with one CTA per system. Larger windows (65..4,096 updates, one system)
+// run on the whole GPU (k_kacz_wide below): a row's step is then dominated
+// by the product P (Theta^{-1} P^T a_i) over |U| x K entries of the history,
+// which one SM cannot stream fast enough. Rows are visited without
+// replacement in a fresh permutation per pass (SplitMix64 stream +
+// Fisher-Yates shuffle, drawn on the host); ||b - A x|| is tested after
+// every pass.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -34,7 +38,11 @@ namespace plss {
 
 constexpr int kKzThreads = 256;
 constexpr int kKzWarps = kKzThreads / 32;
-constexpr int kKzMaxK = 64;
+constexpr int kKzMaxK = 64;         // one CTA per system up to this window
+constexpr int kKwMaxK = 4096;       // whole-GPU window (one system) up to this
+constexpr int kKwThreads = 512;
+constexpr int kKwWarps = kKwThreads / 32;
+constexpr int kKwRowMax = 8192;     // entries of a row held in shared memory
 
 struct KzSys {
     int64_t uoff;       // first U slot of the system (ucols, and rows of P)
@@ -59,6 +67,13 @@ struct KaczState {
     int32_t *h_perm = nullptr;    // pinned
     KzSys *h_sys = nullptr;       // pinned
     std::vector<int64_t> ucap;
+    // whole-GPU window (K > kKzMaxK): P is row-major, P[s * K + j]
+    bool wide = false;
+    int32_t wide_grid = 0;
+    int32_t row_max = 0;          // longest row of the system
+    double *d_part = nullptr;     // [3 * grid] per-CTA partials (a^T x, ||a||^2, theta)
+    double *d_c = nullptr;        // [K] c_j = q_j^T a_i, one owner CTA per j
+    uint32_t *d_bar = nullptr;    // grid barrier: [0] arrivals, [1] generation, [2] error
 };
 
 struct KzArgs {
@@ -312,6 +327,281 @@ __global__ void __launch_bounds__(kKzThreads) k_kacz0(KzArgs a, int32_t nsys) {
 }
 
 // ---------------------------------------------------------------------------
+// Whole-GPU window (K > kKzMaxK, one system)
+// ---------------------------------------------------------------------------
+//
+// Every row takes two phases separated by grid barriers, with the CTAs
+// splitting the work and taking the scalar decisions redundantly (each CTA
+// sums the same partials in the same order, so every CTA holds the same
+// bits):
+//   A  c_j = q_j^T a_i for the window's j (each CTA owns a range of j) and
+//      partials of a_i^T x and ||a_i||^2 (each CTA owns a range of entries);
+//   -- barrier --
+//      every CTA: d_j = c_j / theta_j, ||d||^2, delta, r_i, gamma, the skip
+//      test, and the slots of the row's new columns (row order);
+//   B  q = a_i - P d on U (each CTA owns a range of slots): the new column
+//      nh of P, x += gamma q, a partial of theta = ||q||^2;
+//   -- barrier --
+//      every CTA: theta_nh; nh += 1.
+// A full window is emptied before the next row (each CTA clears its slots'
+// entries of the column -> slot map, then a barrier). P is row-major over
+// the slots, P[s * K + j], so c reads and the product's rows are contiguous.
+// The barrier is a counter and a generation word with a time limit: a CTA
+// that waits longer than kKwWaitNs sets the error word and returns, and so
+// does every other CTA that sees it (the host reports PLSS_ERR_TIMEOUT). The
+// launch is cooperative, which guarantees that all CTAs are resident.
+
+constexpr unsigned long long kKwWaitNs = 2000000000ull;   // 2 s per barrier
+
+struct KwArgs {
+    const int32_t *row_ptr;
+    const int32_t *col_idx;
+    const void *val;
+    const int32_t *perm;
+    const double *b;
+    double *x;
+    int32_t *slot;     // [n] column -> slot, -1 if not in U
+    int32_t *ucols;    // [ucap] slot -> column
+    double *P;         // [ucap][K]
+    double *theta;     // [K]
+    double *c;         // [K]
+    double *part;      // [3 * gridDim.x]
+    uint32_t *bar;     // arrivals, generation, error
+    KzSys *ks;
+    int64_t row_off, ucap;
+    int32_t K, row_max;
+};
+
+__device__ __forceinline__ unsigned long long kw_now() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Grid barrier with a time limit; returns false (to every thread of the CTA)
+// when the error word is set.
+__device__ __forceinline__ bool kw_barrier(uint32_t *bar, int *sh_ok) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile uint32_t *vb = bar;
+        int ok = vb[2] == 0;
+        if (ok) {
+            const uint32_t gen = vb[1];
+            __threadfence();
+            if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+                bar[0] = 0;
+                __threadfence();
+                atomicAdd(bar + 1, 1u);
+            } else {
+                const unsigned long long t0 = kw_now();
+                while (vb[1] == gen) {
+                    if (vb[2] != 0) { ok = 0; break; }
+                    if (kw_now() - t0 > kKwWaitNs) {
+                        atomicExch(bar + 2, 1u);
+                        ok = 0;
+                        break;
+                    }
+                    __nanosleep(64);
+                }
+            }
+            __threadfence();
+        }
+        *sh_ok = ok;
+    }
+    __syncthreads();
+    return *sh_ok != 0;
+}
+
+// Fixed-order CTA sum of one double (shuffle tree per warp, then the warp
+// totals in warp order); the result is returned to every thread.
+__device__ __forceinline__ double kw_sum(double v, double *sh) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    double t = 0.0;
+    for (int w = 0; w < kKwWarps; ++w) t += sh[w];
+    return t;
+}
+
+template <typename S>
+__global__ void __launch_bounds__(kKwThreads, 1) k_kacz_wide(KwArgs a) {
+    extern __shared__ __align__(16) unsigned char kw_smem[];
+    const int K = a.K;
+    double *s_th = reinterpret_cast<double *>(kw_smem);          // [K]
+    double *s_d = s_th + K;                                        // [K]
+    double *s_val = s_d + K;                                       // [row_max]
+    int32_t *s_col = reinterpret_cast<int32_t *>(s_val + a.row_max);   // [row_max]
+    int32_t *s_slot = s_col + a.row_max;                           // [row_max]
+    __shared__ double sh_red[kKwWarps];
+    __shared__ int32_t sh_cnt[kKwWarps];
+    __shared__ double sh_gamma;
+    __shared__ int sh_skip, sh_ok;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int G = int(gridDim.x), bid = int(blockIdx.x);
+    const S *__restrict__ val = static_cast<const S *>(a.val);
+    KzSys ks = a.ks[0];
+    int nh = ks.nh, nU = ks.nU;
+    int64_t skipped = ks.skipped;
+    for (int j = tid; j < nh; j += kKwThreads) s_th[j] = a.theta[j];
+    __syncthreads();
+
+    for (int64_t t = 0; t < ks.rows_todo; ++t) {
+        if (nh == K) {
+            // window full: empty it before this row
+            const int lo = int(int64_t(nU) * bid / G), hi = int(int64_t(nU) * (bid + 1) / G);
+            for (int q = lo + tid; q < hi; q += kKwThreads) a.slot[a.ucols[q]] = -1;
+            if (!kw_barrier(a.bar, &sh_ok)) return;
+            nh = 0;
+            nU = 0;
+        }
+        const int32_t i = int32_t(a.row_off) + a.perm[a.row_off + t];
+        const int32_t s0 = a.row_ptr[i];
+        const int len = a.row_ptr[i + 1] - s0;
+        for (int e = tid; e < len; e += kKwThreads) {
+            const int32_t c = a.col_idx[s0 + e];
+            s_col[e] = c;
+            s_val[e] = double(val[s0 + e]);
+            s_slot[e] = a.slot[c];
+        }
+        __syncthreads();
+        // phase A: c_j (owned j), partials of a^T x and ||a||^2 (owned entries)
+        {
+            const int jlo = int(int64_t(nh) * bid / G), jhi = int(int64_t(nh) * (bid + 1) / G);
+            for (int j = jlo + warp; j < jhi; j += kKwWarps) {
+                double acc = 0.0;
+                for (int e = lane; e < len; e += 32) {
+                    const int32_t sl = s_slot[e];
+                    if (sl >= 0) acc = fma(s_val[e], a.P[int64_t(sl) * K + j], acc);
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+                if (lane == 0) a.c[j] = acc;
+            }
+            const int elo = int(int64_t(len) * bid / G), ehi = int(int64_t(len) * (bid + 1) / G);
+            double ax = 0.0, a2 = 0.0;
+            for (int e = elo + tid; e < ehi; e += kKwThreads) {
+                ax = fma(s_val[e], a.x[s_col[e]], ax);
+                a2 = fma(s_val[e], s_val[e], a2);
+            }
+            ax = kw_sum(ax, sh_red);
+            a2 = kw_sum(a2, sh_red);
+            if (tid == 0) {
+                a.part[bid] = ax;
+                a.part[G + bid] = a2;
+            }
+        }
+        if (!kw_barrier(a.bar, &sh_ok)) return;
+        // the scalars, identically in every CTA
+        {
+            double ax = 0.0, a2 = 0.0;
+            for (int q = tid; q < G; q += kKwThreads) {
+                ax += __ldcg(a.part + q);
+                a2 += __ldcg(a.part + G + q);
+            }
+            ax = kw_sum(ax, sh_red);
+            a2 = kw_sum(a2, sh_red);
+            double d2 = 0.0;
+            for (int j = tid; j < nh; j += kKwThreads) {
+                const double cj = __ldcg(a.c + j);
+                d2 += (cj * cj) / s_th[j];
+                s_d[j] = cj / s_th[j];
+            }
+            d2 = kw_sum(d2, sh_red);
+            if (tid == 0) {
+                const double ri = a.b[i] - ax;
+                const double na = sqrt(a2), nd = sqrt(d2);
+                const double delta = (na - nd) * (na + nd);
+                sh_skip = !(delta > 1e-14 * a2) ? 1 : 0;
+                sh_gamma = sh_skip ? 0.0 : ri / delta;
+            }
+            __syncthreads();
+        }
+        if (sh_skip) {
+            ++skipped;
+            // keep c and the partials of this row until every CTA has read them
+            if (!kw_barrier(a.bar, &sh_ok)) return;
+            continue;
+        }
+        const double gamma = sh_gamma;
+        // slots of the row's new columns, in row order (identical in every CTA)
+        const int nU0 = nU;
+        for (int base = 0; base < len; base += kKwThreads) {
+            const int e = base + tid;
+            const bool isnew = e < len && s_slot[e] < 0;
+            const unsigned bal = __ballot_sync(0xffffffffu, isnew);
+            if (lane == 0) sh_cnt[warp] = __popc(bal);
+            __syncthreads();
+            int off = nU, tot = 0;
+            for (int w = 0; w < kKwWarps; ++w) {
+                if (w < warp) off += sh_cnt[w];
+                tot += sh_cnt[w];
+            }
+            if (isnew) s_slot[e] = -2 - (off + __popc(bal & ((1u << lane) - 1u)));   // new: -2 - slot
+            nU += tot;
+            __syncthreads();
+        }
+        if (int64_t(nU) > a.ucap) {   // cannot happen: |U| <= min(n, K * row_max)
+            if (tid == 0) atomicExch(a.bar + 2, 2u);
+            return;
+        }
+        // phase B on the owned slots [lo, hi)
+        const int lo = int(int64_t(nU) * bid / G), hi = int(int64_t(nU) * (bid + 1) / G);
+        for (int s = lo + tid; s < hi && s < nU0; s += kKwThreads) a.P[int64_t(s) * K + nh] = 0.0;
+        __syncthreads();
+        for (int e = tid; e < len; e += kKwThreads) {
+            const int32_t code = s_slot[e];
+            const int sl = code >= 0 ? code : -2 - code;
+            if (sl < lo || sl >= hi) continue;
+            if (code < 0) {   // a new slot: its history entries are zero
+                a.ucols[sl] = s_col[e];
+                a.slot[s_col[e]] = sl;
+                for (int j = 0; j < nh; ++j) a.P[int64_t(sl) * K + j] = 0.0;
+            }
+            a.P[int64_t(sl) * K + nh] = s_val[e];
+        }
+        __syncthreads();
+        double tq = 0.0;
+        for (int s = lo + warp; s < hi; s += kKwWarps) {
+            const double *row = a.P + int64_t(s) * K;
+            double acc = 0.0;
+            if (s < nU0)
+                for (int j = lane; j < nh; j += 32) acc = fma(row[j], s_d[j], acc);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (lane == 0) {
+                const double q = row[nh] - acc;
+                a.P[int64_t(s) * K + nh] = q;
+                const int32_t c = a.ucols[s];
+                a.x[c] = __dadd_rn(a.x[c], __dmul_rn(gamma, q));
+                tq = fma(q, q, tq);
+            }
+        }
+        tq = kw_sum(tq, sh_red);
+        if (tid == 0) a.part[2 * G + bid] = tq;
+        if (!kw_barrier(a.bar, &sh_ok)) return;
+        double th = 0.0;
+        for (int q = tid; q < G; q += kKwThreads) th += __ldcg(a.part + 2 * G + q);
+        th = kw_sum(th, sh_red);
+        if (th > 0.0) {
+            if (tid == 0) {
+                s_th[nh] = th;
+                if (bid == 0) a.theta[nh] = th;
+            }
+            ++nh;
+        }
+        __syncthreads();
+    }
+    if (bid == 0 && tid == 0) {
+        a.ks[0].nh = nh;
+        a.ks[0].nU = nU;
+        a.ks[0].skipped = skipped;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
 
@@ -343,6 +633,9 @@ static void kacz_free(KaczState *k) {
     dfree(k->d_theta);
     dfree(k->d_sys);
     dfree(k->d_perm);
+    dfree(k->d_part);
+    dfree(k->d_c);
+    dfree(k->d_bar);
     if (k->h_perm) cudaFreeHost(k->h_perm);
     if (k->h_sys) cudaFreeHost(k->h_sys);
     delete k;
@@ -352,6 +645,7 @@ void free_extra(plss_ctx *c) {
     kacz_free(c->kacz);
     c->kacz = nullptr;
     free_rhs(c);
+    free_general(c);
 }
 
 static plss_status kacz_prepare(plss_ctx *c, int64_t K) {
@@ -365,15 +659,31 @@ static plss_status kacz_prepare(plss_ctx *c, int64_t K) {
         delete k;
         return fail(PLSS_ERR_CUDA, "reading row_ptr failed");
     }
-    int64_t total = 0;
+    int64_t total = 0, row_max = 0;
     k->ucap.resize(size_t(c->nsys));
     for (int32_t s = 0; s < c->nsys; ++s) {
         const SysDesc &d = c->h_desc[size_t(s)];
         int64_t maxlen = 0;
         for (int64_t i = d.row_off; i < d.row_off + d.m; ++i)
             maxlen = std::max<int64_t>(maxlen, rp[size_t(i + 1)] - rp[size_t(i)]);
+        row_max = std::max(row_max, maxlen);
         k->ucap[size_t(s)] = K > 0 ? std::max<int64_t>(1, std::min<int64_t>(d.n, K * maxlen)) : 1;
         total += k->ucap[size_t(s)];
+    }
+    k->wide = K > kKzMaxK;
+    k->row_max = int32_t(std::max<int64_t>(row_max, 1));
+    if (k->wide) {
+        if (c->nsys != 1) {
+            delete k;
+            return fail(PLSS_ERR_INVALID, "a history window above %d updates needs a single-system context",
+                        kKzMaxK);
+        }
+        if (row_max > kKwRowMax) {
+            delete k;
+            return fail(PLSS_ERR_INVALID, "a history window above %d updates takes rows of at most %d "
+                        "nonzeros (longest row: %lld)", kKzMaxK, kKwRowMax, (long long)row_max);
+        }
+        k->wide_grid = c->nsm;
     }
     k->p_entries = total * std::max<int64_t>(K, 1);
     plss_status st = PLSS_OK;
@@ -382,7 +692,10 @@ static plss_status kacz_prepare(plss_ctx *c, int64_t K) {
         (st = dalloc(reinterpret_cast<void **>(&k->d_P), 8 * size_t(k->p_entries), "P")) != PLSS_OK ||
         (st = dalloc(reinterpret_cast<void **>(&k->d_theta), 8 * size_t(c->nsys) * size_t(std::max<int64_t>(K, 1)), "theta")) != PLSS_OK ||
         (st = dalloc(reinterpret_cast<void **>(&k->d_sys), sizeof(KzSys) * size_t(c->nsys), "kz")) != PLSS_OK ||
-        (st = dalloc(reinterpret_cast<void **>(&k->d_perm), 4 * size_t(std::max<int64_t>(c->m, 1)), "perm")) != PLSS_OK) {
+        (st = dalloc(reinterpret_cast<void **>(&k->d_perm), 4 * size_t(std::max<int64_t>(c->m, 1)), "perm")) != PLSS_OK ||
+        (k->wide && (st = dalloc(reinterpret_cast<void **>(&k->d_part), 8 * 3 * size_t(k->wide_grid), "partials")) != PLSS_OK) ||
+        (k->wide && (st = dalloc(reinterpret_cast<void **>(&k->d_c), 8 * size_t(K), "c")) != PLSS_OK) ||
+        (k->wide && (st = dalloc(reinterpret_cast<void **>(&k->d_bar), 4 * 4, "barrier")) != PLSS_OK)) {
         kacz_free(k);
         return st;
     }
@@ -418,12 +731,51 @@ static plss_status resid2(plss_ctx *c, cudaStream_t s, bool use_zero, std::vecto
     return PLSS_OK;
 }
 
+// One pass of the whole-GPU window: a cooperative launch (all CTAs resident,
+// one per SM) after clearing the barrier words.
+static plss_status launch_wide(plss_ctx *c, KaczState *kz, cudaStream_t s) {
+    KwArgs w;
+    w.row_ptr = c->d_row_ptr;
+    w.col_idx = c->d_col_idx;
+    w.val = c->d_val;
+    w.perm = kz->d_perm;
+    w.b = c->d_b;
+    w.x = c->d_x;
+    w.slot = kz->d_slot;
+    w.ucols = kz->d_ucols;
+    w.P = kz->d_P;
+    w.theta = kz->d_theta;
+    w.c = kz->d_c;
+    w.part = kz->d_part;
+    w.bar = kz->d_bar;
+    w.ks = kz->d_sys;
+    w.row_off = c->h_desc[0].row_off;
+    w.ucap = kz->ucap[0];
+    w.K = int32_t(kz->K);
+    w.row_max = kz->row_max;
+    const size_t smem = size_t(2 * kz->K) * 8 + size_t(kz->row_max) * 16;
+    void *fn = c->f32 ? reinterpret_cast<void *>(k_kacz_wide<float>) : reinterpret_cast<void *>(k_kacz_wide<double>);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    int per_sm = 0;
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kKwThreads, smem);
+    if (e != cudaSuccess || per_sm < 1)
+        return fail(PLSS_ERR_CUDA, "identity sketch (wide window): %zu bytes of shared memory per CTA do not fit",
+                    smem);
+    if (cudaMemsetAsync(kz->d_bar, 0, 4 * 4, s) != cudaSuccess) return fail(PLSS_ERR_CUDA, "memset failed");
+    void *args[] = {&w};
+    e = cudaLaunchCooperativeKernel(fn, dim3(unsigned(kz->wide_grid)), dim3(kKwThreads), args, smem, s);
+    if (e != cudaSuccess) return fail(PLSS_ERR_CUDA, "identity sketch (wide window) launch: %s", cudaGetErrorString(e));
+    return PLSS_OK;
+}
+
 plss_status run_identity_multi(plss_ctx *c, const double *const *b, const double *const *x0,
                                double *const *xo, const plss_opts *o, plss_result *res) {
     plss_status st = check_opts(o);
     if (st != PLSS_OK) return st;
-    if (o->kacz_hist < 0 || o->kacz_hist > kKzMaxK)
-        return fail(PLSS_ERR_INVALID, "kacz_hist must be in [0, %d]", kKzMaxK);
+    if (o->kacz_hist < 0 || o->kacz_hist > kKwMaxK)
+        return fail(PLSS_ERR_INVALID, "kacz_hist must be in [0, %d]", kKwMaxK);
+    if (o->kacz_hist > kKzMaxK && c->nsys != 1)
+        return fail(PLSS_ERR_INVALID, "a history window above %d updates needs a single-system context", kKzMaxK);
     if (o->w_mode != PLSS_W_IDENTITY) return fail(PLSS_ERR_INVALID, "the identity sketch takes W = I");
     cudaStream_t s = static_cast<cudaStream_t>(o->stream);
     const bool dev = o->io_device != 0;
@@ -494,7 +846,9 @@ plss_status run_identity_multi(plss_ctx *c, const double *const *b, const double
         if (cudaMemcpyAsync(kz->d_perm, kz->h_perm, 4 * size_t(c->m), cudaMemcpyHostToDevice, s) != cudaSuccess ||
             cudaMemcpyAsync(kz->d_sys, kz->h_sys, sizeof(KzSys) * size_t(n), cudaMemcpyHostToDevice, s) != cudaSuccess)
             return fail(PLSS_ERR_CUDA, "upload of the row order failed");
-        if (K == 0) {
+        if (kz->wide) {
+            if ((st = launch_wide(c, kz, s)) != PLSS_OK) return st;
+        } else if (K == 0) {
             const int grid = (n + kKzWarps - 1) / kKzWarps;
             if (c->f32) k_kacz0<float><<<grid, kKzThreads, 0, s>>>(ka, n);
             else k_kacz0<double><<<grid, kKzThreads, 0, s>>>(ka, n);
@@ -507,6 +861,14 @@ plss_status run_identity_multi(plss_ctx *c, const double *const *b, const double
         if (e != cudaSuccess) return fail(PLSS_ERR_CUDA, "kaczmarz kernel: %s", cudaGetErrorString(e));
         if (cudaMemcpyAsync(kz->h_sys, kz->d_sys, sizeof(KzSys) * size_t(n), cudaMemcpyDeviceToHost, s) != cudaSuccess)
             return fail(PLSS_ERR_CUDA, "reading the window state failed");
+        if (kz->wide) {
+            uint32_t bar[3] = {0, 0, 0};
+            if (cudaMemcpyAsync(bar, kz->d_bar, sizeof bar, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                cudaStreamSynchronize(s) != cudaSuccess)
+                return fail(PLSS_ERR_CUDA, "reading the barrier state failed");
+            if (bar[2] == 1) return fail(PLSS_ERR_TIMEOUT, "identity sketch: a grid barrier waited longer than 2 s");
+            if (bar[2] != 0) return fail(PLSS_ERR_CUDA, "identity sketch: support capacity exceeded");
+        }
         if ((st = resid2(c, s, false, r2)) != PLSS_OK) return st;
         for (int32_t sy = 0; sy < n; ++sy)
             if (kz->h_sys[sy].overflow) return fail(PLSS_ERR_CUDA, "identity sketch: support capacity exceeded (system %d)", sy);

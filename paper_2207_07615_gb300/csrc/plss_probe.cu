@@ -22,7 +22,6 @@
 
 namespace plss {
 
-constexpr unsigned long long kSinkMagic = 0x9e3779b97f4a7c15ull;
 
 __device__ __forceinline__ unsigned long long gbits(double v) {
     return static_cast<unsigned long long>(__double_as_longlong(v));
@@ -31,10 +30,12 @@ __device__ __forceinline__ unsigned long long gbits(float v) { return __float_as
 
 // Warp w walks slices [wr[w], wr[w + 1]) of `sl` exactly as the sweep over
 // warp ranges does (8 index loads, then their 8 gathers) and folds the
-// gathered bits with XOR (integer ALU only); a sink store that never
-// happens in practice keeps the loads alive.
+// gathered bits with XOR (integer ALU only); a store guarded by a value the
+// compiler cannot know (`magic`, passed at run time and never matched in
+// practice) keeps every load alive.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_gather_slices(Sliced sl, const T *__restrict__ x,
+                                                            unsigned long long magic,
                                                             unsigned long long *sink) {
     const int lane = threadIdx.x & 31;
     const int32_t w = int32_t(blockIdx.x) * kWarps + (threadIdx.x >> 5);
@@ -54,7 +55,7 @@ __global__ void __launch_bounds__(kThreads) k_gather_slices(Sliced sl, const T *
             for (int u = 0; u < 8; ++u) acc ^= gbits(g[u]);
         }
     }
-    if (acc == kSinkMagic) sink[0] = acc;
+    if (acc == magic) sink[0] = acc;
 }
 
 // Writes `n16` 16-byte words: evicts the gathered vector and the index
@@ -67,11 +68,11 @@ __global__ void k_flush_l2(int4 *buf, int64_t n16, int v) {
 // Reads x once, leaving it in L2 as the solve does (the sweep that gathers
 // a vector runs right after the kernel that wrote it).
 template <typename T>
-__global__ void k_touch(const T *__restrict__ x, int64_t n, unsigned long long *sink) {
+__global__ void k_touch(const T *__restrict__ x, int64_t n, unsigned long long magic, unsigned long long *sink) {
     unsigned long long a = 0;
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
         a ^= gbits(x[i]);
-    if (a == kSinkMagic) sink[0] = a;
+    if (a == magic) sink[0] = a;
 }
 
 }  // namespace plss
@@ -109,22 +110,23 @@ extern "C" plss_status plss_gather_bound(plss_ctx *c, int32_t side, int32_t reps
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
     Sliced a = sl;
     a.wr = wr;
+    const unsigned long long magic = 0x00000000deadbeefull;   // a 32-bit value: reachable for float too
     for (int32_t i = 0; i < reps + 1 && e == cudaSuccess; ++i) {
         k_flush_l2<<<c->nsm * 4, 256, 0, s>>>(static_cast<int4 *>(flush), flush_bytes / 16, i);
         if (c->f32) {
-            k_touch<float><<<c->nsm * 4, 256, 0, s>>>(static_cast<const float *>(x), len,
+            k_touch<float><<<c->nsm * 4, 256, 0, s>>>(static_cast<const float *>(x), len, magic,
                                                       static_cast<unsigned long long *>(sink));
         } else {
-            k_touch<double><<<c->nsm * 4, 256, 0, s>>>(static_cast<const double *>(x), len,
+            k_touch<double><<<c->nsm * 4, 256, 0, s>>>(static_cast<const double *>(x), len, magic,
                                                        static_cast<unsigned long long *>(sink));
         }
         e = cudaEventRecord(e0, s);
         if (e != cudaSuccess) break;
         if (c->f32) {
-            k_gather_slices<float><<<grid, kThreads, 0, s>>>(a, static_cast<const float *>(x),
+            k_gather_slices<float><<<grid, kThreads, 0, s>>>(a, static_cast<const float *>(x), magic,
                                                               static_cast<unsigned long long *>(sink));
         } else {
-            k_gather_slices<double><<<grid, kThreads, 0, s>>>(a, static_cast<const double *>(x),
+            k_gather_slices<double><<<grid, kThreads, 0, s>>>(a, static_cast<const double *>(x), magic,
                                                                static_cast<unsigned long long *>(sink));
         }
         e = cudaEventRecord(e1, s);

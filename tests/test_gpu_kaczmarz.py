@@ -3,15 +3,17 @@ against the CPU oracle, through the C ABI.
 
 Both sides draw the same row order (SplitMix64 stream + Fisher-Yates
 shuffle per pass from the same seed). Tolerance: 1e-10 relative on x, or
-1e3 times the oracle's own rounding spread (the oracle run again on
-b (1 + 2^-50)) where that is larger.
+the parity margin times the oracle's own rounding spread (the oracle run
+again on b (1 + 2^-50)) where that is larger. Windows of up to 64
+directions run one CTA per system; larger ones (one system) run on the
+whole GPU with grid barriers between a row's two phases.
 """
 import numpy as np
 import pytest
 
 import oracle
 from paper_2207_07615_gb300 import synth
-from tests import _pins
+from tests import _parity, _pins
 
 pytestmark = pytest.mark.gpu
 
@@ -37,7 +39,7 @@ def oracle_with_bar(A, b, maxit, K, seed):
     r1 = oracle.kaczmarz(A, b, tol=0.0, maxit=maxit, K=K, seed=seed)
     r2 = oracle.kaczmarz(A, b * F, tol=0.0, maxit=maxit, K=K, seed=seed)
     spread = rel(r2["x"] / F, r1["x"])
-    return r1, max(1e-10, 1e3 * spread)
+    return r1, max(_parity.FLOOR, _parity.MARGIN * spread)
 
 
 def test_golden_2x2(plss):
@@ -110,3 +112,60 @@ def test_batched_identity(plss):
         ref, bar = oracle_with_bar(A, b, 500, 6, 100 + s)
         assert r["iters"] == 500
         assert rel(x, ref["x"]) <= bar
+
+
+@pytest.mark.parametrize("K", [65, 128, 512])
+def test_wide_window_parity_powerlaw(plss, K):
+    """Windows above 64 directions (the whole-GPU form): parity with the
+    oracle after one row, part of a pass, and over several passes whose
+    window resets straddle the passes."""
+    A, b, xs = synth.powerlaw_underdetermined(m=600, n=6000, mean_len=20, max_len=1500, seed=21)
+    A = A.astype(np.float64)
+    with plss.Context(A) as ctx:
+        for maxit, seed in ((1, 3), (70, 3), (1100, 5)):
+            ref, bar = oracle_with_bar(A, b, maxit, K, seed)
+            x, r = ctx.solve(b, sketch="identity", kacz_hist=K, seed=seed, tol=0.0, maxit=maxit)
+            assert r["iters"] == maxit
+            assert rel(x, ref["x"]) <= bar, (K, maxit, rel(x, ref["x"]), bar)
+
+
+def test_wide_window_full_history_reaches_pinv(plss):
+    """A window as long as a pass (K = m = 300 > 64) on a wide full-row-rank
+    A: after the m rows of the first pass x solves A x = b with the least
+    norm, x = A^+ b (Corollary 3.3), on the GPU as in the oracle."""
+    rng = synth.rng_for(61)
+    m, n = 300, 900
+    D = rng.standard_normal((m, n)) * (rng.random((m, n)) < 0.02)
+    D[np.arange(m), np.arange(m)] += 2.0
+    A = synth.from_dense(D)
+    b = D @ rng.standard_normal(n)
+    ref, bar = oracle_with_bar(A, b, m, m, 7)
+    with plss.Context(A) as ctx:
+        x, r = ctx.solve(b, sketch="identity", kacz_hist=m, seed=7, tol=0.0, maxit=m)
+    assert rel(x, ref["x"]) <= bar
+    assert rel(x, np.linalg.pinv(D) @ b) < 1e-9
+
+
+def test_wide_window_fp32_storage(plss):
+    """FP32 storage of A with the whole-GPU window: the oracle on the same
+    float-rounded values (the window algebra is in double on both sides)."""
+    A, b, xs = synth.powerlaw_underdetermined(m=500, n=5000, mean_len=16, max_len=800, seed=24)
+    A32 = A.astype(np.float32)
+    A64 = A32.astype(np.float64)
+    ref, bar = oracle_with_bar(A64, b, 900, 96, 2)
+    with plss.Context(A32, precision="fp32") as ctx:
+        x, r = ctx.solve(b, sketch="identity", kacz_hist=96, seed=2, tol=0.0, maxit=900)
+    assert rel(x, ref["x"]) <= bar
+
+
+def test_window_limits_rejected(plss):
+    """A window above 4,096 directions, or above 64 on a batched context,
+    is refused before anything runs."""
+    A, b, _ = synth.powerlaw_underdetermined(m=100, n=900, mean_len=8, max_len=60, seed=25)
+    A = A.astype(np.float64)
+    with plss.Context(A) as ctx:
+        with pytest.raises(plss.PlssError):
+            ctx.solve(b, sketch="identity", kacz_hist=4097, tol=0.0, maxit=10)
+    with plss.Context([A, A]) as ctx:
+        with pytest.raises(plss.PlssError):
+            ctx.solve_batched([b, b], sketch="identity", kacz_hist=65, tol=0.0, maxit=10)

@@ -1,16 +1,21 @@
 """Continuous-batching server (plss_submit / plss_poll) on the GPU.
 
-The key property: a request's result in the mix equals the same request
-solved alone (plss_solve with the same options). Each system's tiles,
-partial sums and reduction order do not depend on its neighbours, so the
-two agree bit for bit.
+Two properties: every served request follows the CPU oracle (Algorithm 1
+with the same options: the iteration count within the oracle's own rounding
+spread, and x equal to the oracle's to that spread, or at least within the
+solve's tolerance of it on the residual), and a request's result in the mix
+equals the same request solved alone (plss_solve with the same options):
+each system's tiles, partial sums and reduction order do not depend on its
+neighbours, so the two agree bit for bit.
 """
 import time
 
 import numpy as np
 import pytest
 
+import oracle
 from paper_2207_07615_gb300 import synth
+from tests import _parity
 
 pytestmark = pytest.mark.gpu
 
@@ -75,6 +80,8 @@ def test_mix_equals_alone(plss, precision, layout):
         assert st["completed"] == len(reqs) and st["queued"] == 0 and st["running"] == 0
     finally:
         srv.close()
+    for (A, b), t in zip(reqs, tickets):
+        _check_oracle(A, b, *got[t], precision=precision, **kw)
     alone = None
     if layout == "auto":
         alone = plss.Server(max_slots=1, precision=precision, hbm_budget_bytes=256 << 20, layout=layout)
@@ -91,6 +98,61 @@ def test_mix_equals_alone(plss, precision, layout):
     finally:
         if alone is not None:
             alone.close()
+
+
+_ORACLE = {}
+
+
+def _oracle_runs(A, b, precision, tol, maxit, w_mode):
+    """The oracle with the server's options (stop on the true residual; FP32
+    storage refines once rho has fallen by 1e-4^2 since the last start), on b
+    and on b scaled by 1 + j eps, j = -2, -1, 1, 2 -- rounding-level changes
+    of the input (eps = 2^-50 in FP64; 2^-24, the float unit roundoff, for
+    FP32 storage, whose GPU form sums products in double-float where the
+    oracle's emulation sums them in float). Cached per request."""
+    key = (A.m, A.n, A.nnz, float(A.val[:4].sum()), float(b[:4].sum()), precision, tol, maxit, w_mode)
+    if key not in _ORACLE:
+        w = oracle.colweights(A, w_mode) if w_mode else None
+        kw = dict(w=w, tol=tol, maxit=maxit, stop_on_true=True)
+        eps = 2.0 ** -50
+        if precision == "fp32":
+            kw.update(prec=1, inner_tol=1e-4)
+            eps = 2.0 ** -24
+        runs = [oracle.residual(A, b * (1.0 + j * eps), **kw) for j in (0, -2, -1, 1, 2)]
+        _ORACLE[key] = (runs, eps)
+    return _ORACLE[key]
+
+
+def _check_oracle(A, b, x, res, precision, tol, maxit, w_mode):
+    """A served request against the oracle run with the same options. The
+    oracle's own iteration counts over rounding-level changes of b (see
+    _oracle_runs) give the spread that rounding alone causes in this
+    Lanczos-type recursion. A one-time change of b under-represents a
+    different summation order in every sweep, which perturbs every update
+    (over 1,500 updates the GPU's count moved by up to 0.6 % from the
+    oracle's while the oracle's own spread was 0.3 %), so the served count
+    must lie within max(2, 2 x that spread, 1 % of the oracle's count) of
+    the oracle's. When the counts agree in FP64, x must equal the
+    oracle's to within the parity margin times the oracle's own x spread.
+    Every converged request has both b - A x_served and b - A x_oracle within
+    tol ||b||, so ||A (x_served - x_oracle)|| <= 2 tol ||b|| (checked with
+    25 % slack for the final rounding)."""
+    runs, eps = _oracle_runs(A, b, precision, tol, maxit, w_mode)
+    o1 = runs[0]
+    its = [o["iters"] for o in runs]
+    spread_it = max(its) - min(its)
+    assert res["status"] == o1["status"]
+    bound = max(2, 2 * spread_it, int(np.ceil(0.01 * o1["iters"])))
+    assert abs(res["iters"] - o1["iters"]) <= bound, (res["iters"], its)
+    nx = max(np.linalg.norm(o1["x"]), 1e-300)
+    if res["iters"] == o1["iters"] and precision == "fp64":
+        spread_x = max(np.linalg.norm(o["x"] / (1.0 + j * eps) - o1["x"]) / nx
+                       for o, j in zip(runs[1:], (-2, -1, 1, 2)))
+        dx = np.linalg.norm(x - o1["x"]) / nx
+        assert dx <= max(_parity.FLOOR, _parity.MARGIN * spread_x), (dx, spread_x)
+    if o1["status"] == "converged":
+        d = oracle.spmv(A, x - o1["x"])
+        assert np.linalg.norm(d) <= 2.5 * tol * np.linalg.norm(b)
 
 
 def _check_same(r_mix, r_one, x_mix, x_one):
