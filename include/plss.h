@@ -8,7 +8,10 @@
  *     recursion of Theorem 4.1 as laid out in Algorithm 1 (Sec. 5), with an
  *     optional diagonal weight W (Sec. 4.1, eq:pkShortW);
  *   - identity sketch S_k = [e_{i_1} ... e_{i_k}] (Sec. 7, eq:pkKacz), the
- *     generalised Kaczmarz method, with a history window of K updates.
+ *     generalised Kaczmarz method, with a history window of K updates;
+ *   - general sketch S_k = [s_1 ... s_k] (Sec. 2, eq:genS) of random sign
+ *     columns, with the update of Corollary 2.2 (Sec. 2.4) and a history
+ *     of at most K directions.
  *
  * Conventions for every entry point:
  *   - Nothing is thrown across the ABI; each call returns a plss_status and
@@ -50,7 +53,12 @@ typedef enum {
     PLSS_ERR_NOT_FOUND = -7   /* unknown ticket                             */
 } plss_status;
 
-enum { PLSS_SKETCH_RESIDUAL = 0, PLSS_SKETCH_IDENTITY = 1 };
+/* Sketches: RESIDUAL (Sec. 4, Algorithm 1), IDENTITY (Sec. 7), GENERAL
+ * (Sec. 2.4: column k of S has entry i = -1 where bit 63 of output k*m + i
+ * of the SplitMix64 stream seeded with plss_opts.seed is set, else +1; the
+ * history of directions is capped at plss_opts.kacz_hist <= 1,024 and
+ * emptied when full; maxit caps the columns drawn; W = I). */
+enum { PLSS_SKETCH_RESIDUAL = 0, PLSS_SKETCH_IDENTITY = 1, PLSS_SKETCH_GENERAL = 2 };
 /* PLSS_FP64: A, vectors and sums in double.
  * PLSS_FP32: A and the vectors r, p, W y stored as float, sums of products
  * accumulated in float; inner products, the scalar recursion, x and a
@@ -107,8 +115,11 @@ typedef struct {
                             /* < 0 means n                                          */
     int64_t refine_period;  /* PLSS_FP32: also restart from b - A x every this many */
                             /* updates (<= 0: off)                                 */
-    int64_t kacz_hist;      /* identity sketch: history window K (0 = Kaczmarz)     */
-    uint64_t seed;          /* identity sketch: row-order stream seed               */
+    int64_t kacz_hist;      /* identity sketch: history window K (0 = Kaczmarz,    */
+                            /* <= 64 per system, <= 4,096 for one system);         */
+                            /* general sketch: history of directions (<= 1,024)    */
+    uint64_t seed;          /* identity sketch: row-order stream seed; general     */
+                            /* sketch: sketch-column stream seed                   */
     int32_t io_device;      /* 1: b, x0, x_out are device pointers                  */
     int32_t symmetric;      /* create: caller asserts A^T = A (square); A^T r then  */
                             /* reuses the CSR and no transpose is stored           */
@@ -214,7 +225,9 @@ plss_status plss_ctx_layout(const plss_ctx *ctx, int64_t out[6]);
  *   b[m], x0[n] (NULL = zero start), x_out[n]: host, or device when
  *   o->io_device. The residual sketch runs Algorithm 1; the identity sketch
  *   runs eq:pkKacz with rows in a fresh SplitMix64/Fisher-Yates permutation
- *   per pass (seed o->seed) and tests ||b - A x|| after every pass.
+ *   per pass (seed o->seed) and tests ||b - A x|| after every pass; the
+ *   general sketch draws one random sign column per step (Corollary 2.2)
+ *   and tests ||b - A x|| before every step.
  * Returns PLSS_OK, PLSS_NOT_CONVERGED (x_out holds the last iterate), or
  * PLSS_ERR_BREAKDOWN when phi_1 <= 0 (A^T r_0 = 0 with r_0 != 0: b is not in
  * range(A)) or when (sqrt(theta phi)/rho - 1)(sqrt(theta phi)/rho + 1) <= 0,

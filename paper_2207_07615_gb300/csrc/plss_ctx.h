@@ -20,6 +20,7 @@ constexpr int64_t kSmallMaxNnz = 1 << 20;       // cluster schedule: nonzeros pe
 constexpr int64_t kSmallAutoNnz = 1 << 16;      // ... chosen by AUTO up to this size (or for many systems)
 
 struct KaczState;   // identity-sketch buffers (plss_kaczmarz.cu)
+struct GeneralState;   // general-sketch buffers (plss_general.cu)
 struct RhsState;    // multi-right-hand-side buffers (plss_spmm.cu)
 
 }  // namespace plss
@@ -75,6 +76,7 @@ struct plss_ctx {
     int32_t clu_vec_bytes = 0;                    // cluster schedule: shared-memory vector copies (0: none)
 
     plss::KaczState *kacz = nullptr;
+    plss::GeneralState *gen = nullptr;
     plss::RhsState *rhs = nullptr;
 };
 
@@ -109,6 +111,10 @@ plss_status run_identity(plss_ctx *c, const double *b, const double *x0, double 
                          const plss_opts *o, plss_result *res);
 plss_status run_identity_multi(plss_ctx *c, const double *const *b, const double *const *x0,
                                double *const *xo, const plss_opts *o, plss_result *res);
+// general sketch (plss_general.cu)
+plss_status run_general(plss_ctx *c, const double *b, const double *x0, double *x_out,
+                        const plss_opts *o, plss_result *res);
+void free_general(plss_ctx *c);
 // per-context state of the other solvers
 void free_extra(plss_ctx *c);
 void free_rhs(plss_ctx *c);

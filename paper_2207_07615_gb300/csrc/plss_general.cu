@@ -1,0 +1,448 @@
+// plss_general.cu -- PLSS with a general sketch (Sec. 2.4) on the GPU.
+//
+// The sketch S_k = [s_1 ... s_k] (eq:genS) grows by one random sign column
+// per step; column k has entry i = -1 where bit 63 of output k*m + i of the
+// SplitMix64 stream seeded with `seed` is set, else +1, so every entry is
+// computed where it is needed from (seed, k, i) and no sketch is stored.
+// The update of Corollary 2.2 is
+//   p_k = (s_k^T r_{k-1} / delta_k) (y_k - Y_{k-1} N_{k-1} Y_{k-1}^T y_k),
+//   y_k = A^T s_k,  delta_k = y_k^T y_k - y_k^T Y_{k-1} N_{k-1} Y_{k-1}^T y_k.
+// Y_{k-1} N_{k-1} Y_{k-1}^T is the orthogonal projector onto span(Y_{k-1}),
+// which is also span(p_1 ... p_{k-1}) with the p_j mutually orthogonal
+// (Sec. 2.1). The GPU keeps that projector as the directions
+// q_j = y_j - (projection of y_j on the earlier ones), Theta = diag(||q_j||^2):
+//   c = Q^T y,  delta = y^T y - sum_j c_j^2 / theta_j,
+//   q = y - Q Theta^{-1} c,  p = (s^T r / delta) q,
+// the same numbers as Theorem 2.1's recursion for N without a k x k matrix:
+// each step streams the history Q (n x nh, one direction per column, column
+// j contiguous) twice, as two GEMVs spread over the whole GPU. The history
+// holds at most K directions and is emptied when full, as the oracle does.
+//
+// One step is five grid kernels, the kernel boundaries ordering them:
+//   g_rows     r = b - A x (CSR, x gathered), partials of ||r||^2 and s_k^T r;
+//              block 0 first folds the previous step's theta partials
+//              (theta of the last direction; nh += 1) and empties a full
+//              history
+//   g_cols     y = A^T s_k (CSC, s_k from the hash: no gather), ||y||^2 partials
+//   g_qty      partials of c = Q^T y over column ranges
+//   g_decide   one CTA: stop test on ||r||, c, d = c / theta, delta, gamma,
+//              the skip test
+//   g_update   q = y - Q d, column nh of Q, x += gamma q, theta partials
+// The host launches bodies of steps and reads the stop flag between them.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "plss.h"
+#include "plss_ctx.h"
+#include "plss_dev.cuh"
+#include "plss_launch.h"
+
+namespace plss {
+
+#define GS_TRY(expr)                                                                          \
+    do {                                                                                      \
+        cudaError_t e_ = (expr);                                                              \
+        if (e_ != cudaSuccess) {                                                              \
+            cudaGetLastError();                                                               \
+            return fail(PLSS_ERR_CUDA, "general sketch: %s: %s", #expr, cudaGetErrorString(e_)); \
+        }                                                                                     \
+    } while (0)
+
+constexpr int kGsThreads = 256;
+constexpr int kGsWarps = kGsThreads / 32;
+constexpr int kGsMaxK = 1024;
+constexpr int kGsLanes = 8;   // lanes per row / column in the sparse passes
+
+struct GsState {
+    double rr;        // ||r_{k-1}||^2 of the last g_rows
+    double nb2;       // ||b||^2
+    double tol;
+    double gamma;     // step of the current column
+    int64_t k;        // sketch columns drawn
+    int64_t maxit;
+    int64_t skipped;
+    int32_t nh;       // directions in the history
+    int32_t store;    // the last g_update produced a direction to keep
+    int32_t done;     // 0 running, 1 converged, 2 column cap reached
+    int32_t skip;     // this column is skipped (delta at rounding level)
+};
+
+struct GsArgs {
+    const int32_t *row_ptr;
+    const int32_t *col_idx;
+    const void *val;
+    const int32_t *col_ptr;
+    const int32_t *row_idx;
+    const void *cval;
+    const double *b;
+    double *x;
+    double *r;
+    double *y;
+    double *Q;         // [K][n]
+    double *theta;     // [K]
+    double *d;         // [K]: c_j, then c_j / theta_j
+    double *part_r;    // [2 * grid]: ||r||^2, s^T r
+    double *part_y;    // [grid]
+    double *part_c;    // [grid * K]
+    double *part_t;    // [grid]
+    GsState *st;
+    int64_t m, n;
+    uint64_t seed;
+    int32_t K, grid;
+};
+
+struct GeneralState {
+    int32_t K = -1;
+    int32_t grid = 0;
+    double *d_Q = nullptr, *d_theta = nullptr, *d_d = nullptr, *d_y = nullptr, *d_r = nullptr;
+    double *d_part = nullptr;
+    GsState *d_st = nullptr;
+    GsState *h_st = nullptr;   // pinned
+};
+
+// Sign of sketch entry (k, i): bit 63 of SplitMix64 output k*m + i.
+__device__ __forceinline__ double gs_sign(uint64_t seed, int64_t m, int64_t k, int64_t i) {
+    uint64_t z = seed + (uint64_t(k) * uint64_t(m) + uint64_t(i) + 1ull) * 0x9e3779b97f4a7c15ull;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    z ^= z >> 31;
+    return (z >> 63) ? -1.0 : 1.0;
+}
+
+// Fixed-order CTA sum; the result is valid in thread 0.
+__device__ __forceinline__ double gs_sum(double v, double *sh) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < kGsWarps; ++w) t += sh[w];
+    __syncthreads();
+    return t;
+}
+
+// Contiguous share [lo, hi) of `len` items for this CTA.
+__device__ __forceinline__ void gs_range(int64_t len, int64_t &lo, int64_t &hi) {
+    lo = len * int64_t(blockIdx.x) / int64_t(gridDim.x);
+    hi = len * int64_t(blockIdx.x + 1) / int64_t(gridDim.x);
+}
+
+template <typename S>
+__global__ void __launch_bounds__(kGsThreads) g_rows(GsArgs a) {
+    __shared__ double sh[kGsWarps];
+    GsState *st = a.st;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && st->done == 0) {
+        // the previous column's direction: theta = ||q||^2 in block order
+        if (st->store) {
+            double th = 0.0;
+            for (int g = 0; g < a.grid; ++g) th += a.part_t[g];
+            if (th > 0.0) {
+                a.theta[st->nh] = th;
+                st->nh += 1;
+            }
+            st->store = 0;
+        }
+        if (a.K > 0 && st->nh == a.K) st->nh = 0;   // history full: start a new one
+    }
+    if (st->done) return;
+    const S *__restrict__ val = static_cast<const S *>(a.val);
+    const int grp = threadIdx.x / kGsLanes, gl = threadIdx.x % kGsLanes;
+    int64_t lo, hi;
+    gs_range(a.m, lo, hi);
+    const int64_t k = st->k;
+    double rr = 0.0, sr = 0.0;
+    for (int64_t base = lo; base < hi; base += kGsThreads / kGsLanes) {
+        const int64_t i = base + grp;
+        double dsum = 0.0;
+        if (i < hi)
+            for (int32_t q = a.row_ptr[i] + gl; q < a.row_ptr[i + 1]; q += kGsLanes)
+                dsum = fma(double(val[q]), a.x[a.col_idx[q]], dsum);
+#pragma unroll
+        for (int o = kGsLanes / 2; o > 0; o >>= 1) dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
+        if (i < hi && gl == 0) {
+            const double ri = a.b[i] - dsum;
+            a.r[i] = ri;
+            rr = fma(ri, ri, rr);
+            sr = fma(gs_sign(a.seed, a.m, k, i), ri, sr);
+        }
+    }
+    rr = gs_sum(rr, sh);
+    sr = gs_sum(sr, sh);
+    if (threadIdx.x == 0) {
+        a.part_r[2 * blockIdx.x] = rr;
+        a.part_r[2 * blockIdx.x + 1] = sr;
+    }
+}
+
+// y = A^T s_k over the columns (CSC, or the CSR of a symmetric A).
+template <typename S>
+__global__ void __launch_bounds__(kGsThreads) g_cols(GsArgs a) {
+    __shared__ double sh[kGsWarps];
+    const GsState *st = a.st;
+    if (st->done) return;
+    const S *__restrict__ val = static_cast<const S *>(a.cval);
+    const int grp = threadIdx.x / kGsLanes, gl = threadIdx.x % kGsLanes;
+    int64_t lo, hi;
+    gs_range(a.n, lo, hi);
+    const int64_t k = st->k;
+    double yy = 0.0;
+    for (int64_t base = lo; base < hi; base += kGsThreads / kGsLanes) {
+        const int64_t j = base + grp;
+        double dsum = 0.0;
+        if (j < hi)
+            for (int32_t q = a.col_ptr[j] + gl; q < a.col_ptr[j + 1]; q += kGsLanes)
+                dsum = fma(double(val[q]), gs_sign(a.seed, a.m, k, a.row_idx[q]), dsum);
+#pragma unroll
+        for (int o = kGsLanes / 2; o > 0; o >>= 1) dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
+        if (j < hi && gl == 0) {
+            a.y[j] = dsum;
+            yy = fma(dsum, dsum, yy);
+        }
+    }
+    yy = gs_sum(yy, sh);
+    if (threadIdx.x == 0) a.part_y[blockIdx.x] = yy;
+}
+
+// Partials of c_j = q_j^T y over this CTA's column range, all j < nh: warp w
+// takes directions j = w, w + 8, ...; its lanes stride the range.
+__global__ void __launch_bounds__(kGsThreads) g_qty(GsArgs a) {
+    const GsState *st = a.st;
+    if (st->done) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nh = st->nh;
+    int64_t lo, hi;
+    gs_range(a.n, lo, hi);
+    for (int j = warp; j < nh; j += kGsWarps) {
+        const double *q = a.Q + int64_t(j) * a.n;
+        double acc = 0.0;
+        for (int64_t t = lo + lane; t < hi; t += 32) acc = fma(q[t], a.y[t], acc);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) a.part_c[int64_t(blockIdx.x) * a.K + j] = acc;
+    }
+}
+
+// One CTA: the stop test on r_{k-1}, then c, d, delta, gamma for column k.
+__global__ void __launch_bounds__(kGsThreads) g_decide(GsArgs a) {
+    __shared__ double sh[kGsWarps];
+    __shared__ int sh_go;
+    GsState *st = a.st;
+    if (st->done) return;
+    double rr = 0.0, sr = 0.0, yy = 0.0;
+    for (int g = threadIdx.x; g < a.grid; g += kGsThreads) {
+        rr += a.part_r[2 * g];
+        sr += a.part_r[2 * g + 1];
+        yy += a.part_y[g];
+    }
+    rr = gs_sum(rr, sh);
+    sr = gs_sum(sr, sh);
+    yy = gs_sum(yy, sh);
+    if (threadIdx.x == 0) {
+        st->rr = rr;
+        int go = 1;
+        if (st->nb2 == 0.0 || sqrt(rr) <= st->tol * sqrt(st->nb2)) {
+            st->done = 1;
+            go = 0;
+        } else if (st->k >= st->maxit) {
+            st->done = 2;
+            go = 0;
+        }
+        sh_go = go;
+    }
+    __syncthreads();
+    if (!sh_go) return;
+    const int nh = st->nh;
+    // c_j = sum over CTAs of the partials (CTA order), d_j = c_j / theta_j
+    double d2 = 0.0;
+    for (int j = threadIdx.x; j < nh; j += kGsThreads) {
+        double c = 0.0;
+        for (int g = 0; g < a.grid; ++g) c += a.part_c[int64_t(g) * a.K + j];
+        d2 += (c * c) / a.theta[j];
+        a.d[j] = c / a.theta[j];
+    }
+    d2 = gs_sum(d2, sh);
+    if (threadIdx.x == 0) {
+        const double ny = sqrt(yy), nd = sqrt(d2);
+        const double delta = (ny - nd) * (ny + nd);
+        st->skip = !(delta > 1e-14 * yy) ? 1 : 0;
+        st->gamma = st->skip ? 0.0 : sr / delta;
+        if (st->skip) st->skipped += 1;
+        st->k += 1;
+    }
+}
+
+// q = y - Q d on this CTA's column range: column nh of Q (when the history
+// keeps directions), x += gamma q, theta partial.
+__global__ void __launch_bounds__(kGsThreads) g_update(GsArgs a) {
+    __shared__ double sh[kGsWarps];
+    __shared__ double sd[kGsMaxK];
+    GsState *st = a.st;
+    if (st->done || st->skip) return;
+    const int nh = st->nh;
+    const double gamma = st->gamma;
+    for (int j = threadIdx.x; j < nh; j += kGsThreads) sd[j] = a.d[j];
+    __syncthreads();
+    int64_t lo, hi;
+    gs_range(a.n, lo, hi);
+    double tq = 0.0;
+    for (int64_t t = lo + threadIdx.x; t < hi; t += kGsThreads) {
+        double q = a.y[t];
+        for (int j = 0; j < nh; ++j) q -= a.Q[int64_t(j) * a.n + t] * sd[j];
+        if (a.K > 0) a.Q[int64_t(nh) * a.n + t] = q;
+        a.x[t] = __dadd_rn(a.x[t], __dmul_rn(gamma, q));
+        tq = fma(q, q, tq);
+    }
+    tq = gs_sum(tq, sh);
+    if (threadIdx.x == 0) a.part_t[blockIdx.x] = tq;
+    if (blockIdx.x == 0 && threadIdx.x == 0) st->store = a.K > 0 ? 1 : 0;
+}
+
+__global__ void g_norm2(const double *v, int64_t len, double *out) {
+    __shared__ double sh[kGsWarps];
+    double acc = 0.0;
+    for (int64_t i = threadIdx.x; i < len; i += kGsThreads) acc = fma(v[i], v[i], acc);
+    acc = gs_sum(acc, sh);
+    if (threadIdx.x == 0) *out = acc;
+}
+
+static void general_free(GeneralState *g) {
+    if (!g) return;
+    dfree(g->d_Q);
+    dfree(g->d_theta);
+    dfree(g->d_d);
+    dfree(g->d_y);
+    dfree(g->d_r);
+    dfree(g->d_part);
+    dfree(g->d_st);
+    if (g->h_st) cudaFreeHost(g->h_st);
+    delete g;
+}
+
+void free_general(plss_ctx *c) {
+    general_free(c->gen);
+    c->gen = nullptr;
+}
+
+static plss_status general_prepare(plss_ctx *c, int32_t K) {
+    if (c->gen && c->gen->K == K) return PLSS_OK;
+    free_general(c);
+    GeneralState *g = new GeneralState();
+    g->K = K;
+    g->grid = c->nsm * 4;
+    const size_t Kc = size_t(std::max(K, 1));
+    plss_status st = PLSS_OK;
+    if ((st = dalloc(reinterpret_cast<void **>(&g->d_Q), 8 * Kc * size_t(std::max<int64_t>(c->n, 1)), "Q")) != PLSS_OK ||
+        (st = dalloc(reinterpret_cast<void **>(&g->d_theta), 8 * Kc, "theta")) != PLSS_OK ||
+        (st = dalloc(reinterpret_cast<void **>(&g->d_d), 8 * Kc, "d")) != PLSS_OK ||
+        (st = dalloc(reinterpret_cast<void **>(&g->d_y), 8 * size_t(std::max<int64_t>(c->n, 1)), "y")) != PLSS_OK ||
+        (st = dalloc(reinterpret_cast<void **>(&g->d_r), 8 * size_t(std::max<int64_t>(c->m, 1)), "r")) != PLSS_OK ||
+        (st = dalloc(reinterpret_cast<void **>(&g->d_part), 8 * size_t(g->grid) * (4 + Kc), "partials")) != PLSS_OK ||
+        (st = dalloc(reinterpret_cast<void **>(&g->d_st), sizeof(GsState), "state")) != PLSS_OK) {
+        general_free(g);
+        return st;
+    }
+    if (cudaMallocHost(reinterpret_cast<void **>(&g->h_st), sizeof(GsState)) != cudaSuccess) {
+        general_free(g);
+        return fail(PLSS_ERR_NOMEM, "pinned allocation failed");
+    }
+    c->gen = g;
+    return PLSS_OK;
+}
+
+plss_status run_general(plss_ctx *c, const double *b, const double *x0, double *x_out, const plss_opts *o,
+                        plss_result *res) {
+    plss_status st = check_opts(o);
+    if (st != PLSS_OK) return st;
+    if (o->kacz_hist < 0 || o->kacz_hist > kGsMaxK)
+        return fail(PLSS_ERR_INVALID, "the general sketch keeps a history of 0..%d directions (kacz_hist)", kGsMaxK);
+    if (o->w_mode != PLSS_W_IDENTITY) return fail(PLSS_ERR_INVALID, "the general sketch takes W = I");
+    cudaStream_t s = static_cast<cudaStream_t>(o->stream);
+    const bool dev = o->io_device != 0;
+    const int32_t K = int32_t(o->kacz_hist);
+    if ((st = general_prepare(c, K)) != PLSS_OK) return st;
+    GeneralState *g = c->gen;
+    if (c->m > 0 && !b) return fail(PLSS_ERR_INVALID, "b is NULL");
+    if ((st = put_vec(c->d_b, b, c->m, dev, s)) != PLSS_OK) return st;
+    if ((st = put_vec(c->d_x, x0, c->n, dev, s)) != PLSS_OK) return st;
+
+    GsArgs a;
+    a.row_ptr = c->d_row_ptr;
+    a.col_idx = c->d_col_idx;
+    a.val = c->d_val;
+    a.col_ptr = c->d_col_ptr;
+    a.row_idx = c->d_row_idx;
+    a.cval = c->d_cval;
+    a.b = c->d_b;
+    a.x = c->d_x;
+    a.r = g->d_r;
+    a.y = g->d_y;
+    a.Q = g->d_Q;
+    a.theta = g->d_theta;
+    a.d = g->d_d;
+    a.part_r = g->d_part;
+    a.part_y = g->d_part + 2 * g->grid;
+    a.part_t = g->d_part + 3 * g->grid;
+    a.part_c = g->d_part + 4 * g->grid;
+    a.st = g->d_st;
+    a.m = c->m;
+    a.n = c->n;
+    a.seed = o->seed;
+    a.K = K;
+    a.grid = g->grid;
+
+    GsState z{};
+    z.tol = o->tol;
+    z.maxit = o->maxit < 0 ? c->n : o->maxit;
+    *g->h_st = z;
+    GS_TRY(cudaMemcpyAsync(g->d_st, g->h_st, sizeof(GsState), cudaMemcpyHostToDevice, s));
+    g_norm2<<<1, kGsThreads, 0, s>>>(c->d_b, c->m, &g->d_st->nb2);
+    GS_TRY(cudaEventRecord(c->ev0, s));
+    const int grid = g->grid;
+    const int64_t body = 16;   // steps between reads of the stop flag
+    for (int64_t it = 0;; it += body) {
+        for (int64_t q = 0; q < body; ++q) {
+            if (c->f32) {
+                g_rows<float><<<grid, kGsThreads, 0, s>>>(a);
+                g_cols<float><<<grid, kGsThreads, 0, s>>>(a);
+            } else {
+                g_rows<double><<<grid, kGsThreads, 0, s>>>(a);
+                g_cols<double><<<grid, kGsThreads, 0, s>>>(a);
+            }
+            g_qty<<<grid, kGsThreads, 0, s>>>(a);
+            g_decide<<<1, kGsThreads, 0, s>>>(a);
+            g_update<<<grid, kGsThreads, 0, s>>>(a);
+        }
+        GS_TRY(cudaGetLastError());
+        GS_TRY(cudaMemcpyAsync(g->h_st, g->d_st, sizeof(GsState), cudaMemcpyDeviceToHost, s));
+        GS_TRY(cudaStreamSynchronize(s));
+        if (g->h_st->done) break;
+        if (it > z.maxit + 2 * body) return fail(PLSS_ERR_TIMEOUT, "general sketch: step driver overran");
+    }
+    GS_TRY(cudaEventRecord(c->ev1, s));
+    if ((st = get_vec(x_out, c->d_x, c->n, dev, s)) != PLSS_OK) return st;
+    GS_TRY(cudaStreamSynchronize(s));
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+    const GsState &h = *g->h_st;
+    // the last g_rows formed r for the returned x (the stop test ran on it)
+    const double nb = std::sqrt(h.nb2);
+    const double rel = nb > 0.0 ? std::sqrt(h.rr) / nb : 0.0;
+    const plss_status out = h.done == 1 ? PLSS_OK : PLSS_NOT_CONVERGED;
+    if (res) {
+        res->status = out;
+        res->reserved = 0;
+        res->iters = h.k;
+        res->relres_rec = rel;
+        res->relres_true = rel;
+        res->seconds = double(ms) * 1e-3;
+    }
+    return out;
+}
+
+}  // namespace plss

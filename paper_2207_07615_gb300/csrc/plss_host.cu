@@ -846,6 +846,7 @@ plss_status plss_solve(plss_ctx *ctx, const double *b, const double *x0, double 
     plss_opts_default(&od);
     if (!o) o = &od;
     if (o->sketch == PLSS_SKETCH_IDENTITY) return run_identity(ctx, b, x0, x_out, o, res);
+    if (o->sketch == PLSS_SKETCH_GENERAL) return run_general(ctx, b, x0, x_out, o, res);
     if (o->sketch != PLSS_SKETCH_RESIDUAL) return fail(PLSS_ERR_INVALID, "unknown sketch %d", o->sketch);
     const double *bb[1] = {b};
     const double *xx[1] = {x0};

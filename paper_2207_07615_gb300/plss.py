@@ -21,7 +21,7 @@ ERR_INVALID, ERR_NOMEM, ERR_CUDA, ERR_BREAKDOWN, ERR_TIMEOUT, ERR_BUSY, ERR_NOT_
     -1, -2, -3, -4, -5, -6, -7
 STATUS_NAMES = {0: "converged", 1: "not_converged", 2: "pending", -1: "invalid", -2: "nomem",
                 -3: "cuda", -4: "breakdown", -5: "timeout", -6: "busy", -7: "not_found"}
-SKETCH = {"residual": 0, "identity": 1}
+SKETCH = {"residual": 0, "identity": 1, "general": 2}
 PRECISION = {"fp64": 0, "fp32": 1}
 LAYOUT = {"auto": 0, "csr": 1}
 SCHEDULE = {"auto": 0, "grid": 1, "small": 2}
