@@ -73,6 +73,20 @@
 #include <stdlib.h>
 #include <string.h>
 
+/* The same file built with -fopenmp (oracle/__init__.py, residual_omp)
+ * runs the residual sketch's row, column and vector loops on all host cores
+ * (timing only: the pins use the plain build, where these expand to
+ * nothing). Rows, columns and entries are independent; the dot products
+ * become per-thread partial sums combined by OpenMP. */
+#ifdef _OPENMP
+#define PAR_FOR _Pragma("omp parallel for schedule(static)")
+#define PAR_SUM(v) _Pragma(PAR_STR(omp parallel for schedule(static) reduction(+ : v)))
+#define PAR_STR(x) #x
+#else
+#define PAR_FOR
+#define PAR_SUM(v)
+#endif
+
 enum {
     ORC_CONVERGED = 0,
     ORC_NOT_CONVERGED = 1,
@@ -121,6 +135,7 @@ static void csr_to_csc(int64_t m, int64_t n, const int64_t *row_ptr, const int32
 static void csc_spmv(int64_t n, const int64_t *col_ptr, const int64_t *row_idx,
                      const double *cval, const double *r, double *out)
 {
+    PAR_FOR
     for (int64_t j = 0; j < n; ++j) {
         double s = 0.0;
         for (int64_t k = col_ptr[j]; k < col_ptr[j + 1]; ++k)
@@ -147,6 +162,7 @@ int plss_oracle_spmvt(int64_t m, int64_t n, const int64_t *row_ptr, const int32_
 static double dot(int64_t len, const double *a, const double *b)
 {
     double s = 0.0;
+    PAR_SUM(s)
     for (int64_t i = 0; i < len; ++i) s += a[i] * b[i];
     return s;
 }
@@ -179,6 +195,7 @@ static inline double rf(double v, int f32) { return f32 ? (double)(float)v : v; 
 static void true_residual(int64_t m, const int64_t *row_ptr, const int32_t *col_idx,
                           const double *val, const double *b, const double *x, double *r)
 {
+    PAR_FOR
     for (int64_t i = 0; i < m; ++i) {
         double s = 0.0;
         for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k)
@@ -291,8 +308,10 @@ int plss_oracle_residual(int64_t m, int64_t n, const int64_t *row_ptr, const int
                 y[j] = (double)s;
             }
         }
+        PAR_FOR
         for (int64_t j = 0; j < n; ++j) u[j] = rf(w ? w[j] * y[j] : y[j], f32);
         phi = 0.0;
+        PAR_SUM(phi)
         for (int64_t j = 0; j < n; ++j) phi += y[j] * u[j];
 
         if (restart) {
@@ -320,11 +339,14 @@ int plss_oracle_residual(int64_t m, int64_t n, const int64_t *row_ptr, const int
                 gamma = theta / (theta * phi - rho * rho);   /* statement form */
             else
                 gamma = (theta / rho) * beta;                /* Algorithm 1 */
+            PAR_FOR
             for (int64_t j = 0; j < n; ++j) p[j] = rf(beta * p[j] + gamma * u[j], f32);
         }
         /* theta = p^T W^{-1} p; x = x + p */
         theta = 0.0;
+        PAR_SUM(theta)
         for (int64_t j = 0; j < n; ++j) theta += w ? (p[j] * p[j]) / w[j] : p[j] * p[j];
+        PAR_FOR
         for (int64_t j = 0; j < n; ++j) x[j] += p[j];
         if (hist_s && k < hist_cap) {
             double *h = hist_s + k * 5;
@@ -344,6 +366,7 @@ int plss_oracle_residual(int64_t m, int64_t n, const int64_t *row_ptr, const int
             restart = 1; since = 0;
         } else if (!f32) {
             /* r = r - A p */
+            PAR_FOR
             for (int64_t i = 0; i < m; ++i) {
                 double s = 0.0;
                 for (int64_t q = row_ptr[i]; q < row_ptr[i + 1]; ++q)
