@@ -34,9 +34,12 @@ from paper_2207_07615_gb300 import synth  # noqa: E402
 
 WORKLOAD = "plss_overdetermined_1e6x2e5_nnz8_colscale1e-2..1e2"
 METRIC = "time to ||r||/||b||<=1e-8"
-# Updates the FP64 W = I solve of this workload needs on GB300 (measured by
-# this benchmark; the reference arm scales its sampled per-update time by it).
-REF_UPDATES_TO_TOL = 183000
+# Updates the FP64 W = I solve of this workload takes to the tolerance: the
+# GPU arm's own count in its round-end run on GB300 (181,415; rounding moves
+# it by well under 0.1 % between runs). The reference arm runs without the
+# GPU arm's result, so it scales its sampled per-update time by this count;
+# the GPU arm's own cpu_baseline scales by the count its solve just took.
+REF_UPDATES_TO_TOL = 181415
 L2_FLUSH_BYTES = 512 << 20
 PROFILE_PERIOD = 16
 
@@ -59,6 +62,10 @@ def parse():
     ap.add_argument("--oracle-updates", type=int, default=100)
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the compact lines of the other workloads in the headline run")
+    ap.add_argument("--omp-updates", type=int, default=1000,
+                    help="updates of the all-cores oracle sample")
     ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4a", "c4b", "c5"],
                     help="c2 (default): the headline line; the others print one line each for "
                          "the other synthetic workloads (see suite_* below)")
@@ -258,26 +265,42 @@ def make_workload(args):
     return A, b, xs
 
 
-def cpu_baseline(A, b, args, updates_to_tol):
+def cpu_baseline(A, b, args, updates_to_tol, all_cores=True):
     """The oracle (plain C, 1 thread) on a bounded sample: the time of a
     1-update solve (set-up included) plus the per-update time of the next
-    `oracle_updates` updates, scaled to the updates the solve needs."""
+    `oracle_updates` updates, scaled to the updates the solve needs; and the
+    same source built with OpenMP on every host core, sampled over
+    `omp_updates` updates and scaled the same way."""
     import oracle
     oracle.build()
     prec = 1 if args.prec == "fp32" else 0
     w = oracle.colweights(A, args.w_mode) if args.w_mode else None
-    t0 = time.perf_counter()
-    oracle.residual(A, b, w=w, tol=0.0, maxit=1, prec=prec)
-    t1 = time.perf_counter()
-    oracle.residual(A, b, w=w, tol=0.0, maxit=1 + args.oracle_updates, prec=prec)
-    t2 = time.perf_counter()
-    per_update = ((t2 - t1) - (t1 - t0)) / args.oracle_updates
-    value = (t1 - t0) + per_update * max(0, updates_to_tol - 1)
+
+    def sample(updates, threads):
+        t0 = time.perf_counter()
+        oracle.residual(A, b, w=w, tol=0.0, maxit=1, prec=prec, threads=threads)
+        t1 = time.perf_counter()
+        oracle.residual(A, b, w=w, tol=0.0, maxit=1 + updates, prec=prec, threads=threads)
+        t2 = time.perf_counter()
+        per = ((t2 - t1) - (t1 - t0)) / updates
+        return (t1 - t0) + per * max(0, updates_to_tol - 1), t1 - t0, per
+
     cpu, cores = host_info()
-    return {"value": value, "unit": "s", "cores": 1, "kind": "oracle",
-            "sample": (f"1 update ({t1 - t0:.2f} s incl. set-up) + {args.oracle_updates} updates "
-                       f"({per_update * 1e3:.1f} ms/update) of the same system, scaled to "
-                       f"{updates_to_tol} updates; host {cpu}, {cores} cores, 1 used")}
+    value, t_setup, per = sample(args.oracle_updates, False)
+    out = {"value": value, "unit": "s", "cores": 1, "kind": "oracle",
+           "sample": (f"1 update ({t_setup:.2f} s incl. set-up) + {args.oracle_updates} updates "
+                      f"({per * 1e3:.1f} ms/update) of the same system, scaled to "
+                      f"{updates_to_tol} updates; host {cpu}, {cores} cores, 1 used")}
+    if all_cores and prec == 0:
+        try:
+            v2, s2, p2 = sample(args.omp_updates, True)
+            nthreads = int(os.environ.get("OMP_NUM_THREADS", cores or 1))
+            out["all_cores"] = {"value": v2, "unit": "s", "cores": nthreads, "kind": "oracle (OpenMP build)",
+                                "sample": (f"1 update ({s2:.2f} s) + {args.omp_updates} updates "
+                                           f"({p2 * 1e3:.2f} ms/update), scaled to {updates_to_tol} updates")}
+        except RuntimeError as e:
+            out["all_cores"] = {"unavailable": str(e)}
+    return out
 
 
 # ------------------------------------------------------------ reference arm
@@ -295,7 +318,7 @@ def run_reference(args):
     t_all = time.perf_counter()
     vals = []
     for i in range(args.warmup + args.steps):
-        cb = cpu_baseline(A, b, args, REF_UPDATES_TO_TOL)
+        cb = cpu_baseline(A, b, args, REF_UPDATES_TO_TOL, all_cores=False)
         if i >= args.warmup:
             vals.append(cb["value"])
     wall = time.perf_counter() - t_all
@@ -375,17 +398,31 @@ def run_plss(args):
     x_np = x.cpu().numpy()
     err_xstar = float(np.linalg.norm(x_np - xs) / np.linalg.norm(xs))
 
-    # roofline of the dominant sweep
+    # roofline of the dominant sweep. CUDA events bracket every kernel of one
+    # chunk of updates in PROFILE_PERIOD; an event between two kernels stops
+    # the second from starting under the first's tail (programmatic
+    # dependent launch), so the event-timed kernels of an update add up to
+    # more than an unprofiled update takes. Each kernel's time is therefore
+    # its event time scaled by (device time per update of the timed solves,
+    # which carry events in 1 chunk of 16) / (sum of the event times of the
+    # three kernels): its share of the measured update.
     peaks, peak_src = measured_peaks()
     kinds = ("row_sweep", "col_sweep", "update")
     per = {}
     for k in kinds:
         ms, cnt = kt[k]
         if cnt > 0:
-            avg = ms / cnt
-            byt = sweep_bytes(k, m, n, nnz, sv)
-            per[k] = {"ms_total": ms, "launches": cnt, "us_per_launch": avg * 1e3,
-                      "bytes_per_launch": byt, "gbs": byt / (avg * 1e-3) / 1e9}
+            per[k] = {"ms_total_events": ms, "launches": cnt, "us_per_launch_events": ms / cnt * 1e3,
+                      "bytes_per_launch": sweep_bytes(k, m, n, nnz, sv)}
+    us_update = ms_step * 1e3 / max(1, last["iters"])
+    ev_sum = sum(v["us_per_launch_events"] for v in per.values())
+    share = us_update / ev_sum if len(per) == 3 and ev_sum > 0 else 1.0
+    for k, v in per.items():
+        v["us_per_launch"] = v["us_per_launch_events"] * share
+        v["share_of_update"] = v["us_per_launch"] / us_update
+        v["gbs"] = v["bytes_per_launch"] / (v["us_per_launch"] * 1e-6) / 1e9
+        v["gbs_events"] = v["bytes_per_launch"] / (v["us_per_launch_events"] * 1e-6) / 1e9
+        v["ms_total"] = v["us_per_launch"] * v["launches"] * 1e-3
     dom = max(per, key=lambda k: per[k]["ms_total"]) if per else None
     roof = None
     if dom:
@@ -394,7 +431,12 @@ def run_plss(args):
                 "unit": "GB/s", "frac": ach / peaks["hbm_gbs"],
                 "traffic": ncu_traffic(dom), "peak_source": f"{peak_src} hbm_gbs (copy)",
                 "algorithmic_bytes_per_launch": per[dom]["bytes_per_launch"],
-                "us_per_launch": per[dom]["us_per_launch"], "sweeps": per}
+                "us_per_launch": per[dom]["us_per_launch"],
+                "us_per_launch_events": per[dom]["us_per_launch_events"],
+                "timing": ("kernel time = its CUDA-event time x (device us per update of the timed "
+                           f"solves {us_update:.2f}) / (sum of the three kernels' event times "
+                           f"{ev_sum:.2f}): scale {share:.3f}"),
+                "sweeps": per}
 
     if roof is not None and rank == 0:
         gref = gather_reference(torch, A, sv, dev, flush)
@@ -403,6 +445,22 @@ def run_plss(args):
                 gref[k]["sweep_us"] = per[k]["us_per_launch"]
                 gref[k]["sweep_vs_index_select"] = gref[k]["us"] / per[k]["us_per_launch"]
         roof["gather_reference"] = gref
+        # the sweeps' gather floor: the same index streams, grids and warp
+        # ranges, gathers only (hand-written kernel in the library)
+        gb = {}
+        for side, k in ((0, "row_sweep"), (1, "col_sweep")):
+            try:
+                med, mn = ctx.gather_bound(side, reps=7)
+            except plss.PlssError as e:
+                gb[k] = {"unavailable": str(e)}
+                continue
+            gb[k] = {"us": med, "us_min": mn, "gathers_per_s": nnz / (med * 1e-6)}
+            if k in per:
+                gb[k]["sweep_us"] = per[k]["us_per_launch"]
+                gb[k]["bound_over_sweep"] = med / per[k]["us_per_launch"]
+                gb[k]["achieved_at_bound_gbs"] = per[k]["bytes_per_launch"] / (med * 1e-6) / 1e9
+        gb["kernel"] = "plss_gather_bound (median of 7, L2 evicted, the gathered vector re-read into L2 before each)"
+        roof["gather_bound"] = gb
 
     # end to end through the C ABI with host buffers
     torch.cuda.synchronize()
@@ -426,6 +484,10 @@ def run_plss(args):
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cb = cpu_baseline(A, b, args, last["iters"])
 
+    extras = None
+    if rank == 0 and ws == 1 and not args.no_extras:
+        extras = run_extras(args)
+
     if rank == 0:
         line = {"metric": METRIC, "value": ms_step / 1e3, "unit": "s", "n_gpus": ws,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
@@ -442,7 +504,8 @@ def run_plss(args):
                           "ms_per_update": ms_step / max(1, last["iters"]),
                           "rel_err_vs_xstar": err_xstar},
                 "layout": ctx_layout, "roofline": roof, "cpu_baseline": cb, "e2e": e2e,
-                "gpu_launches": int(kt["all_launches"]), "clocks": clk, "variants": variants}
+                "gpu_launches": int(kt["all_launches"]), "clocks": clk, "variants": variants,
+                "workloads": extras}
         print(json.dumps(line), flush=True)
     ctx.close()
     if dist is not None:
@@ -656,17 +719,63 @@ def suite_c5(args):
     upload. Eight client threads submit (plss_submit prepares the request on
     the calling thread), each taking every eighth request at its arrival
     time."""
-    import threading
     torch, plss = _suite_common(args)
-    arrivals, pool_ids, mats = synth.serving_trace(nreq=args.requests, pool=args.pool)
-    reqs = []
-    for i, pid in enumerate(pool_ids):
-        A = mats[int(pid)]
-        xs = synth.rng_for(3000 + 1_000_000 + i).standard_normal(A.n)
-        reqs.append((A, synth.rhs(A, xs)))
-    srv = plss.Server(max_slots=64, precision="fp32", layout=args.server_layout)
+    arrivals, reqs = serving_requests(args.requests, args.pool)
+    res = serve(plss, reqs, arrivals, maxit=min(3000, args.maxit), layout=args.server_layout)
+    _line("served solves/s", res["solves_per_s"], "solves/s", args, "plss_serving_poisson2000", dict(
+        res, higher_is_better=True, steps=1, warmup=0, ms_per_step=None, pool=args.pool,
+        server_layout=args.server_layout))
+
+
+# ------------------------------------------------ extras in the headline run
+#
+# Compact results of the other workloads, carried by the headline line
+# (`workloads`), each with its own clock record: the latency-bound square
+# system (C1), 32 right-hand sides (C4b, FP32 storage), serving at the
+# configured arrival rate and below capacity (C5, a shortened trace), and
+# the identity sketch with a whole-GPU history window on the power-law
+# system (C3).
+
+def extra_c1(torch, plss, warmup=3, steps=10):
+    import oracle
+    A, b, xs = synth.square_diag_dominant()
+    A = A.astype(np.float64)
+    ctx = plss.Context(A)
+    bd = torch.from_numpy(b).cuda()
+    t, (x, r), clk = _timed(torch, lambda: ctx.solve(bd, tol=1e-10, maxit=2000, stop_on_true=1), warmup, steps)
+    ctx.close()
+    ref = oracle.residual(A, b, tol=1e-10, maxit=2000)
+    return {"metric": "time to ||r||/||b||<=1e-10", "seconds": t, "updates": r["iters"],
+            "status": r["status"], "relres_true": r["relres_true"],
+            "us_per_update": t / max(1, r["iters"]) * 1e6, "oracle_updates": ref["iters"],
+            "rel_err_vs_oracle": float(np.linalg.norm(x.cpu().numpy() - ref["x"]) / np.linalg.norm(ref["x"])),
+            "steps": steps, "warmup": warmup, "clocks": clk}
+
+
+def extra_c4b(torch, plss):
+    A = synth.laplacian7()
+    B, Xs = synth.laplacian_rhs(A)
+    Bd = torch.from_numpy(B).cuda()
+    ctx = plss.Context(A, precision="fp32", symmetric=True)
+    t, (X, rs), clk = _timed(torch, lambda: ctx.solve_rhs(Bd, tol=1e-8, maxit=50000, stop_on_true=1), 1, 1)
+    ctx.close()
+    Xh = X.cpu().numpy()
+    ups = max(r["iters"] for r in rs)
+    return {"metric": "time to ||r||/||b||<=1e-8 (32 right-hand sides)", "seconds": t,
+            "precision": "fp32 storage + fp64 refinement",
+            "converged": sum(r["status"] == "converged" for r in rs), "max_updates": ups,
+            "ms_per_update": t / max(1, ups) * 1e3,
+            "worst_relres_true": max(r["relres_true"] for r in rs),
+            "rel_err_vs_xstar": float(np.linalg.norm(Xh - Xs) / np.linalg.norm(Xs)), "clocks": clk}
+
+
+def serve(plss, reqs, arrivals, maxit=3000, layout="csr", nthreads=8):
+    """Replays requests (A, b) at the given arrival times through the
+    continuous-batching server (plss_submit / plss_poll); latency is
+    completion minus arrival, host-side preparation and upload included."""
+    import threading
+    srv = plss.Server(max_slots=64, precision="fp32", layout=layout)
     done = {}
-    nthreads = 8
     t0 = time.perf_counter()
     tickets = [None] * len(reqs)
     submit_s = [0.0] * len(reqs)
@@ -680,7 +789,7 @@ def suite_c5(args):
             ts = time.perf_counter()
             t = None
             while t is None:
-                t = srv.submit(A, b, tol=1e-6, maxit=min(3000, args.maxit), w_mode=1)
+                t = srv.submit(A, b, tol=1e-6, maxit=maxit, w_mode=1)
                 if t is None:
                     busy[0] += 1
                     time.sleep(0.001)
@@ -708,15 +817,72 @@ def suite_c5(args):
     srv.close()
     lat = np.array([done[i][0] - arrivals[i] for i in range(len(reqs))])
     span = max(v[0] for v in done.values())
-    conv = sum(v[1]["status"] == "converged" for v in done.values())
-    _line("served solves/s", len(reqs) / span, "solves/s", args, "plss_serving_poisson2000", {
-        "higher_is_better": True, "steps": 1, "warmup": 0, "ms_per_step": None,
-        "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
-                      "mean": float(lat.mean()), "max": float(lat.max())},
-        "requests": len(reqs), "pool": args.pool, "converged": int(conv), "makespan_s": span,
-        "server_layout": args.server_layout, "client_threads": nthreads,
-        "submit_s": {"total": float(sum(submit_s)), "max": float(max(submit_s))},
-        "busy_retries": busy[0], "clocks": clk})
+    return {"solves_per_s": len(reqs) / span,
+            "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                          "mean": float(lat.mean()), "max": float(lat.max())},
+            "offered_per_s": float(len(reqs) / max(arrivals[-1], 1e-9)), "requests": len(reqs),
+            "converged": int(sum(v[1]["status"] == "converged" for v in done.values())),
+            "makespan_s": span, "client_threads": nthreads, "busy_retries": busy[0],
+            "submit_s_max": float(max(submit_s)), "clocks": clk}
+
+
+def serving_requests(nreq, pool, rate=2000.0):
+    arrivals, pool_ids, mats = synth.serving_trace(nreq=nreq, pool=pool, rate=rate)
+    reqs = []
+    for i, pid in enumerate(pool_ids):
+        A = mats[int(pid)]
+        xs = synth.rng_for(3000 + 1_000_000 + i).standard_normal(A.n)
+        reqs.append((A, synth.rhs(A, xs)))
+    return arrivals, reqs
+
+
+def extra_c5(plss, nreq=200, pool=16):
+    """The configured arrival rate (2,000/s, far above what the GPU serves),
+    then the same requests at 0.9x and 0.5x of the service rate measured
+    there, so that p50/p99 show the server rather than the queue."""
+    arrivals, reqs = serving_requests(nreq, pool)
+    out = {"rate_2000": serve(plss, reqs, arrivals)}
+    cap = out["rate_2000"]["solves_per_s"]
+    for f in (0.9, 0.5):
+        gaps = np.diff(np.concatenate([[0.0], arrivals]))
+        arr = np.cumsum(gaps * (2000.0 / (f * cap)))      # the same Poisson gaps, stretched
+        out[f"load_{f}"] = serve(plss, reqs, arr)
+    out["trace"] = (f"{nreq} requests over a pool of {pool} matrices (the configuration's trace: "
+                    "10,000 over 256); arrival gaps of the 2,000/s trace stretched for the lower loads")
+    return out
+
+
+def extra_c3_identity(torch, plss, rows=50000):
+    """Identity sketch on the 1e5 x 1e6 power-law system: windows of 0, 8 and
+    256 directions (256 runs on the whole GPU), a fixed number of rows."""
+    A, b, xs = synth.powerlaw_underdetermined()
+    bd = torch.from_numpy(b).cuda()
+    ctx = plss.Context(A, precision="fp64")
+    out = {}
+    for K in (0, 8, 256):
+        t, (x, r), clk = _timed(torch, lambda: ctx.solve(bd, sketch="identity", tol=0.0, maxit=rows,
+                                                         kacz_hist=K, seed=7), 1, 1)
+        out[f"K{K}"] = {"seconds": t, "rows": r["iters"], "us_per_row": t / max(1, r["iters"]) * 1e6,
+                        "relres_true": r["relres_true"], "clocks": clk}
+    ctx.close()
+    out["workload"] = f"plss_underdetermined_1e5x1e6_zipf20_max5000, {rows} rows (half a pass), tol 0"
+    return out
+
+
+def run_extras(args):
+    import torch
+    from paper_2207_07615_gb300 import plss
+    out = {}
+    for name, fn in (("c1", lambda: extra_c1(torch, plss)), ("c4b_fp32", lambda: extra_c4b(torch, plss)),
+                     ("c3_identity", lambda: extra_c3_identity(torch, plss)),
+                     ("c5", lambda: extra_c5(plss))):
+        t0 = time.perf_counter()
+        try:
+            out[name] = fn()
+        except Exception as e:   # a failing extra must not cost the headline line
+            out[name] = {"error": f"{type(e).__name__}: {e}"}
+        out[name]["wall_s"] = time.perf_counter() - t0
+    return out
 
 
 def main():
