@@ -90,7 +90,14 @@ enum { PLSS_LAYOUT_AUTO = 0, PLSS_LAYOUT_CSR = 1 };
  * nonzeros or the systems are at least 1/8 as many as the SMs; else GRID.
  * The schedules reduce in different orders: their iterates agree to
  * rounding, not bit for bit. */
-enum { PLSS_SCHED_AUTO = 0, PLSS_SCHED_GRID = 1, PLSS_SCHED_SMALL = 2 };
+enum { PLSS_SCHED_AUTO = 0, PLSS_SCHED_GRID = 1, PLSS_SCHED_SMALL = 2, PLSS_SCHED_COOP = 3 };
+/* COOP: for a single-system context whose rows and columns are both sliced
+ * throughout (plss_ctx_layout), whole iterations run in one cooperative
+ * launch over the GPU (the sweeps and the update as phases that meet at
+ * grid barriers, every CTA taking the scalar steps on its own copy of the
+ * state); any other context runs as AUTO. A grid barrier that waits longer
+ * than 2 s ends the solve with PLSS_ERR_TIMEOUT. No per-kernel timings
+ * (plss_kernel_times records nothing). */
 
 /* A sparse matrix in CSR form (see the conventions above). val holds nnz
  * doubles, or floats when val_f32 = 1. */

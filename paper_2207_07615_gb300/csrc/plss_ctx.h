@@ -71,6 +71,12 @@ struct plss_ctx {
     plss::Sliced rsl{}, csl{};        // sliced copies (csl aliases rsl when symmetric)
     int64_t sl_elems[2] = {0, 0};     // elements of the sliced row / column copies
     int32_t *d_rwr = nullptr, *d_cwr = nullptr;   // warp ranges (Sliced::wr) or null
+    // schedule COOP (one system, both sides sliced throughout): warp ranges
+    // for its grid, per-CTA partials and barrier words
+    int coop_grid = 0;
+    int32_t *d_coop_rwr = nullptr, *d_coop_cwr = nullptr;
+    double *d_coop_part = nullptr;
+    uint32_t *d_coop_bar = nullptr;
     bool small_fits = false;                      // every system fits the cluster schedule
     bool small_auto = false;                      // ... and AUTO picks it
     int32_t clu_vec_bytes = 0;                    // cluster schedule: shared-memory vector copies (0: none)

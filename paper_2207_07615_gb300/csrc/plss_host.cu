@@ -219,6 +219,10 @@ static void ctx_free(plss_ctx *c) {
     if (!c->symmetric) free_sliced(c->csl);
     dfree(c->d_rwr);
     dfree(c->d_cwr);
+    dfree(c->d_coop_rwr);
+    dfree(c->d_coop_cwr);
+    dfree(c->d_coop_part);
+    dfree(c->d_coop_bar);
     if (c->h_st) cudaFreeHost(c->h_st);
     if (c->h_active) cudaFreeHost(c->h_active);
     free_extra(c);
@@ -473,6 +477,16 @@ static plss_status ctx_build(const plss_csr *As, int32_t nsys, const plss_opts *
         c->csl.wr = c->d_cwr;
         if (c->d_rwr) c->grid_r = gr;
         if (c->d_cwr) c->grid_c = gc;
+        // schedule COOP: one cooperative grid for both sides
+        const int per_sm = coop_ctas_per_sm(c->f32);
+        if (c->d_rwr && c->d_cwr && per_sm > 0) {
+            const int g = c->nsm * per_sm;
+            TRY_ST(upload_warp_ranges(c->h_rt, rsl_ptr, int64_t(g) * kWarps, &c->d_coop_rwr));
+            TRY_ST(upload_warp_ranges(c->h_ct, csl_ptr, int64_t(g) * kWarps, &c->d_coop_cwr));
+            TRY_ST(dalloc(reinterpret_cast<void **>(&c->d_coop_part), 8 * 4 * size_t(g), "partials"));
+            TRY_ST(dalloc(reinterpret_cast<void **>(&c->d_coop_bar), 4 * 4, "barrier"));
+            if (c->d_coop_rwr && c->d_coop_cwr) c->coop_grid = g;
+        }
     }
 #undef TRY_ST
 
@@ -584,7 +598,8 @@ plss_status check_opts(const plss_opts *o) {
     if (!(o->inner_tol >= 0.0) || !(o->inner_tol < 1.0)) return fail(PLSS_ERR_INVALID, "inner_tol must be in [0, 1)");
     if (o->hist_cap > 0 && !o->hist) return fail(PLSS_ERR_INVALID, "hist_cap > 0 with hist NULL");
     if (o->profile < 0) return fail(PLSS_ERR_INVALID, "profile < 0");
-    if (o->schedule != PLSS_SCHED_AUTO && o->schedule != PLSS_SCHED_GRID && o->schedule != PLSS_SCHED_SMALL)
+    if (o->schedule != PLSS_SCHED_AUTO && o->schedule != PLSS_SCHED_GRID && o->schedule != PLSS_SCHED_SMALL &&
+        o->schedule != PLSS_SCHED_COOP)
         return fail(PLSS_ERR_INVALID, "unknown schedule %d", o->schedule);
     return PLSS_OK;
 }
@@ -682,6 +697,29 @@ plss_status run_residual(plss_ctx *c, const double *const *b, const double *cons
     int chunk = 1;
     const bool small = o->schedule == PLSS_SCHED_SMALL ? c->small_fits
                                                         : (o->schedule == PLSS_SCHED_AUTO && c->small_auto);
+    const bool coop = !small && o->schedule == PLSS_SCHED_COOP && c->coop_grid > 0;
+    if (coop) {
+        // one system on the whole GPU, whole bodies per cooperative launch
+        SweepArgs a = c->args;
+        a.w = w_on ? c->d_w : nullptr;
+        a.winv = w_on ? c->d_w + c->n : nullptr;
+        a.wf = w_on && c->d_wf ? c->d_wf : nullptr;
+        a.winvf = w_on && c->d_wf ? c->d_wf + c->n : nullptr;
+        int32_t per = 16;
+        for (;;) {
+            CUDA_TRY(launch_coop_solve(a, c->f32, c->coop_grid, c->d_coop_rwr, c->d_coop_cwr, c->d_coop_part,
+                                       c->d_coop_bar, per, s));
+            bodies += per;
+            uint32_t bar[4] = {0, 0, 0, 0};
+            CUDA_TRY(cudaMemcpyAsync(c->h_active, c->d_active, 4, cudaMemcpyDeviceToHost, s));
+            CUDA_TRY(cudaMemcpyAsync(bar, c->d_coop_bar, sizeof bar, cudaMemcpyDeviceToHost, s));
+            CUDA_TRY(cudaStreamSynchronize(s));
+            if (bar[2] != 0) return fail(PLSS_ERR_TIMEOUT, "cooperative schedule: a grid barrier waited longer than 2 s");
+            if (*c->h_active <= 0) break;
+            if (bodies > body_cap) return fail(PLSS_ERR_TIMEOUT, "iteration driver exceeded %lld bodies", (long long)body_cap);
+            per = std::min(per * 4, 4096);
+        }
+    }
     if (small) {
         // one cluster per system, whole bodies per launch
         SweepArgs a = c->args;
@@ -700,7 +738,7 @@ plss_status run_residual(plss_ctx *c, const double *const *b, const double *cons
             per = std::min(per * 4, 4096);
         }
     }
-    while (!small) {
+    while (!small && !coop) {
         const bool pchunk = prof && nchunk++ % period == 0;
         cudaGraphExec_t g;
         st = get_graph(c, chunk, w_on, pchunk, &g);

@@ -1313,6 +1313,167 @@ __global__ void __launch_bounds__(kClusterThreads) k_cluster_solve(SweepArgs a, 
 }
 
 // ---------------------------------------------------------------------------
+// One system on the whole GPU, whole updates per launch (schedule COOP)
+// ---------------------------------------------------------------------------
+//
+// The three sweeps of an update as phases of one cooperative kernel: the
+// column sweep and the row sweep over the sliced sides with this grid's own
+// warp ranges, the update over contiguous column ranges. Phases meet at grid
+// barriers (a counter and a generation word; every wait is limited to 2 s,
+// after which the CTA sets the error word and returns, and so do the others).
+// After a barrier every CTA sums the phase's per-CTA partials in CTA order
+// and takes the scalar step on its own shared-memory copy of the state, so
+// all CTAs hold the same bits and no CTA finishes alone; CTA 0 alone writes
+// the global state, the history and the active count. Vectors written by
+// another CTA within the launch (u, p, r, x gathered) are read through L2.
+
+constexpr unsigned long long kCoopWaitNs = 2000000000ull;
+
+__device__ __forceinline__ unsigned long long coop_now() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ bool coop_barrier(uint32_t *bar, int *sh_ok) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile uint32_t *vb = bar;
+        int ok = vb[2] == 0;
+        if (ok) {
+            const uint32_t gen = vb[1];
+            __threadfence();
+            if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+                bar[0] = 0;
+                __threadfence();
+                atomicAdd(bar + 1, 1u);
+            } else {
+                const unsigned long long t0 = coop_now();
+                while (vb[1] == gen) {
+                    if (vb[2] != 0) { ok = 0; break; }
+                    if (coop_now() - t0 > kCoopWaitNs) {
+                        atomicExch(bar + 2, 1u);
+                        ok = 0;
+                        break;
+                    }
+                    __nanosleep(20);
+                }
+            }
+            __threadfence();
+        }
+        *sh_ok = ok;
+    }
+    __syncthreads();
+    return *sh_ok != 0;
+}
+
+// Sum of part[0..G) in CTA order (every CTA the same), valid in thread 0.
+__device__ __forceinline__ double coop_total(const double *part, int stride, int off) {
+    double v[1] = {0.0};
+    for (int i = threadIdx.x; i < int(gridDim.x); i += kThreads) v[0] += __ldcg(part + stride * i + off);
+    cta_sum<1>(v);
+    return v[0];
+}
+
+template <typename S>
+__global__ void __launch_bounds__(kThreads) k_coop_solve(SweepArgs a, const int32_t *rwr, const int32_t *cwr,
+                                                         double *part, uint32_t *bar, int32_t bodies) {
+    __shared__ SysState sst;
+    __shared__ int32_t done_local;
+    __shared__ int sh_ok;
+    const int lane = threadIdx.x & 31;
+    const int G = int(gridDim.x), bid = int(blockIdx.x);
+    const int32_t w = int32_t(bid) * kWarps + (threadIdx.x >> 5);
+    const int32_t n = a.desc[0].n;
+    const int32_t j0 = int32_t(int64_t(n) * bid / G), j1 = int32_t(int64_t(n) * (bid + 1) / G);
+    double *p_phi = part, *p_th = part + G, *p_rho = part + 2 * G;   // p_rho: pairs (rho, ||b||^2)
+    SweepArgs al = a;
+    if (threadIdx.x == 0) {
+        sst = a.st[0];
+        done_local = 0;
+        if (bid != 0) sst.hist = nullptr;
+    }
+    if (bid != 0) al.n_active = &done_local;
+    __syncthreads();
+    SysState *st = &sst;
+    for (int32_t it = 0; it < bodies; ++it) {
+        __syncthreads();
+        int32_t ph = st->phase;
+        if (ph == PH_DONE) break;   // the same in every CTA
+        if (ph == PH_FIRST || ph == PH_RUN) {
+            double v[1] = {0.0};
+            for (int32_t sl = __ldg(cwr + w); sl < __ldg(cwr + w + 1); ++sl) {
+                const int32_t off = __ldg(a.csl.ptr + sl);
+                const int32_t width = (__ldg(a.csl.ptr + sl + 1) - off) >> 5;
+                col_slot<S>(al, __ldg(a.csl.seg + 32 * sl + lane), off, width, lane, v[0]);
+            }
+            cta_sum<1>(v);
+            if (threadIdx.x == 0) p_phi[bid] = v[0];
+            if (!coop_barrier(bar, &sh_ok)) return;
+            const double phi = coop_total(p_phi, 1, 0);
+            if (threadIdx.x == 0) col_decide(al, st, phi);
+            __syncthreads();
+            if (st->upd != 0) {
+                const bool first = st->upd == 2;
+                const double beta = st->beta, gamma = st->gamma;
+                S *p = static_cast<S *>(a.p);
+                const S *u = static_cast<const S *>(a.u);
+                double th[1] = {0.0};
+                if constexpr (std::is_same<S, float>::value) {
+                    const float bf = float(beta), gf = float(gamma);
+                    DF acc[1] = {{0.0f, 0.0f}};
+                    for (int32_t j = j0 + threadIdx.x; j < j1; j += kThreads) {
+                        const float uj = __ldcg(u + j);
+                        const float pn = first ? gf * uj : fmaf(bf, p[j], gf * uj);
+                        p[j] = pn;
+                        acc[0] = df_add_prod(acc[0], pn, a.winvf ? __fmul_rn(pn, a.winvf[j]) : pn);
+                        a.x[j] = a.x[j] + double(pn);
+                    }
+                    cta_sum_df<1>(acc, th);
+                } else {
+                    for (int32_t j = j0 + threadIdx.x; j < j1; j += kThreads) {
+                        const double gu = gamma * double(__ldcg(u + j));
+                        const double pn = first ? gu : fma(beta, double(p[j]), gu);
+                        const S ps = S(pn);
+                        p[j] = ps;
+                        const double pd = double(ps);
+                        th[0] = fma(pd, a.winv ? pd * a.winv[j] : pd, th[0]);
+                        a.x[j] = a.x[j] + pd;
+                    }
+                    cta_sum<1>(th);
+                }
+                if (threadIdx.x == 0) p_th[bid] = th[0];
+                if (!coop_barrier(bar, &sh_ok)) return;
+                const double theta = coop_total(p_th, 1, 0);
+                if (threadIdx.x == 0) upd_done(st, theta);
+            }
+            __syncthreads();
+            ph = st->phase;
+        }
+        if (ph == PH_SETUP || ph == PH_RUN) {
+            const bool init = ph == PH_SETUP;
+            double v[2] = {0.0, 0.0};
+            for (int32_t sl = __ldg(rwr + w); sl < __ldg(rwr + w + 1); ++sl) {
+                const int32_t off = __ldg(a.rsl.ptr + sl);
+                const int32_t width = (__ldg(a.rsl.ptr + sl + 1) - off) >> 5;
+                row_slot<S>(al, __ldg(a.rsl.seg + 32 * sl + lane), off, width, lane, init, v[0], v[1]);
+            }
+            cta_sum<2>(v);
+            if (threadIdx.x == 0) {
+                p_rho[2 * bid] = v[0];
+                p_rho[2 * bid + 1] = v[1];
+            }
+            if (!coop_barrier(bar, &sh_ok)) return;
+            const double rho = coop_total(p_rho, 2, 0);
+            const double bb = coop_total(p_rho, 2, 1);
+            if (threadIdx.x == 0) row_decide(al, st, init, rho, bb);
+        }
+    }
+    __syncthreads();
+    if (bid == 0 && threadIdx.x == 0) a.st[0] = sst;
+}
+
+// ---------------------------------------------------------------------------
 // Auxiliary kernels: products in double, residual norms, column weights
 // ---------------------------------------------------------------------------
 
@@ -1462,6 +1623,27 @@ cudaError_t launch_cluster_solve(const SweepArgs &a, bool f32, int32_t nsys, int
     if (e != cudaSuccess) return e;
     return f32 ? cudaLaunchKernelEx(&cfg, k_cluster_solve<float, true>, a, bodies)
                : cudaLaunchKernelEx(&cfg, k_cluster_solve<double, true>, a, bodies);
+}
+
+int coop_ctas_per_sm(bool f32) {
+    int n = 0;
+    const cudaError_t e = f32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_coop_solve<float>, kThreads, 0)
+                              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_coop_solve<double>, kThreads, 0);
+    if (e != cudaSuccess || n < 1) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
+}
+
+cudaError_t launch_coop_solve(const SweepArgs &a, bool f32, int grid, const int32_t *rwr, const int32_t *cwr,
+                              double *part, uint32_t *bar, int32_t bodies, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(bar, 0, 4 * sizeof(uint32_t), s);
+    if (e != cudaSuccess) return e;
+    SweepArgs aa = a;
+    void *args[] = {&aa, &rwr, &cwr, &part, &bar, &bodies};
+    void *fn = f32 ? reinterpret_cast<void *>(k_coop_solve<float>) : reinterpret_cast<void *>(k_coop_solve<double>);
+    return cudaLaunchCooperativeKernel(fn, dim3(unsigned(grid)), dim3(kThreads), args, 0, s);
 }
 
 cudaError_t launch_spmv(const int32_t *ptr, const int32_t *idx, const void *val, bool f32,

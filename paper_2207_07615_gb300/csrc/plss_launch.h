@@ -24,6 +24,15 @@ constexpr int32_t kClusterVecBytes = 128 * 1024;
 cudaError_t launch_cluster_solve(const SweepArgs &a, bool f32, int32_t nsys, int32_t bodies, int32_t vec_bytes,
                                  cudaStream_t s);
 
+// One system on the whole GPU (schedule COOP): up to `bodies` bodies per
+// cooperative launch of `grid` CTAs (all resident), with this grid's warp
+// ranges of the sliced rows and columns, per-CTA partials part[4 * grid]
+// and barrier words bar[4] (cleared by the launcher). coop_ctas_per_sm: the
+// kernel's resident CTAs per SM (0 when it cannot run).
+int coop_ctas_per_sm(bool f32);
+cudaError_t launch_coop_solve(const SweepArgs &a, bool f32, int grid, const int32_t *rwr, const int32_t *cwr,
+                              double *part, uint32_t *bar, int32_t bodies, cudaStream_t s);
+
 // Resident CTAs per SM of a sweep kernel (0 row, 1 column, 2 update, 3 row
 // and 4 column over warp ranges).
 int sweep_ctas_per_sm(int which, bool f32);

@@ -24,7 +24,7 @@ STATUS_NAMES = {0: "converged", 1: "not_converged", 2: "pending", -1: "invalid",
 SKETCH = {"residual": 0, "identity": 1, "general": 2}
 PRECISION = {"fp64": 0, "fp32": 1}
 LAYOUT = {"auto": 0, "csr": 1}
-SCHEDULE = {"auto": 0, "grid": 1, "small": 2}
+SCHEDULE = {"auto": 0, "grid": 1, "small": 2, "coop": 3}
 
 #: every symbol declared in include/plss.h
 EXPORTS = ["plss_opts_default", "plss_create", "plss_create_batched", "plss_destroy",

@@ -289,3 +289,36 @@ def test_symmetric_reuses_the_csr(plss, precision):
         xa, ra = cs.solve(b, tol=1e-8, maxit=20000, stop_on_true=1)
     assert ra["status"] == "converged" and ra["relres_true"] <= 1e-8
     assert rel(xa, xs) < 1e-5      # nonsingular: the solution is x*
+
+
+@pytest.mark.parametrize("w_mode", [0, 2])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_coop_schedule_parity(plss, w_mode, precision):
+    """Schedule COOP (whole updates in one cooperative launch, grid barriers
+    between the phases, scalar steps taken by every CTA): per-update scalars
+    and x against the oracle (FP64), or against the oracle's FP32 emulation
+    on the first updates and the FP64 answer (FP32 storage), and the same
+    answer as the GRID schedule."""
+    A, b, xs = synth.overdetermined_scaled(m=40000, n=8000, per_row=8, seed=14, scale_decades=1.0)
+    w = oracle.colweights(A.astype(np.float64), w_mode) if w_mode else None
+    with plss.Context(A if precision == "fp32" else A.astype(np.float64), precision=precision) as ctx:
+        lay = ctx.layout()
+        assert lay["row_sliced"] == lay["row_tiles"] and lay["col_sliced"] == lay["col_tiles"]
+        if precision == "fp64":
+            K = 60
+            ref = _parity.reference(A.astype(np.float64), b, K, w=w)
+            x, res, hist = ctx.solve(b, tol=0.0, maxit=K, hist=K, w_mode=w_mode, schedule="coop")
+            assert res["iters"] == K
+            _parity.check_scalars(hist, ref, min_strict=10)
+            _parity.check_x(x, ref, K)
+        else:
+            K = 8
+            ref = oracle.residual(A.astype(np.float64), b, w=w, tol=0.0, maxit=K, prec=1, hist=K)
+            x, res, hist = ctx.solve(b, tol=0.0, maxit=K, hist=K, w_mode=w_mode, schedule="coop")
+            assert scal_rel(hist, ref["hist_s"]) < 1e-4
+        xc, rc = ctx.solve(b, tol=1e-8, maxit=20000, w_mode=w_mode, stop_on_true=1, schedule="coop")
+        xg, rg = ctx.solve(b, tol=1e-8, maxit=20000, w_mode=w_mode, stop_on_true=1, schedule="grid")
+    fin = oracle.residual(A.astype(np.float64), b, w=w, tol=1e-8, maxit=20000, stop_on_true=True)
+    assert rc["status"] == rg["status"] == fin["status"] == "converged"
+    assert rc["relres_true"] <= 1e-8
+    assert rel(xc, fin["x"]) < 1e-5 and rel(xc, xg) < 1e-5
