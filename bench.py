@@ -869,12 +869,35 @@ def extra_c3_identity(torch, plss, rows=50000):
     return out
 
 
+def extra_general(torch, plss, cols=300, K=64):
+    """The general sketch (Sec. 2.4) on the headline system: random sign
+    columns with a history of K directions, a fixed number of columns."""
+    A, b, xs = synth.overdetermined_scaled(m=1_000_000, n=200_000, per_row=8, seed=1)
+    A = A.astype(np.float64)
+    bd = torch.from_numpy(b).cuda()
+    ctx = plss.Context(A)
+    t, (x, r), clk = _timed(torch, lambda: ctx.solve(bd, sketch="general", tol=0.0, maxit=cols, kacz_hist=K,
+                                                     seed=11), 1, 1)
+    ctx.close()
+    # per column: y = A^T s and r = b - A x (CSR + CSC streams, x gathered), and the history of
+    # on average about K/2 directions of n doubles streamed twice (c = Q^T y, q = y - Q d)
+    nnz, n, m = A.nnz, A.n, A.m
+    hist_bytes = 2 * (min(K, cols) / 2) * n * 8
+    return {"seconds": t, "columns": r["iters"], "us_per_column": t / max(1, r["iters"]) * 1e6,
+            "relres_true": r["relres_true"], "history": K,
+            "history_bytes_per_column": hist_bytes,
+            "sparse_bytes_per_column": 2 * nnz * 12 + 8 * (2 * m + 3 * n),
+            "clocks": clk,
+            "workload": f"{WORKLOAD}, FP64, {cols} sketch columns, history {K}"}
+
+
 def run_extras(args):
     import torch
     from paper_2207_07615_gb300 import plss
     out = {}
     for name, fn in (("c1", lambda: extra_c1(torch, plss)), ("c4b_fp32", lambda: extra_c4b(torch, plss)),
                      ("c3_identity", lambda: extra_c3_identity(torch, plss)),
+                     ("c2_general", lambda: extra_general(torch, plss)),
                      ("c5", lambda: extra_c5(plss))):
         t0 = time.perf_counter()
         try:

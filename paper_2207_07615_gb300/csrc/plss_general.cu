@@ -24,7 +24,7 @@
 //              (theta of the last direction; nh += 1) and empties a full
 //              history
 //   g_cols     y = A^T s_k (CSC, s_k from the hash: no gather), ||y||^2 partials
-//   g_qty      partials of c = Q^T y over column ranges
+//   g_qty      partials of c = Q^T y over column chunks of 8,192
 //   g_decide   one CTA: stop test on ||r||, c, d = c / theta, delta, gamma,
 //              the skip test
 //   g_update   q = y - Q d, column nh of Q, x += gamma q, theta partials
@@ -55,6 +55,7 @@ constexpr int kGsThreads = 256;
 constexpr int kGsWarps = kGsThreads / 32;
 constexpr int kGsMaxK = 1024;
 constexpr int kGsLanes = 8;   // lanes per row / column in the sparse passes
+constexpr int64_t kGsChunk = 8192;   // columns per partial dot product of c = Q^T y
 
 struct GsState {
     double rr;        // ||r_{k-1}||^2 of the last g_rows
@@ -86,12 +87,12 @@ struct GsArgs {
     double *d;         // [K]: c_j, then c_j / theta_j
     double *part_r;    // [2 * grid]: ||r||^2, s^T r
     double *part_y;    // [grid]
-    double *part_c;    // [grid * K]
+    double *part_c;    // [K * nch]: partial c_j over column chunk ch at j * nch + ch
     double *part_t;    // [grid]
     GsState *st;
     int64_t m, n;
     uint64_t seed;
-    int32_t K, grid;
+    int32_t K, grid, nch;
 };
 
 struct GeneralState {
@@ -137,20 +138,22 @@ template <typename S>
 __global__ void __launch_bounds__(kGsThreads) g_rows(GsArgs a) {
     __shared__ double sh[kGsWarps];
     GsState *st = a.st;
-    if (blockIdx.x == 0 && threadIdx.x == 0 && st->done == 0) {
-        // the previous column's direction: theta = ||q||^2 in block order
-        if (st->store) {
-            double th = 0.0;
-            for (int g = 0; g < a.grid; ++g) th += a.part_t[g];
+    if (st->done) return;
+    if (blockIdx.x == 0 && st->store) {
+        // the previous column's direction: theta = ||q||^2 over the CTAs'
+        // partials in a fixed order
+        double th = 0.0;
+        for (int g = threadIdx.x; g < a.grid; g += kGsThreads) th += a.part_t[g];
+        th = gs_sum(th, sh);
+        if (threadIdx.x == 0) {
             if (th > 0.0) {
                 a.theta[st->nh] = th;
                 st->nh += 1;
             }
             st->store = 0;
         }
-        if (a.K > 0 && st->nh == a.K) st->nh = 0;   // history full: start a new one
     }
-    if (st->done) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && a.K > 0 && st->nh == a.K) st->nh = 0;   // history full: start anew
     const S *__restrict__ val = static_cast<const S *>(a.val);
     const int grp = threadIdx.x / kGsLanes, gl = threadIdx.x % kGsLanes;
     int64_t lo, hi;
@@ -209,22 +212,22 @@ __global__ void __launch_bounds__(kGsThreads) g_cols(GsArgs a) {
     if (threadIdx.x == 0) a.part_y[blockIdx.x] = yy;
 }
 
-// Partials of c_j = q_j^T y over this CTA's column range, all j < nh: warp w
-// takes directions j = w, w + 8, ...; its lanes stride the range.
+// c_j = q_j^T y as partial dot products over column chunks: item (j, ch)
+// sums chunk ch of direction j (coalesced over the chunk) into
+// part_c[j * nch + ch]; the CTAs take items in turn.
 __global__ void __launch_bounds__(kGsThreads) g_qty(GsArgs a) {
+    __shared__ double sh[kGsWarps];
     const GsState *st = a.st;
     if (st->done) return;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int nh = st->nh;
-    int64_t lo, hi;
-    gs_range(a.n, lo, hi);
-    for (int j = warp; j < nh; j += kGsWarps) {
-        const double *q = a.Q + int64_t(j) * a.n;
+    const int64_t items = int64_t(st->nh) * a.nch;
+    for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
+        const int64_t j = it / a.nch, ch = it % a.nch;
+        const int64_t lo = ch * kGsChunk, hi = lo + kGsChunk < a.n ? lo + kGsChunk : a.n;
+        const double *q = a.Q + j * a.n;
         double acc = 0.0;
-        for (int64_t t = lo + lane; t < hi; t += 32) acc = fma(q[t], a.y[t], acc);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0) a.part_c[int64_t(blockIdx.x) * a.K + j] = acc;
+        for (int64_t t = lo + threadIdx.x; t < hi; t += kGsThreads) acc = fma(q[t], a.y[t], acc);
+        acc = gs_sum(acc, sh);
+        if (threadIdx.x == 0) a.part_c[it] = acc;
     }
 }
 
@@ -262,7 +265,7 @@ __global__ void __launch_bounds__(kGsThreads) g_decide(GsArgs a) {
     double d2 = 0.0;
     for (int j = threadIdx.x; j < nh; j += kGsThreads) {
         double c = 0.0;
-        for (int g = 0; g < a.grid; ++g) c += a.part_c[int64_t(g) * a.K + j];
+        for (int ch = 0; ch < a.nch; ++ch) c += a.part_c[int64_t(j) * a.nch + ch];
         d2 += (c * c) / a.theta[j];
         a.d[j] = c / a.theta[j];
     }
@@ -342,7 +345,9 @@ static plss_status general_prepare(plss_ctx *c, int32_t K) {
         (st = dalloc(reinterpret_cast<void **>(&g->d_d), 8 * Kc, "d")) != PLSS_OK ||
         (st = dalloc(reinterpret_cast<void **>(&g->d_y), 8 * size_t(std::max<int64_t>(c->n, 1)), "y")) != PLSS_OK ||
         (st = dalloc(reinterpret_cast<void **>(&g->d_r), 8 * size_t(std::max<int64_t>(c->m, 1)), "r")) != PLSS_OK ||
-        (st = dalloc(reinterpret_cast<void **>(&g->d_part), 8 * size_t(g->grid) * (4 + Kc), "partials")) != PLSS_OK ||
+        (st = dalloc(reinterpret_cast<void **>(&g->d_part),
+                     8 * (4 * size_t(g->grid) + Kc * size_t((std::max<int64_t>(c->n, 1) + kGsChunk - 1) / kGsChunk)),
+                     "partials")) != PLSS_OK ||
         (st = dalloc(reinterpret_cast<void **>(&g->d_st), sizeof(GsState), "state")) != PLSS_OK) {
         general_free(g);
         return st;
@@ -395,6 +400,7 @@ plss_status run_general(plss_ctx *c, const double *b, const double *x0, double *
     a.seed = o->seed;
     a.K = K;
     a.grid = g->grid;
+    a.nch = int32_t((std::max<int64_t>(c->n, 1) + kGsChunk - 1) / kGsChunk);
 
     GsState z{};
     z.tol = o->tol;

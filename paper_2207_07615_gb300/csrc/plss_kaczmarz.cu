@@ -426,16 +426,41 @@ __device__ __forceinline__ double kw_sum(double v, double *sh) {
     return t;
 }
 
+// Fixed-order CTA sums of N doubles at once (one pair of block barriers);
+// the results are returned to every thread.
+template <int N>
+__device__ __forceinline__ void kw_sums(double (&v)[N], double (*sh)[kKwWarps]) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
+    }
+    __syncthreads();
+    if (lane == 0) {
+#pragma unroll
+        for (int i = 0; i < N; ++i) sh[i][warp] = v[i];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        double t = 0.0;
+        for (int w = 0; w < kKwWarps; ++w) t += sh[i][w];
+        v[i] = t;
+    }
+}
+
 template <typename S>
 __global__ void __launch_bounds__(kKwThreads, 1) k_kacz_wide(KwArgs a) {
     extern __shared__ __align__(16) unsigned char kw_smem[];
     const int K = a.K;
-    double *s_th = reinterpret_cast<double *>(kw_smem);          // [K]
-    double *s_d = s_th + K;                                        // [K]
+    double *s_ith = reinterpret_cast<double *>(kw_smem);         // [K] 1 / theta_j
+    double *s_d = s_ith + K;                                       // [K]
     double *s_val = s_d + K;                                       // [row_max]
     int32_t *s_col = reinterpret_cast<int32_t *>(s_val + a.row_max);   // [row_max]
     int32_t *s_slot = s_col + a.row_max;                           // [row_max]
     __shared__ double sh_red[kKwWarps];
+    __shared__ double sh_red3[3][kKwWarps];
     __shared__ int32_t sh_cnt[kKwWarps];
     __shared__ double sh_gamma;
     __shared__ int sh_skip, sh_ok;
@@ -445,7 +470,7 @@ __global__ void __launch_bounds__(kKwThreads, 1) k_kacz_wide(KwArgs a) {
     KzSys ks = a.ks[0];
     int nh = ks.nh, nU = ks.nU;
     int64_t skipped = ks.skipped;
-    for (int j = tid; j < nh; j += kKwThreads) s_th[j] = a.theta[j];
+    for (int j = tid; j < nh; j += kKwThreads) s_ith[j] = 1.0 / a.theta[j];
     __syncthreads();
 
     for (int64_t t = 0; t < ks.rows_todo; ++t) {
@@ -481,35 +506,33 @@ __global__ void __launch_bounds__(kKwThreads, 1) k_kacz_wide(KwArgs a) {
                 if (lane == 0) a.c[j] = acc;
             }
             const int elo = int(int64_t(len) * bid / G), ehi = int(int64_t(len) * (bid + 1) / G);
-            double ax = 0.0, a2 = 0.0;
+            double v[2] = {0.0, 0.0};   // a^T x, ||a||^2
             for (int e = elo + tid; e < ehi; e += kKwThreads) {
-                ax = fma(s_val[e], a.x[s_col[e]], ax);
-                a2 = fma(s_val[e], s_val[e], a2);
+                v[0] = fma(s_val[e], a.x[s_col[e]], v[0]);
+                v[1] = fma(s_val[e], s_val[e], v[1]);
             }
-            ax = kw_sum(ax, sh_red);
-            a2 = kw_sum(a2, sh_red);
+            kw_sums<2>(v, sh_red3);
             if (tid == 0) {
-                a.part[bid] = ax;
-                a.part[G + bid] = a2;
+                a.part[bid] = v[0];
+                a.part[G + bid] = v[1];
             }
         }
         if (!kw_barrier(a.bar, &sh_ok)) return;
         // the scalars, identically in every CTA
         {
-            double ax = 0.0, a2 = 0.0;
+            double v[3] = {0.0, 0.0, 0.0};   // a^T x, ||a||^2, ||d||^2
             for (int q = tid; q < G; q += kKwThreads) {
-                ax += __ldcg(a.part + q);
-                a2 += __ldcg(a.part + G + q);
+                v[0] += __ldcg(a.part + q);
+                v[1] += __ldcg(a.part + G + q);
             }
-            ax = kw_sum(ax, sh_red);
-            a2 = kw_sum(a2, sh_red);
-            double d2 = 0.0;
             for (int j = tid; j < nh; j += kKwThreads) {
                 const double cj = __ldcg(a.c + j);
-                d2 += (cj * cj) / s_th[j];
-                s_d[j] = cj / s_th[j];
+                const double dj = cj * s_ith[j];
+                v[2] = fma(cj, dj, v[2]);
+                s_d[j] = dj;
             }
-            d2 = kw_sum(d2, sh_red);
+            kw_sums<3>(v, sh_red3);
+            const double ax = v[0], a2 = v[1], d2 = v[2];
             if (tid == 0) {
                 const double ri = a.b[i] - ax;
                 const double na = sqrt(a2), nd = sqrt(d2);
@@ -587,7 +610,7 @@ __global__ void __launch_bounds__(kKwThreads, 1) k_kacz_wide(KwArgs a) {
         th = kw_sum(th, sh_red);
         if (th > 0.0) {
             if (tid == 0) {
-                s_th[nh] = th;
+                s_ith[nh] = 1.0 / th;
                 if (bid == 0) a.theta[nh] = th;
             }
             ++nh;
