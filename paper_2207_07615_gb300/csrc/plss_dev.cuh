@@ -43,9 +43,11 @@ struct Sliced {
     const int32_t *seg;     // [32 * slices] segment of each slot, -1 if none
     const int32_t *idx;     // padded indices
     const void *val;        // padded values (storage type)
-    // Single-system contexts whose every tile of this side is sliced: warp w
-    // of the sweep's grid takes slices [wr[w], wr[w + 1]) (balanced by
-    // elements); null otherwise.
+    // Single-system contexts whose every tile of this side is sliced: the
+    // sweep's grid has one range of slices [wr[w], wr[w + 1]) per warp
+    // (balanced by elements); warp k of CTA b takes range k * gridDim.x + b,
+    // so each CTA's warps draw from all along the length-sorted slices;
+    // null otherwise.
     const int32_t *wr;
 };
 

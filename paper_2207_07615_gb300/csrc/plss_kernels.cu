@@ -623,8 +623,8 @@ __global__ void __launch_bounds__(kThreads) k_row_sweep(SweepArgs a) {
         finish_row(a, cur, init, a.desc[cur].rt_begin, a.desc[cur].rt_count);
 }
 
-// Row sweep of a single-system context whose row tiles are all sliced: warp
-// w takes slices [wr[w], wr[w + 1]), one partial per CTA, one barrier per
+// Row sweep of a single-system context whose row tiles are all sliced: each
+// warp takes one range of slices (Sliced::wr), one partial per CTA, one barrier per
 // CTA (its closing sum) instead of one per tile.
 template <typename S>
 __global__ void __launch_bounds__(kThreads) k_row_sweep_w(SweepArgs a) {
@@ -633,7 +633,9 @@ __global__ void __launch_bounds__(kThreads) k_row_sweep_w(SweepArgs a) {
     if (ph != PH_SETUP && ph != PH_RUN) return;   // uniform over the grid
     const bool init = ph == PH_SETUP;
     const int lane = threadIdx.x & 31;
-    const int32_t w = int32_t(blockIdx.x) * kWarps + (threadIdx.x >> 5);
+    // warp k of CTA b takes range k * gridDim.x + b: a CTA's (and an SM's)
+    // warps draw ranges from all along the length-sorted slices
+    const int32_t w = int32_t(threadIdx.x >> 5) * int32_t(gridDim.x) + int32_t(blockIdx.x);
     const int32_t s0 = __ldg(a.rsl.wr + w), s1 = __ldg(a.rsl.wr + w + 1);
     double acc[2] = {0.0, 0.0};
     for (int32_t s = s0; s < s1; ++s) {
@@ -842,7 +844,9 @@ __global__ void __launch_bounds__(kThreads) k_col_sweep_w(SweepArgs a) {
     const int32_t ph = load_phase(a.st);
     if (ph != PH_FIRST && ph != PH_RUN) return;   // uniform over the grid
     const int lane = threadIdx.x & 31;
-    const int32_t w = int32_t(blockIdx.x) * kWarps + (threadIdx.x >> 5);
+    // warp k of CTA b takes range k * gridDim.x + b: a CTA's (and an SM's)
+    // warps draw ranges from all along the length-sorted slices
+    const int32_t w = int32_t(threadIdx.x >> 5) * int32_t(gridDim.x) + int32_t(blockIdx.x);
     const int32_t s0 = __ldg(a.csl.wr + w), s1 = __ldg(a.csl.wr + w + 1);
     double acc[1] = {0.0};
     for (int32_t s = s0; s < s1; ++s) {

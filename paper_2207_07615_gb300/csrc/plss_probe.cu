@@ -38,7 +38,7 @@ __global__ void __launch_bounds__(kThreads) k_gather_slices(Sliced sl, const T *
                                                             unsigned long long magic,
                                                             unsigned long long *sink) {
     const int lane = threadIdx.x & 31;
-    const int32_t w = int32_t(blockIdx.x) * kWarps + (threadIdx.x >> 5);
+    const int32_t w = int32_t(threadIdx.x >> 5) * int32_t(gridDim.x) + int32_t(blockIdx.x);   // as the sweeps
     const int32_t s0 = __ldg(sl.wr + w), s1 = __ldg(sl.wr + w + 1);
     unsigned long long acc = 0;
     for (int32_t s = s0; s < s1; ++s) {
