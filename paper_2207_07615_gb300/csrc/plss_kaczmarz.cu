@@ -471,6 +471,21 @@ __global__ void __launch_bounds__(kKwThreads, 1) k_kacz_wide(KwArgs a) {
     int nh = ks.nh, nU = ks.nU;
     int64_t skipped = ks.skipped;
     for (int j = tid; j < nh; j += kKwThreads) s_ith[j] = 1.0 / a.theta[j];
+    // a row's index, bounds and entries do not depend on earlier rows: each
+    // row's are loaded during the previous row's second phase (the first
+    // row's here), leaving only the slot lookups for after the barrier
+    int32_t i = 0;
+    int len = 0;
+    auto load_row = [&](int64_t t) {
+        i = int32_t(a.row_off) + a.perm[a.row_off + t];
+        const int32_t s0 = a.row_ptr[i];
+        len = a.row_ptr[i + 1] - s0;
+        for (int e = tid; e < len; e += kKwThreads) {
+            s_col[e] = a.col_idx[s0 + e];
+            s_val[e] = double(val[s0 + e]);
+        }
+    };
+    if (ks.rows_todo > 0) load_row(0);
     __syncthreads();
 
     for (int64_t t = 0; t < ks.rows_todo; ++t) {
@@ -482,15 +497,8 @@ __global__ void __launch_bounds__(kKwThreads, 1) k_kacz_wide(KwArgs a) {
             nh = 0;
             nU = 0;
         }
-        const int32_t i = int32_t(a.row_off) + a.perm[a.row_off + t];
-        const int32_t s0 = a.row_ptr[i];
-        const int len = a.row_ptr[i + 1] - s0;
-        for (int e = tid; e < len; e += kKwThreads) {
-            const int32_t c = a.col_idx[s0 + e];
-            s_col[e] = c;
-            s_val[e] = double(val[s0 + e]);
-            s_slot[e] = a.slot[c];
-        }
+        __syncthreads();   // the row's entries (loaded by every thread) are in place
+        for (int e = tid; e < len; e += kKwThreads) s_slot[e] = a.slot[s_col[e]];
         __syncthreads();
         // phase A: c_j (owned j), partials of a^T x and ||a||^2 (owned entries)
         {
@@ -544,6 +552,7 @@ __global__ void __launch_bounds__(kKwThreads, 1) k_kacz_wide(KwArgs a) {
         }
         if (sh_skip) {
             ++skipped;
+            if (t + 1 < ks.rows_todo) load_row(t + 1);   // this row's entries are no longer read
             // keep c and the partials of this row until every CTA has read them
             if (!kw_barrier(a.bar, &sh_ok)) return;
             continue;
@@ -602,6 +611,7 @@ __global__ void __launch_bounds__(kKwThreads, 1) k_kacz_wide(KwArgs a) {
                 tq = fma(q, q, tq);
             }
         }
+        if (t + 1 < ks.rows_todo) load_row(t + 1);   // the scatter above was this row's last use
         tq = kw_sum(tq, sh_red);
         if (tid == 0) a.part[2 * G + bid] = tq;
         if (!kw_barrier(a.bar, &sh_ok)) return;

@@ -322,3 +322,23 @@ def test_coop_schedule_parity(plss, w_mode, precision):
     assert rc["status"] == rg["status"] == fin["status"] == "converged"
     assert rc["relres_true"] <= 1e-8
     assert rel(xc, fin["x"]) < 1e-5 and rel(xc, xg) < 1e-5
+
+
+def test_gather_bound_diagnostic(plss):
+    """plss_gather_bound times the gather-only walk of a sweep's own index
+    stream on both sides (positive times, min <= median), and refuses an
+    unknown side and a context whose sweeps run over plain CSR tiles (no
+    warp ranges)."""
+    A, b, _ = synth.overdetermined_scaled(m=200_000, n=40_000, per_row=8, seed=15)
+    A = A.astype(np.float64)
+    with plss.Context(A) as ctx:
+        lay = ctx.layout()
+        assert lay["row_sliced"] == lay["row_tiles"] and lay["col_sliced"] == lay["col_tiles"]
+        for side in (0, 1):
+            med, mn = ctx.gather_bound(side, reps=3)
+            assert 0.0 < mn <= med
+        with pytest.raises(plss.PlssError):
+            ctx.gather_bound(2)
+    with plss.Context(A, layout="csr") as ctx:
+        with pytest.raises(plss.PlssError):
+            ctx.gather_bound(0)
