@@ -6,7 +6,9 @@ the oracle, sampled where the oracle would be too slow in full.
   x_12 in FP64 (calibrated bar, at least 8 updates at the plain 1e-10), and
   the first updates of FP32 storage against the oracle's FP32 emulation.
 * C3, 100,000 x 1,000,000 power-law rows: 10 updates of the residual sketch,
-  and 3,000 rows of the identity sketch (K = 0 and K = 8).
+  3,000 rows of the identity sketch (K = 0 and K = 8) and 120 rows with a
+  window of 256 (the whole-GPU form).
+* The general sketch on C2: the first 8 sketch columns, history 64.
 * C4b, the 126^3 Laplacian with 32 right-hand sides (SpMM sweeps): 6
   updates, columns 0 and 31 against single-right-hand-side oracle solves.
 * C4a-shaped batch: the first 24 of the 256 systems (seeds 1000..1023) in one
@@ -85,13 +87,13 @@ def test_c3_residual_first_updates(plss, c3):
     _parity.check_x(x, ref, K)
 
 
-@pytest.mark.parametrize("K", [0, 8])
-def test_c3_identity_rows(plss, c3, K):
+@pytest.mark.parametrize("K,rows", [(0, 3000), (8, 3000), (256, 120)])
+def test_c3_identity_rows(plss, c3, K, rows):
     A, b = c3
-    rows, seed = 3000, 11
+    seed = 11
     r1 = oracle.kaczmarz(A, b, tol=0.0, maxit=rows, K=K, seed=seed)
     r2 = oracle.kaczmarz(A, b * _parity.F, tol=0.0, maxit=rows, K=K, seed=seed)
-    bar = max(1e-10, 1e3 * rel(r2["x"] / _parity.F, r1["x"]))
+    bar = max(_parity.FLOOR, _parity.MARGIN * rel(r2["x"] / _parity.F, r1["x"]))
     with plss.Context(A) as ctx:
         x, res = ctx.solve(b, sketch="identity", kacz_hist=K, seed=seed, tol=0.0, maxit=rows)
     assert res["iters"] == rows
@@ -121,3 +123,18 @@ def test_c4a_batched_first_systems(plss):
         assert r["iters"] == K
         ref = _parity.reference(A, b, K, w=oracle.colweights(A, 2))
         _parity.check_x(x, ref, K)
+
+
+def test_c2_general_first_columns(plss, c2):
+    """The general sketch (Sec. 2.4) on the headline system: 8 random sign
+    columns with a history of 64, against the oracle's Theorem 2.1."""
+    A, b = c2
+    A64 = A.astype(np.float64)
+    cols, seed = 8, 21
+    r1 = oracle.general(A64, b, tol=0.0, maxit=cols, K=64, seed=seed)
+    r2 = oracle.general(A64, b * _parity.F, tol=0.0, maxit=cols, K=64, seed=seed)
+    bar = max(_parity.FLOOR, _parity.MARGIN * rel(r2["x"] / _parity.F, r1["x"]))
+    with plss.Context(A64) as ctx:
+        x, res = ctx.solve(b, sketch="general", kacz_hist=64, seed=seed, tol=0.0, maxit=cols)
+    assert res["iters"] == cols
+    assert rel(x, r1["x"]) <= bar
