@@ -54,7 +54,6 @@ namespace plss {
 constexpr int kGsThreads = 256;
 constexpr int kGsWarps = kGsThreads / 32;
 constexpr int kGsMaxK = 1024;
-constexpr int kGsLanes = 8;   // lanes per row / column in the sparse passes
 constexpr int64_t kGsChunk = 8192;   // columns per partial dot product of c = Q^T y
 
 struct GsState {
@@ -134,7 +133,53 @@ __device__ __forceinline__ void gs_range(int64_t len, int64_t &lo, int64_t &hi) 
     hi = len * int64_t(blockIdx.x + 1) / int64_t(gridDim.x);
 }
 
-template <typename S>
+// Dot product of segment [s, e) of (idx, val) with a vector fetched by
+// `get` (a gather of x, or the sketch sign of a row), split over the G
+// lanes of a group: every lane issues 8 index/value loads, then its 8
+// fetches, then its 8 FMAs; the sum lands in every lane of the group.
+template <int G, typename S, typename F>
+__device__ __forceinline__ double gs_dot(const int32_t *__restrict__ idx, const S *__restrict__ val, int32_t s,
+                                         int32_t e, int gl, F &&get) {
+    double acc = 0.0;
+    for (int32_t base = s + gl; base < e; base += 8 * G) {
+        int32_t c[8];
+        double v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int32_t q = base + u * G;
+            const bool in = q < e;
+            c[u] = in ? __ldg(idx + q) : 0;
+            v[u] = in ? double(__ldg(val + q)) : 0.0;
+        }
+        double g[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) g[u] = base + u * G < e ? get(c[u]) : 0.0;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) acc = fma(v[u], g[u], acc);
+    }
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    return acc;
+}
+
+// Calls body(seg, d) for the segments [lo, hi) of ptr, G lanes each (d the
+// group's dot product, in the group's first lane); warp-uniform loop.
+template <int G, typename S, typename F, typename B>
+__device__ __forceinline__ void gs_segments(const int32_t *__restrict__ ptr, const int32_t *__restrict__ idx,
+                                            const S *__restrict__ val, int64_t lo, int64_t hi, F &&get, B &&body) {
+    constexpr int SPW = 32 / G;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int gid = lane / G, gl = lane & (G - 1);
+    for (int64_t base = lo + int64_t(warp) * SPW; base < hi; base += int64_t(kGsWarps) * SPW) {
+        const int64_t seg = base + gid;
+        const bool valid = seg < hi;
+        const int32_t s0 = valid ? __ldg(ptr + seg) : 0, s1 = valid ? __ldg(ptr + seg + 1) : 0;
+        const double d = gs_dot<G, S>(idx, val, s0, s1, gl, get);
+        if (valid && gl == 0) body(seg, d);
+    }
+}
+
+template <int G, typename S>
 __global__ void __launch_bounds__(kGsThreads) g_rows(GsArgs a) {
     __shared__ double sh[kGsWarps];
     GsState *st = a.st;
@@ -154,27 +199,19 @@ __global__ void __launch_bounds__(kGsThreads) g_rows(GsArgs a) {
         }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0 && a.K > 0 && st->nh == a.K) st->nh = 0;   // history full: start anew
-    const S *__restrict__ val = static_cast<const S *>(a.val);
-    const int grp = threadIdx.x / kGsLanes, gl = threadIdx.x % kGsLanes;
     int64_t lo, hi;
     gs_range(a.m, lo, hi);
     const int64_t k = st->k;
     double rr = 0.0, sr = 0.0;
-    for (int64_t base = lo; base < hi; base += kGsThreads / kGsLanes) {
-        const int64_t i = base + grp;
-        double dsum = 0.0;
-        if (i < hi)
-            for (int32_t q = a.row_ptr[i] + gl; q < a.row_ptr[i + 1]; q += kGsLanes)
-                dsum = fma(double(val[q]), a.x[a.col_idx[q]], dsum);
-#pragma unroll
-        for (int o = kGsLanes / 2; o > 0; o >>= 1) dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
-        if (i < hi && gl == 0) {
-            const double ri = a.b[i] - dsum;
-            a.r[i] = ri;
-            rr = fma(ri, ri, rr);
-            sr = fma(gs_sign(a.seed, a.m, k, i), ri, sr);
-        }
-    }
+    const double *__restrict__ x = a.x;
+    gs_segments<G, S>(a.row_ptr, a.col_idx, static_cast<const S *>(a.val), lo, hi,
+                      [&](int32_t c) { return __ldcg(x + c); },
+                      [&](int64_t i, double d) {
+                          const double ri = a.b[i] - d;
+                          a.r[i] = ri;
+                          rr = fma(ri, ri, rr);
+                          sr = fma(gs_sign(a.seed, a.m, k, i), ri, sr);
+                      });
     rr = gs_sum(rr, sh);
     sr = gs_sum(sr, sh);
     if (threadIdx.x == 0) {
@@ -183,33 +220,59 @@ __global__ void __launch_bounds__(kGsThreads) g_rows(GsArgs a) {
     }
 }
 
-// y = A^T s_k over the columns (CSC, or the CSR of a symmetric A).
-template <typename S>
+// y = A^T s_k over the columns (CSC, or the CSR of a symmetric A); the
+// sketch entry of row i is computed from (seed, k, i), nothing is gathered.
+template <int G, typename S>
 __global__ void __launch_bounds__(kGsThreads) g_cols(GsArgs a) {
     __shared__ double sh[kGsWarps];
     const GsState *st = a.st;
     if (st->done) return;
-    const S *__restrict__ val = static_cast<const S *>(a.cval);
-    const int grp = threadIdx.x / kGsLanes, gl = threadIdx.x % kGsLanes;
     int64_t lo, hi;
     gs_range(a.n, lo, hi);
     const int64_t k = st->k;
+    const uint64_t seed = a.seed;
+    const int64_t m = a.m;
     double yy = 0.0;
-    for (int64_t base = lo; base < hi; base += kGsThreads / kGsLanes) {
-        const int64_t j = base + grp;
-        double dsum = 0.0;
-        if (j < hi)
-            for (int32_t q = a.col_ptr[j] + gl; q < a.col_ptr[j + 1]; q += kGsLanes)
-                dsum = fma(double(val[q]), gs_sign(a.seed, a.m, k, a.row_idx[q]), dsum);
-#pragma unroll
-        for (int o = kGsLanes / 2; o > 0; o >>= 1) dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
-        if (j < hi && gl == 0) {
-            a.y[j] = dsum;
-            yy = fma(dsum, dsum, yy);
-        }
-    }
+    gs_segments<G, S>(a.col_ptr, a.row_idx, static_cast<const S *>(a.cval), lo, hi,
+                      [&](int32_t i) { return gs_sign(seed, m, k, i); },
+                      [&](int64_t j, double d) {
+                          a.y[j] = d;
+                          yy = fma(d, d, yy);
+                      });
     yy = gs_sum(yy, sh);
     if (threadIdx.x == 0) a.part_y[blockIdx.x] = yy;
+}
+
+// Lanes per segment for a mean segment length: the largest power of two G
+// <= 32 with 8 G <= the mean (each lane then has at least 8 entries).
+static int gs_lanes(int64_t nnz, int64_t segs) {
+    int g = 1;
+    while (g < 32 && 2 * g * 8 * std::max<int64_t>(segs, 1) <= nnz) g <<= 1;
+    return g;
+}
+
+template <typename S>
+static void launch_rows(int G, int grid, cudaStream_t s, const GsArgs &a) {
+    switch (G) {
+        case 1: g_rows<1, S><<<grid, kGsThreads, 0, s>>>(a); break;
+        case 2: g_rows<2, S><<<grid, kGsThreads, 0, s>>>(a); break;
+        case 4: g_rows<4, S><<<grid, kGsThreads, 0, s>>>(a); break;
+        case 8: g_rows<8, S><<<grid, kGsThreads, 0, s>>>(a); break;
+        case 16: g_rows<16, S><<<grid, kGsThreads, 0, s>>>(a); break;
+        default: g_rows<32, S><<<grid, kGsThreads, 0, s>>>(a); break;
+    }
+}
+
+template <typename S>
+static void launch_cols(int G, int grid, cudaStream_t s, const GsArgs &a) {
+    switch (G) {
+        case 1: g_cols<1, S><<<grid, kGsThreads, 0, s>>>(a); break;
+        case 2: g_cols<2, S><<<grid, kGsThreads, 0, s>>>(a); break;
+        case 4: g_cols<4, S><<<grid, kGsThreads, 0, s>>>(a); break;
+        case 8: g_cols<8, S><<<grid, kGsThreads, 0, s>>>(a); break;
+        case 16: g_cols<16, S><<<grid, kGsThreads, 0, s>>>(a); break;
+        default: g_cols<32, S><<<grid, kGsThreads, 0, s>>>(a); break;
+    }
 }
 
 // c_j = q_j^T y as partial dot products over column chunks: item (j, ch)
@@ -410,15 +473,16 @@ plss_status run_general(plss_ctx *c, const double *b, const double *x0, double *
     g_norm2<<<1, kGsThreads, 0, s>>>(c->d_b, c->m, &g->d_st->nb2);
     GS_TRY(cudaEventRecord(c->ev0, s));
     const int grid = g->grid;
+    const int gr = gs_lanes(c->nnz, c->m), gc = gs_lanes(c->nnz, c->n);
     const int64_t body = 16;   // steps between reads of the stop flag
     for (int64_t it = 0;; it += body) {
         for (int64_t q = 0; q < body; ++q) {
             if (c->f32) {
-                g_rows<float><<<grid, kGsThreads, 0, s>>>(a);
-                g_cols<float><<<grid, kGsThreads, 0, s>>>(a);
+                launch_rows<float>(gr, grid, s, a);
+                launch_cols<float>(gc, grid, s, a);
             } else {
-                g_rows<double><<<grid, kGsThreads, 0, s>>>(a);
-                g_cols<double><<<grid, kGsThreads, 0, s>>>(a);
+                launch_rows<double>(gr, grid, s, a);
+                launch_cols<double>(gc, grid, s, a);
             }
             g_qty<<<grid, kGsThreads, 0, s>>>(a);
             g_decide<<<1, kGsThreads, 0, s>>>(a);

@@ -22,7 +22,6 @@
 
 namespace plss {
 
-
 __device__ __forceinline__ unsigned long long gbits(double v) {
     return static_cast<unsigned long long>(__double_as_longlong(v));
 }
