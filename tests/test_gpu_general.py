@@ -34,9 +34,9 @@ def rel(a, b):
     return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300))
 
 
-def oracle_with_bar(A, b, **kw):
-    r1 = oracle.general(A, b, **kw)
-    r2 = oracle.general(A, b * F, **kw)
+def oracle_with_bar(A, b, x0=None, **kw):
+    r1 = oracle.general(A, b, x0=x0, **kw)
+    r2 = oracle.general(A, b * F, x0=None if x0 is None else x0 * F, **kw)
     spread = rel(r2["x"] / F, r1["x"])
     return r1, max(_parity.FLOOR, _parity.MARGIN * spread)
 
@@ -105,3 +105,18 @@ def test_options_rejected(plss):
             ctx.solve(b, sketch="general", kacz_hist=1025, tol=0.0, maxit=5)
         with pytest.raises(plss.PlssError):
             ctx.solve(b, sketch="general", w_mode=1, tol=0.0, maxit=5)
+
+
+def test_zero_rhs_and_start_vector(plss):
+    """b = 0 returns x0 at once (converged, no column drawn); a nonzero start
+    vector follows the oracle."""
+    A, b, _ = synth.overdetermined_scaled(m=2000, n=300, per_row=6, seed=37, scale_decades=0.5)
+    A = A.astype(np.float64)
+    x0 = synth.rng_for(5).standard_normal(A.n)
+    with plss.Context(A) as ctx:
+        x, r = ctx.solve(np.zeros(A.m), x0, sketch="general", kacz_hist=8, tol=1e-8, maxit=50)
+        assert r["status"] == "converged" and r["iters"] == 0
+        np.testing.assert_array_equal(x, x0)
+        ref, bar = oracle_with_bar(A, b, x0=x0, tol=0.0, maxit=40, K=8, seed=6)
+        x, r = ctx.solve(b, x0, sketch="general", kacz_hist=8, seed=6, tol=0.0, maxit=40)
+    assert rel(x, ref["x"]) <= bar

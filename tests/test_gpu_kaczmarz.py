@@ -35,9 +35,9 @@ def rel(a, b):
     return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300))
 
 
-def oracle_with_bar(A, b, maxit, K, seed):
-    r1 = oracle.kaczmarz(A, b, tol=0.0, maxit=maxit, K=K, seed=seed)
-    r2 = oracle.kaczmarz(A, b * F, tol=0.0, maxit=maxit, K=K, seed=seed)
+def oracle_with_bar(A, b, maxit, K, seed, x0=None):
+    r1 = oracle.kaczmarz(A, b, x0=x0, tol=0.0, maxit=maxit, K=K, seed=seed)
+    r2 = oracle.kaczmarz(A, b * F, x0=None if x0 is None else x0 * F, tol=0.0, maxit=maxit, K=K, seed=seed)
     spread = rel(r2["x"] / F, r1["x"])
     return r1, max(_parity.FLOOR, _parity.MARGIN * spread)
 
@@ -169,3 +169,23 @@ def test_window_limits_rejected(plss):
     with plss.Context([A, A]) as ctx:
         with pytest.raises(plss.PlssError):
             ctx.solve_batched([b, b], sketch="identity", kacz_hist=65, tol=0.0, maxit=10)
+
+
+def test_wide_window_largest_cap_and_start_vector(plss):
+    """The largest window (4,096 directions) on a small system with a start
+    vector, against the oracle; and a system with a row longer than the
+    8,192 entries a CTA holds is refused for windows above 64."""
+    A, b, _ = synth.powerlaw_underdetermined(m=300, n=3000, mean_len=12, max_len=200, seed=26)
+    A = A.astype(np.float64)
+    x0 = synth.rng_for(8).standard_normal(A.n)
+    ref, bar = oracle_with_bar(A, b, 700, 4096, 4, x0=x0)
+    with plss.Context(A) as ctx:
+        x, r = ctx.solve(b, x0, sketch="identity", kacz_hist=4096, seed=4, tol=0.0, maxit=700)
+    assert rel(x, ref["x"]) <= bar
+    m, n = 2, 9000
+    rp = np.array([0, 8300, 8302], dtype=np.int64)
+    ci = np.concatenate([np.arange(8300), [0, 1]]).astype(np.int32)
+    Along = synth.CSR(m, n, rp, ci, np.ones(8302))
+    with plss.Context(Along) as ctx:
+        with pytest.raises(plss.PlssError):
+            ctx.solve(np.ones(2), sketch="identity", kacz_hist=65, tol=0.0, maxit=2)
