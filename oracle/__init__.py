@@ -58,7 +58,7 @@ def _load():
             i64, i32, d, vp, u64 = C.c_int64, C.c_int, C.c_double, C.c_void_p, C.c_uint64
             lib.plss_oracle_residual.restype = i32
             lib.plss_oracle_residual.argtypes = [i64, i64, vp, vp, vp, vp, vp, vp, d, i64, i32, i64,
-                                                 d, i32, i32, vp, vp, vp, vp, i64, vp, vp, vp, vp,
+                                                 d, i32, i32, i32, vp, vp, vp, vp, i64, vp, vp, vp, vp,
                                                  vp]
             lib.plss_oracle_kaczmarz.restype = i32
             lib.plss_oracle_kaczmarz.argtypes = [i64, i64, vp, vp, vp, vp, vp, d, i64, i64, u64,
@@ -153,14 +153,15 @@ def permutation(state: int, m: int):
 
 
 def residual(A, b, x0=None, w=None, tol=1e-10, maxit=None, prec=0, refine=0, inner_tol=0.0,
-             stop_on_true=False, gamma_form=0, hist=0, plant=0, threads=False):
+             stop_on_true=False, gamma_form=0, hist=0, plant=0, threads=False, replace=False):
     """PLSS residual sketch (Algorithm 1). Returns a dict with x, iters,
     status, relres_rec, relres_true and, when hist > 0, the per-update
     history: s[k] = (rho_k, phi_{k+1}, beta_k, gamma_k, theta_{k+1}),
     x[k] = x_{k+1}, p[k] = p_{k+1}, y[k] = A^T r_k, r[k] = r_k.
     gamma_form=1 (same as plant=1) and plant=2/3 plant a defect for the
     tests that show the pins reject it (see plss_oracle.c). threads=True
-    runs the OpenMP build on all host cores (for timing)."""
+    runs the OpenMP build on all host cores (for timing). replace=True:
+    refinement refreshes replace the residual instead of restarting."""
     lib = _load_omp() if threads else _load()
     rp, ci, val = _csr(A)
     b = _vec(b, A.m, "b")
@@ -181,7 +182,7 @@ def residual(A, b, x0=None, w=None, tol=1e-10, maxit=None, prec=0, refine=0, inn
     st = lib.plss_oracle_residual(A.m, A.n, _p(rp), _p(ci), _p(val), _p(b), _p(x0), _p(w),
                                   float(tol), int(maxit), int(prec), int(refine), float(inner_tol),
                                   int(bool(stop_on_true)), 1 if gamma_form == 1 else int(plant),
-                                  _p(x), _p(it),
+                                  int(bool(replace)), _p(x), _p(it),
                                   _p(rr), _p(rt), H, _p(hs), _p(hx), _p(hp), _p(hy), _p(hr))
     if st == -2:
         raise MemoryError("oracle residual")

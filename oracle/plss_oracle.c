@@ -37,11 +37,17 @@
  *   - FP32 storage (prec = 1): A's values, r, p and W y are held as float,
  *     sums of products are accumulated in float, inner products and the
  *     scalar recursion in double, x in double; the residual is recomputed as
- *     b - A x in double and the recursion restarts from it every `refine`
- *     updates and whenever rho has fallen by inner_tol^2 since the last
- *     start (or risen above 4x its starting value) -- iterative refinement,
- *     which keeps the float recursion away from its rounding floor where it
- *     turns unstable (this extension is not in the paper).
+ *     b - A x in double every `refine` updates and whenever rho has fallen
+ *     by inner_tol^2 since the last start (or risen above 4x its starting
+ *     value) -- iterative refinement, which keeps the float recursion away
+ *     from its rounding floor where it turns unstable (this extension is not
+ *     in the paper). With replace = 0 the recursion restarts from the fresh
+ *     residual (a new first step); with replace = 1 the fresh residual only
+ *     replaces the recursive one and the recursion goes on with its p and
+ *     theta (residual replacement; in exact arithmetic the two residuals are
+ *     equal, so the iterates are unchanged). A stop confirmed false on
+ *     b - A x refreshes the residual the same way. replace = 1 also applies
+ *     the period in FP64 storage.
  *   - Kaczmarz order: rows are visited without replacement in a fresh
  *     permutation per pass (SplitMix64 stream + Fisher-Yates shuffle); the
  *     history holds at most K updates and, once full, is emptied before the
@@ -221,7 +227,8 @@ static void true_residual(int64_t m, const int64_t *row_ptr, const int32_t *col_
  * restart from b - A x once rho has fallen by inner_tol^2 since the last
  * start (the inner solve of iterative refinement; 0 = never), stop_on_true:
  * the stop decision uses the residual b - A x recomputed in double,
- * plant = a planted defect (see the file header; 0 = none).
+ * plant = a planted defect (see the file header; 0 = none), replace = 1:
+ * refreshes replace the residual instead of restarting (see the header).
  * Outputs: x_out[n], *iters (updates applied), *relres_rec (sqrt(rho)/||b||
  * of the last rho), *relres_true (||b - A x||/||b||), return value = status.
  * Optional history (any pointer may be NULL; hist_cap rows):
@@ -233,7 +240,7 @@ static void true_residual(int64_t m, const int64_t *row_ptr, const int32_t *col_
 int plss_oracle_residual(int64_t m, int64_t n, const int64_t *row_ptr, const int32_t *col_idx,
                          const double *val_in, const double *b, const double *x0, const double *w,
                          double tol, int64_t maxit, int prec, int64_t refine, double inner_tol,
-                         int stop_on_true, int plant, double *x_out, int64_t *iters_out,
+                         int stop_on_true, int plant, int replace, double *x_out, int64_t *iters_out,
                          double *relres_rec,
                          double *relres_true, int64_t hist_cap, double *hist_s, double *hist_x,
                          double *hist_p, double *hist_y, double *hist_r)
@@ -263,6 +270,7 @@ int plss_oracle_residual(int64_t m, int64_t n, const int64_t *row_ptr, const int
     int64_t k = 0;          /* updates applied */
     int64_t since = 0;      /* updates since the last (re)start */
     int restart = 1;        /* next update is the initial one (p = (rho/phi) u) */
+    int fresh = 0;          /* r was just recomputed as b - A x (replace = 1) */
 
     /* r_0 = b - A x_0 (Algorithm 1, initialization) */
     true_residual(m, row_ptr, col_idx, val, b, x, rt);
@@ -271,16 +279,17 @@ int plss_oracle_residual(int64_t m, int64_t n, const int64_t *row_ptr, const int
     if (nb == 0.0) { status = ORC_CONVERGED; goto done; }
 
     for (;;) {
-        if (restart) rho_start = rho;
+        if (restart || fresh) rho_start = rho;
         if (hist_r && k <= hist_cap) memcpy(hist_r + k * m, r, (size_t)m * sizeof(double));
         /* stopping rule (Sec. 5): sqrt(rho)/||b|| <= tol */
         if (sqrt(rho) / nb <= tol) {
-            if (!stop_on_true || restart) { status = ORC_CONVERGED; break; }
+            if (!stop_on_true || restart || fresh) { status = ORC_CONVERGED; break; }
             /* confirm on b - A x before stopping */
             true_residual(m, row_ptr, col_idx, val, b, x, rt);
             for (int64_t i = 0; i < m; ++i) r[i] = rf(rt[i], f32);
             rho = dot(m, r, r);
-            restart = 1; since = 0;
+            if (replace) fresh = 1; else restart = 1;
+            since = 0;
             continue;
         }
         if (k >= maxit) { status = ORC_NOT_CONVERGED; break; }
@@ -293,7 +302,8 @@ int plss_oracle_residual(int64_t m, int64_t n, const int64_t *row_ptr, const int
             true_residual(m, row_ptr, col_idx, val, b, x, rt);
             for (int64_t i = 0; i < m; ++i) r[i] = rf(rt[i], f32);
             rho = dot(m, r, r);
-            restart = 1; since = 0;
+            if (replace) fresh = 1; else restart = 1;
+            since = 0;
             continue;
         }
 
@@ -358,12 +368,15 @@ int plss_oracle_residual(int64_t m, int64_t n, const int64_t *row_ptr, const int
         k += 1;
         since += 1;
         restart = 0;
+        fresh = 0;
 
-        if (f32 && refine > 0 && since >= refine) {
-            /* FP64 refinement: recompute the residual and restart */
+        if ((f32 || replace) && refine > 0 && since >= refine) {
+            /* FP64 refinement: recompute the residual, then restart from it
+             * or let it replace the recursive one */
             true_residual(m, row_ptr, col_idx, val, b, x, rt);
             for (int64_t i = 0; i < m; ++i) r[i] = rf(rt[i], f32);
-            restart = 1; since = 0;
+            if (replace) fresh = 1; else restart = 1;
+            since = 0;
         } else if (!f32) {
             /* r = r - A p */
             PAR_FOR

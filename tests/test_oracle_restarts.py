@@ -233,3 +233,43 @@ def test_refine_period():
     assert starts == [0, 3, 6, 9]
     for k in range(K):
         assert rel(out["hist_x"][k], xs[k]) < 1e-4, k
+
+
+# ------------------------------------------------ residual replacement
+
+@pytest.mark.parametrize("ci", range(5))
+def test_replacement_leaves_fp64_iterates_unchanged(ci):
+    """Residual replacement (refinement mode `replace`): every 2 updates the
+    residual is recomputed as b - A x and replaces the recursive one while
+    the recursion goes on. In exact arithmetic the two residuals are equal,
+    so the iterates are those of eq:pkLong with the full residual sketch
+    (no restart) for every k up to rank(A) -- to the same bar as the plain
+    recursion's pin (test_oracle_pins.test_recursion_equals_pklong), on the
+    same systems."""
+    from tests.test_oracle_pins import CASES
+    D, b, rank = CASES[ci]
+    A = synth.from_dense(D)
+    n = D.shape[1]
+    x0 = synth.rng_for(11 + ci).standard_normal(n)
+    xs, ps, _ = _pins.projection_run(D, b, x0, np.ones(n), rank, "residual")
+    out = oracle.residual(A, b, x0=x0, tol=0.0, maxit=rank, refine=2, replace=True, hist=rank)
+    assert all(out["hist_s"][k, 2] != 0.0 for k in range(1, rank))   # no restart after the first update
+    for k in range(rank):
+        assert rel(out["hist_x"][k], xs[k]) < 1e-10, k
+
+
+def test_replacement_refreshes_the_fp32_residual():
+    """FP32 storage with replacement every 3 updates: after updates 3, 6, 9
+    the residual the recursion continues from is b - A x recomputed in double
+    and rounded to float (and nothing restarts), while a restart of the same
+    schedule begins a new recursion (beta = 0) at those updates."""
+    D, b = _restart_case()
+    A = synth.from_dense(D)
+    K, R = 10, 3
+    out = oracle.residual(A, b, tol=0.0, maxit=K, prec=1, refine=R, replace=True, hist=K)
+    assert all(out["hist_s"][k, 2] != 0.0 for k in range(1, K))
+    for k in (3, 6, 9):
+        r_true = (b - D @ out["hist_x"][k - 1]).astype(np.float32).astype(np.float64)
+        np.testing.assert_array_equal(out["hist_r"][k], r_true)
+    rst = oracle.residual(A, b, tol=0.0, maxit=K, prec=1, refine=R, hist=K)
+    assert [k for k in range(K) if rst["hist_s"][k, 2] == 0.0] == [0, 3, 6, 9]
