@@ -147,7 +147,21 @@ typedef struct {
     int32_t tile_shift;     /* create: sweep tiles of 2^tile_shift times the       */
                             /* default nonzeros, -2..2 (0 = default; the knob     */
                             /* plss_tune measures)                                */
+    int32_t refine_mode;    /* residual sketch: PLSS_REFINE_* (what a refresh of  */
+                            /* the residual from b - A x does)                    */
 } plss_opts;
+
+/* Refinement modes of the residual sketch (an extension, not in the paper).
+ * A refresh recomputes r = b - A x in double: every refine_period updates,
+ * when the recursive residual has fallen by inner_tol (FP32 storage), and
+ * when a stop is confirmed false on b - A x (stop_on_true). RESTART: the
+ * recursion starts anew from the fresh residual (a first step p = (rho/phi)
+ * W y). REPLACE: the fresh residual replaces the recursive one and the
+ * recursion goes on with its p and theta (residual replacement; in exact
+ * arithmetic nothing changes); it also applies refine_period in FP64
+ * storage. A breakdown always restarts. Single and batched residual-sketch
+ * solves; plss_solve_rhs and the server use RESTART. */
+enum { PLSS_REFINE_RESTART = 0, PLSS_REFINE_REPLACE = 1 };
 
 /* Outcome of one solve. relres_rec is sqrt(rho)/||b|| of the last recursive
  * (or refined) residual; relres_true is ||b - A x||/||b|| recomputed in

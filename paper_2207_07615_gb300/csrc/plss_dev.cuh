@@ -95,6 +95,8 @@ struct SysState {
     int32_t stop_on_true;
     int32_t upd;        // update due in this body: 0 none, 1 p = beta p + gamma u, 2 p = gamma u (first)
     uint32_t cnt_row, cnt_col, cnt_upd, pad1;
+    int32_t replace;       // refinement mode: 0 a refresh restarts the recursion, 1 it replaces r
+    int32_t restart_next;  // the next set-up row sweep begins a new recursion (solve start, breakdown)
 };
 
 // Arguments of the three residual-sketch sweeps (one struct for all).

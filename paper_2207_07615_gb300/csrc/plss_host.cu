@@ -598,6 +598,8 @@ plss_status check_opts(const plss_opts *o) {
     if (!(o->inner_tol >= 0.0) || !(o->inner_tol < 1.0)) return fail(PLSS_ERR_INVALID, "inner_tol must be in [0, 1)");
     if (o->hist_cap > 0 && !o->hist) return fail(PLSS_ERR_INVALID, "hist_cap > 0 with hist NULL");
     if (o->profile < 0) return fail(PLSS_ERR_INVALID, "profile < 0");
+    if (o->refine_mode != PLSS_REFINE_RESTART && o->refine_mode != PLSS_REFINE_REPLACE)
+        return fail(PLSS_ERR_INVALID, "unknown refine_mode %d", o->refine_mode);
     if (o->schedule != PLSS_SCHED_AUTO && o->schedule != PLSS_SCHED_GRID && o->schedule != PLSS_SCHED_SMALL &&
         o->schedule != PLSS_SCHED_COOP)
         return fail(PLSS_ERR_INVALID, "unknown schedule %d", o->schedule);
@@ -672,9 +674,12 @@ plss_status run_residual(plss_ctx *c, const double *const *b, const double *cons
         std::memset(&z, 0, sizeof z);
         z.tol = o->tol;
         z.maxit = o->maxit < 0 ? int64_t(d.n) : o->maxit;
-        z.refine = c->f32 ? std::max<int64_t>(0, o->refine_period) : 0;
+        const bool replace = o->refine_mode == PLSS_REFINE_REPLACE;
+        z.refine = (c->f32 || replace) ? std::max<int64_t>(0, o->refine_period) : 0;
         z.inner_tol2 = c->f32 ? o->inner_tol * o->inner_tol : 0.0;
         z.stop_on_true = (c->f32 || o->stop_on_true) ? 1 : 0;
+        z.replace = replace ? 1 : 0;
+        z.restart_next = 1;   // the first set-up row sweep begins the recursion
         z.phase = PH_SETUP;
         z.nb = 0.0;
         if (sy == 0 && o->hist_cap > 0) {
@@ -834,6 +839,7 @@ void plss_opts_default(plss_opts *o) {
     o->schedule = PLSS_SCHED_AUTO;
     o->tile_shift = 0;
     o->inner_tol = 1e-4;
+    o->refine_mode = PLSS_REFINE_RESTART;
 }
 
 plss_status plss_create(const plss_csr *A, const plss_opts *o, plss_ctx **out) {

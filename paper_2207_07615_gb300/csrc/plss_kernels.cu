@@ -515,8 +515,13 @@ __device__ void row_decide(const SweepArgs &a, SysState *st, bool init, double r
         // refine from b - A x
         st->since = 0;
         st->phase = PH_SETUP;
+    } else if (init) {
+        // after a refresh of r from b - A x: a new recursion, or (residual
+        // replacement) the same one going on with the fresh residual
+        st->phase = (st->replace && !st->restart_next) ? PH_RUN : PH_FIRST;
+        st->restart_next = 0;
     } else {
-        st->phase = init ? PH_FIRST : PH_RUN;
+        st->phase = PH_RUN;
     }
 }
 
@@ -757,6 +762,7 @@ __device__ void col_decide(const SweepArgs &a, SysState *st, double phi) {
                 // b - A x (the next row sweep) instead of stopping
                 st->since = 0;
                 st->phase = PH_SETUP;
+                st->restart_next = 1;
             } else {
                 finish_system(a, st, -4);
             }

@@ -25,6 +25,7 @@ SKETCH = {"residual": 0, "identity": 1, "general": 2}
 PRECISION = {"fp64": 0, "fp32": 1}
 LAYOUT = {"auto": 0, "csr": 1}
 SCHEDULE = {"auto": 0, "grid": 1, "small": 2, "coop": 3}
+REFINE = {"restart": 0, "replace": 1}
 
 #: every symbol declared in include/plss.h
 EXPORTS = ["plss_opts_default", "plss_create", "plss_create_batched", "plss_destroy",
@@ -47,7 +48,7 @@ class Opts(C.Structure):
                 ("io_device", C.c_int32), ("symmetric", C.c_int32), ("stream", C.c_void_p),
                 ("hist", C.c_void_p), ("hist_cap", C.c_int64), ("profile", C.c_int32),
                 ("layout", C.c_int32), ("inner_tol", C.c_double), ("schedule", C.c_int32),
-                ("tile_shift", C.c_int32)]
+                ("tile_shift", C.c_int32), ("refine_mode", C.c_int32)]
 
 
 class TuneEntry(C.Structure):
@@ -194,6 +195,8 @@ def make_opts(**kw) -> Opts:
             v = LAYOUT[v]
         if k == "schedule" and isinstance(v, str):
             v = SCHEDULE[v]
+        if k == "refine_mode" and isinstance(v, str):
+            v = REFINE[v]
         setattr(o, k, v)
     return o
 

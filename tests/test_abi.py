@@ -33,7 +33,7 @@ def test_exports_match_header(L):
 
 
 def test_struct_layouts(L):
-    assert C.sizeof(plss.Opts) == 112
+    assert C.sizeof(plss.Opts) == 120
     assert C.sizeof(plss.Csr) == 56
     assert C.sizeof(plss.Result) == 40
     assert C.sizeof(plss.ServerOpts) == 32
@@ -41,7 +41,7 @@ def test_struct_layouts(L):
     o = plss.Opts()
     L.plss_opts_default(C.byref(o))
     assert o.tol == 1e-8 and o.maxit == -1 and o.sketch == 0 and o.precision == 0
-    assert o.inner_tol == 1e-4 and o.tile_shift == 0
+    assert o.inner_tol == 1e-4 and o.tile_shift == 0 and o.refine_mode == 0
 
 
 def _create(L, csr):
