@@ -45,6 +45,13 @@
 namespace plss {
 
 constexpr int kBatch = 8;   // loads each lane issues before using any of them
+// Steps of a column slice each lane loads before its gathers: four in FP64,
+// eight in FP32 (C2's ~40-element columns: the FP64 column sweep takes
+// 40.5 us with four and 42.0 us with eight; the FP32 one took 54.9 us with
+// four against 38.3 us with eight).
+template <typename S>
+constexpr int kColBatch = std::is_same<S, double>::value ? 4 : 8;
+constexpr int kWarpSweepCtas = 4;   // resident CTAs per SM of the warp-range sweeps
 
 __device__ __forceinline__ double fma_t(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ float fma_t(float a, float b, float c) { return fmaf(a, b, c); }
@@ -281,30 +288,49 @@ __device__ __forceinline__ void for_segments(const int32_t *__restrict__ ptr, co
 template <typename T>
 __device__ __forceinline__ T kGather(const T *p) { return __ldcg(p); }
 
+// Loads of A's sliced index and value streams, each element read once per
+// sweep: non-coherent, and not allocated in L1 (nothing there is read
+// again). On C2 this took 2-4 % off a sweep against plain __ldg.
+__device__ __forceinline__ int32_t ld_stream(const int32_t *p) {
+    int32_t v;
+    asm volatile("ld.global.nc.L1::no_allocate.s32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ float ld_stream(const float *p) {
+    float v;
+    asm volatile("ld.global.nc.L1::no_allocate.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ double ld_stream(const double *p) {
+    double v;
+    asm volatile("ld.global.nc.L1::no_allocate.f64 %0, [%1];" : "=d"(v) : "l"(p));
+    return v;
+}
+
 // Dot product of slot `lane` of a slice (element offset `off`, `width`
 // elements per slot) with a dense vector: the warp loads 32 consecutive
-// indices and values per step, 8 steps before their gathers, and each lane
+// indices and values per step, B steps before their gathers, and each lane
 // sums its own segment in element order with one FMA per element. Padding
 // (index -1, value 0) gathers nothing and adds an exact zero.
-template <typename VT, typename XT, typename ACC>
+template <typename VT, typename XT, typename ACC, int B = kBatch>
 __device__ __forceinline__ ACC slice_dot(const int32_t *__restrict__ idx, const VT *__restrict__ val,
                                          int32_t off, int32_t width, int lane, const XT *__restrict__ x) {
     ACC acc = ACC(0);
-    for (int32_t k0 = 0; k0 < width; k0 += kBatch) {
-        int32_t c[kBatch];
-        VT v[kBatch];
+    for (int32_t k0 = 0; k0 < width; k0 += B) {
+        int32_t c[B];
+        VT v[B];
 #pragma unroll
-        for (int u = 0; u < kBatch; ++u) {
+        for (int u = 0; u < B; ++u) {
             const bool in = k0 + u < width;
             const int32_t e = off + 32 * (k0 + u) + lane;
-            c[u] = in ? __ldg(idx + e) : -1;
-            v[u] = in ? __ldg(val + e) : VT(0);
+            c[u] = in ? ld_stream(idx + e) : -1;
+            v[u] = in ? ld_stream(val + e) : VT(0);
         }
-        XT g[kBatch];
+        XT g[B];
 #pragma unroll
-        for (int u = 0; u < kBatch; ++u) g[u] = c[u] >= 0 ? kGather(x + c[u]) : XT(0);
+        for (int u = 0; u < B; ++u) g[u] = c[u] >= 0 ? kGather(x + c[u]) : XT(0);
 #pragma unroll
-        for (int u = 0; u < kBatch; ++u) acc = fma_t(ACC(v[u]), ACC(g[u]), acc);
+        for (int u = 0; u < B; ++u) acc = fma_t(ACC(v[u]), ACC(g[u]), acc);
     }
     return acc;
 }
@@ -633,15 +659,15 @@ __global__ void __launch_bounds__(kThreads) k_row_sweep(SweepArgs a) {
 // CTA (its closing sum) instead of one per tile.
 template <typename S>
 __global__ void __launch_bounds__(kThreads) k_row_sweep_w(SweepArgs a) {
-    wait_prior_grid();
-    const int32_t ph = load_phase(a.st);
-    if (ph != PH_SETUP && ph != PH_RUN) return;   // uniform over the grid
-    const bool init = ph == PH_SETUP;
     const int lane = threadIdx.x & 31;
     // warp k of CTA b takes range k * gridDim.x + b: a CTA's (and an SM's)
     // warps draw ranges from all along the length-sorted slices
     const int32_t w = int32_t(threadIdx.x >> 5) * int32_t(gridDim.x) + int32_t(blockIdx.x);
     const int32_t s0 = __ldg(a.rsl.wr + w), s1 = __ldg(a.rsl.wr + w + 1);
+    wait_prior_grid();
+    const int32_t ph = load_phase(a.st);
+    if (ph != PH_SETUP && ph != PH_RUN) return;   // uniform over the grid
+    const bool init = ph == PH_SETUP;
     double acc[2] = {0.0, 0.0};
     for (int32_t s = s0; s < s1; ++s) {
         const int32_t off = __ldg(a.rsl.ptr + s);
@@ -716,8 +742,8 @@ template <typename S>
 __device__ __forceinline__ void col_slot(const SweepArgs &a, int32_t col, int32_t off, int32_t width,
                                          int lane, double &acc) {
     const int g = a.csl.g;
-    const S y = group_sum(slice_dot<S, S, S>(a.csl.idx, static_cast<const S *>(a.csl.val), off, width, lane,
-                                             static_cast<const S *>(a.r)), g);
+    const S y = group_sum(slice_dot<S, S, S, kColBatch<S>>(a.csl.idx, static_cast<const S *>(a.csl.val), off, width,
+                                                           lane, static_cast<const S *>(a.r)), g);
     if (col >= 0 && (lane & (g - 1)) == 0) {
         if constexpr (std::is_same<S, float>::value) {
             const float uj = a.wf ? __fmul_rn(a.wf[col], y) : y;
@@ -846,14 +872,14 @@ __global__ void __launch_bounds__(kThreads) k_col_sweep(SweepArgs a) {
 // sliced (warp ranges as in k_row_sweep_w).
 template <typename S>
 __global__ void __launch_bounds__(kThreads) k_col_sweep_w(SweepArgs a) {
-    wait_prior_grid();
-    const int32_t ph = load_phase(a.st);
-    if (ph != PH_FIRST && ph != PH_RUN) return;   // uniform over the grid
     const int lane = threadIdx.x & 31;
     // warp k of CTA b takes range k * gridDim.x + b: a CTA's (and an SM's)
     // warps draw ranges from all along the length-sorted slices
     const int32_t w = int32_t(threadIdx.x >> 5) * int32_t(gridDim.x) + int32_t(blockIdx.x);
     const int32_t s0 = __ldg(a.csl.wr + w), s1 = __ldg(a.csl.wr + w + 1);
+    wait_prior_grid();
+    const int32_t ph = load_phase(a.st);
+    if (ph != PH_FIRST && ph != PH_RUN) return;   // uniform over the grid
     double acc[1] = {0.0};
     for (int32_t s = s0; s < s1; ++s) {
         const int32_t off = __ldg(a.csl.ptr + s);
@@ -870,95 +896,101 @@ __global__ void __launch_bounds__(kThreads) k_col_sweep_w(SweepArgs a) {
 // Update: p = beta p + gamma u, theta = p^T W^{-1} p, x = x + p
 // ---------------------------------------------------------------------------
 
+constexpr int kUpdU = 4;   // entries per thread in one pass (a pass covers 1,024 entries: one tile)
+
+// The entries one thread updates in a pass (base, base + kThreads, ...).
+template <typename S>
+struct UpdRegs {
+    using W = typename std::conditional<std::is_same<S, float>::value, float, double>::type;
+    S u[kUpdU], p[kUpdU];
+    double x[kUpdU];
+    W w[kUpdU];
+};
+
+// Loads u, p, x and the weights of a pass (all of them, before any is
+// used: one memory round trip). p is loaded on the first update too, and
+// not used there.
+template <typename S>
+__device__ __forceinline__ void upd_load(const SweepArgs &a, int32_t base, int32_t end, UpdRegs<S> &g) {
+    using W = typename UpdRegs<S>::W;
+    const S *__restrict__ p = static_cast<const S *>(a.p);
+    const S *__restrict__ u = static_cast<const S *>(a.u);
+    const W *__restrict__ winv;
+    if constexpr (std::is_same<S, float>::value) winv = a.winvf;
+    else winv = a.winv;
+#pragma unroll
+    for (int q = 0; q < kUpdU; ++q) {
+        const int32_t j = base + q * kThreads;
+        const bool in = j < end;
+        g.u[q] = in ? u[j] : S(0);
+        g.p[q] = in ? p[j] : S(0);
+        g.x[q] = in ? a.x[j] : 0.0;
+        g.w[q] = in && winv ? winv[j] : W(1);
+    }
+}
+
 // FP32 storage: p = beta p + gamma u in float (p is stored in float; beta
 // and gamma rounded to float), theta partials in float per thread, x in
 // double -- two FP64-pipe operations per entry.
-__device__ __forceinline__ DF update_tile_f32(const SweepArgs &a, const Tile &t, bool first, double beta,
-                                              double gamma) {
+__device__ __forceinline__ void upd_pass_f32(const SweepArgs &a, int32_t base, int32_t end, bool first,
+                                             double beta, double gamma, const UpdRegs<float> &g, DF &acc) {
     float *__restrict__ p = static_cast<float *>(a.p);
-    const float *__restrict__ u = static_cast<const float *>(a.u);
-    double *__restrict__ x = a.x;
-    const float *__restrict__ winv = a.winvf;
+    const bool weighted = a.winvf != nullptr;
     const float bf = float(beta), gf = float(gamma);
-    DF acc = {0.0f, 0.0f};
-    constexpr int U = 4;
-    for (int32_t base = t.begin + threadIdx.x; base < t.end; base += kThreads * U) {
-        float uj[U], pj[U], wj[U];
-        double xj[U];
 #pragma unroll
-        for (int q = 0; q < U; ++q) {
-            const int32_t j = base + q * kThreads;
-            const bool in = j < t.end;
-            uj[q] = in ? u[j] : 0.0f;
-            pj[q] = in && !first ? p[j] : 0.0f;
-            xj[q] = in ? x[j] : 0.0;
-            wj[q] = in && winv ? winv[j] : 1.0f;
-        }
-#pragma unroll
-        for (int q = 0; q < U; ++q) {
-            const int32_t j = base + q * kThreads;
-            if (j < t.end) {
-                const float pn = first ? gf * uj[q] : fmaf(bf, pj[q], gf * uj[q]);
-                p[j] = pn;
-                acc = df_add_prod(acc, pn, winv ? __fmul_rn(pn, wj[q]) : pn);
-                x[j] = xj[q] + double(pn);
-            }
+    for (int q = 0; q < kUpdU; ++q) {
+        const int32_t j = base + q * kThreads;
+        if (j < end) {
+            const float pn = first ? gf * g.u[q] : fmaf(bf, g.p[q], gf * g.u[q]);
+            p[j] = pn;
+            acc = df_add_prod(acc, pn, weighted ? __fmul_rn(pn, g.w[q]) : pn);
+            a.x[j] = g.x[q] + double(pn);
         }
     }
-    return acc;
 }
 
 template <typename S>
-__device__ __forceinline__ double update_tile(const SweepArgs &a, const Tile &t, bool first,
-                                              double beta, double gamma) {
+__device__ __forceinline__ void upd_pass(const SweepArgs &a, int32_t base, int32_t end, bool first, double beta,
+                                         double gamma, const UpdRegs<S> &g, double &acc) {
     S *__restrict__ p = static_cast<S *>(a.p);
-    const S *__restrict__ u = static_cast<const S *>(a.u);
-    double *__restrict__ x = a.x;
-    const double *__restrict__ winv = a.winv;
-    double acc = 0.0;
-    constexpr int U = 4;
-    for (int32_t base = t.begin + threadIdx.x; base < t.end; base += kThreads * U) {
-        double uj[U], pj[U], xj[U], wj[U];
+    const bool weighted = a.winv != nullptr;
 #pragma unroll
-        for (int q = 0; q < U; ++q) {
-            const int32_t j = base + q * kThreads;
-            const bool in = j < t.end;
-            uj[q] = in ? double(u[j]) : 0.0;
-            pj[q] = in && !first ? double(p[j]) : 0.0;
-            xj[q] = in ? x[j] : 0.0;
-            wj[q] = in && winv ? winv[j] : 1.0;
-        }
-#pragma unroll
-        for (int q = 0; q < U; ++q) {
-            const int32_t j = base + q * kThreads;
-            if (j < t.end) {
-                const double gu = gamma * uj[q];
-                const double pn = first ? gu : fma(beta, pj[q], gu);
-                const S ps = S(pn);
-                p[j] = ps;
-                const double pd = double(ps);
-                acc = fma(pd, winv ? pd * wj[q] : pd, acc);
-                x[j] = xj[q] + pd;
-            }
+    for (int q = 0; q < kUpdU; ++q) {
+        const int32_t j = base + q * kThreads;
+        if (j < end) {
+            const double gu = gamma * double(g.u[q]);
+            const double pn = first ? gu : fma(beta, double(g.p[q]), gu);
+            const S ps = S(pn);
+            p[j] = ps;
+            const double pd = double(ps);
+            acc = fma(pd, weighted ? pd * double(g.w[q]) : pd, acc);
+            a.x[j] = g.x[q] + pd;
         }
     }
-    return acc;
 }
 
 // The update writes one theta partial per tile and finishes nothing: the
 // row sweep that follows sums them (it has to wait for the whole update
 // anyway), which takes the arrival and the last-CTA reduction off this
-// short kernel's critical path.
+// short kernel's critical path. The tile list is fixed for the context, so
+// the first tile is read before the wait; a tile's vector entries are then
+// requested together with its system's scalars (they do not depend on
+// them), so the kernel's work after the wait is a single memory round trip
+// before the arithmetic.
 template <typename S>
 __global__ void __launch_bounds__(kThreads) k_update(SweepArgs a) {
-    wait_prior_grid();
     int32_t t0, t1;
     tile_range(a.n_vtiles, t0, t1);
+    Tile t = t0 < t1 ? a.vtiles[t0] : Tile{0, 0, 0, 0};
+    wait_prior_grid();
     int32_t cur = -1;
     bool active = false, first = false;
     double beta = 0.0, gamma = 0.0;
     for (int32_t ti = t0; ti < t1; ++ti) {
-        const Tile t = a.vtiles[ti];
+        if (ti > t0) t = a.vtiles[ti];
+        const int32_t base0 = t.begin + int32_t(threadIdx.x);
+        UpdRegs<S> g;
+        upd_load<S>(a, base0, t.end, g);
         if (t.sys != cur) {
             cur = t.sys;
             const int32_t upd = reinterpret_cast<const volatile int32_t *>(&a.st[cur].upd)[0];
@@ -970,10 +1002,18 @@ __global__ void __launch_bounds__(kThreads) k_update(SweepArgs a) {
         if (!active) continue;
         double acc[1];
         if constexpr (std::is_same<S, float>::value) {
-            const DF f[1] = {update_tile_f32(a, t, first, beta, gamma)};
+            DF f[1] = {{0.0f, 0.0f}};
+            for (int32_t base = base0; base < t.end; base += kThreads * kUpdU) {
+                if (base != base0) upd_load<S>(a, base, t.end, g);
+                upd_pass_f32(a, base, t.end, first, beta, gamma, g, f[0]);
+            }
             cta_sum_df<1>(f, acc);
         } else {
-            acc[0] = update_tile<S>(a, t, first, beta, gamma);
+            acc[0] = 0.0;
+            for (int32_t base = base0; base < t.end; base += kThreads * kUpdU) {
+                if (base != base0) upd_load<S>(a, base, t.end, g);
+                upd_pass<S>(a, base, t.end, first, beta, gamma, g, acc[0]);
+            }
             cta_sum<1>(acc);
         }
         if (threadIdx.x == 0) a.part_upd[ti] = acc[0];
@@ -1590,6 +1630,12 @@ int sweep_ctas_per_sm(int which, bool f32) {
         cudaGetLastError();
         return 1;
     }
+    // the sweeps over warp ranges run best at four CTAs per SM: more
+    // resident warps only add to the L1 requests the random gathers queue
+    // behind (C2, FP32 storage: 85.4 us per update at four against 88.4 at
+    // the six and eight their registers allow; FP64 column sweep: 40.5 us
+    // against 42.0 at six)
+    if (which == 3 || which == 4) n = std::min(n, kWarpSweepCtas);
     return n;
 }
 
