@@ -61,10 +61,11 @@ def test_golden_2x2(plss):
         np.testing.assert_allclose(x2k0, g["kz01_k0_x2"], rtol=1e-14)
 
 
-@pytest.mark.parametrize("K", [0, 1, 4, 16])
+@pytest.mark.parametrize("K", [0, 1, 4, 16, 17, 64])
 def test_parity_powerlaw_rows(plss, K):
     """Underdetermined power-law rows (some longer than the CTA), several
-    passes with restarts of the window."""
+    passes with restarts of the window, up to the one-CTA kernel's largest
+    window."""
     A, b, xs = synth.powerlaw_underdetermined(m=600, n=6000, mean_len=20, max_len=1500, seed=21)
     A = A.astype(np.float64)
     with plss.Context(A) as ctx:
@@ -100,16 +101,18 @@ def test_square_overdetermined_and_x0(plss):
     assert rel(x, ref["x"]) < 1e-9
 
 
-def test_batched_identity(plss):
-    """One CTA per system; system s uses the row stream seeded seed + s."""
+@pytest.mark.parametrize("K,nsys", [(6, 11), (24, 4)])
+def test_batched_identity(plss, K, nsys):
+    """One CTA per system (eleven systems with a window of 6, four with 24);
+    system s uses the row stream seeded seed + s."""
     systems = [synth.powerlaw_underdetermined(m=100 + 37 * s, n=900 + 100 * s, mean_len=8,
-                                              max_len=120, seed=40 + s) for s in range(4)]
+                                              max_len=120, seed=40 + s) for s in range(nsys)]
     As = [A.astype(np.float64) for A, _, _ in systems]
     bs = [b for _, b, _ in systems]
     with plss.Context(As) as ctx:
-        xs, rs = ctx.solve_batched(bs, sketch="identity", kacz_hist=6, seed=100, tol=0.0, maxit=500)
+        xs, rs = ctx.solve_batched(bs, sketch="identity", kacz_hist=K, seed=100, tol=0.0, maxit=500)
     for s, (A, b, x, r) in enumerate(zip(As, bs, xs, rs)):
-        ref, bar = oracle_with_bar(A, b, 500, 6, 100 + s)
+        ref, bar = oracle_with_bar(A, b, 500, K, 100 + s)
         assert r["iters"] == 500
         assert rel(x, ref["x"]) <= bar
 
@@ -146,15 +149,17 @@ def test_wide_window_full_history_reaches_pinv(plss):
     assert rel(x, np.linalg.pinv(D) @ b) < 1e-9
 
 
-def test_wide_window_fp32_storage(plss):
-    """FP32 storage of A with the whole-GPU window: the oracle on the same
-    float-rounded values (the window algebra is in double on both sides)."""
+@pytest.mark.parametrize("K", [8, 40, 96])
+def test_window_fp32_storage(plss, K):
+    """FP32 storage of A with the one-CTA window (K = 8, 40) and the
+    whole-GPU window (K = 96): the oracle on the same float-rounded values
+    (the window algebra is in double on both sides)."""
     A, b, xs = synth.powerlaw_underdetermined(m=500, n=5000, mean_len=16, max_len=800, seed=24)
     A32 = A.astype(np.float32)
     A64 = A32.astype(np.float64)
-    ref, bar = oracle_with_bar(A64, b, 900, 96, 2)
+    ref, bar = oracle_with_bar(A64, b, 900, K, 2)
     with plss.Context(A32, precision="fp32") as ctx:
-        x, r = ctx.solve(b, sketch="identity", kacz_hist=96, seed=2, tol=0.0, maxit=900)
+        x, r = ctx.solve(b, sketch="identity", kacz_hist=K, seed=2, tol=0.0, maxit=900)
     assert rel(x, ref["x"]) <= bar
 
 
