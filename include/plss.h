@@ -265,6 +265,46 @@ plss_status plss_solve(plss_ctx *ctx, const double *b, const double *x0, double 
 plss_status plss_solve_batched(plss_ctx *ctx, const double *const *b, const double *const *x0,
                                double *const *x_out, const plss_opts *o, plss_result *res);
 
+/*
+ * Checkpoint and resume of a residual-sketch solve (no counterpart in the
+ * paper, whose whole iteration state -- Algorithm 1's x, r, p and the
+ * scalars rho, theta and k -- is small enough to carry across a stop).
+ *
+ * A solve that the update cap (opts.maxit) stopped returns
+ * PLSS_NOT_CONVERGED and leaves its state in the context: b, x, r, p, u = W y
+ * and per system the scalars, the phase the recursion would have entered
+ * next, the refinement counters and the update count. plss_resume goes on
+ * from that state for every system the cap stopped, up to opts->maxit
+ * updates in total (the count includes the updates already taken) and to
+ * opts->tol; systems that converged or broke down are left as they are
+ * (their x is still written to x_out). The iterates are the ones the
+ * uninterrupted solve would have produced, bit for bit: every reduction
+ * runs in a fixed order. opts must be the interrupted solve's (w_mode,
+ * refine_period, inner_tol, refine_mode, stop_on_true) except maxit, tol,
+ * stream, io_device, hist and hist_cap (the history of a resume starts at
+ * row k of hist, k = the updates taken before); schedule may differ.
+ * x_out[nsys] (entries may be NULL) and res[nsys] as in plss_solve_batched.
+ * PLSS_ERR_INVALID when the context holds no such state (no residual-sketch
+ * solve since it was created or loaded, or another sketch or plss_solve_rhs
+ * ran since; they overwrite x and b).
+ *
+ * plss_state_save copies that state into a host buffer of
+ * plss_state_bytes(ctx) bytes (a header, the per-system scalars, then b, x,
+ * r, p, u in the context's storage type); plss_state_load copies it back
+ * into a context built from the same matrices with the same precision and
+ * layout of systems (checked: sizes, nonzero count, storage type; the
+ * values of A are the caller's to keep equal), after which plss_resume
+ * continues the saved solve. Both are synchronous (cudaMemcpy) and need no
+ * solve in flight on the context. plss_state_bytes returns -1 for a NULL
+ * context; save and load return PLSS_ERR_INVALID for a NULL argument or a
+ * buffer shorter than plss_state_bytes, load also for a buffer from
+ * another library version or another context shape.
+ */
+plss_status plss_resume(plss_ctx *ctx, double *const *x_out, const plss_opts *o, plss_result *res);
+int64_t plss_state_bytes(const plss_ctx *ctx);
+plss_status plss_state_save(plss_ctx *ctx, void *buf, int64_t bytes);
+plss_status plss_state_load(plss_ctx *ctx, const void *buf, int64_t bytes);
+
 /* Many right-hand sides on one matrix (SpMM form): B is m x nrhs, X0 and X
  * are n x nrhs, all row-major double (X0 may be NULL). Each column is an
  * independent PLSS solve with its own scalars; converged columns freeze.

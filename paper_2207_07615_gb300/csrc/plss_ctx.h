@@ -76,6 +76,7 @@ struct plss_ctx {
     int coop_grid = 0;
     int32_t *d_coop_rwr = nullptr, *d_coop_cwr = nullptr;
     double *d_coop_part = nullptr;
+    bool state_valid = false;        // the device holds a residual-sketch state (a solve ran, or a load)
     uint32_t *d_coop_bar = nullptr;
     bool small_fits = false;                      // every system fits the cluster schedule
     bool small_auto = false;                      // ... and AUTO picks it

@@ -94,7 +94,9 @@ struct SysState {
     int32_t status;     // plss_status once phase == PH_DONE
     int32_t stop_on_true;
     int32_t upd;        // update due in this body: 0 none, 1 p = beta p + gamma u, 2 p = gamma u (first)
-    uint32_t cnt_row, cnt_col, cnt_upd, pad1;
+    uint32_t cnt_row, cnt_col, cnt_upd;
+    int32_t resume;     // set when the update cap stopped the system: the transition it would
+                        // have taken (phase | 0x10 reset `since` | 0x20 clear restart_next | 0x100)
     int32_t replace;       // refinement mode: 0 a refresh restarts the recursion, 1 it replaces r
     int32_t restart_next;  // the next set-up row sweep begins a new recursion (solve start, breakdown)
 };

@@ -430,6 +430,7 @@ plss_status run_general(plss_ctx *c, const double *b, const double *x0, double *
     if (o->kacz_hist < 0 || o->kacz_hist > kGsMaxK)
         return fail(PLSS_ERR_INVALID, "the general sketch keeps a history of 0..%d directions (kacz_hist)", kGsMaxK);
     if (o->w_mode != PLSS_W_IDENTITY) return fail(PLSS_ERR_INVALID, "the general sketch takes W = I");
+    c->state_valid = false;   // x and b of the context are overwritten: nothing to resume
     cudaStream_t s = static_cast<cudaStream_t>(o->stream);
     const bool dev = o->io_device != 0;
     const int32_t K = int32_t(o->kacz_hist);

@@ -641,13 +641,16 @@ plss_status true_relres(plss_ctx *c, cudaStream_t s, std::vector<double> &rel) {
     return PLSS_OK;
 }
 
+// resume: go on from the state the context holds (b, x, r, p, u and the
+// per-system scalars of a solve the update cap stopped, or of
+// plss_state_load) instead of starting from b and x0.
 plss_status run_residual(plss_ctx *c, const double *const *b, const double *const *x0,
-                         double *const *xo, const plss_opts *o, plss_result *res) {
+                         double *const *xo, const plss_opts *o, plss_result *res, bool resume = false) {
     plss_status st = check_opts(o);
     if (st != PLSS_OK) return st;
     cudaStream_t s = static_cast<cudaStream_t>(o->stream);
     const bool dev = o->io_device != 0;
-    for (int32_t sy = 0; sy < c->nsys; ++sy) {
+    for (int32_t sy = 0; sy < c->nsys && !resume; ++sy) {
         const SysDesc &d = c->h_desc[size_t(sy)];
         if (d.m > 0 && !b[sy]) return fail(PLSS_ERR_INVALID, "b is NULL (system %d)", sy);
         st = put_vec(c->d_b + d.row_off, b[sy], d.m, dev, s);
@@ -666,9 +669,38 @@ plss_status run_residual(plss_ctx *c, const double *const *b, const double *cons
         if (st != PLSS_OK) return st;
         c->hist_cap_alloc = o->hist_cap;
     }
-    int64_t maxit_all = 0;
+    int64_t maxit_all = 0, hist_k0 = 0;
     CUDA_TRY(cudaStreamSynchronize(s));   // h_st may still be read by an earlier copy
-    for (int32_t sy = 0; sy < c->nsys; ++sy) {
+    if (resume) {
+        if (!c->state_valid) return fail(PLSS_ERR_INVALID, "no residual-sketch state to resume: solve or load one first");
+        CUDA_TRY(cudaMemcpy(c->h_st, c->d_st, sizeof(SysState) * size_t(c->nsys), cudaMemcpyDeviceToHost));
+        int32_t active = 0;
+        for (int32_t sy = 0; sy < c->nsys; ++sy) {
+            const SysDesc &d = c->h_desc[size_t(sy)];
+            SysState &z = c->h_st[sy];
+            z.hist = nullptr;
+            z.hist_cap = 0;
+            if (sy == 0 && o->hist_cap > 0) {
+                z.hist = c->d_hist;
+                z.hist_cap = o->hist_cap;
+            }
+            z.tol = o->tol;
+            z.maxit = o->maxit < 0 ? int64_t(d.n) : o->maxit;
+            if (z.phase == PH_DONE && z.status == PLSS_NOT_CONVERGED && (z.resume & 0x100) && z.iters < z.maxit) {
+                // the transition the stopping rule kept when the cap stopped it
+                z.phase = z.resume & 0xf;
+                if (z.resume & 0x10) z.since = 0;
+                if (z.resume & 0x20) z.restart_next = 0;
+                z.status = 0;
+                z.resume = 0;
+                ++active;
+            }
+            maxit_all = std::max(maxit_all, z.maxit);
+        }
+        *c->h_active = active;
+        hist_k0 = c->h_st[0].iters;
+    }
+    for (int32_t sy = 0; sy < c->nsys && !resume; ++sy) {
         const SysDesc &d = c->h_desc[size_t(sy)];
         SysState z;
         std::memset(&z, 0, sizeof z);
@@ -689,7 +721,8 @@ plss_status run_residual(plss_ctx *c, const double *const *b, const double *cons
         c->h_st[sy] = z;
         maxit_all = std::max(maxit_all, z.maxit);
     }
-    *c->h_active = c->nsys;
+    if (!resume) *c->h_active = c->nsys;
+    c->state_valid = true;
     CUDA_TRY(cudaMemcpyAsync(c->d_st, c->h_st, sizeof(SysState) * size_t(c->nsys), cudaMemcpyHostToDevice, s));
     CUDA_TRY(cudaMemcpyAsync(c->d_active, c->h_active, 4, cudaMemcpyHostToDevice, s));
     CUDA_TRY(cudaEventRecord(c->ev0, s));
@@ -700,9 +733,10 @@ plss_status run_residual(plss_ctx *c, const double *const *b, const double *cons
     const int64_t period = std::max<int64_t>(1, o->profile);   // profile one chunk in `period`
     int64_t bodies = 0, nchunk = 0;
     int chunk = 1;
-    const bool small = o->schedule == PLSS_SCHED_SMALL ? c->small_fits
-                                                        : (o->schedule == PLSS_SCHED_AUTO && c->small_auto);
-    const bool coop = !small && o->schedule == PLSS_SCHED_COOP && c->coop_grid > 0;
+    const bool idle = *c->h_active <= 0;   // a resume with nothing left to do
+    const bool small = !idle && (o->schedule == PLSS_SCHED_SMALL ? c->small_fits
+                                                                  : (o->schedule == PLSS_SCHED_AUTO && c->small_auto));
+    const bool coop = !idle && !small && o->schedule == PLSS_SCHED_COOP && c->coop_grid > 0;
     if (coop) {
         // one system on the whole GPU, whole bodies per cooperative launch
         SweepArgs a = c->args;
@@ -743,7 +777,7 @@ plss_status run_residual(plss_ctx *c, const double *const *b, const double *cons
             per = std::min(per * 4, 4096);
         }
     }
-    while (!small && !coop) {
+    while (!idle && !small && !coop) {
         const bool pchunk = prof && nchunk++ % period == 0;
         cudaGraphExec_t g;
         st = get_graph(c, chunk, w_on, pchunk, &g);
@@ -782,8 +816,11 @@ plss_status run_residual(plss_ctx *c, const double *const *b, const double *cons
     }
     CUDA_TRY(cudaStreamSynchronize(s));
     if (o->hist_cap > 0) {
+        // rows [k0, updates) of system 0: a resume leaves the rows before it untouched
         const int64_t k = std::min<int64_t>(o->hist_cap, c->h_st[0].iters);
-        if (k > 0) CUDA_TRY(cudaMemcpy(o->hist, c->d_hist, size_t(k) * 5 * 8, cudaMemcpyDeviceToHost));
+        if (k > hist_k0)
+            CUDA_TRY(cudaMemcpy(o->hist + 5 * hist_k0, c->d_hist + 5 * hist_k0, size_t(k - hist_k0) * 5 * 8,
+                                cudaMemcpyDeviceToHost));
     }
     float ms = 0.0f;
     cudaEventElapsedTime(&ms, c->ev0, c->ev1);
@@ -805,6 +842,100 @@ plss_status run_residual(plss_ctx *c, const double *const *b, const double *cons
         if (overall == PLSS_OK && z.status != PLSS_OK) overall = plss_status(z.status);
     }
     return overall;
+}
+
+// ---------------------------------------------------------------------------
+// Checkpoint / resume: the state of a residual-sketch solve is the vectors
+// b, x, r, p, u and one SysState per system. The buffer is a header, the
+// states (device pointers cleared), then the vectors in device layout.
+// ---------------------------------------------------------------------------
+
+struct StateHeader {
+    char magic[8];        // "PLSSST01"
+    int32_t f32, nsys;
+    int64_t m, n, nnz;
+    int64_t state_size;   // sizeof(SysState)
+};
+
+struct StateLayout {
+    int64_t states, b, x, r, p, u, total;   // byte offsets and the total size
+};
+
+StateLayout state_layout(const plss_ctx *c) {
+    const int64_t sb = c->f32 ? 4 : 8;
+    auto up8 = [](int64_t v) { return (v + 7) / 8 * 8; };
+    StateLayout L;
+    L.states = int64_t(sizeof(StateHeader));
+    L.b = up8(L.states + int64_t(sizeof(SysState)) * c->nsys);
+    L.x = up8(L.b + 8 * c->m);
+    L.r = up8(L.x + 8 * c->n);
+    L.p = up8(L.r + sb * c->m);
+    L.u = up8(L.p + sb * c->n);
+    L.total = up8(L.u + sb * c->n);
+    return L;
+}
+
+plss_status state_copy(plss_ctx *c, unsigned char *buf, int64_t bytes, bool save) {
+    const StateLayout L = state_layout(c);
+    // a load checks the header (when there is one) before the size, so that
+    // a state of another context is named as such
+    const int64_t need = save ? L.total : int64_t(sizeof(StateHeader));
+    if (bytes < need) return fail(PLSS_ERR_INVALID, "state buffer of %lld bytes, %lld needed", (long long)bytes,
+                                  (long long)L.total);
+    if (cudaSetDevice(c->device) != cudaSuccess) return fail(PLSS_ERR_CUDA, "cudaSetDevice");
+    const int64_t sb = c->f32 ? 4 : 8;
+    StateHeader h;
+    std::memset(&h, 0, sizeof h);
+    std::memcpy(h.magic, "PLSSST01", 8);
+    h.f32 = c->f32 ? 1 : 0;
+    h.nsys = c->nsys;
+    h.m = c->m;
+    h.n = c->n;
+    h.nnz = c->nnz;
+    h.state_size = int64_t(sizeof(SysState));
+    struct Part {
+        int64_t off;
+        void *dev;
+        int64_t len;
+    } parts[] = {{L.b, c->d_b, 8 * c->m}, {L.x, c->d_x, 8 * c->n}, {L.r, c->d_r, sb * c->m},
+                 {L.p, c->d_p, sb * c->n}, {L.u, c->d_u, sb * c->n}};
+    std::vector<SysState> z(static_cast<size_t>(c->nsys));
+    if (save) {
+        if (!c->state_valid) return fail(PLSS_ERR_INVALID, "no residual-sketch state to save: solve first");
+        CUDA_TRY(cudaDeviceSynchronize());
+        CUDA_TRY(cudaMemcpy(z.data(), c->d_st, sizeof(SysState) * z.size(), cudaMemcpyDeviceToHost));
+        for (SysState &q : z) {
+            q.hist = nullptr;
+            q.hist_cap = 0;
+        }
+        std::memcpy(buf, &h, sizeof h);
+        std::memcpy(buf + L.states, z.data(), sizeof(SysState) * z.size());
+        for (const Part &p : parts)
+            if (p.len > 0) CUDA_TRY(cudaMemcpy(buf + p.off, p.dev, size_t(p.len), cudaMemcpyDeviceToHost));
+        return PLSS_OK;
+    }
+    StateHeader g;
+    std::memcpy(&g, buf, sizeof g);
+    if (std::memcmp(g.magic, h.magic, 8) != 0 || g.state_size != h.state_size)
+        return fail(PLSS_ERR_INVALID, "not a state saved by this library version");
+    if (g.f32 != h.f32 || g.nsys != h.nsys || g.m != h.m || g.n != h.n || g.nnz != h.nnz)
+        return fail(PLSS_ERR_INVALID, "the state belongs to a context of other sizes or storage "
+                    "(saved: %d systems, %lld x %lld, %lld nonzeros, %s)", g.nsys, (long long)g.m, (long long)g.n,
+                    (long long)g.nnz, g.f32 ? "FP32" : "FP64");
+    if (bytes < L.total) return fail(PLSS_ERR_INVALID, "state buffer of %lld bytes, %lld needed", (long long)bytes,
+                                     (long long)L.total);
+    std::memcpy(z.data(), buf + L.states, sizeof(SysState) * z.size());
+    for (SysState &q : z) {
+        q.hist = nullptr;
+        q.hist_cap = 0;
+        q.cnt_row = q.cnt_col = q.cnt_upd = 0;
+    }
+    CUDA_TRY(cudaDeviceSynchronize());
+    CUDA_TRY(cudaMemcpy(c->d_st, z.data(), sizeof(SysState) * z.size(), cudaMemcpyHostToDevice));
+    for (const Part &p : parts)
+        if (p.len > 0) CUDA_TRY(cudaMemcpy(p.dev, buf + p.off, size_t(p.len), cudaMemcpyHostToDevice));
+    c->state_valid = true;
+    return PLSS_OK;
 }
 
 }  // namespace plss
@@ -896,6 +1027,37 @@ plss_status plss_solve(plss_ctx *ctx, const double *b, const double *x0, double 
     const double *xx[1] = {x0};
     double *oo[1] = {x_out};
     return run_residual(ctx, bb, xx, oo, o, res);
+}
+
+plss_status plss_resume(plss_ctx *ctx, double *const *x_out, const plss_opts *o, plss_result *res) {
+    clear_error();
+    if (!ctx) return fail(PLSS_ERR_INVALID, "ctx is NULL");
+    plss_opts od;
+    plss_opts_default(&od);
+    if (!o) o = &od;
+    if (o->sketch != PLSS_SKETCH_RESIDUAL) return fail(PLSS_ERR_INVALID, "only the residual sketch resumes");
+    return run_residual(ctx, nullptr, nullptr, x_out, o, res, true);
+}
+
+int64_t plss_state_bytes(const plss_ctx *ctx) {
+    clear_error();
+    if (!ctx) {
+        fail(PLSS_ERR_INVALID, "ctx is NULL");
+        return -1;
+    }
+    return state_layout(ctx).total;
+}
+
+plss_status plss_state_save(plss_ctx *ctx, void *buf, int64_t bytes) {
+    clear_error();
+    if (!ctx || !buf) return fail(PLSS_ERR_INVALID, "NULL argument");
+    return state_copy(ctx, static_cast<unsigned char *>(buf), bytes, true);
+}
+
+plss_status plss_state_load(plss_ctx *ctx, const void *buf, int64_t bytes) {
+    clear_error();
+    if (!ctx || !buf) return fail(PLSS_ERR_INVALID, "NULL argument");
+    return state_copy(ctx, const_cast<unsigned char *>(static_cast<const unsigned char *>(buf)), bytes, false);
 }
 
 plss_status plss_solve_batched(plss_ctx *ctx, const double *const *b, const double *const *x0,

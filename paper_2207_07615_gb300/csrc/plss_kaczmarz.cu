@@ -805,6 +805,7 @@ plss_status run_identity_multi(plss_ctx *c, const double *const *b, const double
                                double *const *xo, const plss_opts *o, plss_result *res) {
     plss_status st = check_opts(o);
     if (st != PLSS_OK) return st;
+    c->state_valid = false;   // x and b of the context are overwritten: nothing to resume
     if (o->kacz_hist < 0 || o->kacz_hist > kKwMaxK)
         return fail(PLSS_ERR_INVALID, "kacz_hist must be in [0, %d]", kKwMaxK);
     if (o->kacz_hist > kKzMaxK && c->nsys != 1)

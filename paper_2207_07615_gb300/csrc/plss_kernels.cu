@@ -534,20 +534,29 @@ __device__ void row_decide(const SweepArgs &a, SysState *st, bool init, double r
             st->since = 0;
             st->phase = PH_SETUP;   // confirm on b - A x before stopping
         }
-    } else if (st->iters >= st->maxit) {
-        finish_system(a, st, 1);
-    } else if (!init && st->inner_tol2 > 0.0 && (rho <= st->inner_tol2 * st->rho0 || rho > 4.0 * st->rho0)) {
-        // inner solve done, or the float recursion has drifted upwards:
-        // refine from b - A x
-        st->since = 0;
-        st->phase = PH_SETUP;
-    } else if (init) {
-        // after a refresh of r from b - A x: a new recursion, or (residual
-        // replacement) the same one going on with the fresh residual
-        st->phase = (st->replace && !st->restart_next) ? PH_RUN : PH_FIRST;
-        st->restart_next = 0;
     } else {
-        st->phase = PH_RUN;
+        // the transition the recursion takes next
+        int32_t next = PH_RUN, flags = 0;
+        if (!init && st->inner_tol2 > 0.0 && (rho <= st->inner_tol2 * st->rho0 || rho > 4.0 * st->rho0)) {
+            // inner solve done, or the float recursion has drifted upwards:
+            // refine from b - A x
+            next = PH_SETUP;
+            flags = 0x10;
+        } else if (init) {
+            // after a refresh of r from b - A x: a new recursion, or (residual
+            // replacement) the same one going on with the fresh residual
+            next = (st->replace && !st->restart_next) ? PH_RUN : PH_FIRST;
+            flags = 0x20;
+        }
+        if (st->iters >= st->maxit) {
+            // the update cap: stop, keeping the transition for a resume
+            st->resume = next | flags | 0x100;
+            finish_system(a, st, 1);
+        } else {
+            if (flags & 0x10) st->since = 0;
+            if (flags & 0x20) st->restart_next = 0;
+            st->phase = next;
+        }
     }
 }
 

@@ -833,6 +833,7 @@ plss_status run_rhs(plss_ctx *c, int32_t k, const double *B, const double *X0, d
     if (c->nsys != 1) return fail(PLSS_ERR_INVALID, "plss_solve_rhs needs a single-system context");
     if (k < 1 || k > kRhsMax) return fail(PLSS_ERR_INVALID, "nrhs must be in [1, %d]", kRhsMax);
     if (o->sketch != PLSS_SKETCH_RESIDUAL) return fail(PLSS_ERR_INVALID, "plss_solve_rhs runs the residual sketch");
+    c->state_valid = false;   // x and b of the context are overwritten: nothing to resume
     if (o->refine_mode != PLSS_REFINE_RESTART)
         return fail(PLSS_ERR_INVALID, "plss_solve_rhs refines by restarts only (refine_mode RESTART)");
     if ((c->m > 0 && !B) || (c->n > 0 && !X)) return fail(PLSS_ERR_INVALID, "NULL block");

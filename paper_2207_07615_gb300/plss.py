@@ -32,7 +32,8 @@ EXPORTS = ["plss_opts_default", "plss_create", "plss_create_batched", "plss_dest
            "plss_ctx_info", "plss_ctx_layout", "plss_solve", "plss_solve_batched", "plss_solve_rhs", "plss_spmv",
            "plss_kernel_times", "plss_residual_noalloc", "plss_last_error", "plss_server_opts_default",
            "plss_server_create", "plss_submit", "plss_poll", "plss_server_stats", "plss_server_destroy",
-           "plss_tune", "plss_gather_bound"]
+           "plss_tune", "plss_gather_bound", "plss_resume", "plss_state_bytes", "plss_state_save",
+           "plss_state_load"]
 
 
 class Csr(C.Structure):
@@ -114,12 +115,17 @@ def lib() -> C.CDLL:
             L.plss_server_destroy.restype = None
             L.plss_tune.argtypes = [vp, i32, vp, i32, vp, vp, i32, vp]
             L.plss_gather_bound.argtypes = [vp, i32, i32, vp, vp]
+            L.plss_resume.argtypes = [vp, vp, vp, vp]
+            L.plss_state_bytes.argtypes = [vp]
+            L.plss_state_bytes.restype = i64
+            L.plss_state_save.argtypes = [vp, vp, i64]
+            L.plss_state_load.argtypes = [vp, vp, i64]
             for name in ("plss_create", "plss_create_batched", "plss_ctx_info", "plss_ctx_layout",
                          "plss_solve",
                          "plss_kernel_times",
                          "plss_solve_batched", "plss_solve_rhs", "plss_spmv",
                          "plss_server_create", "plss_submit", "plss_poll", "plss_server_stats", "plss_tune",
-                         "plss_gather_bound"):
+                         "plss_gather_bound", "plss_resume", "plss_state_save", "plss_state_load"):
                 getattr(L, name).restype = C.c_int32
             _lib = L
     return _lib
@@ -329,6 +335,46 @@ class Context:
         o = make_opts(io_device=int(dev), stream=_stream_of(bl[0]), **kw)
         _check(lib().plss_solve_batched(self._h, bp, xp, op, C.byref(o), res))
         return outs, [r.as_dict() for r in res]
+
+    def resume(self, *, hist=0, device=False, **kw):
+        """Goes on with the residual-sketch solve the update cap stopped (or a
+        loaded state) up to maxit updates in total; returns (xs, results),
+        one entry per system, or (xs, results, hist) with hist=k (system 0's
+        rows from the update count it resumed at)."""
+        outs = []
+        for (m, n) in self.shapes:
+            if device:
+                import torch
+                outs.append(torch.empty(n, dtype=torch.float64, device="cuda"))
+            else:
+                outs.append(np.empty(n))
+        P = C.c_void_p * self.nsys
+        op = P(*[_ptr(x) for x in outs])
+        H = np.zeros((int(hist), 5)) if hist else None
+        o = make_opts(io_device=int(device), stream=_stream_of(outs[0]) if device else None, **kw)
+        if H is not None:
+            o.hist = H.ctypes.data_as(C.c_void_p).value
+            o.hist_cap = int(hist)
+        res = (Result * self.nsys)()
+        _check(lib().plss_resume(self._h, op, C.byref(o), res))
+        rs = [r.as_dict() for r in res]
+        if H is not None:
+            return outs, rs, H
+        return outs, rs
+
+    def state_save(self):
+        """The context's residual-sketch state as bytes (plss_state_save)."""
+        nb = int(lib().plss_state_bytes(self._h))
+        if nb < 0:
+            raise PlssError(ERR_INVALID, lib().plss_last_error().decode())
+        buf = (C.c_ubyte * nb)()
+        _check(lib().plss_state_save(self._h, buf, nb), (OK,))
+        return bytes(buf)
+
+    def state_load(self, data):
+        """Loads a state saved from a context of the same shape (plss_state_load)."""
+        buf = (C.c_ubyte * len(data)).from_buffer_copy(data)
+        _check(lib().plss_state_load(self._h, buf, len(data)), (OK,))
 
     def solve_rhs(self, B, X0=None, **kw):
         """Many right-hand sides: B (m x k), X0 (n x k) row-major; returns (X, results)."""

@@ -205,6 +205,12 @@ def test_context_calls_refuse_a_null_context(L):
     assert L.plss_ctx_info(None, None, None, None, None) == plss.ERR_INVALID
     assert L.plss_ctx_layout(None, None) == plss.ERR_INVALID
     assert L.plss_gather_bound(None, 0, 1, None, None) == plss.ERR_INVALID
+    assert L.plss_resume(None, None, None, None) == plss.ERR_INVALID
+    assert L.plss_state_bytes(None) == -1
+    assert "NULL" in L.plss_last_error().decode()
+    buf = (C.c_ubyte * 64)()
+    assert L.plss_state_save(None, buf, 64) == plss.ERR_INVALID
+    assert L.plss_state_load(None, buf, 64) == plss.ERR_INVALID
     L.plss_destroy(None)                                          # a no-op
 
 

@@ -38,11 +38,11 @@ def test_counters_follow_the_sweep_code(tmp_path, monkeypatch):
     src = open(KERNELS, encoding="utf-8").read()
     traffic = open(os.path.join(ROOT, "profiles", "ncu_traffic.txt")).read()
     monkeypatch.setattr(bench, "ROOT", _tree(tmp_path / "a", src, traffic))
-    assert bench.ncu_traffic("col_sweep") == 113669632.0     # the committed record matches the source
+    assert bench.ncu_traffic("col_sweep") == 113637120.0     # the committed record matches the source
     # a comment edit keeps the counters
     monkeypatch.setattr(bench, "ROOT", _tree(tmp_path / "b", "// note\n" + src.replace(
         "namespace plss {", "namespace plss {  // edited comment", 1), traffic))
-    assert bench.ncu_traffic("col_sweep") == 113669632.0
+    assert bench.ncu_traffic("col_sweep") == 113637120.0
     # a code change in the grid sweeps voids them
     body = src.replace("constexpr int kBatch = 8;", "constexpr int kBatch = 4;", 1)
     assert body != src
@@ -52,7 +52,7 @@ def test_counters_follow_the_sweep_code(tmp_path, monkeypatch):
     cl = src.replace("constexpr int kClusterThreads = 512;", "constexpr int kClusterThreads = 256;", 1)
     assert cl != src
     monkeypatch.setattr(bench, "ROOT", _tree(tmp_path / "d", cl, traffic))
-    assert bench.ncu_traffic("col_sweep") == 113669632.0
+    assert bench.ncu_traffic("col_sweep") == 113637120.0
     # no record: None
     shutil.rmtree(os.path.join(str(tmp_path / "d"), "profiles"))
     assert bench.ncu_traffic("col_sweep") is None
