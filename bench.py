@@ -35,11 +35,12 @@ from paper_2207_07615_gb300 import synth  # noqa: E402
 WORKLOAD = "plss_overdetermined_1e6x2e5_nnz8_colscale1e-2..1e2"
 METRIC = "time to ||r||/||b||<=1e-8"
 # Updates the FP64 W = I solve of this workload takes to the tolerance: the
-# GPU arm's own count in its round-end run on GB300 (181,415; rounding moves
-# it by well under 0.1 % between runs). The reference arm runs without the
-# GPU arm's result, so it scales its sampled per-update time by this count;
-# the GPU arm's own cpu_baseline scales by the count its solve just took.
-REF_UPDATES_TO_TOL = 181415
+# GPU arm's own count on GB300 (181,143 with the current kernels, the same in
+# every run: its reductions have a fixed order). The reference arm runs
+# without the GPU arm's result, so it scales its sampled per-update time by
+# this count; the GPU arm's own cpu_baseline scales by the count its solve
+# just took.
+REF_UPDATES_TO_TOL = 181143
 L2_FLUSH_BYTES = 512 << 20
 PROFILE_PERIOD = 16
 
@@ -305,6 +306,17 @@ def cpu_baseline(A, b, args, updates_to_tol, all_cores=True):
 
 # ------------------------------------------------------------ reference arm
 
+def run_config(args, m, n, nnz, ws):
+    """The workload's config, the same dict in both arms."""
+    sv = 8 if args.prec == "fp64" else 4
+    work = (sweep_bytes("row_sweep", m, n, nnz, sv) + sweep_bytes("col_sweep", m, n, nnz, sv)) / 1e6
+    return {"workload": WORKLOAD, "m": m, "n": n, "nnz": int(nnz), "tol": args.tol,
+            "w_mode": args.w_mode, "precision": args.prec,
+            "parallelism": "replicas" if ws > 1 else "single",
+            "l2": f"inputs larger than L2 (per-update working set {work:.0f} MB) and a 512 MB write "
+                  "between GPU steps"}
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -328,9 +340,7 @@ def run_reference(args):
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if args.prec == "fp64" else "f32+f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": WORKLOAD, "m": args.m, "n": args.n, "nnz": int(A.nnz),
-                       "tol": args.tol, "w_mode": args.w_mode, "precision": args.prec,
-                       "parallelism": "single", "l2": "n/a (CPU)"},
+            "config": run_config(args, args.m, args.n, int(A.nnz), ws),
             "cpu_baseline": {"value": v, "unit": "s", "cores": 1, "kind": "oracle",
                              "sample": cb["sample"]},
             "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -493,12 +503,7 @@ def run_plss(args):
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
                 "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f64" if args.prec == "fp64" else "f32+f64", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "m": m, "n": n, "nnz": int(nnz), "tol": args.tol,
-                           "w_mode": args.w_mode, "precision": args.prec,
-                           "parallelism": "replicas" if ws > 1 else "single",
-                           "l2": "inputs larger than L2 (per-update working set "
-                                 f"{(sweep_bytes('row_sweep', m, n, nnz, sv) + sweep_bytes('col_sweep', m, n, nnz, sv)) / 1e6:.0f} MB)"
-                                 " and a 512 MB write between steps"},
+                "config": run_config(args, m, n, int(nnz), ws),
                 "solve": {"updates": last["iters"], "status": last["status"],
                           "relres_true": last["relres_true"], "relres_rec": last["relres_rec"],
                           "ms_per_update": ms_step / max(1, last["iters"]),
