@@ -70,7 +70,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if errors:
         raise RuntimeError("nvcc failed:\n" + "\n".join(errors))
     tmp = LIB + f".tmp{os.getpid()}"
-    subprocess.check_call([cc, *ARCH, "-shared", "-o", tmp, *objs, "-lpthread"])
+    subprocess.check_call([cc, *ARCH, "-shared", "-o", tmp, *objs, "-lpthread", "-ldl"])
     os.replace(tmp, LIB)
     return LIB
 

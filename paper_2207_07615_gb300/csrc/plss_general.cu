@@ -39,6 +39,7 @@
 #include "plss_ctx.h"
 #include "plss_dev.cuh"
 #include "plss_launch.h"
+#include "plss_trace.h"
 
 namespace plss {
 
@@ -425,6 +426,7 @@ static plss_status general_prepare(plss_ctx *c, int32_t K) {
 
 plss_status run_general(plss_ctx *c, const double *b, const double *x0, double *x_out, const plss_opts *o,
                         plss_result *res) {
+    TraceRange tr("plss: solve (general sketch)");
     plss_status st = check_opts(o);
     if (st != PLSS_OK) return st;
     if (o->kacz_hist < 0 || o->kacz_hist > kGsMaxK)

@@ -15,6 +15,7 @@
 #include "plss_ctx.h"
 #include "plss_dev.cuh"
 #include "plss_launch.h"
+#include "plss_trace.h"
 
 namespace plss {
 
@@ -230,6 +231,7 @@ static void ctx_free(plss_ctx *c) {
 }
 
 static plss_status ctx_build(const plss_csr *As, int32_t nsys, const plss_opts *o, plss_ctx **out) {
+    TraceRange tr("plss: create context");
     *out = nullptr;
     if (nsys <= 0) return fail(PLSS_ERR_INVALID, "nsys must be positive");
     if (!As) return fail(PLSS_ERR_INVALID, "A is NULL");
@@ -646,6 +648,7 @@ plss_status true_relres(plss_ctx *c, cudaStream_t s, std::vector<double> &rel) {
 // plss_state_load) instead of starting from b and x0.
 plss_status run_residual(plss_ctx *c, const double *const *b, const double *const *x0,
                          double *const *xo, const plss_opts *o, plss_result *res, bool resume = false) {
+    TraceRange tr(resume ? "plss: resume (residual sketch)" : "plss: solve (residual sketch)");
     plss_status st = check_opts(o);
     if (st != PLSS_OK) return st;
     cudaStream_t s = static_cast<cudaStream_t>(o->stream);

@@ -33,6 +33,7 @@
 #include "plss_ctx.h"
 #include "plss_dev.cuh"
 #include "plss_launch.h"
+#include "plss_trace.h"
 
 namespace plss {
 
@@ -803,6 +804,7 @@ static plss_status launch_wide(plss_ctx *c, KaczState *kz, cudaStream_t s) {
 
 plss_status run_identity_multi(plss_ctx *c, const double *const *b, const double *const *x0,
                                double *const *xo, const plss_opts *o, plss_result *res) {
+    TraceRange tr("plss: solve (identity sketch)");
     plss_status st = check_opts(o);
     if (st != PLSS_OK) return st;
     c->state_valid = false;   // x and b of the context are overwritten: nothing to resume

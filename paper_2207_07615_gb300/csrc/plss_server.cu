@@ -33,6 +33,7 @@
 #include "plss_ctx.h"
 #include "plss_dev.cuh"
 #include "plss_launch.h"
+#include "plss_trace.h"
 
 namespace plss {
 
@@ -457,6 +458,7 @@ static void srv_worker(plss_server *s) {
                 continue;
             }
         }
+        TraceRange tr("plss server: scheduling round");
         bool ok = true;
         for (SrvRequest *r : admitted) ok = ok && srv_upload(s, r);
         if (ok && (dirty || !admitted.empty())) ok = srv_rebuild(s);

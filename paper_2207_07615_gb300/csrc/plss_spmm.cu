@@ -22,6 +22,7 @@
 #include "plss_dev.cuh"
 #include "plss_devfn.cuh"
 #include "plss_launch.h"
+#include "plss_trace.h"
 
 namespace plss {
 
@@ -828,6 +829,7 @@ static plss_status rhs_put(double *dst, const double *src, int64_t rows, int32_t
 
 plss_status run_rhs(plss_ctx *c, int32_t k, const double *B, const double *X0, double *X,
                     const plss_opts *o, plss_result *res) {
+    TraceRange tr("plss: solve (many right-hand sides)");
     plss_status st = check_opts(o);
     if (st != PLSS_OK) return st;
     if (c->nsys != 1) return fail(PLSS_ERR_INVALID, "plss_solve_rhs needs a single-system context");

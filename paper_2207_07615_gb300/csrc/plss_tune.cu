@@ -8,6 +8,7 @@
 
 #include "plss_ctx.h"
 #include "plss_launch.h"
+#include "plss_trace.h"
 
 using namespace plss;
 
@@ -106,6 +107,7 @@ extern "C" plss_status plss_tune(const plss_csr *As, int32_t nsys, const plss_op
     plss_opts_default(&base);
     if (o) base = *o;
 
+    TraceRange tr("plss: tune");
     std::vector<plss_tune_entry> table;
     for (int32_t layout : {PLSS_LAYOUT_AUTO, PLSS_LAYOUT_CSR}) {
         for (int32_t shift : {-1, 0, 1}) {

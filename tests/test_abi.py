@@ -226,3 +226,12 @@ def test_noalloc_residual_checks_sizes_first(L):
     assert f(1, 1, 0, None, None, None, None, None, None, n2, None) == plss.ERR_INVALID
     assert f(1, 1, 0, rp.ctypes.data, None, None, None, None, None, None, None) == plss.ERR_INVALID
     assert f(1, 1, 1, rp.ctypes.data, None, None, None, None, None, n2, None) == plss.ERR_INVALID
+
+
+def test_trace_ranges_are_compiled_in(L):
+    """The host phases carry NVTX range names for timeline profilers."""
+    so = open(pbuild.build(), "rb").read()
+    for name in (b"plss: create context", b"plss: solve (residual sketch)", b"plss: resume (residual sketch)",
+                 b"plss: solve (identity sketch)", b"plss: solve (general sketch)",
+                 b"plss: solve (many right-hand sides)", b"plss server: scheduling round", b"plss: tune"):
+        assert name in so, name
