@@ -33,11 +33,13 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <vector>
 
 #include "plss.h"
 #include "plss_ctx.h"
 #include "plss_dev.cuh"
+#include "plss_devfn.cuh"
 #include "plss_launch.h"
 #include "plss_trace.h"
 
@@ -102,6 +104,12 @@ struct GeneralState {
     double *d_part = nullptr;
     GsState *d_st = nullptr;
     GsState *h_st = nullptr;   // pinned
+    // the body of kGsBody sketch columns captured as a CUDA graph for the
+    // arguments it was captured with
+    cudaGraphExec_t body = nullptr;
+    GsArgs body_args{};
+    int body_gr = 0, body_gc = 0;
+    bool body_f32 = false;
 };
 
 // Sign of sketch entry (k, i): bit 63 of SplitMix64 output k*m + i.
@@ -183,6 +191,7 @@ __device__ __forceinline__ void gs_segments(const int32_t *__restrict__ ptr, con
 template <int G, typename S>
 __global__ void __launch_bounds__(kGsThreads) g_rows(GsArgs a) {
     __shared__ double sh[kGsWarps];
+    wait_prior_grid();
     GsState *st = a.st;
     if (st->done) return;
     if (blockIdx.x == 0 && st->store) {
@@ -226,6 +235,7 @@ __global__ void __launch_bounds__(kGsThreads) g_rows(GsArgs a) {
 template <int G, typename S>
 __global__ void __launch_bounds__(kGsThreads) g_cols(GsArgs a) {
     __shared__ double sh[kGsWarps];
+    wait_prior_grid();
     const GsState *st = a.st;
     if (st->done) return;
     int64_t lo, hi;
@@ -252,35 +262,40 @@ static int gs_lanes(int64_t nnz, int64_t segs) {
     return g;
 }
 
+// The per-column kernels are launched with programmatic dependent launch
+// (launch_pdl): each waits for its predecessor in wait_prior_grid() before
+// reading anything, and the launch of the next overlaps the end of the last.
 template <typename S>
-static void launch_rows(int G, int grid, cudaStream_t s, const GsArgs &a) {
+static cudaError_t launch_rows(int G, int grid, cudaStream_t s, const GsArgs &a) {
     switch (G) {
-        case 1: g_rows<1, S><<<grid, kGsThreads, 0, s>>>(a); break;
-        case 2: g_rows<2, S><<<grid, kGsThreads, 0, s>>>(a); break;
-        case 4: g_rows<4, S><<<grid, kGsThreads, 0, s>>>(a); break;
-        case 8: g_rows<8, S><<<grid, kGsThreads, 0, s>>>(a); break;
-        case 16: g_rows<16, S><<<grid, kGsThreads, 0, s>>>(a); break;
-        default: g_rows<32, S><<<grid, kGsThreads, 0, s>>>(a); break;
+        case 1: return launch_pdl(g_rows<1, S>, grid, s, a);
+        case 2: return launch_pdl(g_rows<2, S>, grid, s, a);
+        case 4: return launch_pdl(g_rows<4, S>, grid, s, a);
+        case 8: return launch_pdl(g_rows<8, S>, grid, s, a);
+        case 16: return launch_pdl(g_rows<16, S>, grid, s, a);
+        default: return launch_pdl(g_rows<32, S>, grid, s, a);
     }
 }
 
 template <typename S>
-static void launch_cols(int G, int grid, cudaStream_t s, const GsArgs &a) {
+static cudaError_t launch_cols(int G, int grid, cudaStream_t s, const GsArgs &a) {
     switch (G) {
-        case 1: g_cols<1, S><<<grid, kGsThreads, 0, s>>>(a); break;
-        case 2: g_cols<2, S><<<grid, kGsThreads, 0, s>>>(a); break;
-        case 4: g_cols<4, S><<<grid, kGsThreads, 0, s>>>(a); break;
-        case 8: g_cols<8, S><<<grid, kGsThreads, 0, s>>>(a); break;
-        case 16: g_cols<16, S><<<grid, kGsThreads, 0, s>>>(a); break;
-        default: g_cols<32, S><<<grid, kGsThreads, 0, s>>>(a); break;
+        case 1: return launch_pdl(g_cols<1, S>, grid, s, a);
+        case 2: return launch_pdl(g_cols<2, S>, grid, s, a);
+        case 4: return launch_pdl(g_cols<4, S>, grid, s, a);
+        case 8: return launch_pdl(g_cols<8, S>, grid, s, a);
+        case 16: return launch_pdl(g_cols<16, S>, grid, s, a);
+        default: return launch_pdl(g_cols<32, S>, grid, s, a);
     }
 }
+
 
 // c_j = q_j^T y as partial dot products over column chunks: item (j, ch)
 // sums chunk ch of direction j (coalesced over the chunk) into
 // part_c[j * nch + ch]; the CTAs take items in turn.
 __global__ void __launch_bounds__(kGsThreads) g_qty(GsArgs a) {
     __shared__ double sh[kGsWarps];
+    wait_prior_grid();
     const GsState *st = a.st;
     if (st->done) return;
     const int64_t items = int64_t(st->nh) * a.nch;
@@ -299,6 +314,7 @@ __global__ void __launch_bounds__(kGsThreads) g_qty(GsArgs a) {
 __global__ void __launch_bounds__(kGsThreads) g_decide(GsArgs a) {
     __shared__ double sh[kGsWarps];
     __shared__ int sh_go;
+    wait_prior_grid();
     GsState *st = a.st;
     if (st->done) return;
     double rr = 0.0, sr = 0.0, yy = 0.0;
@@ -349,6 +365,7 @@ __global__ void __launch_bounds__(kGsThreads) g_decide(GsArgs a) {
 __global__ void __launch_bounds__(kGsThreads) g_update(GsArgs a) {
     __shared__ double sh[kGsWarps];
     __shared__ double sd[kGsMaxK];
+    wait_prior_grid();
     GsState *st = a.st;
     if (st->done || st->skip) return;
     const int nh = st->nh;
@@ -370,10 +387,34 @@ __global__ void __launch_bounds__(kGsThreads) g_update(GsArgs a) {
     if (blockIdx.x == 0 && threadIdx.x == 0) st->store = a.K > 0 ? 1 : 0;
 }
 
-__global__ void g_norm2(const double *v, int64_t len, double *out) {
+constexpr int64_t kGsBody = 16;   // sketch columns between reads of the stop flag
+
+// One column: the five kernels in order.
+static cudaError_t launch_column(bool f32, int gr, int gc, int grid, cudaStream_t s, const GsArgs &a) {
+    cudaError_t e = f32 ? launch_rows<float>(gr, grid, s, a) : launch_rows<double>(gr, grid, s, a);
+    if (e == cudaSuccess) e = f32 ? launch_cols<float>(gc, grid, s, a) : launch_cols<double>(gc, grid, s, a);
+    if (e == cudaSuccess) e = launch_pdl(g_qty, grid, s, a);
+    if (e == cudaSuccess) e = launch_pdl(g_decide, 1, s, a);
+    if (e == cudaSuccess) e = launch_pdl(g_update, grid, s, a);
+    return e;
+}
+
+// ||v||^2 in two launches: one partial per CTA over its contiguous share,
+// then one CTA sums the partials in CTA order.
+__global__ void __launch_bounds__(kGsThreads) g_norm2_part(const double *v, int64_t len, double *part) {
+    __shared__ double sh[kGsWarps];
+    int64_t lo, hi;
+    gs_range(len, lo, hi);
+    double acc = 0.0;
+    for (int64_t i = lo + threadIdx.x; i < hi; i += kGsThreads) acc = fma(v[i], v[i], acc);
+    acc = gs_sum(acc, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = acc;
+}
+
+__global__ void __launch_bounds__(kGsThreads) g_norm2_sum(const double *part, int32_t np, double *out) {
     __shared__ double sh[kGsWarps];
     double acc = 0.0;
-    for (int64_t i = threadIdx.x; i < len; i += kGsThreads) acc = fma(v[i], v[i], acc);
+    for (int32_t g = threadIdx.x; g < np; g += kGsThreads) acc += part[g];
     acc = gs_sum(acc, sh);
     if (threadIdx.x == 0) *out = acc;
 }
@@ -388,6 +429,7 @@ static void general_free(GeneralState *g) {
     dfree(g->d_part);
     dfree(g->d_st);
     if (g->h_st) cudaFreeHost(g->h_st);
+    if (g->body) cudaGraphExecDestroy(g->body);
     delete g;
 }
 
@@ -443,6 +485,7 @@ plss_status run_general(plss_ctx *c, const double *b, const double *x0, double *
     if ((st = put_vec(c->d_x, x0, c->n, dev, s)) != PLSS_OK) return st;
 
     GsArgs a;
+    std::memset(&a, 0, sizeof a);   // padding too: the body graph is keyed by these bytes
     a.row_ptr = c->d_row_ptr;
     a.col_idx = c->d_col_idx;
     a.val = c->d_val;
@@ -473,25 +516,43 @@ plss_status run_general(plss_ctx *c, const double *b, const double *x0, double *
     z.maxit = o->maxit < 0 ? c->n : o->maxit;
     *g->h_st = z;
     GS_TRY(cudaMemcpyAsync(g->d_st, g->h_st, sizeof(GsState), cudaMemcpyHostToDevice, s));
-    g_norm2<<<1, kGsThreads, 0, s>>>(c->d_b, c->m, &g->d_st->nb2);
+    g_norm2_part<<<g->grid, kGsThreads, 0, s>>>(c->d_b, c->m, g->d_part);
+    g_norm2_sum<<<1, kGsThreads, 0, s>>>(g->d_part, g->grid, &g->d_st->nb2);
     GS_TRY(cudaEventRecord(c->ev0, s));
     const int grid = g->grid;
     const int gr = gs_lanes(c->nnz, c->m), gc = gs_lanes(c->nnz, c->n);
-    const int64_t body = 16;   // steps between reads of the stop flag
-    for (int64_t it = 0;; it += body) {
-        for (int64_t q = 0; q < body; ++q) {
-            if (c->f32) {
-                launch_rows<float>(gr, grid, s, a);
-                launch_cols<float>(gc, grid, s, a);
-            } else {
-                launch_rows<double>(gr, grid, s, a);
-                launch_cols<double>(gc, grid, s, a);
-            }
-            g_qty<<<grid, kGsThreads, 0, s>>>(a);
-            g_decide<<<1, kGsThreads, 0, s>>>(a);
-            g_update<<<grid, kGsThreads, 0, s>>>(a);
+    const int64_t body = kGsBody;
+    // the body of kGsBody columns as a CUDA graph, captured again only when
+    // its arguments change (a new seed, tolerance-independent otherwise)
+    if (!g->body || std::memcmp(&g->body_args, &a, sizeof a) != 0 || g->body_gr != gr || g->body_gc != gc ||
+        g->body_f32 != c->f32) {
+        if (g->body) cudaGraphExecDestroy(g->body);
+        g->body = nullptr;
+        cudaGraph_t graph = nullptr;
+        GS_TRY(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = cudaSuccess;
+        for (int64_t q = 0; q < body && e == cudaSuccess; ++q) e = launch_column(c->f32, gr, gc, grid, c->cap_stream, a);
+        const cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &graph);
+        if (e != cudaSuccess || e2 != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            cudaGetLastError();
+            return fail(PLSS_ERR_CUDA, "general sketch: graph capture failed: %s",
+                        cudaGetErrorString(e != cudaSuccess ? e : e2));
         }
-        GS_TRY(cudaGetLastError());
+        const cudaError_t e3 = cudaGraphInstantiate(&g->body, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e3 != cudaSuccess) {
+            g->body = nullptr;
+            cudaGetLastError();
+            return fail(PLSS_ERR_CUDA, "general sketch: graph instantiate failed: %s", cudaGetErrorString(e3));
+        }
+        g->body_args = a;
+        g->body_gr = gr;
+        g->body_gc = gc;
+        g->body_f32 = c->f32;
+    }
+    for (int64_t it = 0;; it += body) {
+        GS_TRY(cudaGraphLaunch(g->body, s));
         GS_TRY(cudaMemcpyAsync(g->h_st, g->d_st, sizeof(GsState), cudaMemcpyDeviceToHost, s));
         GS_TRY(cudaStreamSynchronize(s));
         if (g->h_st->done) break;
