@@ -677,6 +677,9 @@ plss_status run_residual(plss_ctx *c, const double *const *b, const double *cons
     if (resume) {
         if (!c->state_valid) return fail(PLSS_ERR_INVALID, "no residual-sketch state to resume: solve or load one first");
         CUDA_TRY(cudaMemcpy(c->h_st, c->d_st, sizeof(SysState) * size_t(c->nsys), cudaMemcpyDeviceToHost));
+        for (int32_t sy = 0; sy < c->nsys; ++sy)
+            if (c->h_st[sy].phase != PH_DONE)
+                return fail(PLSS_ERR_INVALID, "the state to resume is not that of a finished solve (system %d)", sy);
         int32_t active = 0;
         for (int32_t sy = 0; sy < c->nsys; ++sy) {
             const SysDesc &d = c->h_desc[size_t(sy)];
