@@ -228,6 +228,26 @@ def test_edge_cases(plss):
     assert rel(x, ref["x"]) < RTOL
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("schedule", ["grid", "small"])
+def test_nonfinite_right_hand_side_ends_in_breakdown(plss, precision, schedule):
+    """A NaN or an infinity in b (the library does not scan b) makes the
+    first scalar step non-finite: the solve ends with PLSS_ERR_BREAKDOWN
+    within a few bodies instead of running to the cap, in either storage
+    and on either schedule, and the context solves the next system."""
+    A, b, xs = synth.square_diag_dominant(n=300, per_row=4, seed=2)
+    Ap = A.astype(np.float32) if precision == "fp32" else A
+    with plss.Context(Ap, precision=precision) as ctx:
+        for bad in (np.nan, np.inf):
+            bb = b.copy()
+            bb[17] = bad
+            x, r = ctx.solve(bb, tol=1e-10, maxit=5000, schedule=schedule)
+            assert r["status"] == "breakdown", r
+            assert r["iters"] <= 1, r
+        x, r = ctx.solve(b, tol=1e-8, maxit=5000, schedule=schedule)
+        assert r["status"] == "converged" and r["relres_true"] <= 1e-8, r
+
+
 @pytest.mark.parametrize("layout,schedule", SCHEDULES)
 def test_ragged_tails(plss, layout, schedule):
     """Row counts just off the tile, slice and group boundaries."""
