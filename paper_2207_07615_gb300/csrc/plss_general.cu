@@ -95,6 +95,8 @@ struct GsArgs {
     int64_t m, n;
     uint64_t seed;
     int32_t K, grid, nch;
+    Sliced csl;   // the context's sliced columns with their warp ranges, or wr = null
+    int32_t csl_grid, pad;   // the grid those warp ranges were cut for (<= grid)
 };
 
 struct GeneralState {
@@ -254,6 +256,58 @@ __global__ void __launch_bounds__(kGsThreads) g_cols(GsArgs a) {
     if (threadIdx.x == 0) a.part_y[blockIdx.x] = yy;
 }
 
+// y = A^T s_k over the context's sliced columns (a single system whose
+// columns are sliced throughout, warp ranges cut for this grid): the
+// residual sketch's column-sweep walk -- 32 consecutive indices and values
+// per warp load, 8 steps in flight -- with the sketch sign of each entry's
+// row computed from its index in place of a gathered r.
+template <typename S>
+__global__ void __launch_bounds__(kGsThreads) g_cols_sliced(GsArgs a) {
+    __shared__ double sh[kGsWarps];
+    wait_prior_grid();
+    const GsState *st = a.st;
+    if (st->done) return;
+    const int64_t k = st->k;
+    const uint64_t seed = a.seed;
+    const int64_t m = a.m;
+    const int lane = threadIdx.x & 31;
+    const int g = a.csl.g;
+    const int32_t w = int32_t(threadIdx.x >> 5) * int32_t(gridDim.x) + int32_t(blockIdx.x);
+    const int32_t s0 = __ldg(a.csl.wr + w), s1 = __ldg(a.csl.wr + w + 1);
+    const int32_t *__restrict__ idx = a.csl.idx;
+    const S *__restrict__ val = static_cast<const S *>(a.csl.val);
+    double yy = 0.0;
+    for (int32_t sl = s0; sl < s1; ++sl) {
+        const int32_t off = __ldg(a.csl.ptr + sl);
+        const int32_t width = (__ldg(a.csl.ptr + sl + 1) - off) >> 5;
+        const int32_t col = __ldg(a.csl.seg + 32 * sl + lane);
+        double d = 0.0;
+        for (int32_t k0 = 0; k0 < width; k0 += 8) {
+            int32_t c[8];
+            double v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const bool in = k0 + u < width;
+                const int32_t e = off + 32 * (k0 + u) + lane;
+                c[u] = in ? __ldg(idx + e) : -1;
+                v[u] = in ? double(__ldg(val + e)) : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) d = fma(v[u], c[u] >= 0 ? gs_sign(seed, m, k, c[u]) : 0.0, d);
+        }
+        for (int o = g >> 1; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+        if (col >= 0 && (lane & (g - 1)) == 0) {
+            a.y[col] = d;
+            yy = fma(d, d, yy);
+        }
+    }
+    yy = gs_sum(yy, sh);
+    if (threadIdx.x == 0) a.part_y[blockIdx.x] = yy;
+    // the decision sums `grid` partials: those past this launch's are zero
+    if (blockIdx.x == 0)
+        for (int32_t b = int32_t(gridDim.x) + int32_t(threadIdx.x); b < a.grid; b += kGsThreads) a.part_y[b] = 0.0;
+}
+
 // Lanes per segment for a mean segment length: the largest power of two G
 // <= 32 with 8 G <= the mean (each lane then has at least 8 entries).
 static int gs_lanes(int64_t nnz, int64_t segs) {
@@ -392,7 +446,11 @@ constexpr int64_t kGsBody = 16;   // sketch columns between reads of the stop fl
 // One column: the five kernels in order.
 static cudaError_t launch_column(bool f32, int gr, int gc, int grid, cudaStream_t s, const GsArgs &a) {
     cudaError_t e = f32 ? launch_rows<float>(gr, grid, s, a) : launch_rows<double>(gr, grid, s, a);
-    if (e == cudaSuccess) e = f32 ? launch_cols<float>(gc, grid, s, a) : launch_cols<double>(gc, grid, s, a);
+    if (e == cudaSuccess) {
+        if (a.csl.wr)
+            e = f32 ? launch_pdl(g_cols_sliced<float>, a.csl_grid, s, a) : launch_pdl(g_cols_sliced<double>, a.csl_grid, s, a);
+        else e = f32 ? launch_cols<float>(gc, grid, s, a) : launch_cols<double>(gc, grid, s, a);
+    }
     if (e == cudaSuccess) e = launch_pdl(g_qty, grid, s, a);
     if (e == cudaSuccess) e = launch_pdl(g_decide, 1, s, a);
     if (e == cudaSuccess) e = launch_pdl(g_update, grid, s, a);
@@ -510,6 +568,11 @@ plss_status run_general(plss_ctx *c, const double *b, const double *x0, double *
     a.K = K;
     a.grid = g->grid;
     a.nch = int32_t((std::max<int64_t>(c->n, 1) + kGsChunk - 1) / kGsChunk);
+    // the sliced columns, over the grid their warp ranges were cut for
+    if (c->d_cwr && c->csl.wr && c->grid_c <= g->grid) {
+        a.csl = c->csl;
+        a.csl_grid = c->grid_c;
+    }
 
     GsState z{};
     z.tol = o->tol;
