@@ -56,3 +56,14 @@ def test_counters_follow_the_sweep_code(tmp_path, monkeypatch):
     # no record: None
     shutil.rmtree(os.path.join(str(tmp_path / "d"), "profiles"))
     assert bench.ncu_traffic("col_sweep") is None
+
+
+def test_both_arms_name_the_same_config():
+    """The reference arm's line carries the GPU arm's config dict."""
+    import argparse
+    args = argparse.Namespace(prec="fp64", tol=1e-8, w_mode=0)
+    a = bench.run_config(args, 1_000_000, 200_000, 8_000_000, 1)
+    b = bench.run_config(args, 1_000_000, 200_000, 8_000_000, 1)
+    assert a == b and a["workload"] == bench.WORKLOAD and a["parallelism"] == "single"
+    assert "224 MB" in a["l2"]
+    assert bench.run_config(args, 1_000_000, 200_000, 8_000_000, 4)["parallelism"] == "replicas"
