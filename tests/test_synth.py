@@ -9,6 +9,7 @@ import numpy as np
 
 from paper_2207_07615_gb300 import synth
 
+
 def _rows(A):
     rp = np.asarray(A.row_ptr)
     ci = np.asarray(A.col_idx)
