@@ -1,6 +1,7 @@
-"""Host-side arithmetic of the benchmark's roofline (no GPU): the
-algorithmic bytes per launch, and the rule that recorded ncu counters are
-used only for the kernel code they were taken on."""
+"""Host side of the benchmark (no GPU): the roofline's algorithmic bytes
+per launch, the rule that recorded ncu counters are used only for the
+kernel code they were taken on, the config both arms name, and the
+reference arm (the oracle on the host cores) run end to end."""
 import os
 import shutil
 
@@ -67,3 +68,40 @@ def test_both_arms_name_the_same_config():
     assert a == b and a["workload"] == bench.WORKLOAD and a["parallelism"] == "single"
     assert "224 MB" in a["l2"]
     assert bench.run_config(args, 1_000_000, 200_000, 8_000_000, 4)["parallelism"] == "replicas"
+
+
+def _run_bench(*argv, env_extra=None):
+    import json
+    import subprocess
+    import sys
+    env = dict(os.environ)
+    env.update(env_extra or {})
+    p = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), *argv], cwd=ROOT, env=env,
+                       capture_output=True, text=True, timeout=600)
+    assert p.returncode == 0, p.stderr[-2000:]
+    lines = [l for l in p.stdout.splitlines() if l.startswith("{")]
+    return [json.loads(l) for l in lines]
+
+
+def test_reference_arm_prints_one_line_of_the_contract():
+    """The reference arm (the oracle, host cores only) runs without a GPU:
+    one JSON line with the GPU arm's metric, unit, direction and config, a
+    cpu_baseline describing the run, and an e2e object with no copies."""
+    (line,) = _run_bench("--impl", "reference", "--steps", "1", "--warmup", "0")
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC and line["unit"] == "s"
+    assert line["higher_is_better"] is False and line["steps"] == 1 and line["warmup"] == 0
+    assert line["n_gpus"] == 1 and line["data"] == "synthetic" and line["dtype"] == "f64"
+    assert line["config"]["workload"] == bench.WORKLOAD and line["config"]["nnz"] == 8_000_000
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == line["value"]
+    assert "100 updates" in cb["sample"] and str(bench.REF_UPDATES_TO_TOL) in cb["sample"]
+    assert line["e2e"] == {"value": line["value"], "unit": "s", "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
+    # an update of the oracle costs milliseconds, so the extrapolated solve is hours, not zero
+    assert line["value"] > bench.REF_UPDATES_TO_TOL * 1e-4
+
+
+def test_reference_arm_other_ranks_exit_quietly():
+    """Under torchrun only rank 0 runs the oracle; the others print nothing."""
+    assert _run_bench("--impl", "reference", "--steps", "1", "--warmup", "0",
+                      env_extra={"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"}) == []
