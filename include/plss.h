@@ -298,7 +298,10 @@ plss_status plss_solve_batched(plss_ctx *ctx, const double *const *b, const doub
  * solve in flight on the context. plss_state_bytes returns -1 for a NULL
  * context; save and load return PLSS_ERR_INVALID for a NULL argument or a
  * buffer shorter than plss_state_bytes, load also for a buffer from
- * another library version or another context shape.
+ * another library version or another context shape, or whose per-system
+ * scalars are not those of a finished solve (a phase other than finished,
+ * a negative update count, a kept transition into no running phase). The
+ * vectors are not checked: the buffer is otherwise trusted.
  */
 plss_status plss_resume(plss_ctx *ctx, double *const *x_out, const plss_opts *o, plss_result *res);
 int64_t plss_state_bytes(const plss_ctx *ctx);

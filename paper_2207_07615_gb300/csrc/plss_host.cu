@@ -931,6 +931,17 @@ plss_status state_copy(plss_ctx *c, unsigned char *buf, int64_t bytes, bool save
     if (bytes < L.total) return fail(PLSS_ERR_INVALID, "state buffer of %lld bytes, %lld needed", (long long)bytes,
                                      (long long)L.total);
     std::memcpy(z.data(), buf + L.states, sizeof(SysState) * z.size());
+    // the counters index the history rows and the phases select the kernels'
+    // work: a saved state is always that of a finished solve, with counts >= 0
+    // and a kept transition into one of the three running phases
+    for (size_t i = 0; i < z.size(); ++i) {
+        const SysState &q = z[i];
+        const int32_t next = q.resume & 0xf;
+        if (q.phase != PH_DONE || q.iters < 0 || q.maxit < 0 || q.since < 0 || q.refine < 0 ||
+            ((q.resume & 0x100) && (next != PH_SETUP && next != PH_FIRST && next != PH_RUN)))
+            return fail(PLSS_ERR_INVALID, "the state's scalars of system %d are not those of a finished solve",
+                        int(i));
+    }
     for (SysState &q : z) {
         q.hist = nullptr;
         q.hist_cap = 0;

@@ -138,6 +138,17 @@ def test_resume_and_load_refusals(plss):
             ctx.state_load(blob[: len(blob) // 2])
         with pytest.raises(plss.PlssError, match="version"):
             ctx.state_load(b"X" + blob[1:])
+        # the scalars of system 0 start after the 48-byte header; its update
+        # count is at +64 (after eight doubles), its phase at +128
+        import struct
+        for fmt, off, val in (("<q", 48 + 64, -1), ("<i", 48 + 128, 1)):
+            bad = bytearray(blob)
+            struct.pack_into(fmt, bad, off, val)
+            with pytest.raises(plss.PlssError, match="not those of a finished solve"):
+                ctx.state_load(bytes(bad))
+        ctx.state_load(blob)                                  # the intact state still loads
+        xs, rs = ctx.resume(tol=0.0, maxit=30)
+        assert rs[0]["iters"] == 30
         ctx.solve(b, sketch="identity", tol=0.0, maxit=10)   # overwrites x and b
         with pytest.raises(plss.PlssError, match="no residual-sketch state"):
             ctx.resume(tol=0.0, maxit=30)
