@@ -39,7 +39,7 @@ def pytest_terminal_summary(terminalreporter):
         g, a = per.get(test, (0.0, 0.0))
         per[test] = (max(g, gov), max(a, allr))
     tr = terminalreporter
-    tr.write_sep("-", f"parity: GPU deviation / oracle spread (margin {_parity.MARGIN:g}); "
+    tr.write_sep("-", f"parity: deviation from the oracle / its own spread (margin {_parity.MARGIN:g}); "
                       f"deviation / 1e-10 where the plain bar holds")
     for test, (g, a) in sorted(per.items(), key=lambda kv: -kv[1][0]):
         tr.write_line(f"{g:10.3g} {a:10.3g}  {test}")
