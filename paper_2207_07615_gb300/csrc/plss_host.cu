@@ -785,7 +785,7 @@ plss_status run_residual(plss_ctx *c, const double *const *b, const double *cons
     }
     while (!idle && !small && !coop) {
         const bool pchunk = prof && nchunk++ % period == 0;
-        cudaGraphExec_t g;
+        cudaGraphExec_t g = nullptr;
         st = get_graph(c, chunk, w_on, pchunk, &g);
         if (st != PLSS_OK) return st;
         CUDA_TRY(cudaGraphLaunch(g, s));
