@@ -174,3 +174,120 @@ def test_tile_shift_scales_the_target(shim):
             for shift in (-2, -1, 1, 2):
                 want = base * 2 ** shift if shift > 0 else base >> -shift
                 assert shim.shim_tile_target(nnz, slots, f32, shift) == min(cap, max(256, want))
+
+
+def _check_sliced_vectorized(p, ptr, idx, val, g):
+    """The sliced copy holds every nonzero of the sliced tiles exactly once,
+    where the layout says, and padding elsewhere: numpy over all elements at
+    once (the loop form above is for the small cases)."""
+    tiles, sl_ptr, seg, sidx, sval, first = p["tiles"], p["ptr"], p["seg"], p["idx"], p["val"], p["first"]
+    nseg = len(ptr) - 1
+    lens = np.diff(ptr).astype(np.int64)
+    per = 32 // g
+    S = len(sl_ptr) - 1
+    widths = np.diff(sl_ptr).astype(np.int64)
+    assert np.all(widths % 32 == 0) and sl_ptr[0] == 0 and len(seg) == 32 * S
+    widths //= 32
+    # slices of each sliced tile, consecutive from first[ti]; rows inside the tile
+    owner_b = np.full(S, -1, dtype=np.int64)
+    owner_e = np.full(S, -1, dtype=np.int64)
+    sliced_rows = np.zeros(nseg, dtype=bool)
+    for ti, (sys, b, e, grp) in enumerate(tiles):
+        if not grp & K_SLICED:
+            continue
+        nsl = (e - b + per - 1) // per
+        sl = slice(first[ti], first[ti] + nsl)
+        assert np.all(owner_b[sl] == -1)                      # no slice shared by two tiles
+        owner_b[sl], owner_e[sl] = b, e
+        sliced_rows[b:e] = True
+        pad = int(32 * widths[sl].sum())
+        assert pad * 4 <= int(ptr[e] - ptr[b]) * 5 + 32 * g * 4
+    assert np.all(owner_b >= 0)                                # every slice belongs to a tile
+    lanes = seg.reshape(S, per, g).astype(np.int64)
+    assert np.all(lanes == lanes[:, :, :1])                   # g lanes share a segment
+    r = lanes[:, :, 0]
+    used = r >= 0
+    rs = r[used]
+    assert np.all((rs >= np.repeat(owner_b, per).reshape(S, per)[used]) &
+                  (rs < np.repeat(owner_e, per).reshape(S, per)[used]))
+    seen = np.bincount(rs, minlength=nseg)
+    assert np.all(seen[sliced_rows] == 1) and np.all(seen[~sliced_rows] == 0)
+    wide = np.repeat(widths, per).reshape(S, per)
+    assert np.all((lens[rs] + g - 1) // g <= wide[used])
+    # element by element: position -> (slice, step j, lane) -> (row, k)
+    E = int(sl_ptr[-1])
+    pos = np.arange(E, dtype=np.int64)
+    s_of = np.repeat(np.arange(S, dtype=np.int64), 32 * widths)
+    local = pos - sl_ptr[s_of]
+    j, lane = local // 32, local % 32
+    row = seg[32 * s_of + lane].astype(np.int64)
+    k = j * g + lane % g
+    real = row >= 0
+    real[real] = k[real] < lens[row[real]]
+    src = np.asarray(ptr, dtype=np.int64)[row[real]] + k[real]
+    assert np.array_equal(sidx[real], np.asarray(idx)[src])
+    assert np.array_equal(sval[real], np.asarray(val, dtype=np.float64)[src])
+    assert np.all(sidx[~real] == -1) and np.all(sval[~real] == 0.0)
+    assert int(real.sum()) == int(lens[sliced_rows].sum())
+
+
+@pytest.mark.parametrize("side", ["rows", "cols"])
+@pytest.mark.parametrize("f32", [0, 1])
+def test_plan_invariants_at_benchmark_size(shim, side, f32):
+    """The 1,000,000 x 200,000 system with 8 nonzeros a row, planned as a
+    context on one GB300 plans it (152 SMs x 4 CTAs x 8 warps of warp
+    ranges): tiles partition each side, the sliced copy holds every nonzero
+    exactly once, and the warp ranges cover every slice in balanced shares."""
+    A, _, _ = synth.overdetermined_scaled(m=1_000_000, n=200_000, per_row=8, seed=0)
+    if side == "rows":
+        ptr, idx, val = np.asarray(A.row_ptr), np.asarray(A.col_idx), np.asarray(A.val)
+    else:
+        At = A.scipy().T.tocsr()
+        ptr, idx, val = At.indptr, At.indices, At.data
+    nseg, nnz = len(ptr) - 1, int(ptr[-1])
+    nwarps = 152 * 4 * 8
+    g = shim.shim_slice_lanes(nnz, nseg)
+    assert g == (1 if side == "rows" else 4)
+    p = plan(shim, ptr, idx, val, f32, 1, g, nwarps=nwarps)
+    tiles = p["tiles"]
+    assert tiles[0, 1] == 0 and tiles[-1, 2] == nseg and np.all(tiles[1:, 1] == tiles[:-1, 2])
+    assert np.all(tiles[:, 3] & K_SLICED)                    # short uniform segments: all sliced
+    _check_sliced_vectorized(p, ptr, idx, val, g)
+    wr, sl_ptr = p["wr"], p["ptr"]
+    assert len(wr) == nwarps + 1 and wr[0] == 0 and wr[-1] == len(sl_ptr) - 1 and np.all(np.diff(wr) >= 0)
+    cost = np.diff(sl_ptr).astype(np.int64) + 256
+    prefix = np.concatenate([[0], np.cumsum(cost)])
+    share = -(-int(prefix[-1]) // nwarps)
+    assert (prefix[wr[1:]] - prefix[wr[:-1]]).max() <= share + cost.max()
+
+
+def test_vectorized_check_rejects_planted_defects(shim):
+    """The whole-array check fails on a swapped element, a row sliced twice
+    and a padding slot that holds an index."""
+    ptr, idx, val = (np.asarray(a) for a in CASES["uniform_cols"])
+    g = shim.shim_slice_lanes(int(ptr[-1]), len(ptr) - 1)
+    p = plan(shim, ptr, idx, val, 0, 1, g, nwarps=64)
+    _check_sliced_vectorized(p, ptr, idx, val, g)
+    real = np.nonzero(p["idx"] >= 0)[0]
+    pad = np.nonzero(p["idx"] < 0)[0]
+    assert len(pad) > 0
+
+    def planted(key, fn):
+        q = {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in p.items()}
+        fn(q[key])
+        with pytest.raises(AssertionError):
+            _check_sliced_vectorized(q, ptr, idx, val, g)
+
+    def swap(a):
+        i, j = real[0], real[-1]
+        a[i], a[j] = a[j], a[i]
+
+    def twice(a):
+        a[g:2 * g] = a[0]                       # the second lane group repeats the first's segment
+
+    def fill(a):
+        a[pad[0]] = 0
+
+    planted("idx", swap)
+    planted("seg", twice)
+    planted("idx", fill)
