@@ -105,3 +105,29 @@ def test_reference_arm_other_ranks_exit_quietly():
     """Under torchrun only rank 0 runs the oracle; the others print nothing."""
     assert _run_bench("--impl", "reference", "--steps", "1", "--warmup", "0",
                       env_extra={"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"}) == []
+
+
+def test_clock_record_from_sampled_rows(tmp_path, monkeypatch):
+    """The clocks key: median SM clock over the samples drawn under load
+    (power at or above the median), the maximum clock, and every throttle
+    reason seen Active -- here from a stand-in nvidia-smi that prints three
+    rows in the queried column order and waits to be stopped."""
+    import time
+    fake = tmp_path / "nvidia-smi"
+    fake.write_text("#!/bin/sh\n"
+                    "printf '2070, 2070, 700.5, 0x0, Not Active, Not Active, Not Active, Not Active\\n'\n"
+                    "printf '1900, 2070, 720.0, 0x4, Not Active, Not Active, Not Active, Active\\n'\n"
+                    "printf '1500, 2070, 150.0, 0x0, Not Active, Not Active, Not Active, Not Active\\n'\n"
+                    "exec sleep 30\n")
+    fake.chmod(0o755)
+    monkeypatch.setenv("PATH", f"{tmp_path}{os.pathsep}{os.environ['PATH']}")
+    c = bench.Clocks(0)
+    time.sleep(0.5)
+    rec = c.stop()
+    assert rec == {"sm_mhz": 1985.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3,
+                   "power_w_max": 720.0}
+
+
+def test_clock_record_without_nvidia_smi(tmp_path, monkeypatch):
+    monkeypatch.setenv("PATH", str(tmp_path))
+    assert bench.Clocks(0).stop() is None
