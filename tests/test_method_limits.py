@@ -1,5 +1,5 @@
-"""What the method itself does on the batched benchmark's inputs, from the
-oracle alone (CPU): of the 256 systems of uneven size, the rectangular ones
+"""What the method itself does on the batched and served benchmarks' inputs,
+from the oracle alone (CPU). Of the 256 batched systems of uneven size, the rectangular ones
 (n = m/2, consistent and overdetermined) converge in about 60 updates,
 while the square ones (n = m, random sparse N(0,1) entries) need about 2.5 n
 updates and, beyond ~2,000 rows, do not reach 1e-8 within the 5,000-update
@@ -7,7 +7,10 @@ cap. So the share of the batch that reaches the tolerance within the cap is
 set by the method and the inputs, not by the GPU kernels (Theorem 3.1:
 termination within rank(A) updates holds in exact arithmetic only; in
 floating point the Lanczos-type recursion loses orthogonality and takes
-longer on ill-conditioned systems)."""
+longer on ill-conditioned systems). The served requests split the same
+way: those on square matrices stall within their cap, the others converge
+in under 100 updates."""
+import functools
 import math
 
 import numpy as np
@@ -64,3 +67,37 @@ def test_larger_square_systems_stall_within_the_cap(s):
     A, out = _solve(s)                                                 # 2,426 and 3,156 rows
     assert A.n == A.m and A.m > 2400
     assert out["status"] == "not_converged" and out["iters"] == 5000 and out["relres_true"] > 1e-6
+
+
+# The serving benchmark's compact run: 200 requests over a pool of 16
+# matrices (aspect n/m in {0.5, 1, 2}), FP32 storage with FP64 refinement,
+# W = diag(1/||A_j||), tol 1e-6, at most 3,000 updates per request.
+
+@functools.lru_cache(maxsize=1)
+def _serving_pool():
+    return synth.serving_trace(nreq=200, pool=16, rate=2000.0)
+
+
+def test_serving_trace_has_78_square_requests():
+    """The 122 of 200 served requests that reach 1e-6 are exactly the ones
+    on non-square matrices."""
+    arrivals, ids, mats = _serving_pool()
+    square = np.array([A.n == A.m for A in mats])
+    assert int(square[ids].sum()) == 78 and int((~square)[ids].sum()) == 122
+
+
+@pytest.mark.parametrize("pid,converges", [(2, True), (4, True), (5, True), (12, False), (14, False)])
+def test_served_matrices_converge_unless_square(pid, converges):
+    arrivals, ids, mats = _serving_pool()
+    A = mats[pid]
+    i = int(np.nonzero(ids == pid)[0][0])
+    b = synth.rhs(A, synth.rng_for(3000 + 1_000_000 + i).standard_normal(A.n))   # the request's b
+    Ad = A.astype(np.float64).scipy()
+    cn = np.sqrt(np.asarray(Ad.multiply(Ad).sum(axis=0)).ravel())
+    w = np.where(cn > 0, 1.0 / np.where(cn > 0, cn, 1.0), 1.0)
+    out = oracle.residual(A, b, w=w, tol=1e-6, maxit=3000, prec=1, inner_tol=1e-4, stop_on_true=True)
+    assert (A.n == A.m) == (not converges)
+    if converges:
+        assert out["status"] == "converged" and out["iters"] < 100
+    else:
+        assert out["status"] == "not_converged" and out["relres_true"] > 1e-5
