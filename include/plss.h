@@ -193,10 +193,13 @@ plss_status plss_create(const plss_csr *A, const plss_opts *o, plss_ctx **out);
 
 /* As plss_create for nsys independent systems As[0..nsys-1], packed into one
  * block-diagonal context so that every sweep covers all systems in one
- * launch while scalars, stopping and status stay per system. */
+ * launch while scalars, stopping and status stay per system. Each system
+ * runs the paper's Algorithm 1 on its own; solving many systems at once has
+ * no counterpart in the paper. */
 plss_status plss_create_batched(const plss_csr *As, int32_t nsys, const plss_opts *o,
                                 plss_ctx **out);
 
+/* Frees the context and all device memory it owns; NULL is ignored. */
 void plss_destroy(plss_ctx *ctx);
 
 /* One candidate plan measured by plss_tune. */
@@ -308,15 +311,18 @@ int64_t plss_state_bytes(const plss_ctx *ctx);
 plss_status plss_state_save(plss_ctx *ctx, void *buf, int64_t bytes);
 plss_status plss_state_load(plss_ctx *ctx, const void *buf, int64_t bytes);
 
-/* Many right-hand sides on one matrix (SpMM form): B is m x nrhs, X0 and X
- * are n x nrhs, all row-major double (X0 may be NULL). Each column is an
- * independent PLSS solve with its own scalars; converged columns freeze.
+/* Many right-hand sides on one matrix (SpMM form; no counterpart in the
+ * paper): B is m x nrhs, X0 and X are n x nrhs, all row-major double (X0 may
+ * be NULL). Each column is an independent Algorithm 1 solve with its own
+ * scalars, A p and A^T r taken for all columns in one sweep over A;
+ * converged columns freeze.
  * res[nrhs]. Residual sketch only; 1 <= nrhs <= 32 (one warp lane per
  * column), else PLSS_ERR_INVALID. */
 plss_status plss_solve_rhs(plss_ctx *ctx, int32_t nrhs, const double *B, const double *X0,
                            double *X, const plss_opts *o, plss_result *res);
 
-/* One sparse product with the context's stored matrix in double:
+/* One sparse product with the context's stored matrix in double -- the two
+ * products of Algorithm 1 (A p and A^T r) as a service of their own:
  * transpose = 0: out[m] = A v[n]; transpose = 1: out[n] = A^T v[m].
  * v and out follow o->io_device. Single-system contexts. */
 plss_status plss_spmv(plss_ctx *ctx, int32_t transpose, const double *v, double *out,
@@ -391,7 +397,8 @@ plss_status plss_gather_bound(plss_ctx *ctx, int32_t side, int32_t reps, double 
 const char *plss_last_error(void);
 
 /* ------------------------------------------------------------------ */
-/* Serving: continuous batching of independent solves                  */
+/* Serving: continuous batching of independent solves (no counterpart  */
+/* in the paper; every request is an Algorithm 1 solve of its own)     */
 /* ------------------------------------------------------------------ */
 
 typedef struct plss_server plss_server;
