@@ -261,7 +261,8 @@ plss_status plss_ctx_layout(const plss_ctx *ctx, int64_t out[6]);
 plss_status plss_solve(plss_ctx *ctx, const double *b, const double *x0, double *x_out,
                        const plss_opts *o, plss_result *res);
 
-/* Solves every system of a batched context at once: b[s], x0[s] (array of
+/* Solves every system of a batched context at once (Algorithm 1 per
+ * system, all systems' sweeps in the same launches): b[s], x0[s] (array of
  * NULL or NULL entries = zero start), x_out[s] for s < nsys; res[nsys].
  * Systems stop independently; the return value is PLSS_OK when all
  * converged, else the first non-OK system status. Residual sketch only. */
